@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the MRCM Darcy solve on one GB300 (or N replicas).
+
+One step = the whole hot path (factor_local, build_basis, solve_interface,
+reconstruct) on the 256x64 channelised workload (binary K, contrast 1e6,
+16x16 subdomains, cubic interface spaces: 8 unknowns per interface), replayed
+from a CUDA graph with inputs resident in HBM.  The workload (0.4 MB) fits in
+L2, so L2 is flushed (a 256 MB write) before every timed step; only the step
+itself is inside the CUDA events.  Prints one JSON line.
+
+--impl reference times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+if str(ROOT) not in sys.path:
+    sys.path.insert(0, str(ROOT))
+
+METRIC = "fine cells/s of MRCM Darcy solve, mixed vs FP64 GPU, at rel L2 err ≤1e-8"
+WORKLOAD = "channels-256x64 binary K 1e3/1e-3, 16x16 subdomains (64), m=8 per interface (864 unknowns)"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = Path(os.environ.get("TMPDIR", "/tmp")) / f"mrcm_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = [l.split(",") for l in self.path.read_text().splitlines() if l.strip()]
+        try:
+            self.path.unlink()
+        except Exception:
+            pass
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- peaks
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        try:
+            return json.loads(p.read_text()), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ----------------------------------------------------------------- CPU arm
+def _oracle_worker(seconds: float, max_solves: int):
+    """Times the oracle as it stands on the workload; one thread."""
+    from oracle import mrcm_oracle as O
+    from paper_2104_04653_gb300 import workloads as W
+    prob = W.config2()
+    cells = prob.cells()
+    times = []
+    t_end = time.perf_counter() + seconds
+    while len(times) < max_solves and (not times or time.perf_counter() < t_end):
+        t0 = time.perf_counter()
+        O.mrcm_solve(prob)
+        times.append(time.perf_counter() - t0)
+    return {"cells": cells, "times": times}
+
+
+def cpu_baseline(seconds: float = 12.0, max_solves: int = 50):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench._oracle_worker(%f, %d)))" % (str(ROOT), seconds, max_solves))
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         cwd=str(ROOT), timeout=600)
+    if res.returncode != 0:
+        return {"value": None, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                "sample": "failed: " + res.stderr.strip().splitlines()[-1][:200]}
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    t = statistics.median(d["times"])
+    return {"value": d["cells"] / t, "unit": "cells/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(d['times'])} full solves of the workload (median {t * 1e3:.1f} ms), "
+                      f"numpy/scipy FP64, 1 thread"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import mrcm_oracle as O
+    from paper_2104_04653_gb300 import workloads as W
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    prob = W.config2()
+    cells = prob.cells()
+    for _ in range(args.warmup):
+        O.mrcm_solve(prob)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.mrcm_solve(prob)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = cells * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "cells/s",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (numpy/scipy)"},
+            "cpu_baseline": {"value": val, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full solves of the workload"},
+            "e2e": {"value": val, "unit": "cells/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+def _capture(solver, K, L, Q, out, torch):
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        solver.L.mrcm_set_stream(solver.ctx, side.cuda_stream)
+        for _ in range(2):
+            solver.solve(K, L, Q, out=out)
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        solver.L.mrcm_set_stream(solver.ctx, torch.cuda.current_stream().cuda_stream)
+        solver.solve(K, L, Q, out=out)
+    solver.L.mrcm_set_stream(solver.ctx, torch.cuda.current_stream().cuda_stream)
+    return g
+
+
+def _time_graph(g, steps, flush, torch):
+    st = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(st)
+        g.replay()
+        b.record(st)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) * 1e-3 for a, b in ev]
+
+
+def _time_calls(solver, K, L, Q, out, steps, flush, torch):
+    """Per-ABI-call device time (eager launches, L2 flushed before each step)."""
+    st = torch.cuda.current_stream()
+    names = ["factor_local", "build_basis", "solve_interface", "reconstruct"]
+    recs = []
+    for _ in range(steps):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        e[0].record(st)
+        solver.mrcm_factor_local(K, L)
+        e[1].record(st)
+        solver.mrcm_build_basis(Q)
+        e[2].record(st)
+        solver.mrcm_solve_interface()
+        e[3].record(st)
+        solver.mrcm_reconstruct(*out)
+        e[4].record(st)
+        recs.append(e)
+    torch.cuda.synchronize()
+    res = {}
+    for i, n in enumerate(names):
+        res[n] = statistics.median(r[i].elapsed_time(r[i + 1]) * 1e-3 for r in recs)
+    return res
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2104_04653_gb300 import build, mrcm, workloads as W
+    build.build()
+    prob = W.config2()
+    cells = prob.cells()
+    K, L, Q = mrcm.device_inputs(prob)
+    opts = {"fp32_ir": mrcm.SolverOptions(prec=mrcm.PREC_FP32_IR),
+            "fp64": mrcm.SolverOptions(prec=mrcm.PREC_FP64)}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    results = {}
+    for name, o in opts.items():
+        s = mrcm.Mrcm(prob, o)
+        out = s.alloc_outputs()
+        s.solve(K, L, Q, out=out)
+        info = s.mrcm_get_info()
+        g = _capture(s, K, L, Q, out, torch)
+        for _ in range(args.warmup):
+            flush.zero_()
+            g.replay()
+        torch.cuda.synchronize()
+        results[name] = dict(solver=s, graph=g, out=out, info=info,
+                             launches=s.launch_count())
+    # accuracy against the oracle (computed once on the host)
+    acc = {}
+    if rank == 0 and not args.no_accuracy:
+        from oracle import mrcm_oracle as O
+        ref = O.mrcm_solve(prob)
+        for name, r in results.items():
+            p, ux, uy = (t.cpu().numpy() for t in r["out"])
+            ep, eu = O.errors(dict(p=p, ux=ux, uy=uy), ref)
+            acc[name] = {"p": ep, "u": eu}
+    # timed region: mixed path (the headline), clocks sampled meanwhile
+    clock = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clock.start()
+    time.sleep(0.3)
+    t_mixed = _time_graph(results["fp32_ir"]["graph"], args.steps, flush, torch)
+    torch.cuda.synchronize()
+    clocks = clock.stop()
+    t_fp64 = _time_graph(results["fp64"]["graph"], max(args.steps // 4, 3), flush, torch)
+    if ws > 1:
+        torch.distributed.barrier()
+    tot = sum(t_mixed)
+    if ws > 1:
+        tt = torch.tensor([tot], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        tot = float(tt.item())
+    value = cells * args.steps * ws / tot
+    ms = 1e3 * tot / args.steps
+    fp64_ms = 1e3 * statistics.mean(t_fp64)
+    # per-call breakdown (eager) and the dominant kernel's roofline
+    s = results["fp32_ir"]["solver"]
+    calls = _time_calls(s, K, L, Q, results["fp32_ir"]["out"], 30, flush, torch)
+    calls64 = _time_calls(results["fp64"]["solver"], K, L, Q, results["fp64"]["out"], 10, flush,
+                          torch)
+    # e2e: host buffers in pinned memory, copies inside the timed region
+    hK, hL, hQ = (t.cpu().pin_memory() for t in (K, L, Q))
+    outs = results["fp32_ir"]["out"]
+    hout = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
+    st = torch.cuda.current_stream()
+    e2e_steps = max(args.steps // 4, 3)
+    evs = []
+    for _ in range(e2e_steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        K.copy_(hK, non_blocking=True)
+        L.copy_(hL, non_blocking=True)
+        Q.copy_(hQ, non_blocking=True)
+        results["fp32_ir"]["graph"].replay()
+        for h, d in zip(hout, outs):
+            h.copy_(d, non_blocking=True)
+        b.record(st)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    e2e_t = statistics.mean(a.elapsed_time(b) * 1e-3 for a, b in evs)
+    h2d = sum(t.numel() * t.element_size() for t in (hK, hL, hQ))
+    d2h = sum(t.numel() * t.element_size() for t in hout)
+    if rank != 0:
+        return
+    peaks, src = measured_peaks()
+    dom = max(calls, key=calls.get)
+    roof = roofline_entry(dom, calls[dom], prob, s, peaks, src, clocks)
+    line = {
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64-refine", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "FP32 factors/solves, FP64 refinement",
+                   "parallelism": f"replicas x{ws}", "l2": "flushed (256 MB write) before each step",
+                   "graph": "CUDA graph replay"},
+        "fp64_path": {"value": cells * ws / (fp64_ms * 1e-3), "ms_per_step": fp64_ms,
+                      "calls_ms": {k: v * 1e3 for k, v in calls64.items()}},
+        "speedup_vs_fp64": fp64_ms / ms,
+        "rel_err_vs_oracle": acc,
+        "calls_ms": {k: v * 1e3 for k, v in calls.items()},
+        "solver_info": {k: {kk: vv for kk, vv in r["info"].items()} for k, r in results.items()},
+        "roofline": roof,
+        "e2e": {"value": cells * ws / e2e_t, "unit": "cells/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": results["fp32_ir"]["launches"] * args.steps,
+        "clocks": clocks,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def roofline_entry(call, seconds, prob, solver, peaks, src, clocks):
+    """Algorithmic work of the dominant call per launch, over its device
+    time; the bound and per-unit figures are stated in the design doc."""
+    from paper_2104_04653_gb300 import perfmodel
+    w = perfmodel.call_work(call, prob, solver)
+    sm_mhz = (clocks or {}).get("sm_mhz") or 1900.0
+    if w["bound"] == "hbm":
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        ach = w["bytes"] / seconds / 1e9
+        unit = "GB/s"
+        note = f"{src} HBM copy bandwidth"
+    else:
+        # FP32 SIMT issue rate: 152 SMs x 128 FP32 lanes x 2 flop x clock
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        ach = w["flops"] / seconds / 1e12
+        unit = "TFLOP/s"
+        note = f"FP32 SIMT peak at the sampled {sm_mhz:.0f} MHz (152 SMs x 128 lanes x 2)"
+    return {"kernel": w["kernel"], "bound": w["bound"], "achieved": ach, "peak": peak,
+            "unit": unit, "frac": ach / peak, "traffic": None, "peak_source": note,
+            "call_ms": seconds * 1e3, "algorithmic": w}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="mrcm", choices=["mrcm", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * mrcm.h — C ABI of the GB300 Multiscale Robin Coupled Method (MRCM) Darcy
+ * pressure–velocity solve.
+ *
+ * The solved problem is the Darcy system of Section 2 (Eq. "Darcy"):
+ *     u = -lambda(s) K grad p,  div u = q  in Omega,
+ *     p = p_b on the Dirichlet part, u.n = u_b on the Neumann part,
+ * on a uniform grid of square cells, decomposed into s x s-cell subdomains.
+ * MRCM (Section 3) solves local Robin problems (Eq. "mrc1") with
+ * beta = alpha H / kappa (Eq. "beta"), builds a multiscale basis from them,
+ * and couples the subdomains through the interface system (Eq. "mrc2"); the
+ * solution is the linear combination of the basis (text after Eq. "beta").
+ *
+ * The five hot-path calls, in calling order:
+ *   mrcm_setup            host: tables, workspace (the only allocation)
+ *   mrcm_factor_local     (a) assemble + (b) factor every local operator
+ *   mrcm_build_basis      (c) multi-RHS local solves, FP64 refinement
+ *   mrcm_solve_interface  (d) interface assembly + solve
+ *   mrcm_reconstruct      (e) fine pressure and face velocities
+ *
+ * Conventions shared by every call
+ *   Grid: one realisation is nx x ny square cells of side h = ly/ny on
+ *   [0, nx h] x [0, ly].  Cell arrays are [n_real][ny][nx] FP64, x fastest.
+ *   Face velocities are NORMAL velocities (not integrated fluxes):
+ *   ux is [n_real][ny][nx+1] (face i sits at x = i h, positive along +x),
+ *   uy is [n_real][ny+1][nx] (face j sits at y = j h, positive along +y).
+ *   Subdomains are numbered row-major S = J*Sx + I.  Interfaces of one
+ *   realisation are in canonical order: vertical ones (between (I,J) and
+ *   (I+1,J)) row-major by (J,I), then horizontal ones (between (I,J) and
+ *   (I,J+1)) row-major by (J,I).  The fixed normal n_check points out of the
+ *   smaller-index subdomain (Section 3, after Eq. "compatibility"): +x or +y.
+ *   Interface unknowns are ordered [U_0..U_{nU-1}, P_0..P_{nP-1}]: flux
+ *   coefficients then pressure coefficients.  Interface functions are
+ *   polynomials of t in [-1,1] along the interface (+y for vertical, +x for
+ *   horizontal interfaces), sampled at face midpoints.
+ *   Boundary faces are listed left (ny), right (ny), bottom (nx), top (nx).
+ *
+ * Ownership: every d_* pointer is DEVICE memory owned by the caller, and the
+ * CUDA stream is owned by the caller.  The library owns its workspace, which
+ * is allocated in mrcm_setup only and freed by mrcm_destroy; calls 2–5
+ * allocate nothing, synchronise nothing (unless an info pointer is passed)
+ * and only enqueue kernels on the stream.
+ *
+ * Errors: every call returns an mrcm_status, never aborts.  Host-side
+ * validation failures return MRCM_EINVAL; CUDA launch failures MRCM_ECUDA.
+ * Numerical failures detected on the device (non-SPD pivot, NaN, stalled
+ * refinement) are accumulated in a device status word and reported by
+ * mrcm_get_info (or by mrcm_solve_interface when given an info pointer).
+ * mrcm_last_error returns a message for the last failing call.
+ */
+#ifndef MRCM_H
+#define MRCM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MRCM_OK = 0,
+  MRCM_EINVAL = 1,     /* bad descriptor, argument or calling order        */
+  MRCM_ENOMEM = 2,     /* workspace allocation failed in mrcm_setup        */
+  MRCM_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed      */
+  MRCM_ENOTSPD = 4,    /* a local pivot was <= 0 or not finite             */
+  MRCM_EIRSTALL = 5,   /* refinement stopped above its tolerance           */
+  MRCM_ENOCONV = 6,    /* interface refinement did not converge            */
+  MRCM_ENAN = 7,       /* NaN / Inf in inputs or results                   */
+  MRCM_ETIMEOUT = 8    /* reserved: a bounded device wait ran out          */
+} mrcm_status;
+
+/* Device status flags (bit OR), see mrcm_info.flags. */
+#define MRCM_FLAG_NOTSPD      0x1
+#define MRCM_FLAG_LOCAL_STALL 0x2
+#define MRCM_FLAG_IFACE_STALL 0x4
+#define MRCM_FLAG_NAN         0x8
+#define MRCM_FLAG_IFACE_PIVOT 0x10
+#define MRCM_FLAG_LAYOUT      0x20  /* internal table inconsistency (a bug) */
+
+typedef enum {
+  MRCM_PREC_FP64 = 0,     /* plain path: FP64 factors and solves            */
+  MRCM_PREC_FP32_IR = 1   /* FP32 factors/solves, FP64 residual refinement  */
+} mrcm_precision;
+
+typedef enum {
+  MRCM_BASIS_LEGENDRE = 0,  /* P_k(t), Legendre polynomials                 */
+  MRCM_BASIS_MONOMIAL = 1   /* t^k (same spans; for invariance checks)      */
+} mrcm_basis_family;
+
+typedef struct mrcm_ctx mrcm_ctx;   /* opaque, owned by the library */
+
+/* Problem descriptor.  All pointers are HOST pointers; their contents are
+ * copied by mrcm_setup and not referenced afterwards. */
+typedef struct {
+  int32_t nx, ny;            /* cells per realisation                         */
+  int32_t n_real;            /* independent realisations solved together      */
+  double  ly;                /* domain height; h = ly / ny                    */
+  const int32_t *sub_size;   /* [n_real] subdomain edge s in cells (16);      */
+                             /* nx and ny must be multiples of s              */
+  const int32_t *iface_nU;   /* flux-space size per interface, realisations   */
+  const int32_t *iface_nP;   /* concatenated, canonical order; 0 <= n <= s,   */
+                             /* nU + nP >= 1; pure Neumann needs nP >= 1      */
+  const double  *alpha;      /* NULL: alpha = 1 everywhere; else per face:    */
+                             /* realisations concatenated, per interface s    */
+                             /* values along the interface; alpha > 0         */
+  const int8_t  *bc_type;    /* [2ny+2nx]: 0 = u.n = bc_val (outward normal   */
+  const double  *bc_val;     /* velocity), 1 = p = bc_val; shared by all      */
+                             /* realisations                                  */
+  int32_t pure_neumann;      /* 1: no Dirichlet face; pressure is returned    */
+                             /* with zero cell mean per realisation           */
+  int32_t basis_family;      /* mrcm_basis_family                             */
+  int32_t prec;              /* mrcm_precision                                */
+  double  ir_tol;            /* local refinement: stop when ||r||/||b|| <= tol */
+  int32_t ir_max;            /* max local refinement sweeps (FP32_IR)         */
+  double  iface_tol;         /* interface refinement tolerance (relative)     */
+  int32_t iface_ir_max;      /* max interface refinement sweeps after the     */
+                             /* first solve                                   */
+} mrcm_desc;
+
+typedef struct {
+  int32_t flags;             /* OR of MRCM_FLAG_*                              */
+  int32_t local_sweeps_max;  /* most local refinement sweeps any RHS took      */
+  int32_t iface_sweeps;      /* interface refinement sweeps (max over real.)   */
+  int32_t reserved;
+  double  local_resid_max;   /* max ||b - A x|| / ||b|| over local solves      */
+  double  iface_resid;       /* max over realisations ||f - M x|| / ||f||      */
+} mrcm_info;
+
+/* Validate the descriptor, build subdomain / interface / slab tables, choose
+ * the launch shapes and allocate all workspace on the current device.  The
+ * stream (a cudaStream_t, NULL = legacy default stream) is used by every
+ * later call.  On success *out owns the context; on failure *out is NULL
+ * and the return value says why.  Section 3 ("mrc1", "mrc2"). */
+mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out);
+
+/* Steps (a)+(b).  d_K, d_lambda: device [n_real][ny][nx] FP64, kappa =
+ * lambda*K > 0.  Assembles every subdomain's 5-point Robin operator
+ * (two-point fluxes: harmonic mean inside, T_R = kappa/(alpha H/h + 1/2) on
+ * interface faces, 2 kappa on Dirichlet faces) and factors all of them in
+ * one batched launch.  Re-callable with new lambda (re-factors).
+ * Eq. "mrc1", Eq. "beta". */
+mrcm_status mrcm_factor_local(mrcm_ctx *ctx, const double *d_K, const double *d_lambda);
+
+/* Step (c).  d_q: device [n_real][ny][nx] FP64 source density.  Solves every
+ * subdomain for one RHS per interface function on each of its interface
+ * edges plus one RHS for sources and boundary data; FP32_IR refines each RHS
+ * in FP64 until ||r||/||b|| <= ir_tol or ir_max sweeps.  Writes the basis and
+ * its interface traces to workspace.  Text after Eq. "beta". */
+mrcm_status mrcm_build_basis(mrcm_ctx *ctx, const double *d_q);
+
+/* Step (d).  Assembles the interface system (Eq. "mrc2") from the basis
+ * traces, factors it (FP64, or FP32 with FP64 refinement) and solves for
+ * (U_H, P_H).  info: NULL = fully asynchronous; else the stream is
+ * synchronised and *info filled (and the return value reflects device
+ * flags). */
+mrcm_status mrcm_solve_interface(mrcm_ctx *ctx, mrcm_info *info);
+
+/* Step (e).  Writes p [n_real][ny][nx], ux [n_real][ny][nx+1],
+ * uy [n_real][ny+1][nx] (device FP64).  On interface faces ux/uy hold the
+ * mean of the two one-sided normal velocities.  d_gamma_u (optional, may be
+ * NULL) receives the one-sided outward normal velocities: for every
+ * interface in canonical order (realisations concatenated) 2*s values, the
+ * smaller-index side first.  Text after Eq. "beta". */
+mrcm_status mrcm_reconstruct(mrcm_ctx *ctx, double *d_p, double *d_ux, double *d_uy,
+                             double *d_gamma_u);
+
+/* Synchronise the stream and read the device status (see mrcm_info). */
+mrcm_status mrcm_get_info(mrcm_ctx *ctx, mrcm_info *info);
+
+/* Replace the stream used by later calls. */
+mrcm_status mrcm_set_stream(mrcm_ctx *ctx, void *cuda_stream);
+
+/* Number of kernel launches the last factor/basis/interface/reconstruct
+ * sequence enqueued (for launch accounting). */
+int32_t mrcm_launch_count(const mrcm_ctx *ctx);
+
+/* Total interface unknowns (sum over realisations) and the length of the
+ * d_gamma_u array of mrcm_reconstruct. */
+int64_t mrcm_num_interface_unknowns(const mrcm_ctx *ctx);
+int64_t mrcm_num_gamma_values(const mrcm_ctx *ctx);
+
+/* Copy the interface solution (U_H, P_H), realisations concatenated in
+ * canonical order, to the device buffer d_x (FP64). */
+mrcm_status mrcm_copy_interface_solution(mrcm_ctx *ctx, double *d_x);
+
+void mrcm_destroy(mrcm_ctx *ctx);
+const char *mrcm_last_error(const mrcm_ctx *ctx);
+int32_t mrcm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRCM_H */

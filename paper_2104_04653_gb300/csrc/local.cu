@@ -1,0 +1,438 @@
+// Steps (a)+(b) and (c) of the MRCM solve: per-subdomain assembly of the
+// local Robin operator (Eq. "mrc1" with beta of Eq. "beta"), its batched
+// factorisation, and the multi-RHS basis solves with FP64 refinement.
+//
+// The local operator of an s x s subdomain, with cells ordered row by row,
+// is block tridiagonal: diagonal blocks D_j (one grid row, tridiagonal) and
+// diagonal couplings E_j between rows j and j+1.  After symmetric Jacobi
+// scaling (unit diagonal) it is factored as a block LDL^T whose pivots are
+// the Schur complements S_j = D_j - E_{j-1} S_{j-1}^{-1} E_{j-1}; the kernel
+// keeps their explicit inverses W_j = S_j^{-1}, so every step of a solve is
+// a dense s x s matrix times a block of right-hand sides, with no
+// sequential dependence inside a grid row.
+#include "mrcm_internal.h"
+#include "../../include/mrcm.h"
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mrcm {
+namespace {
+
+constexpr int kS = 16;      // subdomain edge handled by these kernels
+constexpr int kNC = 12;     // right-hand sides per CTA of the basis kernel
+
+__device__ __forceinline__ void atomic_max_pos_double(double *addr, double v) {
+  // valid for v >= 0: IEEE order of non-negative doubles matches their bits
+  if (!(v >= 0.0)) v = 1e300;
+  atomicMax(reinterpret_cast<unsigned long long *>(addr),
+            static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+// Transmissibilities of the four faces of local cell (a, b) of subdomain sb,
+// in the order W, E, S, N.  Two-point fluxes on square cells: harmonic mean
+// between cells, kappa/(alpha H/h + 1/2) on a Robin face, 2 kappa on a
+// Dirichlet face, 0 on a Neumann face.
+__device__ void face_T(const DeviceTables &t, const SubInfo &sb, const double *kap, int a,
+                       int b, double out[4]) {
+  const int S = kS;
+  const double kc = kap[b * S + a];
+  const int nb_a[4] = {a - 1, a + 1, a, a};
+  const int nb_b[4] = {b, b, b - 1, b + 1};
+#pragma unroll
+  for (int side = 0; side < 4; ++side) {
+    const int na = nb_a[side], nbb = nb_b[side];
+    double T;
+    if (na >= 0 && na < S && nbb >= 0 && nbb < S) {
+      const double kn = kap[nbb * S + na];
+      T = 2.0 * kc * kn / (kc + kn);
+    } else if (sb.edge_iface[side] >= 0) {
+      const int e = (side < 2) ? b : a;
+      const double al = t.alpha[t.iface[sb.edge_iface[side]].alpha_off + e];
+      T = kc / (al * t.H / t.h + 0.5);
+    } else {
+      const int gi = sb.x0 + a, gj = sb.y0 + b;
+      int k;
+      if (side == kEdgeW) k = gj;
+      else if (side == kEdgeE) k = t.ny + gj;
+      else if (side == kEdgeS) k = 2 * t.ny + gi;
+      else k = 2 * t.ny + t.nx + gi;
+      T = (t.bc_type[k] == 1) ? 2.0 * kc : 0.0;
+    }
+    out[side] = T;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// (a)+(b): one CTA per subdomain, one thread per cell / per block element.
+template <typename T>
+__global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, const double *K,
+                                                   const double *lam) {
+  constexpr int S = kS, N = S * S;
+  const int g = blockIdx.x;
+  const SubInfo sb = t.sub[g];
+  const int tid = threadIdx.x;
+  const int a = tid % S, b = tid / S;
+  __shared__ double kap[N];
+  __shared__ double dsc[N];
+  __shared__ double tE[N], tN[N];
+  __shared__ T M[N];
+  __shared__ T Wp[N];
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+
+  const int64_t cell = (static_cast<int64_t>(sb.r) * t.ny + sb.y0 + b) * t.nx + sb.x0 + a;
+  const double kc = K[cell] * lam[cell];
+  if (!(kc > 0.0) || !isfinite(kc)) atomicOr(&w.status[0], MRCM_FLAG_NAN);
+  kap[tid] = kc;
+  __syncthreads();
+  double T4[4];
+  face_T(t, sb, kap, a, b, T4);
+  const double diag = T4[0] + T4[1] + T4[2] + T4[3];
+  const double d = 1.0 / sqrt(diag);
+  double *coef = w.coef + static_cast<int64_t>(g) * 6 * N;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) coef[k * N + tid] = T4[k];
+  coef[4 * N + tid] = d;
+  coef[5 * N + tid] = kc;
+  dsc[tid] = d;
+  tE[tid] = T4[1];
+  tN[tid] = T4[3];
+  __syncthreads();
+
+  // block element (ra, cb) of the current S x S Schur block
+  const int ra = tid / S, cb = tid % S;
+  T *Wg = static_cast<T *>(w.W) + static_cast<int64_t>(g) * S * N;
+  for (int j = 0; j < S; ++j) {
+    double v = 0.0;
+    if (ra == cb) {
+      v = 1.0;
+    } else if (ra - cb == 1 || cb - ra == 1) {
+      const int lo = ra < cb ? ra : cb;
+      v = -tE[j * S + lo] * dsc[j * S + ra] * dsc[j * S + cb];
+    }
+    if (j > 0) {
+      const double ea = -tN[(j - 1) * S + ra] * dsc[(j - 1) * S + ra] * dsc[j * S + ra];
+      const double eb = -tN[(j - 1) * S + cb] * dsc[(j - 1) * S + cb] * dsc[j * S + cb];
+      v -= ea * eb * static_cast<double>(Wp[tid]);
+    }
+    M[tid] = static_cast<T>(v);
+    __syncthreads();
+    // in-place Gauss-Jordan inverse; no pivoting (the block is SPD)
+    for (int k = 0; k < S; ++k) {
+      const T piv = M[k * S + k];
+      const T mak = M[ra * S + k];
+      const T mkb = M[k * S + cb];
+      __syncthreads();
+      if (!(piv > T(0))) {
+        if (tid == 0) bad = 1;
+      }
+      const T ipiv = T(1) / piv;
+      T nv;
+      if (ra == k && cb == k) nv = ipiv;
+      else if (ra == k) nv = mkb * ipiv;
+      else if (cb == k) nv = -mak * ipiv;
+      else nv = M[tid] - mak * mkb * ipiv;
+      M[tid] = nv;
+      __syncthreads();
+    }
+    Wg[j * N + tid] = M[tid];
+    Wp[tid] = M[tid];
+    __syncthreads();
+  }
+  if (tid == 0 && bad) atomicOr(&w.status[0], MRCM_FLAG_NOTSPD);
+}
+
+// ---------------------------------------------------------------------------
+// (c): one CTA per (subdomain, block of up to kNC basis columns).
+template <typename T>
+struct BasisSmem {
+  T Ws[kS * kS * kS];       // W_j, j = 0..S-1 (symmetric)
+  T ec[kS * kS];            // scaled row couplings e_j[a]
+  T z[kNC * kS * kS];       // scaled residual (input of the solve)
+  T v[kNC * kS * kS];       // forward values, then the solution
+  double coef[6 * kS * kS]; // tW tE tS tN d kappa
+  double x[kNC * kS * kS];  // FP64 iterate
+  double bb[kNC * kS * kS]; // FP64 right-hand sides
+  double red[kNC][kS * kS / 32];
+  double bn[kNC];
+  double rel;
+  ColInfo col[kNC];
+};
+
+template <typename T>
+__device__ void block_solve(BasisSmem<T> &sm, int nc) {
+  // y = L^{-T} D^{-1} L^{-1} z for the block LDL^T of the scaled operator
+  constexpr int S = kS, N = S * S;
+  const int tid = threadIdx.x;
+  const int a = tid % S, c = tid / S;
+  const bool act = c < nc;
+  // forward: v_j = W_j (z_j - e_{j-1} * v_{j-1})
+  for (int j = 0; j < S; ++j) {
+    if (act) {
+      const T *Wj = sm.Ws + j * N;
+      const T *zj = sm.z + c * N + j * S;
+      T acc = T(0);
+      if (j == 0) {
+#pragma unroll
+        for (int bq = 0; bq < S; ++bq) acc += Wj[bq * S + a] * zj[bq];
+      } else {
+        const T *vp = sm.v + c * N + (j - 1) * S;
+        const T *ep = sm.ec + (j - 1) * S;
+#pragma unroll
+        for (int bq = 0; bq < S; ++bq) acc += Wj[bq * S + a] * (zj[bq] - ep[bq] * vp[bq]);
+      }
+      sm.v[c * N + j * S + a] = acc;
+    }
+    __syncthreads();
+  }
+  // backward: y_j = v_j - W_j (e_j * y_{j+1})
+  for (int j = S - 2; j >= 0; --j) {
+    if (act) {
+      const T *Wj = sm.Ws + j * N;
+      const T *yn = sm.v + c * N + (j + 1) * S;
+      const T *ep = sm.ec + j * S;
+      T acc = T(0);
+#pragma unroll
+      for (int bq = 0; bq < S; ++bq) acc += Wj[bq * S + a] * (ep[bq] * yn[bq]);
+      sm.v[c * N + j * S + a] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
+// per-column sum over the CTA of val[c] (c < nc), result in sm.red[c][0]
+template <typename T>
+__device__ void column_sums(BasisSmem<T> &sm, const double *val, int nc, double *out) {
+  constexpr int NW = kS * kS / 32;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int c = 0; c < nc; ++c) {
+    double s = val[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sm.red[c][wid] = s;
+  }
+  __syncthreads();
+  if (tid < nc) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) s += sm.red[tid][k];
+    out[tid] = s;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
+                                                  const BasisItem *items, const double *q,
+                                                  double tol, int ir_max) {
+  constexpr int S = kS, N = S * S;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  BasisSmem<T> &sm = *reinterpret_cast<BasisSmem<T> *>(smraw);
+  __shared__ double colres[kNC];
+  const BasisItem it = items[blockIdx.x];
+  const int g = it.sub;
+  const SubInfo sb = t.sub[g];
+  const int nc = it.nc;
+  const int tid = threadIdx.x;
+  const int a = tid % S, b = tid / S;
+  const double h = t.h;
+
+  // stage W_j, the coefficients and the column descriptors
+  {
+    const T *Wg = static_cast<const T *>(w.W) + static_cast<int64_t>(g) * S * N;
+    for (int k = tid; k < S * N; k += N) sm.Ws[k] = Wg[k];
+    const double *coef = w.coef + static_cast<int64_t>(g) * 6 * N;
+    for (int k = tid; k < 6 * N; k += N) sm.coef[k] = coef[k];
+    if (tid < nc) sm.col[tid] = t.col[sb.col_off + it.c0 + tid];
+  }
+  __syncthreads();
+  const double *tWs = sm.coef, *tEs = sm.coef + N, *tSs = sm.coef + 2 * N,
+               *tNs = sm.coef + 3 * N, *ds = sm.coef + 4 * N, *ks = sm.coef + 5 * N;
+  if (b < S - 1) sm.ec[tid] = static_cast<T>(-tNs[tid] * ds[tid] * ds[tid + S]);
+  else sm.ec[tid] = T(0);
+
+  // right-hand sides (FP64)
+  const double myT[4] = {tWs[tid], tEs[tid], tSs[tid], tNs[tid]};
+  const double kc = ks[tid];
+  const int gi = sb.x0 + a, gj = sb.y0 + b;
+  double bnl[kNC];
+  for (int c = 0; c < nc; ++c) {
+    const ColInfo ci = sm.col[c];
+    double val = 0.0;
+    if (ci.unk < 0) {
+      const int64_t cell = (static_cast<int64_t>(sb.r) * t.ny + gj) * t.nx + gi;
+      val = q[cell] * h * h;
+      // physical faces of this cell
+      const bool onface[4] = {a == 0, a == S - 1, b == 0, b == S - 1};
+#pragma unroll
+      for (int side = 0; side < 4; ++side) {
+        if (!onface[side] || sb.edge_iface[side] >= 0) continue;
+        int k;
+        if (side == kEdgeW) k = gj;
+        else if (side == kEdgeE) k = t.ny + gj;
+        else if (side == kEdgeS) k = 2 * t.ny + gi;
+        else k = 2 * t.ny + t.nx + gi;
+        if (t.bc_type[k] == 1) val += myT[side] * t.bc_val[k];
+        else val -= t.bc_val[k] * h;
+      }
+    } else {
+      const int side = ci.edge;
+      const bool adj = (side == kEdgeW && a == 0) || (side == kEdgeE && a == S - 1) ||
+                       (side == kEdgeS && b == 0) || (side == kEdgeN && b == S - 1);
+      if (adj) {
+        const int e = (side < 2) ? b : a;
+        const double fv = t.fnval[ci.fn * t.fn_stride + e];
+        double gval;
+        if (ci.is_u) {
+          const double al = t.alpha[t.iface[sb.edge_iface[side]].alpha_off + e];
+          const double beta = al * t.H / kc;
+          const double sigma = (side == kEdgeE || side == kEdgeN) ? 1.0 : -1.0;
+          gval = -beta * sigma * fv;
+        } else {
+          gval = fv;
+        }
+        val = myT[side] * gval;
+      }
+    }
+    sm.bb[c * N + tid] = val;
+    sm.x[c * N + tid] = 0.0;
+    sm.z[c * N + tid] = static_cast<T>(ds[tid] * val);
+    bnl[c] = val * val;
+  }
+  column_sums(sm, bnl, nc, sm.bn);
+
+  // refinement loop: z holds D r in the working precision
+  int sweep = 0;
+  double prev = 1e300, rel = 0.0;
+  for (;;) {
+    block_solve(sm, nc);
+    for (int c = 0; c < nc; ++c)
+      sm.x[c * N + tid] += ds[tid] * static_cast<double>(sm.v[c * N + tid]);
+    __syncthreads();
+    if (sweep >= ir_max) break;
+    // FP64 residual r = b - A x
+    double rn[kNC];
+    for (int c = 0; c < nc; ++c) {
+      const double *xc = sm.x + c * N;
+      double ax = (myT[0] + myT[1] + myT[2] + myT[3]) * xc[tid];
+      if (a > 0) ax -= myT[0] * xc[tid - 1];
+      if (a < S - 1) ax -= myT[1] * xc[tid + 1];
+      if (b > 0) ax -= myT[2] * xc[tid - S];
+      if (b < S - 1) ax -= myT[3] * xc[tid + S];
+      const double r = sm.bb[c * N + tid] - ax;
+      sm.z[c * N + tid] = static_cast<T>(ds[tid] * r);
+      rn[c] = r * r;
+    }
+    column_sums(sm, rn, nc, colres);
+    if (tid == 0) {
+      double m = 0.0;
+      for (int c = 0; c < nc; ++c) {
+        const double bnc = sm.bn[c];
+        const double rr = bnc > 0.0 ? sqrt(colres[c] / bnc) : 0.0;
+        m = (rr > m || rr != rr) ? rr : m;
+      }
+      sm.rel = m;
+    }
+    __syncthreads();
+    rel = sm.rel;
+    ++sweep;
+    if (!(rel == rel)) break;
+    if (rel <= tol) break;
+    if (sweep > 2 && rel > 0.5 * prev) break;  // stalled
+    prev = rel;
+  }
+  if (tid == 0 && ir_max > 0) {
+    atomicMax(&w.status[1], sweep);
+    atomic_max_pos_double(&w.dstat[0], rel);
+    if (!(rel <= 1e3 * tol)) atomicOr(&w.status[0], MRCM_FLAG_LOCAL_STALL);
+  }
+
+  // basis columns (FP64)
+  double *bas = w.basis + sb.basis_off;
+  for (int c = 0; c < nc; ++c) bas[static_cast<int64_t>(it.c0 + c) * N + tid] = sm.x[c * N + tid];
+
+  // interface traces -> rows of G (Eq. "mrc2"):
+  //   U rows: sigma * sum_e h phi_k(e) p_face(e)    (pressure continuity)
+  //   P rows: sum_e h psi_k(e) u(e)                 (flux continuity)
+  // with u(e) = T_R (p_c - g_e)/h and p_face = g_e + beta_e u(e).
+  double *G = w.G + sb.g_off;
+  const int nrow = sb.nrows;
+  for (int pr = tid; pr < nrow * nc; pr += N) {
+    const int row = pr / nc, c = pr % nc;
+    int side = 0;
+    while (side < 3 && !(sb.edge_iface[side] >= 0 && row >= sb.edge_row[side] &&
+                         row < sb.edge_row[side] + t.iface[sb.edge_iface[side]].nU +
+                                   t.iface[sb.edge_iface[side]].nP))
+      ++side;
+    const IfaceInfo fi = t.iface[sb.edge_iface[side]];
+    const int k = row - sb.edge_row[side];
+    const double sigma = (side == kEdgeE || side == kEdgeN) ? 1.0 : -1.0;
+    const ColInfo ci = sm.col[c];
+    const bool own = (ci.edge == side);
+    const double *tside = sm.coef + side * N;
+    double acc = 0.0;
+    for (int e = 0; e < S; ++e) {
+      int la, lb;
+      if (side == kEdgeW) { la = 0; lb = e; }
+      else if (side == kEdgeE) { la = S - 1; lb = e; }
+      else if (side == kEdgeS) { la = e; lb = 0; }
+      else { la = e; lb = S - 1; }
+      const int cl = lb * S + la;
+      const double TR = tside[cl];
+      const double beta = t.alpha[fi.alpha_off + e] * t.H / ks[cl];
+      double ge = 0.0;
+      if (own) {
+        const double fv = t.fnval[ci.fn * t.fn_stride + e];
+        ge = ci.is_u ? -beta * sigma * fv : fv;
+      }
+      const double u = TR * (sm.x[c * N + cl] - ge) / h;
+      if (k < fi.nU) {
+        const double pf = ge + beta * u;
+        acc += h * t.fnval[k * t.fn_stride + e] * pf;
+      } else {
+        acc += h * t.fnval[(k - fi.nU) * t.fn_stride + e] * u;
+      }
+    }
+    if (k < fi.nU) acc *= sigma;
+    G[static_cast<int64_t>(row) * sb.ncols + it.c0 + c] = acc;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_factor(const DeviceTables &t, const Workspace &w, int prec, const double *K,
+                          const double *lam, cudaStream_t st) {
+  if (t.s != kS) return cudaErrorInvalidValue;
+  if (prec == MRCM_PREC_FP64)
+    k_factor<double><<<t.nsub, kS * kS, 0, st>>>(t, w, K, lam);
+  else
+    k_factor<float><<<t.nsub, kS * kS, 0, st>>>(t, w, K, lam);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_basis_t(const DeviceTables &t, const Workspace &w,
+                                  const BasisItem *items, int nitems, const double *q,
+                                  double tol, int ir_max, cudaStream_t st) {
+  k_basis<T><<<nitems, kS * kS, sizeof(BasisSmem<T>), st>>>(t, w, items, q, tol, ir_max);
+  return cudaGetLastError();
+}
+
+cudaError_t init_local_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_basis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sizeof(BasisSmem<float>)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_basis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(sizeof(BasisSmem<double>)));
+}
+
+cudaError_t launch_basis(const DeviceTables &t, const Workspace &w, int prec,
+                         const BasisItem *items, int nitems, const double *q, double ir_tol,
+                         int ir_max, cudaStream_t st) {
+  if (t.s != kS) return cudaErrorInvalidValue;
+  if (prec == MRCM_PREC_FP64) return launch_basis_t<double>(t, w, items, nitems, q, ir_tol, 0, st);
+  return launch_basis_t<float>(t, w, items, nitems, q, ir_tol, ir_max, st);
+}
+
+}  // namespace mrcm

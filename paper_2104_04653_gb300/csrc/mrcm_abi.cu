@@ -1,0 +1,596 @@
+// Host side of the C ABI (include/mrcm.h): descriptor validation, the
+// subdomain / interface / slab tables of Section 3, workspace allocation and
+// the launch sequence of the five hot-path calls.
+#include "mrcm_internal.h"
+#include "../../include/mrcm.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+using namespace mrcm;
+
+struct mrcm_ctx {
+  mrcm_desc d{};
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  int prec = 0;
+  int S = 16;
+  int state = 0;           // 0 set up, 1 factored, 2 basis, 3 interface solved
+  int launches = 0;
+  std::string err;
+  // host tables
+  std::vector<SubInfo> sub;
+  std::vector<IfaceInfo> iface;
+  std::vector<ColInfo> col;
+  std::vector<RealInfo> real;
+  std::vector<BasisItem> items;
+  std::vector<int> unk_iface, unk_slabpos, pos2unk;
+  std::vector<int64_t> pos_real_off;
+  int64_t slab_elems = 0, xy_elems = 0, npos = 0, basis_elems = 0, g_elems = 0, gam_elems = 0;
+  int max_vec = 0;
+  int nunk = 0;
+  // device
+  void *arena = nullptr;
+  DeviceTables t{};
+  Workspace w{};
+  BasisItem *d_items = nullptr;
+  int *d_pos2unk = nullptr;
+  int64_t *d_pos_real_off = nullptr;
+  int solve_grid = 1;
+};
+
+static thread_local std::string g_setup_err;
+
+static mrcm_status fail(mrcm_ctx *c, mrcm_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_setup_err = buf;
+  return s;
+}
+
+static mrcm_status cuda_fail(mrcm_ctx *c, cudaError_t e, const char *where) {
+  return fail(c, MRCM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Interface functions at face midpoints t_e = -1 + (2e+1)/s: Legendre
+// polynomials by their three-term recurrence, or monomials.
+static void fn_table(int family, int s, std::vector<double> &out) {
+  out.assign(static_cast<size_t>(s) * s, 0.0);
+  for (int e = 0; e < s; ++e) {
+    const double tt = -1.0 + (2.0 * e + 1.0) / s;
+    double pm1 = 0.0, p = 1.0;
+    for (int k = 0; k < s; ++k) {
+      if (family == MRCM_BASIS_LEGENDRE) {
+        out[static_cast<size_t>(k) * s + e] = p;
+        const double pn = ((2.0 * k + 1.0) * tt * p - k * pm1) / (k + 1.0);
+        pm1 = p;
+        p = pn;
+      } else {
+        out[static_cast<size_t>(k) * s + e] = std::pow(tt, k);
+      }
+    }
+  }
+}
+
+static mrcm_status validate(const mrcm_desc *d) {
+  if (!d) return fail(nullptr, MRCM_EINVAL, "descriptor is NULL");
+  if (d->nx <= 0 || d->ny <= 0) return fail(nullptr, MRCM_EINVAL, "nx, ny must be positive");
+  if (d->n_real <= 0 || d->n_real > kMaxRealisations)
+    return fail(nullptr, MRCM_EINVAL, "n_real out of range");
+  if (!(d->ly > 0.0) || !std::isfinite(d->ly)) return fail(nullptr, MRCM_EINVAL, "ly must be > 0");
+  if (!d->sub_size || !d->iface_nU || !d->iface_nP || !d->bc_type || !d->bc_val)
+    return fail(nullptr, MRCM_EINVAL, "sub_size, iface_nU, iface_nP, bc_type, bc_val are required");
+  if (d->prec != MRCM_PREC_FP64 && d->prec != MRCM_PREC_FP32_IR)
+    return fail(nullptr, MRCM_EINVAL, "unknown precision %d", d->prec);
+  if (d->basis_family != MRCM_BASIS_LEGENDRE && d->basis_family != MRCM_BASIS_MONOMIAL)
+    return fail(nullptr, MRCM_EINVAL, "unknown basis family %d", d->basis_family);
+  if (!(d->ir_tol > 0.0) || !(d->iface_tol > 0.0) || d->ir_max < 0 || d->iface_ir_max < 0)
+    return fail(nullptr, MRCM_EINVAL, "tolerances must be > 0 and sweep limits >= 0");
+  if (d->ir_max > 1000 || d->iface_ir_max > 1000)
+    return fail(nullptr, MRCM_EINVAL, "sweep limits above 1000");
+  const int s0 = d->sub_size[0];
+  for (int r = 0; r < d->n_real; ++r) {
+    const int s = d->sub_size[r];
+    if (s != 16)
+      return fail(nullptr, MRCM_EINVAL, "subdomain size %d not supported (16 only)", s);
+    if (s != s0)
+      return fail(nullptr, MRCM_EINVAL, "mixed subdomain sizes across realisations not supported");
+    if (d->nx % s || d->ny % s)
+      return fail(nullptr, MRCM_EINVAL, "grid %dx%d not divisible by subdomain size %d", d->nx,
+                  d->ny, s);
+  }
+  const int nb = 2 * d->nx + 2 * d->ny;
+  for (int k = 0; k < nb; ++k) {
+    if (d->bc_type[k] != 0 && d->bc_type[k] != 1)
+      return fail(nullptr, MRCM_EINVAL, "bc_type[%d] must be 0 or 1", k);
+    if (!std::isfinite(d->bc_val[k])) return fail(nullptr, MRCM_EINVAL, "bc_val[%d] not finite", k);
+    if (d->pure_neumann && d->bc_type[k] != 0)
+      return fail(nullptr, MRCM_EINVAL, "pure_neumann with a Dirichlet face");
+  }
+  return MRCM_OK;
+}
+
+static mrcm_status build_tables(mrcm_ctx *c) {
+  const mrcm_desc &d = c->d;
+  const int S = c->S;
+  const double h = d.ly / d.ny;
+  int nsub_tot = 0, nif_tot = 0, unk_tot = 0;
+  int64_t alpha_off = 0, gam_off = 0, slab_off = 0, xy_off = 0, vec_off = 0;
+  int64_t basis_off = 0, g_off = 0;
+  int col_off = 0;
+  for (int r = 0; r < d.n_real; ++r) {
+    RealInfo ri{};
+    ri.s = S;
+    ri.Sx = d.nx / S;
+    ri.Sy = d.ny / S;
+    ri.sub0 = nsub_tot;
+    ri.nsub = ri.Sx * ri.Sy;
+    ri.iface0 = nif_tot;
+    ri.niface = (ri.Sx - 1) * ri.Sy + ri.Sx * (ri.Sy - 1);
+    ri.unk0 = unk_tot;
+    ri.h = h;
+    ri.H = S * h;
+    if (d.pure_neumann && ri.nsub < 2)
+      return fail(nullptr, MRCM_EINVAL, "pure_neumann needs at least two subdomains");
+    // interfaces in canonical order
+    const int nV = (ri.Sx - 1) * ri.Sy;
+    for (int g = 0; g < ri.niface; ++g) {
+      IfaceInfo fi{};
+      fi.r = r;
+      int I, J;
+      if (g < nV) {
+        fi.kind = 0;
+        J = g / (ri.Sx - 1);
+        I = g % (ri.Sx - 1);
+        fi.L = ri.sub0 + J * ri.Sx + I;
+        fi.R = fi.L + 1;
+      } else {
+        fi.kind = 1;
+        J = (g - nV) / ri.Sx;
+        I = (g - nV) % ri.Sx;
+        fi.L = ri.sub0 + J * ri.Sx + I;
+        fi.R = fi.L + ri.Sx;
+      }
+      fi.nU = d.iface_nU[nif_tot + g];
+      fi.nP = d.iface_nP[nif_tot + g];
+      if (fi.nU < 0 || fi.nP < 0 || fi.nU > S || fi.nP > S || fi.nU + fi.nP < 1)
+        return fail(nullptr, MRCM_EINVAL, "interface %d: need 0 <= nU,nP <= %d, nU+nP >= 1",
+                    nif_tot + g, S);
+      if (d.pure_neumann && fi.nP < 1)
+        return fail(nullptr, MRCM_EINVAL, "pure_neumann needs nP >= 1 on every interface");
+      fi.unk = unk_tot;
+      unk_tot += fi.nU + fi.nP;
+      fi.alpha_off = alpha_off;
+      alpha_off += S;
+      fi.gam_off = gam_off;
+      gam_off += 2 * S;
+      c->iface.push_back(fi);
+    }
+    ri.nunk = unk_tot - ri.unk0;
+    ri.pin = -1;
+    if (d.pure_neumann) {
+      const IfaceInfo &f0 = c->iface[ri.iface0];
+      ri.pin = f0.unk + f0.nU;   // P_0 of the first interface
+    }
+    // subdomains
+    for (int J = 0; J < ri.Sy; ++J)
+      for (int I = 0; I < ri.Sx; ++I) {
+        SubInfo sb{};
+        sb.r = r;
+        sb.I = I;
+        sb.J = J;
+        sb.x0 = I * S;
+        sb.y0 = J * S;
+        const int ifW = (I > 0) ? ri.iface0 + J * (ri.Sx - 1) + (I - 1) : -1;
+        const int ifE = (I < ri.Sx - 1) ? ri.iface0 + J * (ri.Sx - 1) + I : -1;
+        const int ifS = (J > 0) ? ri.iface0 + nV + (J - 1) * ri.Sx + I : -1;
+        const int ifN = (J < ri.Sy - 1) ? ri.iface0 + nV + J * ri.Sx + I : -1;
+        sb.edge_iface[0] = ifW;
+        sb.edge_iface[1] = ifE;
+        sb.edge_iface[2] = ifS;
+        sb.edge_iface[3] = ifN;
+        sb.col_off = col_off;
+        c->col.push_back(ColInfo{-1, -1, 0, 0});
+        int ncol = 1, nrow = 0;
+        for (int e = 0; e < 4; ++e) {
+          sb.edge_col[e] = ncol;
+          sb.edge_row[e] = nrow;
+          if (sb.edge_iface[e] < 0) continue;
+          const IfaceInfo &fi = c->iface[sb.edge_iface[e]];
+          for (int k = 0; k < fi.nU; ++k) c->col.push_back(ColInfo{fi.unk + k, e, k, 1});
+          for (int k = 0; k < fi.nP; ++k) c->col.push_back(ColInfo{fi.unk + fi.nU + k, e, k, 0});
+          ncol += fi.nU + fi.nP;
+          nrow += fi.nU + fi.nP;
+        }
+        sb.ncols = ncol;
+        sb.nrows = nrow;
+        col_off += ncol;
+        sb.basis_off = basis_off;
+        basis_off += static_cast<int64_t>(ncol) * S * S;
+        sb.g_off = g_off;
+        g_off += static_cast<int64_t>(nrow) * ncol;
+        const int gid = static_cast<int>(c->sub.size());
+        for (int c0 = 0; c0 < ncol; c0 += 12)
+          c->items.push_back(BasisItem{gid, c0, (ncol - c0) < 12 ? (ncol - c0) : 12});
+        c->sub.push_back(sb);
+      }
+    // slabs: block-tridiagonal grouping of the interfaces
+    const bool xdir = ri.Sx >= ri.Sy;
+    ri.nslab = xdir ? ri.Sx : ri.Sy;
+    std::vector<std::vector<int>> slabs(ri.nslab);
+    for (int k = 0; k < ri.nslab; ++k) {
+      if (xdir) {
+        for (int J = 0; J < ri.Sy - 1; ++J) slabs[k].push_back(ri.iface0 + nV + J * ri.Sx + k);
+        if (k < ri.Sx - 1)
+          for (int J = 0; J < ri.Sy; ++J) slabs[k].push_back(ri.iface0 + J * (ri.Sx - 1) + k);
+      } else {
+        for (int I = 0; I < ri.Sx - 1; ++I) slabs[k].push_back(ri.iface0 + k * (ri.Sx - 1) + I);
+        if (k < ri.Sy - 1)
+          for (int I = 0; I < ri.Sx; ++I) slabs[k].push_back(ri.iface0 + nV + k * ri.Sx + I);
+      }
+    }
+    ri.bmax = 1;
+    for (int k = 0; k < ri.nslab; ++k) {
+      int pos = 0;
+      for (int g : slabs[k]) {
+        IfaceInfo &fi = c->iface[g];
+        fi.slab = k;
+        fi.pos = pos;
+        pos += fi.nU + fi.nP;
+      }
+      if (pos > ri.bmax) ri.bmax = pos;
+    }
+    if (ri.bmax > 64)
+      return fail(nullptr, MRCM_EINVAL,
+                  "interface slab of %d unknowns exceeds the supported 64 (grid too wide)", ri.bmax);
+    int nlev = 0;
+    while ((1 << nlev) < ri.nslab) ++nlev;
+    ri.nlev = nlev;
+    ri.slab_off = slab_off;
+    slab_off += static_cast<int64_t>(ri.nslab) * ri.bmax * ri.bmax;
+    ri.xy_off = xy_off;
+    xy_off += static_cast<int64_t>(nlev) * ri.nslab * ri.bmax * ri.bmax;
+    ri.vec_off = vec_off;
+    c->pos_real_off.push_back(vec_off);
+    vec_off += static_cast<int64_t>(ri.nslab) * ri.bmax;
+    if (ri.nslab * ri.bmax > c->max_vec) c->max_vec = ri.nslab * ri.bmax;
+    c->real.push_back(ri);
+    nsub_tot += ri.nsub;
+    nif_tot += ri.niface;
+  }
+  c->nunk = unk_tot;
+  c->unk_iface.assign(unk_tot, -1);
+  c->unk_slabpos.assign(unk_tot, -1);
+  c->pos2unk.assign(vec_off, -1);
+  for (size_t g = 0; g < c->iface.size(); ++g) {
+    const IfaceInfo &fi = c->iface[g];
+    const RealInfo &ri = c->real[fi.r];
+    for (int i = 0; i < fi.nU + fi.nP; ++i) {
+      const int u = fi.unk + i;
+      c->unk_iface[u] = static_cast<int>(g);
+      c->unk_slabpos[u] = fi.slab * ri.bmax + fi.pos + i;
+      c->pos2unk[ri.vec_off + fi.slab * ri.bmax + fi.pos + i] = u;
+    }
+  }
+  c->slab_elems = slab_off;
+  c->xy_elems = xy_off;
+  c->npos = vec_off;
+  c->basis_elems = basis_off;
+  c->g_elems = g_off;
+  c->gam_elems = gam_off;
+  return MRCM_OK;
+}
+
+namespace {
+struct Arena {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t n) {
+    const size_t o = (off + 255) & ~size_t(255);
+    off = o + n * sizeof(T);
+    return o;
+  }
+};
+}  // namespace
+
+extern "C" {
+
+int32_t mrcm_version(void) { return 1; }
+
+const char *mrcm_last_error(const mrcm_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : g_setup_err.c_str();
+}
+
+mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out) {
+  if (!out) return fail(nullptr, MRCM_EINVAL, "out is NULL");
+  *out = nullptr;
+  mrcm_status st = validate(desc);
+  if (st != MRCM_OK) return st;
+  mrcm_ctx *c = new mrcm_ctx();
+  c->d = *desc;
+  c->prec = desc->prec;
+  c->S = desc->sub_size[0];
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  st = build_tables(c);
+  if (st != MRCM_OK) {
+    delete c;
+    return st;
+  }
+  cudaError_t e = cudaGetDevice(&c->dev);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(nullptr, e, "cudaGetDevice");
+  }
+  const mrcm_desc &d = c->d;
+  const int S = c->S;
+  const int N = S * S;
+  const size_t esz = c->prec == MRCM_PREC_FP64 ? sizeof(double) : sizeof(float);
+  const int nsub = static_cast<int>(c->sub.size());
+  const int nif = static_cast<int>(c->iface.size());
+  const int nunk = c->nunk;
+  const int nb = 2 * d.nx + 2 * d.ny;
+  std::vector<double> fnv;
+  fn_table(d.basis_family, S, fnv);
+  std::vector<double> alpha(static_cast<size_t>(nif) * S, 1.0);
+  if (d.alpha) {
+    for (size_t k = 0; k < alpha.size(); ++k) {
+      alpha[k] = d.alpha[k];
+      if (!(alpha[k] > 0.0) || !std::isfinite(alpha[k])) {
+        delete c;
+        return fail(nullptr, MRCM_EINVAL, "alpha[%zu] must be positive and finite", k);
+      }
+    }
+  }
+  // one arena for tables and workspace
+  Arena A;
+  const size_t o_sub = A.take<SubInfo>(nsub), o_if = A.take<IfaceInfo>(nif ? nif : 1),
+               o_col = A.take<ColInfo>(c->col.size()), o_real = A.take<RealInfo>(c->real.size()),
+               o_ui = A.take<int>(nunk ? nunk : 1), o_usp = A.take<int>(nunk ? nunk : 1),
+               o_fn = A.take<double>(fnv.size()), o_al = A.take<double>(alpha.size() ? alpha.size() : 1),
+               o_bt = A.take<int8_t>(nb), o_bv = A.take<double>(nb),
+               o_items = A.take<BasisItem>(c->items.size()),
+               o_p2u = A.take<int>(c->npos ? c->npos : 1),
+               o_pro = A.take<int64_t>(c->pos_real_off.size()),
+               o_coef = A.take<double>(static_cast<size_t>(nsub) * 6 * N),
+               o_W = A.take<char>(static_cast<size_t>(nsub) * S * N * esz),
+               o_basis = A.take<double>(c->basis_elems), o_G = A.take<double>(c->g_elems ? c->g_elems : 1),
+               o_sB = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
+               o_sA = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
+               o_sC = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
+               o_X = A.take<char>((c->xy_elems ? c->xy_elems : 1) * esz),
+               o_Y = A.take<char>((c->xy_elems ? c->xy_elems : 1) * esz),
+               o_ds = A.take<double>(nunk ? nunk : 1), o_f = A.take<double>(nunk ? nunk : 1),
+               o_x = A.take<double>(nunk ? nunk : 1), o_r = A.take<double>(nunk ? nunk : 1),
+               o_ps = A.take<double>(nsub), o_gt = A.take<double>(c->gam_elems ? c->gam_elems : 1),
+               o_st = A.take<int>(4), o_dst = A.take<double>(2 + 2 * d.n_real),
+               o_done = A.take<int>(d.n_real + 1);
+  e = cudaMalloc(&c->arena, A.off);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, MRCM_ENOMEM, "cudaMalloc(%zu bytes): %s", A.off, cudaGetErrorString(e));
+  }
+  char *base = static_cast<char *>(c->arena);
+  auto up = [&](size_t off, const void *src, size_t bytes) {
+    if (!bytes) return cudaSuccess;
+    return cudaMemcpy(base + off, src, bytes, cudaMemcpyHostToDevice);
+  };
+  // tables
+  if ((e = up(o_sub, c->sub.data(), nsub * sizeof(SubInfo))) != cudaSuccess ||
+      (e = up(o_if, c->iface.data(), nif * sizeof(IfaceInfo))) != cudaSuccess ||
+      (e = up(o_col, c->col.data(), c->col.size() * sizeof(ColInfo))) != cudaSuccess ||
+      (e = up(o_real, c->real.data(), c->real.size() * sizeof(RealInfo))) != cudaSuccess ||
+      (e = up(o_ui, c->unk_iface.data(), nunk * sizeof(int))) != cudaSuccess ||
+      (e = up(o_usp, c->unk_slabpos.data(), nunk * sizeof(int))) != cudaSuccess ||
+      (e = up(o_fn, fnv.data(), fnv.size() * sizeof(double))) != cudaSuccess ||
+      (e = up(o_al, alpha.data(), alpha.size() * sizeof(double))) != cudaSuccess ||
+      (e = up(o_bt, d.bc_type, nb * sizeof(int8_t))) != cudaSuccess ||
+      (e = up(o_bv, d.bc_val, nb * sizeof(double))) != cudaSuccess ||
+      (e = up(o_items, c->items.data(), c->items.size() * sizeof(BasisItem))) != cudaSuccess ||
+      (e = up(o_p2u, c->pos2unk.data(), c->npos * sizeof(int))) != cudaSuccess ||
+      (e = up(o_pro, c->pos_real_off.data(), c->pos_real_off.size() * sizeof(int64_t))) !=
+          cudaSuccess ||
+      (e = cudaMemset(base + o_st, 0, 4 * sizeof(int))) != cudaSuccess ||
+      (e = cudaMemset(base + o_dst, 0, (2 + 2 * d.n_real) * sizeof(double))) != cudaSuccess) {
+    cudaFree(c->arena);
+    delete c;
+    return cuda_fail(nullptr, e, "mrcm_setup upload");
+  }
+  DeviceTables &t = c->t;
+  t.nx = d.nx;
+  t.ny = d.ny;
+  t.n_real = d.n_real;
+  t.nsub = nsub;
+  t.niface = nif;
+  t.nunk = nunk;
+  t.pure_neumann = d.pure_neumann ? 1 : 0;
+  t.s = S;
+  t.h = d.ly / d.ny;
+  t.H = S * t.h;
+  t.sub = reinterpret_cast<const SubInfo *>(base + o_sub);
+  t.iface = reinterpret_cast<const IfaceInfo *>(base + o_if);
+  t.col = reinterpret_cast<const ColInfo *>(base + o_col);
+  t.real = reinterpret_cast<const RealInfo *>(base + o_real);
+  t.unk_iface = reinterpret_cast<const int *>(base + o_ui);
+  t.unk_slabpos = reinterpret_cast<const int *>(base + o_usp);
+  t.fnval = reinterpret_cast<const double *>(base + o_fn);
+  t.fn_stride = S;
+  t.alpha = reinterpret_cast<const double *>(base + o_al);
+  t.bc_type = reinterpret_cast<const int8_t *>(base + o_bt);
+  t.bc_val = reinterpret_cast<const double *>(base + o_bv);
+  c->d_items = reinterpret_cast<BasisItem *>(base + o_items);
+  c->d_pos2unk = reinterpret_cast<int *>(base + o_p2u);
+  c->d_pos_real_off = reinterpret_cast<int64_t *>(base + o_pro);
+  Workspace &w = c->w;
+  w.coef = reinterpret_cast<double *>(base + o_coef);
+  w.W = base + o_W;
+  w.basis = reinterpret_cast<double *>(base + o_basis);
+  w.G = reinterpret_cast<double *>(base + o_G);
+  w.slabB = base + o_sB;
+  w.slabA = base + o_sA;
+  w.slabC = base + o_sC;
+  w.X = base + o_X;
+  w.Y = base + o_Y;
+  w.dscale = reinterpret_cast<double *>(base + o_ds);
+  w.f = reinterpret_cast<double *>(base + o_f);
+  w.x = reinterpret_cast<double *>(base + o_x);
+  w.r = reinterpret_cast<double *>(base + o_r);
+  w.vec = nullptr;
+  w.psum = reinterpret_cast<double *>(base + o_ps);
+  w.gamma_tmp = reinterpret_cast<double *>(base + o_gt);
+  w.status = reinterpret_cast<int *>(base + o_st);
+  w.dstat = reinterpret_cast<double *>(base + o_dst);
+  w.ifnorm = nullptr;
+  w.done = reinterpret_cast<int *>(base + o_done);
+  int bmax = 1;
+  for (const RealInfo &ri : c->real) bmax = ri.bmax > bmax ? ri.bmax : bmax;
+  if ((e = init_local_attributes()) != cudaSuccess ||
+      (e = init_iface_attributes(c->prec, bmax, c->max_vec)) != cudaSuccess) {
+    cudaFree(c->arena);
+    delete c;
+    return cuda_fail(nullptr, e, "kernel attributes");
+  }
+  c->solve_grid = iface_solve_grid(c->prec, c->dev, c->max_vec);
+  if (nunk > 0 && (c->solve_grid < 1 || d.n_real > c->solve_grid)) {
+    cudaFree(c->arena);
+    delete c;
+    return fail(nullptr, MRCM_EINVAL,
+                "n_real %d exceeds the %d co-resident interface solvers", d.n_real,
+                c->solve_grid);
+  }
+  *out = c;
+  return MRCM_OK;
+}
+
+void mrcm_destroy(mrcm_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->arena) cudaFree(ctx->arena);
+  delete ctx;
+}
+
+mrcm_status mrcm_set_stream(mrcm_ctx *ctx, void *cuda_stream) {
+  if (!ctx) return MRCM_EINVAL;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_factor_local(mrcm_ctx *ctx, const double *d_K, const double *d_lambda) {
+  if (!ctx) return MRCM_EINVAL;
+  if (!d_K || !d_lambda) return fail(ctx, MRCM_EINVAL, "K and lambda must be device pointers");
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ctx->w.status, 0, 4 * sizeof(int), ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "reset status");
+  if ((e = cudaMemsetAsync(ctx->w.dstat, 0, (2 + 2 * ctx->d.n_real) * sizeof(double),
+                           ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "reset status");
+  e = launch_factor(ctx->t, ctx->w, ctx->prec, d_K, d_lambda, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "factor_local launch");
+  ctx->launches = 1;
+  ctx->state = 1;
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_build_basis(mrcm_ctx *ctx, const double *d_q) {
+  if (!ctx) return MRCM_EINVAL;
+  if (ctx->state < 1) return fail(ctx, MRCM_EINVAL, "build_basis before factor_local");
+  if (!d_q) return fail(ctx, MRCM_EINVAL, "q must be a device pointer");
+  cudaError_t e = launch_basis(ctx->t, ctx->w, ctx->prec, ctx->d_items,
+                               static_cast<int>(ctx->items.size()), d_q, ctx->d.ir_tol,
+                               ctx->d.ir_max, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "build_basis launch");
+  ctx->launches += 1;
+  ctx->state = 2;
+  return MRCM_OK;
+}
+
+static mrcm_status read_info(mrcm_ctx *ctx, mrcm_info *info) {
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  int st[4];
+  double ds[2];
+  if ((e = cudaMemcpy(st, ctx->w.status, sizeof st, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(ds, ctx->w.dstat, sizeof ds, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(ctx, e, "status read");
+  info->flags = st[0];
+  info->local_sweeps_max = st[1];
+  info->iface_sweeps = st[2];
+  info->reserved = 0;
+  info->local_resid_max = ds[0];
+  info->iface_resid = ds[1];
+  if (st[0] & MRCM_FLAG_LAYOUT) return fail(ctx, MRCM_EINVAL, "internal slab layout error");
+  if (st[0] & MRCM_FLAG_NAN) return fail(ctx, MRCM_ENAN, "NaN/Inf or non-positive kappa");
+  if (st[0] & MRCM_FLAG_NOTSPD) return fail(ctx, MRCM_ENOTSPD, "local pivot <= 0");
+  if (st[0] & MRCM_FLAG_IFACE_PIVOT)
+    return fail(ctx, MRCM_ENOTSPD, "interface pivot zero or not finite");
+  if (st[0] & MRCM_FLAG_IFACE_STALL)
+    return fail(ctx, MRCM_ENOCONV, "interface refinement stopped at %.3e", ds[1]);
+  if (st[0] & MRCM_FLAG_LOCAL_STALL)
+    return fail(ctx, MRCM_EIRSTALL, "local refinement stopped at %.3e", ds[0]);
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_solve_interface(mrcm_ctx *ctx, mrcm_info *info) {
+  if (!ctx) return MRCM_EINVAL;
+  if (ctx->state < 2) return fail(ctx, MRCM_EINVAL, "solve_interface before build_basis");
+  if (ctx->nunk > 0) {
+    cudaError_t e = launch_iface_assemble(ctx->t, ctx->w, ctx->prec, ctx->slab_elems,
+                                          ctx->d_pos2unk, ctx->npos, ctx->d_pos_real_off,
+                                          ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "interface assembly launch");
+    ctx->launches += 2;
+    int nl = 0;
+    e = launch_bcr_factor(ctx->t, ctx->w, ctx->prec, ctx->real.data(), &nl, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "interface factor launch");
+    ctx->launches += nl;
+    const int max_solves = 1 + (ctx->prec == MRCM_PREC_FP64 ? 0 : ctx->d.iface_ir_max);
+    e = launch_iface_solve(ctx->t, ctx->w, ctx->prec, ctx->d_pos2unk, ctx->d.iface_tol,
+                           max_solves, ctx->solve_grid, ctx->max_vec, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "interface solve launch");
+    ctx->launches += 1;
+  }
+  ctx->state = 3;
+  if (info) return read_info(ctx, info);
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_reconstruct(mrcm_ctx *ctx, double *d_p, double *d_ux, double *d_uy,
+                             double *d_gamma_u) {
+  if (!ctx) return MRCM_EINVAL;
+  if (ctx->state < 3) return fail(ctx, MRCM_EINVAL, "reconstruct before solve_interface");
+  if (!d_p || !d_ux || !d_uy) return fail(ctx, MRCM_EINVAL, "p, ux, uy must be device pointers");
+  cudaError_t e = launch_reconstruct(ctx->t, ctx->w, d_p, d_ux, d_uy, d_gamma_u, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reconstruct launch");
+  ctx->launches += ctx->d.pure_neumann ? 3 : 2;
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_get_info(mrcm_ctx *ctx, mrcm_info *info) {
+  if (!ctx || !info) return MRCM_EINVAL;
+  return read_info(ctx, info);
+}
+
+int32_t mrcm_launch_count(const mrcm_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int64_t mrcm_num_interface_unknowns(const mrcm_ctx *ctx) { return ctx ? ctx->nunk : 0; }
+
+int64_t mrcm_num_gamma_values(const mrcm_ctx *ctx) { return ctx ? ctx->gam_elems : 0; }
+
+mrcm_status mrcm_copy_interface_solution(mrcm_ctx *ctx, double *d_x) {
+  if (!ctx || !d_x) return MRCM_EINVAL;
+  if (ctx->state < 3) return fail(ctx, MRCM_EINVAL, "no interface solution yet");
+  cudaError_t e = cudaMemcpyAsync(d_x, ctx->w.x, sizeof(double) * ctx->nunk,
+                                  cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "copy interface solution");
+  return MRCM_OK;
+}
+
+}  // extern "C"

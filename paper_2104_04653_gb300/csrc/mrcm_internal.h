@@ -1,0 +1,127 @@
+// Internal tables and launch entry points shared by the host orchestrator
+// (mrcm_abi.cu) and the kernels (local.cu, iface.cu, recon.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mrcm {
+
+constexpr int kMaxRealisations = 1 << 16;
+constexpr int kEdgeW = 0, kEdgeE = 1, kEdgeS = 2, kEdgeN = 3;
+
+// One subdomain (all realisations concatenated).
+struct SubInfo {
+  int r;             // realisation
+  int I, J;          // subdomain coordinates
+  int x0, y0;        // first cell (global x, y within the realisation)
+  int ncols;         // 1 (sources/BC) + sum over interface edges of nU+nP
+  int nrows;         // sum over interface edges of nU+nP (rows of G)
+  int edge_iface[4]; // W,E,S,N: global interface id, -1 on the physical boundary
+  int edge_col[4];   // first basis column of the edge's functions
+  int edge_row[4];   // first row of the edge in G
+  int col_off;       // offset into the column table (ncols entries)
+  int64_t basis_off; // offset (doubles) of basis [ncols][S*S]
+  int64_t g_off;     // offset (doubles) of G [nrows][ncols]
+};
+
+// One interface (all realisations concatenated, canonical order).
+struct IfaceInfo {
+  int r;
+  int kind;          // 0 vertical (normal +x), 1 horizontal (normal +y)
+  int L, R;          // global subdomain ids, L < R
+  int nU, nP;
+  int unk;           // global unknown offset of U_0
+  int slab, pos;     // BCR slab index (within realisation), row offset in slab
+  int64_t alpha_off; // offset into the per-face alpha array (s values)
+  int64_t gam_off;   // offset into the one-sided velocity output (2*s values)
+};
+
+// Column c of a subdomain: global unknown it multiplies (-1: particular),
+// the edge (0..3) whose Robin data it carries, and the function index.
+struct ColInfo {
+  int unk;           // global unknown, -1 for the particular column
+  int edge;          // 0..3, -1 for the particular column
+  int fn;            // function index k
+  int is_u;          // 1: flux function phi_k, 0: pressure function psi_k
+};
+
+struct RealInfo {
+  int s, Sx, Sy;
+  int sub0, nsub;
+  int iface0, niface;
+  int unk0, nunk;
+  int pin;           // pinned global unknown (pure Neumann) or -1
+  int nslab, bmax;   // BCR slabs and padded slab size
+  int nlev;          // BCR reduction levels
+  int64_t slab_off;  // offset (elements) of this realisation's slab blocks
+  int64_t xy_off;    // offset (elements) of this realisation's X/Y blocks
+  int64_t vec_off;   // offset (elements) of slab-padded vectors
+  double h, H;
+};
+
+struct BasisItem {   // one CTA of the basis kernel
+  int sub;
+  int c0, nc;        // column range
+};
+
+// Everything the kernels read, as device pointers (one struct by value).
+struct DeviceTables {
+  int nx, ny, n_real, nsub, niface, nunk;
+  int pure_neumann;
+  int s;             // subdomain edge (uniform across realisations for now)
+  double h, H;
+  const SubInfo *sub;
+  const IfaceInfo *iface;
+  const ColInfo *col;
+  const RealInfo *real;
+  const int *unk_iface;     // global unknown -> interface id
+  const int *unk_slabpos;   // global unknown -> slab*bmax + pos (within realisation)
+  const double *fnval;      // [kMaxFn][s] interface function values at midpoints
+  int fn_stride;            // = s
+  const double *alpha;      // per face
+  const int8_t *bc_type;
+  const double *bc_val;
+};
+
+// Workspace (device pointers), owned by the context.
+struct Workspace {
+  double *coef;       // [nsub][5][S*S]: tW, tE, tS, tN, d (=1/sqrt(diag))
+  void *W;            // [nsub][S][S][S] inverse Schur blocks, prec-typed
+  double *basis;      // basis columns (FP64)
+  double *G;          // local interface contributions (FP64)
+  void *slabB, *slabA, *slabC;  // [per real][nslab][bmax*bmax], prec-typed
+  void *X, *Y;        // BCR forward multipliers, prec-typed
+  double *dscale;     // [nunk] symmetric scaling of the interface matrix
+  double *f;          // [nunk] interface RHS
+  double *x;          // [nunk] interface solution
+  double *r;          // [nunk] interface residual
+  void *vec;          // [per real][nslab*bmax] BCR work vector, prec-typed
+  double *psum;       // [nsub] per-subdomain pressure sums
+  double *gamma_tmp;  // one-sided velocities scratch (if user passes none)
+  int *status;        // [4] flags, local sweeps max, iface sweeps, spare
+  double *dstat;      // [2 + n_real] local resid max, iface resid, per real
+  double *ifnorm;     // [n_real] ||f|| per realisation
+  int *done;          // [n_real + 1] convergence flags
+};
+
+// Launch wrappers (return cudaGetLastError()).
+cudaError_t launch_factor(const DeviceTables &t, const Workspace &w, int prec,
+                          const double *K, const double *lam, cudaStream_t st);
+cudaError_t launch_basis(const DeviceTables &t, const Workspace &w, int prec,
+                         const BasisItem *items, int nitems, const double *q,
+                         double ir_tol, int ir_max, cudaStream_t st);
+cudaError_t launch_iface_assemble(const DeviceTables &t, const Workspace &w, int prec,
+                                  int64_t slab_elems, const int *pos2unk, int64_t npos,
+                                  const int64_t *pos_real_off, cudaStream_t st);
+cudaError_t launch_bcr_factor(const DeviceTables &t, const Workspace &w, int prec,
+                              const RealInfo *host_real, int *nlaunch, cudaStream_t st);
+cudaError_t launch_iface_solve(const DeviceTables &t, const Workspace &w, int prec,
+                               const int *pos2unk, double tol, int max_solves, int grid,
+                               int max_vec, cudaStream_t st);
+cudaError_t launch_reconstruct(const DeviceTables &t, const Workspace &w, double *p,
+                               double *ux, double *uy, double *gam, cudaStream_t st);
+int iface_solve_grid(int prec, int dev, int max_vec);
+cudaError_t init_local_attributes();
+cudaError_t init_iface_attributes(int prec, int bmax, int max_vec);
+
+}  // namespace mrcm

@@ -1,0 +1,155 @@
+// Step (e) of the MRCM solve: fine-scale pressure as the linear combination
+// of the multiscale basis with the interface coefficients (text after
+// Eq. "beta"), and face normal velocities from it: two-point fluxes inside a
+// subdomain, the Robin flux T_R (p_c - g)/h on each side of an interface
+// face (g = -beta sigma U_H + P_H, Eq. "mrc1"), reported as the mean of the
+// two one-sided values, and the boundary data or Dirichlet flux on physical
+// faces.
+#include "mrcm_internal.h"
+#include "../../include/mrcm.h"
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mrcm {
+namespace {
+
+constexpr int kS = 16;
+
+__global__ void __launch_bounds__(kS *kS) k_recon_cells(DeviceTables t, Workspace w, double *P,
+                                                        double *UX, double *UY, double *GAM) {
+  constexpr int S = kS, N = S * S;
+  const int g = blockIdx.x;
+  const SubInfo sb = t.sub[g];
+  const int tid = threadIdx.x, a = tid % S, b = tid / S;
+  __shared__ double p[N];
+  __shared__ double coefc[160];
+  __shared__ double red[N / 32];
+  for (int c = tid; c < sb.ncols; c += N) {
+    const int u = t.col[sb.col_off + c].unk;
+    coefc[c] = u < 0 ? 1.0 : w.x[u];
+  }
+  __syncthreads();
+  const double *bas = w.basis + sb.basis_off;
+  double pc = 0.0;
+  for (int c = 0; c < sb.ncols; ++c) pc += coefc[c] * bas[static_cast<int64_t>(c) * N + tid];
+  p[tid] = pc;
+  __syncthreads();
+  const double *coef = w.coef + static_cast<int64_t>(g) * 6 * N;
+  const double tW = coef[tid], tE = coef[N + tid], tS = coef[2 * N + tid], tN = coef[3 * N + tid];
+  const double kc = coef[5 * N + tid];
+  const double h = t.h;
+  const int gi = sb.x0 + a, gj = sb.y0 + b;
+  const int nx = t.nx, ny = t.ny;
+  const int64_t cell = (static_cast<int64_t>(sb.r) * ny + gj) * nx + gi;
+  P[cell] = pc;
+  double *ux = UX + static_cast<int64_t>(sb.r) * ny * (nx + 1);
+  double *uy = UY + static_cast<int64_t>(sb.r) * (ny + 1) * nx;
+  if (a < S - 1) ux[static_cast<int64_t>(gj) * (nx + 1) + gi + 1] = tE * (pc - p[tid + 1]) / h;
+  if (b < S - 1) uy[static_cast<int64_t>(gj + 1) * nx + gi] = tN * (pc - p[tid + S]) / h;
+  const bool onface[4] = {a == 0, a == S - 1, b == 0, b == S - 1};
+  const double Tf[4] = {tW, tE, tS, tN};
+#pragma unroll
+  for (int side = 0; side < 4; ++side) {
+    if (!onface[side]) continue;
+    const int e = side < 2 ? b : a;
+    const double sgn = (side == kEdgeE || side == kEdgeN) ? 1.0 : -1.0;  // outward along +x/+y
+    double un;  // outward normal velocity
+    if (sb.edge_iface[side] >= 0) {
+      const IfaceInfo fi = t.iface[sb.edge_iface[side]];
+      const double beta = t.alpha[fi.alpha_off + e] * t.H / kc;
+      double UH = 0.0, PH = 0.0;
+      for (int k = 0; k < fi.nU; ++k) UH += w.x[fi.unk + k] * t.fnval[k * t.fn_stride + e];
+      for (int k = 0; k < fi.nP; ++k) PH += w.x[fi.unk + fi.nU + k] * t.fnval[k * t.fn_stride + e];
+      const double gval = -beta * sgn * UH + PH;
+      un = Tf[side] * (pc - gval) / h;
+      GAM[fi.gam_off + (sgn > 0 ? 0 : S) + e] = un;
+      continue;
+    }
+    int k;
+    if (side == kEdgeW) k = gj;
+    else if (side == kEdgeE) k = ny + gj;
+    else if (side == kEdgeS) k = 2 * ny + gi;
+    else k = 2 * ny + nx + gi;
+    un = t.bc_type[k] == 1 ? Tf[side] * (pc - t.bc_val[k]) / h : t.bc_val[k];
+    if (side == kEdgeW) ux[static_cast<int64_t>(gj) * (nx + 1)] = -un;
+    else if (side == kEdgeE) ux[static_cast<int64_t>(gj) * (nx + 1) + nx] = un;
+    else if (side == kEdgeS) uy[gi] = -un;
+    else uy[static_cast<int64_t>(ny) * nx + gi] = un;
+  }
+  // per-subdomain pressure sum (deterministic order) for the mean shift
+  double s = pc;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((tid & 31) == 0) red[tid >> 5] = s;
+  __syncthreads();
+  if (tid == 0) {
+    double acc = 0.0;
+    for (int k = 0; k < N / 32; ++k) acc += red[k];
+    w.psum[g] = acc;
+  }
+}
+
+__global__ void k_recon_mean(DeviceTables t, Workspace w, double *pmean) {
+  const RealInfo ri = t.real[blockIdx.x];
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < ri.nsub; k += blockDim.x) s += w.psum[ri.sub0 + k];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int k = 0; k < (int)(blockDim.x / 32); ++k) acc += red[k];
+    pmean[blockIdx.x] = acc / (static_cast<double>(t.nx) * t.ny);
+  }
+}
+
+// interface faces: mean of the one-sided velocities (n_check-oriented);
+// pure Neumann: shift p to zero cell mean.
+__global__ void k_recon_final(DeviceTables t, Workspace w, double *P, double *UX, double *UY,
+                              const double *GAM, const double *pmean, int64_t ncells,
+                              int64_t nfaces) {
+  const int S = t.s;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < nfaces;
+       k += stride) {
+    const int gi = static_cast<int>(k / S), e = static_cast<int>(k % S);
+    const IfaceInfo fi = t.iface[gi];
+    const SubInfo L = t.sub[fi.L];
+    const double v = 0.5 * (GAM[fi.gam_off + e] - GAM[fi.gam_off + S + e]);
+    if (fi.kind == 0) {
+      const int i = L.x0 + S, j = L.y0 + e;
+      UX[(static_cast<int64_t>(fi.r) * t.ny + j) * (t.nx + 1) + i] = v;
+    } else {
+      const int i = L.x0 + e, j = L.y0 + S;
+      UY[(static_cast<int64_t>(fi.r) * (t.ny + 1) + j) * t.nx + i] = v;
+    }
+  }
+  if (t.pure_neumann) {
+    const int64_t per = static_cast<int64_t>(t.nx) * t.ny;
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < ncells;
+         k += stride)
+      P[k] -= pmean[k / per];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_reconstruct(const DeviceTables &t, const Workspace &w, double *p, double *ux,
+                               double *uy, double *gam, cudaStream_t st) {
+  if (t.s != kS) return cudaErrorInvalidValue;
+  double *G = gam ? gam : w.gamma_tmp;
+  k_recon_cells<<<t.nsub, kS * kS, 0, st>>>(t, w, p, ux, uy, G);
+  double *pmean = w.dstat + 2 + t.n_real;
+  if (t.pure_neumann) k_recon_mean<<<t.n_real, 256, 0, st>>>(t, w, pmean);
+  const int64_t ncells = static_cast<int64_t>(t.n_real) * t.nx * t.ny;
+  const int64_t nfaces = static_cast<int64_t>(t.niface) * t.s;
+  const int64_t work = nfaces > ncells ? nfaces : ncells;
+  int blocks = static_cast<int>((work + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_recon_final<<<blocks, 256, 0, st>>>(t, w, p, ux, uy, G, pmean, ncells, nfaces);
+  return cudaGetLastError();
+}
+
+}  // namespace mrcm
