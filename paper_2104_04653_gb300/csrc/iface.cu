@@ -47,10 +47,8 @@ struct RowRef {
   int offL, offR;          // col table offsets
 };
 
-__device__ __forceinline__ RowRef row_ref(const DeviceTables &t, const Workspace &w, int u) {
-  const int gi = t.unk_iface[u];
-  const IfaceInfo fi = t.iface[gi];
-  const int i = u - fi.unk;
+__device__ __forceinline__ RowRef row_ref(const DeviceTables &t, const Workspace &w,
+                                          const IfaceInfo &fi, int i) {
   const SubInfo &L = t.sub[fi.L];
   const SubInfo &R = t.sub[fi.R];
   const int eL = fi.kind == 0 ? kEdgeE : kEdgeN;
@@ -67,72 +65,173 @@ __device__ __forceinline__ RowRef row_ref(const DeviceTables &t, const Workspace
   return rr;
 }
 
-// (1) scaling, right-hand side and padding identity, one thread per padded
-// slab position of every realisation.
+// (1) per-interface congruence scaling.  With the flux-continuity (P) rows
+// negated the interface matrix is symmetric quasi-definite: S = [-A B; B^T C]
+// on every interface block, A and C SPD.  T = blockdiag(L_A^{-1}, L_C^{-1})
+// from the Cholesky factors of the interface's own A and C makes the
+// diagonal blocks of T S T^T equal to -I and +I, which removes the
+// contrast-driven spread of the interface matrix.  Also writes f.
+constexpr int kMmax = 32;
+__global__ void __launch_bounds__(32) k_iface_prep(DeviceTables t, Workspace w) {
+  const int g = blockIdx.x;
+  const IfaceInfo fi = t.iface[g];
+  const RealInfo &ri = t.real[fi.r];
+  const int m = fi.nU + fi.nP;
+  __shared__ double Sd[kMmax][kMmax + 1];
+  __shared__ double Xd[kMmax][kMmax + 1];
+  __shared__ int bad;
+  const int i = threadIdx.x;
+  if (i == 0) bad = 0;
+  if (i < m) {
+    const RowRef rr = row_ref(t, w, fi, i);
+    const bool pin_i = (fi.unk + i == ri.pin);
+    for (int j = 0; j < m; ++j) {
+      const bool pin_j = (fi.unk + j == ri.pin);
+      double v = rr.gL[rr.colL - i + j] + rr.gR[rr.colR - i + j];
+      // A = -M_UU, C = -M_PP (both SPD); U-P coupling not needed here
+      const bool same = (i < fi.nU) == (j < fi.nU);
+      v = same ? -v : 0.0;
+      if (pin_i || pin_j) v = (i == j) ? 1.0 : 0.0;
+      Sd[i][j] = v;
+    }
+    w.f[fi.unk + i] = pin_i ? 0.0 : -(rr.gL[0] + rr.gR[0]);
+  }
+  __syncwarp();
+  // Cholesky of the two diagonal sub-blocks in place (lower), row i per lane
+  for (int k = 0; k < m; ++k) {
+    const int lo = k < fi.nU ? 0 : fi.nU;      // first index of k's sub-block
+    const int hi = k < fi.nU ? fi.nU : m;
+    if (i == k) {
+      double d = Sd[k][k];
+      for (int q = lo; q < k; ++q) d -= Sd[k][q] * Sd[k][q];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+        d = 1.0;
+      }
+      Sd[k][k] = sqrt(d);
+    }
+    __syncwarp();
+    if (i > k && i < hi) {
+      double v = Sd[i][k];
+      for (int q = lo; q < k; ++q) v -= Sd[i][q] * Sd[k][q];
+      Sd[i][k] = v / Sd[k][k];
+    }
+    __syncwarp();
+  }
+  // X = L^{-1} (block lower triangular), column j per lane
+  if (i < m) {
+    const int lo = i < fi.nU ? 0 : fi.nU;
+    const int hi = i < fi.nU ? fi.nU : m;
+    for (int r = 0; r < m; ++r) Xd[r][i] = 0.0;
+    for (int r = lo; r < hi; ++r) {
+      if (r < i) continue;
+      double v = (r == i) ? 1.0 : 0.0;
+      for (int q = i; q < r; ++q) v -= Sd[r][q] * Xd[q][i];
+      Xd[r][i] = v / Sd[r][r];
+    }
+  }
+  __syncwarp();
+  double *T = w.tsc + fi.tsc_off;
+  if (i < m) {
+    if (bad) {
+      // not quasi-definite: fall back to diagonal scaling
+      const RowRef rr = row_ref(t, w, fi, i);
+      const double dg = fabs(rr.gL[rr.colL] + rr.gR[rr.colR]);
+      for (int j = 0; j < m; ++j) T[i * m + j] = (i == j) ? (dg > 0.0 ? 1.0 / sqrt(dg) : 1.0) : 0.0;
+    } else {
+      for (int j = 0; j < m; ++j) T[i * m + j] = Xd[i][j];
+    }
+  }
+  if (i == 0 && bad) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
+}
+
+// (2) identity on padded slab positions and on the pinned unknown
 template <typename T>
-__global__ void k_iface_diag(DeviceTables t, Workspace w, const int *pos2unk, int64_t npos,
-                             const int64_t *pos_real_off, int nreal) {
+__global__ void k_iface_pad(DeviceTables t, Workspace w, const int *pos2unk, int64_t npos,
+                            const int64_t *pos_real_off, int nreal) {
   const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (p >= npos) return;
-  // realisation of this position (npos is small; linear search is fine)
   int r = 0;
   while (r + 1 < nreal && pos_real_off[r + 1] <= p) ++r;
   const RealInfo ri = t.real[r];
   const int64_t lp = p - pos_real_off[r];
   const int slab = static_cast<int>(lp / ri.bmax), pos = static_cast<int>(lp % ri.bmax);
-  T *B = static_cast<T *>(w.slabB) + ri.slab_off + static_cast<int64_t>(slab) * ri.bmax * ri.bmax;
   const int u = pos2unk[p];
   if (u < 0 || u == ri.pin) {
+    T *B = static_cast<T *>(w.slabB) + ri.slab_off +
+           static_cast<int64_t>(slab) * ri.bmax * ri.bmax;
     B[pos * ri.bmax + pos] = T(1);
-    if (u >= 0) {
-      w.dscale[u] = 1.0;
-      w.f[u] = 0.0;
-    }
-    return;
   }
-  const RowRef rr = row_ref(t, w, u);
-  const double dg = rr.gL[rr.colL] + rr.gR[rr.colR];
-  const double ad = fabs(dg);
-  w.dscale[u] = ad > 0.0 ? 1.0 / sqrt(ad) : 1.0;
-  if (!(ad > 0.0) || !isfinite(ad)) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
-  w.f[u] = -(rr.gL[0] + rr.gR[0]);
 }
 
-// (2) scaled block-tridiagonal slab matrix, one thread per interface row.
+// (3) scaled blocks T_g S_{g g'} T_{g'}^T of the block-tridiagonal slab
+// matrix; one CTA per interface g, one pass per neighbouring interface g'.
 template <typename T>
-__global__ void k_iface_assemble(DeviceTables t, Workspace w) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= t.nunk) return;
-  const IfaceInfo fi = t.iface[t.unk_iface[u]];
+__global__ void __launch_bounds__(64) k_iface_assemble(DeviceTables t, Workspace w) {
+  const int g = blockIdx.x;
+  const IfaceInfo fi = t.iface[g];
   const RealInfo ri = t.real[fi.r];
-  if (u == ri.pin) return;
-  const RowRef rr = row_ref(t, w, u);
-  const int sp = t.unk_slabpos[u];
-  const int slab = sp / ri.bmax, row = sp % ri.bmax;
-  const double du = w.dscale[u];
+  const int m = fi.nU + fi.nP;
+  const SubInfo &L = t.sub[fi.L];
+  const SubInfo &R = t.sub[fi.R];
+  __shared__ double Tg[kMmax][kMmax + 1], Tn[kMmax][kMmax + 1];
+  __shared__ double Sb[kMmax][kMmax + 1], Xb[kMmax][kMmax + 1];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < m * m; e += blockDim.x) Tg[e / m][e % m] = w.tsc[fi.tsc_off + e];
   const int64_t bb = static_cast<int64_t>(ri.bmax) * ri.bmax;
   T *Bs = static_cast<T *>(w.slabB) + ri.slab_off;
   T *As = static_cast<T *>(w.slabA) + ri.slab_off;
   T *Cs = static_cast<T *>(w.slabC) + ri.slab_off;
-  for (int side = 0; side < 2; ++side) {
-    const double *gr = side == 0 ? rr.gL : rr.gR;
-    const int nc = side == 0 ? rr.ncL : rr.ncR;
-    const int off = side == 0 ? rr.offL : rr.offR;
-    for (int c = 1; c < nc; ++c) {
-      const int v = t.col[off + c].unk;
-      if (v == ri.pin) continue;
-      const int vsp = t.unk_slabpos[v];
-      const int vs = vsp / ri.bmax, vc = vsp % ri.bmax;
-      const double val = gr[c] * du * w.dscale[v];
-      T *blk;
-      if (vs == slab) blk = Bs + slab * bb;
-      else if (vs == slab - 1) blk = As + slab * bb;
-      else if (vs == slab + 1) blk = Cs + slab * bb;
-      else {
-        atomicOr(&w.status[0], MRCM_FLAG_LAYOUT);
-        continue;
-      }
-      blk[row * ri.bmax + vc] += static_cast<T>(val);
+  // neighbour interfaces: the 4 edges of L then the 4 edges of R (g once)
+  for (int k = 0; k < 8; ++k) {
+    const int gn = k < 4 ? L.edge_iface[k] : R.edge_iface[k - 4];
+    if (gn < 0) continue;
+    bool dup = false;
+    for (int q = 0; q < k; ++q)
+      if ((q < 4 ? L.edge_iface[q] : R.edge_iface[q - 4]) == gn) dup = true;
+    if (dup) continue;
+    const IfaceInfo fn = t.iface[gn];
+    const int mn = fn.nU + fn.nP;
+    // edges of L and R carrying gn
+    int eL = -1, eR = -1;
+    for (int q = 0; q < 4; ++q) {
+      if (L.edge_iface[q] == gn) eL = q;
+      if (R.edge_iface[q] == gn) eR = q;
+    }
+    __syncthreads();
+    for (int e = tid; e < mn * mn; e += blockDim.x) Tn[e / mn][e % mn] = w.tsc[fn.tsc_off + e];
+    for (int e = tid; e < m * mn; e += blockDim.x) {
+      const int i = e / mn, j = e % mn;
+      const RowRef rr = row_ref(t, w, fi, i);
+      double v = 0.0;
+      if (eL >= 0) v += rr.gL[L.edge_col[eL] + j];
+      if (eR >= 0) v += rr.gR[R.edge_col[eR] + j];
+      if (i >= fi.nU) v = -v;                       // symmetrising sign
+      if (fi.unk + i == ri.pin || fn.unk + j == ri.pin) v = 0.0;
+      Sb[i][j] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < m * mn; e += blockDim.x) {     // X = T_g S
+      const int i = e / mn, j = e % mn;
+      double v = 0.0;
+      for (int q = 0; q <= i; ++q) v += Tg[i][q] * Sb[q][j];
+      Xb[i][j] = v;
+    }
+    __syncthreads();
+    T *blk;
+    const int ds = fn.slab - fi.slab;
+    if (ds == 0) blk = Bs + fi.slab * bb;
+    else if (ds == -1) blk = As + fi.slab * bb;
+    else if (ds == 1) blk = Cs + fi.slab * bb;
+    else {
+      if (tid == 0) atomicOr(&w.status[0], MRCM_FLAG_LAYOUT);
+      continue;
+    }
+    for (int e = tid; e < m * mn; e += blockDim.x) {     // Y = X T_gn^T
+      const int i = e / mn, j = e % mn;
+      double v = 0.0;
+      for (int q = 0; q <= j; ++q) v += Xb[i][q] * Tn[j][q];
+      blk[static_cast<int64_t>(fi.pos + i) * ri.bmax + fn.pos + j] = static_cast<T>(v);
     }
   }
 }
@@ -380,8 +479,13 @@ __device__ void bcr_solve_cta(const DeviceTables &t, const Workspace &w, const R
 }
 
 // ------------------------------------------------------------ refinement
-// Cooperative kernel: residual of all realisations by the whole grid, then
-// one CTA per realisation checks convergence and applies the BCR solve.
+// Cooperative kernel.  Each sweep:
+//   A (all CTAs, one warp per interface): x_g += T_g^T y_g   (previous solve)
+//   B (all CTAs, one warp per interface): r_g = f_g - (M x)_g in FP64 from
+//     the two G rows of every unknown; z_g = T_g (sign r_g) in the working
+//     precision into the slab-ordered vector
+//   C (one CTA per realisation): stop test on ||r||/||f||, else y = BCR(z)
+// with a grid-wide barrier between phases.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_iface_solve(DeviceTables t, Workspace w,
                                                          const int *pos2unk, double tol,
@@ -390,37 +494,71 @@ __global__ void __launch_bounds__(kThreads) k_iface_solve(DeviceTables t, Worksp
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[kThreads / 32];
   __shared__ double s_rel;
-  const int nthreads = gridDim.x * blockDim.x;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double wbuf[kThreads / 32][kMmax];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gwarp = blockIdx.x * (kThreads / 32) + wid;
+  const int nwarps = gridDim.x * (kThreads / 32);
+  T *vec = static_cast<T *>(w.vec);
   int nsolve = 0;
   for (int sweep = 0;; ++sweep) {
-    // phase 1: r = f - M x (FP64), from the two G rows of every unknown
-    for (int u = gtid; u < t.nunk; u += nthreads) {
-      const IfaceInfo fi = t.iface[t.unk_iface[u]];
-      const RealInfo &ri = t.real[fi.r];
-      double s = 0.0;
-      if (u != ri.pin) {
-        const RowRef rr = row_ref(t, w, u);
-        s = w.f[u];
-        for (int c = 1; c < rr.ncL; ++c) s -= rr.gL[c] * w.x[t.col[rr.offL + c].unk];
-        for (int c = 1; c < rr.ncR; ++c) s -= rr.gR[c] * w.x[t.col[rr.offR + c].unk];
+    // phase A
+    if (sweep > 0) {
+      for (int g = gwarp; g < t.niface; g += nwarps) {
+        const IfaceInfo fi = t.iface[g];
+        const RealInfo &ri = t.real[fi.r];
+        if (w.done[fi.r]) continue;
+        const int m = fi.nU + fi.nP;
+        const T *yv = vec + ri.vec_off + static_cast<int64_t>(fi.slab) * ri.bmax + fi.pos;
+        const double *Tg = w.tsc + fi.tsc_off;
+        if (lane < m) {
+          double d = 0.0;
+          for (int q = lane; q < m; ++q) d += Tg[q * m + lane] * static_cast<double>(yv[q]);
+          w.x[fi.unk + lane] += d;
+        }
       }
-      w.r[u] = s;
+      grid.sync();
+    }
+    // phase B
+    for (int g = gwarp; g < t.niface; g += nwarps) {
+      const IfaceInfo fi = t.iface[g];
+      const RealInfo &ri = t.real[fi.r];
+      if (w.done[fi.r]) continue;
+      const int m = fi.nU + fi.nP;
+      double rv = 0.0;
+      if (lane < m && fi.unk + lane != ri.pin) {
+        const RowRef rr = row_ref(t, w, fi, lane);
+        double sacc = w.f[fi.unk + lane];
+        for (int c = 1; c < rr.ncL; ++c) sacc -= rr.gL[c] * w.x[t.col[rr.offL + c].unk];
+        for (int c = 1; c < rr.ncR; ++c) sacc -= rr.gR[c] * w.x[t.col[rr.offR + c].unk];
+        rv = sacc;
+      }
+      double sq = rv * rv;
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if (lane == 0) w.r[g] = sq;                      // per-interface ||r||^2
+      wbuf[wid][lane] = (lane >= fi.nU) ? -rv : rv;      // symmetrising sign
+      __syncwarp();
+      if (lane < m) {
+        const double *Tg = w.tsc + fi.tsc_off;
+        double zv = 0.0;
+        for (int q = 0; q <= lane; ++q) zv += Tg[lane * m + q] * wbuf[wid][q];
+        vec[ri.vec_off + static_cast<int64_t>(fi.slab) * ri.bmax + fi.pos + lane] =
+            static_cast<T>(zv);
+      }
+      __syncwarp();
     }
     grid.sync();
-    // phase 2: per realisation
+    // phase C
     for (int r = blockIdx.x; r < t.n_real; r += gridDim.x) {
       const RealInfo ri = t.real[r];
       if (w.done[r]) continue;
       double rn = 0.0, fn = 0.0;
-      for (int u = ri.unk0 + threadIdx.x; u < ri.unk0 + ri.nunk; u += blockDim.x) {
-        rn += w.r[u] * w.r[u];
+      for (int g = ri.iface0 + threadIdx.x; g < ri.iface0 + ri.niface; g += blockDim.x) rn += w.r[g];
+      for (int u = ri.unk0 + threadIdx.x; u < ri.unk0 + ri.nunk; u += blockDim.x)
         fn += w.f[u] * w.f[u];
-      }
       for (int pass = 0; pass < 2; ++pass) {
         double v = pass == 0 ? rn : fn;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        if (lane == 0) red[wid] = v;
         __syncthreads();
         if (threadIdx.x == 0) {
           double sacc = 0.0;
@@ -435,7 +573,7 @@ __global__ void __launch_bounds__(kThreads) k_iface_solve(DeviceTables t, Worksp
       __syncthreads();
       if (threadIdx.x == 0) w.dstat[2 + r] = rel;
       const bool stop = (rel <= tol) || (nsolve >= max_solves) || !(rel == rel) ||
-                        (nsolve > 2 && rel > 0.5 * prev);
+                        (nsolve >= 2 && rel > 0.5 * prev);
       if (stop) {
         if (threadIdx.x == 0) {
           w.done[r] = 1;
@@ -445,20 +583,18 @@ __global__ void __launch_bounds__(kThreads) k_iface_solve(DeviceTables t, Worksp
         }
         continue;
       }
-      // z = D r (slab padded), y = M_s^{-1} z, x += D y
+      // y = Shat^{-1} z by block cyclic reduction, in shared memory
       T *v = reinterpret_cast<T *>(smraw);
       T *tmp = v + ri.nslab * ri.bmax;
       const int np = ri.nslab * ri.bmax;
+      T *gv = vec + ri.vec_off;
       for (int p = threadIdx.x; p < np; p += blockDim.x) {
         const int u = pos2unk[ri.vec_off + p];
-        v[p] = (u >= 0 && u != ri.pin) ? static_cast<T>(w.dscale[u] * w.r[u]) : T(0);
+        v[p] = (u >= 0 && u != ri.pin) ? gv[p] : T(0);
       }
       __syncthreads();
       bcr_solve_cta(t, w, ri, v, tmp);
-      for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        const int u = pos2unk[ri.vec_off + p];
-        if (u >= 0 && u != ri.pin) w.x[u] += w.dscale[u] * static_cast<double>(v[p]);
-      }
+      for (int p = threadIdx.x; p < np; p += blockDim.x) gv[p] = v[p];
       __syncthreads();
     }
     ++nsolve;
@@ -481,13 +617,13 @@ cudaError_t launch_iface_assemble(const DeviceTables &t, const Workspace &w, int
   if ((e = cudaMemsetAsync(w.slabC, 0, slab_elems * esz, st)) != cudaSuccess) return e;
   const int thr = 256;
   const int nb1 = static_cast<int>((npos + thr - 1) / thr);
-  const int nb2 = (t.nunk + thr - 1) / thr;
+  k_iface_prep<<<t.niface, 32, 0, st>>>(t, w);
   if (prec == MRCM_PREC_FP64) {
-    k_iface_diag<double><<<nb1, thr, 0, st>>>(t, w, pos2unk, npos, pos_real_off, t.n_real);
-    k_iface_assemble<double><<<nb2, thr, 0, st>>>(t, w);
+    k_iface_assemble<double><<<t.niface, 64, 0, st>>>(t, w);
+    k_iface_pad<double><<<nb1, thr, 0, st>>>(t, w, pos2unk, npos, pos_real_off, t.n_real);
   } else {
-    k_iface_diag<float><<<nb1, thr, 0, st>>>(t, w, pos2unk, npos, pos_real_off, t.n_real);
-    k_iface_assemble<float><<<nb2, thr, 0, st>>>(t, w);
+    k_iface_assemble<float><<<t.niface, 64, 0, st>>>(t, w);
+    k_iface_pad<float><<<nb1, thr, 0, st>>>(t, w, pos2unk, npos, pos_real_off, t.n_real);
   }
   return cudaGetLastError();
 }
@@ -546,6 +682,7 @@ cudaError_t launch_iface_solve(const DeviceTables &t, const Workspace &w, int pr
                                int max_vec, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(w.x, 0, sizeof(double) * t.nunk, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(w.dstat + 2, 0, sizeof(double) * t.n_real, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(w.done, 0, sizeof(int) * (t.n_real + 1), st)) != cudaSuccess) return e;
   if (prec == MRCM_PREC_FP64)
     return iface_solve_t<double>(t, w, pos2unk, tol, max_solves, grid,

@@ -33,6 +33,7 @@ struct mrcm_ctx {
   std::vector<int> unk_iface, unk_slabpos, pos2unk;
   std::vector<int64_t> pos_real_off;
   int64_t slab_elems = 0, xy_elems = 0, npos = 0, basis_elems = 0, g_elems = 0, gam_elems = 0;
+  int64_t tsc_elems = 0;
   int max_vec = 0;
   int nunk = 0;
   // device
@@ -126,7 +127,7 @@ static mrcm_status build_tables(mrcm_ctx *c) {
   const double h = d.ly / d.ny;
   int nsub_tot = 0, nif_tot = 0, unk_tot = 0;
   int64_t alpha_off = 0, gam_off = 0, slab_off = 0, xy_off = 0, vec_off = 0;
-  int64_t basis_off = 0, g_off = 0;
+  int64_t basis_off = 0, g_off = 0, tsc_off = 0;
   int col_off = 0;
   for (int r = 0; r < d.n_real; ++r) {
     RealInfo ri{};
@@ -174,6 +175,8 @@ static mrcm_status build_tables(mrcm_ctx *c) {
       alpha_off += S;
       fi.gam_off = gam_off;
       gam_off += 2 * S;
+      fi.tsc_off = tsc_off;
+      tsc_off += static_cast<int64_t>(fi.nU + fi.nP) * (fi.nU + fi.nP);
       c->iface.push_back(fi);
     }
     ri.nunk = unk_tot - ri.unk0;
@@ -288,6 +291,7 @@ static mrcm_status build_tables(mrcm_ctx *c) {
   c->basis_elems = basis_off;
   c->g_elems = g_off;
   c->gam_elems = gam_off;
+  c->tsc_elems = tsc_off;
   return MRCM_OK;
 }
 
@@ -369,8 +373,10 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                o_sC = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
                o_X = A.take<char>((c->xy_elems ? c->xy_elems : 1) * esz),
                o_Y = A.take<char>((c->xy_elems ? c->xy_elems : 1) * esz),
-               o_ds = A.take<double>(nunk ? nunk : 1), o_f = A.take<double>(nunk ? nunk : 1),
-               o_x = A.take<double>(nunk ? nunk : 1), o_r = A.take<double>(nunk ? nunk : 1),
+               o_ds = A.take<double>(c->tsc_elems ? c->tsc_elems : 1),
+               o_f = A.take<double>(nunk ? nunk : 1), o_x = A.take<double>(nunk ? nunk : 1),
+               o_r = A.take<double>(nif ? nif : 1),
+               o_vec = A.take<char>((c->npos ? c->npos : 1) * esz),
                o_ps = A.take<double>(nsub), o_gt = A.take<double>(c->gam_elems ? c->gam_elems : 1),
                o_st = A.take<int>(4), o_dst = A.take<double>(2 + 2 * d.n_real),
                o_done = A.take<int>(d.n_real + 1);
@@ -440,11 +446,11 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   w.slabC = base + o_sC;
   w.X = base + o_X;
   w.Y = base + o_Y;
-  w.dscale = reinterpret_cast<double *>(base + o_ds);
+  w.tsc = reinterpret_cast<double *>(base + o_ds);
   w.f = reinterpret_cast<double *>(base + o_f);
   w.x = reinterpret_cast<double *>(base + o_x);
   w.r = reinterpret_cast<double *>(base + o_r);
-  w.vec = nullptr;
+  w.vec = base + o_vec;
   w.psum = reinterpret_cast<double *>(base + o_ps);
   w.gamma_tmp = reinterpret_cast<double *>(base + o_gt);
   w.status = reinterpret_cast<int *>(base + o_st);
@@ -546,12 +552,12 @@ mrcm_status mrcm_solve_interface(mrcm_ctx *ctx, mrcm_info *info) {
                                           ctx->d_pos2unk, ctx->npos, ctx->d_pos_real_off,
                                           ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "interface assembly launch");
-    ctx->launches += 2;
+    ctx->launches += 3;
     int nl = 0;
     e = launch_bcr_factor(ctx->t, ctx->w, ctx->prec, ctx->real.data(), &nl, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "interface factor launch");
     ctx->launches += nl;
-    const int max_solves = 1 + (ctx->prec == MRCM_PREC_FP64 ? 0 : ctx->d.iface_ir_max);
+    const int max_solves = 1 + ctx->d.iface_ir_max;
     e = launch_iface_solve(ctx->t, ctx->w, ctx->prec, ctx->d_pos2unk, ctx->d.iface_tol,
                            max_solves, ctx->solve_grid, ctx->max_vec, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "interface solve launch");
@@ -585,7 +591,9 @@ int64_t mrcm_num_interface_unknowns(const mrcm_ctx *ctx) { return ctx ? ctx->nun
 int64_t mrcm_num_gamma_values(const mrcm_ctx *ctx) { return ctx ? ctx->gam_elems : 0; }
 
 mrcm_status mrcm_copy_interface_solution(mrcm_ctx *ctx, double *d_x) {
-  if (!ctx || !d_x) return MRCM_EINVAL;
+  if (!ctx) return MRCM_EINVAL;
+  if (ctx->nunk == 0) return MRCM_OK;
+  if (!d_x) return fail(ctx, MRCM_EINVAL, "d_x must be a device pointer");
   if (ctx->state < 3) return fail(ctx, MRCM_EINVAL, "no interface solution yet");
   cudaError_t e = cudaMemcpyAsync(d_x, ctx->w.x, sizeof(double) * ctx->nunk,
                                   cudaMemcpyDeviceToDevice, ctx->stream);

@@ -34,6 +34,7 @@ struct IfaceInfo {
   int slab, pos;     // BCR slab index (within realisation), row offset in slab
   int64_t alpha_off; // offset into the per-face alpha array (s values)
   int64_t gam_off;   // offset into the one-sided velocity output (2*s values)
+  int64_t tsc_off;   // offset into the congruence scaling blocks (m*m values)
 };
 
 // Column c of a subdomain: global unknown it multiplies (-1: particular),
@@ -91,11 +92,11 @@ struct Workspace {
   double *G;          // local interface contributions (FP64)
   void *slabB, *slabA, *slabC;  // [per real][nslab][bmax*bmax], prec-typed
   void *X, *Y;        // BCR forward multipliers, prec-typed
-  double *dscale;     // [nunk] symmetric scaling of the interface matrix
+  double *tsc;        // per interface m x m congruence scaling T_g (FP64)
   double *f;          // [nunk] interface RHS
   double *x;          // [nunk] interface solution
-  double *r;          // [nunk] interface residual
-  void *vec;          // [per real][nslab*bmax] BCR work vector, prec-typed
+  double *r;          // [niface] per-interface squared residual norms
+  void *vec;          // [per real][nslab*bmax] BCR right-hand side / solution, prec-typed
   double *psum;       // [nsub] per-subdomain pressure sums
   double *gamma_tmp;  // one-sided velocities scratch (if user passes none)
   int *status;        // [4] flags, local sweeps max, iface sweeps, spare

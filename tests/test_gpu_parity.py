@@ -95,16 +95,19 @@ def test_multi_realisation_ragged_spaces(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_full_spaces_reproduce_fine_grid(prec):
-    """n_U = n_P = s: the CUDA path equals the fine-grid two-point solve."""
+@pytest.mark.parametrize("shape", [(32, 16), (16, 48)])
+def test_full_spaces_reproduce_fine_grid(prec, shape):
+    """n_U = n_P = s: the CUDA path equals the fine-grid two-point solve
+    (slabs of one interface: 32 unknowns)."""
     O, mrcm, W = _mods()
+    nx, ny = shape
     rng = np.random.default_rng(3)
-    K = np.exp(rng.standard_normal((32, 48)))
-    prob = W.make_problem(48, 32, 16, K, bc=W.bc_left_right(48, 32), n_u=16, n_p=16)
+    K = np.exp(rng.standard_normal((ny, nx)))
+    prob = W.make_problem(nx, ny, 16, K, bc=W.bc_left_right(nx, ny), n_u=16, n_p=16)
     got = _run(prob, prec)
     fine = O.fine_solve(prob)
     ep, eu = O.errors(got, fine)
-    assert ep <= TOL and eu <= TOL
+    assert ep <= TOL and eu <= TOL, (ep, eu, got["info"])
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -233,8 +236,8 @@ def test_calling_order_enforced():
 
 
 def test_refinement_limit_reports_stall():
-    """With zero interface refinement sweeps the FP32 path cannot reach
-    1e-13 on the 1e6-contrast workload: the status says so (no hang)."""
+    """With no interface refinement sweep the FP32 path cannot reach 1e-13
+    on the 1e6-contrast workload: the status says so (no hang)."""
     O, mrcm, W = _mods()
     prob = W.config2()
     s = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=1, iface_ir_max=0))
