@@ -20,6 +20,7 @@
 // residual reaches the tolerance.
 #include "mrcm_internal.h"
 #include "../../include/mrcm.h"
+#include "iface_common.cuh"
 
 #include <cooperative_groups.h>
 #include <cstdint>
@@ -33,116 +34,12 @@ namespace {
 constexpr int kBmax = 64;        // largest padded slab handled in shared memory
 constexpr int kThreads = 512;
 
-__device__ __forceinline__ void atomic_max_pos_double(double *addr, double v) {
-  if (!(v >= 0.0)) v = 1e300;
-  atomicMax(reinterpret_cast<unsigned long long *>(addr),
-            static_cast<unsigned long long>(__double_as_longlong(v)));
-}
-
-// G rows of interface fi on side L and R, and the column of its own unknown i
-struct RowRef {
-  const double *gL, *gR;   // pointers to the two G rows
-  int ncL, ncR;
-  int colL, colR;          // column of the row's own unknown (diagonal)
-  int offL, offR;          // col table offsets
-};
-
-__device__ __forceinline__ RowRef row_ref(const DeviceTables &t, const Workspace &w,
-                                          const IfaceInfo &fi, int i) {
-  const SubInfo &L = t.sub[fi.L];
-  const SubInfo &R = t.sub[fi.R];
-  const int eL = fi.kind == 0 ? kEdgeE : kEdgeN;
-  const int eR = fi.kind == 0 ? kEdgeW : kEdgeS;
-  RowRef rr;
-  rr.ncL = L.ncols;
-  rr.ncR = R.ncols;
-  rr.gL = w.G + L.g_off + static_cast<int64_t>(L.edge_row[eL] + i) * L.ncols;
-  rr.gR = w.G + R.g_off + static_cast<int64_t>(R.edge_row[eR] + i) * R.ncols;
-  rr.colL = L.edge_col[eL] + i;
-  rr.colR = R.edge_col[eR] + i;
-  rr.offL = L.col_off;
-  rr.offR = R.col_off;
-  return rr;
-}
-
-// (1) per-interface congruence scaling.  With the flux-continuity (P) rows
-// negated the interface matrix is symmetric quasi-definite: S = [-A B; B^T C]
-// on every interface block, A and C SPD.  T = blockdiag(L_A^{-1}, L_C^{-1})
-// from the Cholesky factors of the interface's own A and C makes the
-// diagonal blocks of T S T^T equal to -I and +I, which removes the
-// contrast-driven spread of the interface matrix.  Also writes f.
-constexpr int kMmax = 32;
+// (1) per-interface congruence scaling (see iface_common.cuh), one warp per
+// interface.
 __global__ void __launch_bounds__(32) k_iface_prep(DeviceTables t, Workspace w) {
-  const int g = blockIdx.x;
-  const IfaceInfo fi = t.iface[g];
-  const RealInfo &ri = t.real[fi.r];
-  const int m = fi.nU + fi.nP;
-  __shared__ double Sd[kMmax][kMmax + 1];
-  __shared__ double Xd[kMmax][kMmax + 1];
-  __shared__ int bad;
-  const int i = threadIdx.x;
-  if (i == 0) bad = 0;
-  if (i < m) {
-    const RowRef rr = row_ref(t, w, fi, i);
-    const bool pin_i = (fi.unk + i == ri.pin);
-    for (int j = 0; j < m; ++j) {
-      const bool pin_j = (fi.unk + j == ri.pin);
-      double v = rr.gL[rr.colL - i + j] + rr.gR[rr.colR - i + j];
-      // A = -M_UU, C = -M_PP (both SPD); U-P coupling not needed here
-      const bool same = (i < fi.nU) == (j < fi.nU);
-      v = same ? -v : 0.0;
-      if (pin_i || pin_j) v = (i == j) ? 1.0 : 0.0;
-      Sd[i][j] = v;
-    }
-    w.f[fi.unk + i] = pin_i ? 0.0 : -(rr.gL[0] + rr.gR[0]);
-  }
-  __syncwarp();
-  // Cholesky of the two diagonal sub-blocks in place (lower), row i per lane
-  for (int k = 0; k < m; ++k) {
-    const int lo = k < fi.nU ? 0 : fi.nU;      // first index of k's sub-block
-    const int hi = k < fi.nU ? fi.nU : m;
-    if (i == k) {
-      double d = Sd[k][k];
-      for (int q = lo; q < k; ++q) d -= Sd[k][q] * Sd[k][q];
-      if (!(d > 0.0) || !isfinite(d)) {
-        bad = 1;
-        d = 1.0;
-      }
-      Sd[k][k] = sqrt(d);
-    }
-    __syncwarp();
-    if (i > k && i < hi) {
-      double v = Sd[i][k];
-      for (int q = lo; q < k; ++q) v -= Sd[i][q] * Sd[k][q];
-      Sd[i][k] = v / Sd[k][k];
-    }
-    __syncwarp();
-  }
-  // X = L^{-1} (block lower triangular), column j per lane
-  if (i < m) {
-    const int lo = i < fi.nU ? 0 : fi.nU;
-    const int hi = i < fi.nU ? fi.nU : m;
-    for (int r = 0; r < m; ++r) Xd[r][i] = 0.0;
-    for (int r = lo; r < hi; ++r) {
-      if (r < i) continue;
-      double v = (r == i) ? 1.0 : 0.0;
-      for (int q = i; q < r; ++q) v -= Sd[r][q] * Xd[q][i];
-      Xd[r][i] = v / Sd[r][r];
-    }
-  }
-  __syncwarp();
-  double *T = w.tsc + fi.tsc_off;
-  if (i < m) {
-    if (bad) {
-      // not quasi-definite: fall back to diagonal scaling
-      const RowRef rr = row_ref(t, w, fi, i);
-      const double dg = fabs(rr.gL[rr.colL] + rr.gR[rr.colR]);
-      for (int j = 0; j < m; ++j) T[i * m + j] = (i == j) ? (dg > 0.0 ? 1.0 / sqrt(dg) : 1.0) : 0.0;
-    } else {
-      for (int j = 0; j < m; ++j) T[i * m + j] = Xd[i][j];
-    }
-  }
-  if (i == 0 && bad) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
+  __shared__ double Sd[kMmax * (kMmax + 1)];
+  __shared__ double Xd[kMmax * (kMmax + 1)];
+  iface_scale_warp(t, w, blockIdx.x, Sd, Xd, kMmax + 1);
 }
 
 // (2) identity on padded slab positions and on the pinned unknown
@@ -237,242 +134,262 @@ __global__ void __launch_bounds__(64) k_iface_assemble(DeviceTables t, Workspace
 }
 
 // ------------------------------------------------------------ BCR factor
+// Slab blocks live in global memory as compact b x b row-major matrices and
+// in shared memory as 64 x 64 tiles (zero outside b x b).  512 threads.
+constexpr int kTile = 64;
+
 template <typename T>
-__device__ void smem_gj_inverse(T *M, int b, int *bad) {
-  // in-place Gauss-Jordan inverse, no pivoting (quasi-definite pivots)
-  __shared__ T colk[kBmax], rowk[kBmax];
-  __shared__ T piv;
+__device__ void tile_load(T *dst, const T *src, int b) {
+  for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+    const int i = e / kTile, j = e % kTile;
+    dst[e] = (i < b && j < b) ? src[i * b + j] : T(0);
+  }
+}
+template <typename T>
+__device__ void tile_store(T *dst, const T *src, int b, T scale = T(1)) {
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e / b, j = e % b;
+    dst[e] = scale * src[i * kTile + j];
+  }
+}
+template <typename T>
+__device__ void tile_zero_global(T *dst, int b) {
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) dst[e] = T(0);
+}
+
+// In-place Gauss-Jordan inverse of the b x b tile M, no pivoting (the
+// pivots of the scaled quasi-definite matrix are bounded away from zero).
+// Thread t keeps column j = t % 64, rows i = t/64 + 8q (q < 8) in registers;
+// only the pivot row and column go through shared memory (double buffer).
+template <typename T>
+__device__ void tile_gj_inverse(T *M, int b, int *bad) {
+  __shared__ T colk[2][kTile], rowk[2][kTile];
+  const int t = threadIdx.x, j = t & (kTile - 1), rg = t >> 6;
+  T R[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) R[q] = M[(rg + 8 * q) * kTile + j];
+  __syncthreads();
   for (int k = 0; k < b; ++k) {
-    for (int i = threadIdx.x; i < b; i += blockDim.x) {
-      colk[i] = M[i * b + k];
-      rowk[i] = M[k * b + i];
+    const int buf = k & 1;
+    if (j == k) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) colk[buf][rg + 8 * q] = R[q];
     }
-    if (threadIdx.x == 0) {
-      piv = M[k * b + k];
-      if (!(piv != T(0)) || !isfinite(static_cast<double>(piv))) *bad = 1;
+    if (rg == (k & 7)) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q == (k >> 3)) rowk[buf][j] = R[q];
     }
     __syncthreads();
+    const T piv = rowk[buf][k];
+    if (t == 0 && (!(piv != T(0)) || !isfinite(static_cast<double>(piv)))) *bad = 1;
     const T ip = T(1) / piv;
-    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-      const int i = e / b, j = e % b;
-      T nv;
-      if (i == k && j == k) nv = ip;
-      else if (i == k) nv = rowk[j] * ip;
-      else if (j == k) nv = -colk[i] * ip;
-      else nv = M[e] - colk[i] * rowk[j] * ip;
-      M[e] = nv;
+    const T rj = rowk[buf][j] * ip;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = rg + 8 * q;
+      const T ci = colk[buf][i];
+      if (i == k) R[q] = (j == k) ? ip : rj;
+      else if (j == k) R[q] = -ci * ip;
+      else R[q] -= ci * rj;
     }
-    __syncthreads();
   }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) M[(rg + 8 * q) * kTile + j] = R[q];
+  __syncthreads();
 }
 
-// C = beta*C + alpha * A B, all b x b row-major in shared memory; 4x4
-// register tiles per thread.
+// C = alpha * A B (+ C if acc), 64 x 64 tiles, k < b.  Thread t owns rows
+// 4*(t/32)..+3 and columns 2*(t%32)..+1.
 template <typename T>
-__device__ void smem_gemm(T *C, const T *A, const T *B, int b, T alpha, bool accumulate) {
-  const int nt = (b + 3) / 4;
-  for (int tile = threadIdx.x; tile < nt * nt; tile += blockDim.x) {
-    const int i0 = (tile / nt) * 4, j0 = (tile % nt) * 4;
-    T acc[4][4];
+__device__ void tile_gemm(T *C, const T *A, const T *B, int b, T alpha, bool acc) {
+  const int t = threadIdx.x, jp = t & 31, iq = t >> 5;
+  const int i0 = 4 * iq, j0 = 2 * jp;
+  T c[4][2];
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < 4; ++p) c[p][0] = c[p][1] = T(0);
+  for (int k = 0; k < b; ++k) {
+    const T b0 = B[k * kTile + j0], b1 = B[k * kTile + j0 + 1];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
-    for (int k = 0; k < b; ++k) {
-      T av[4], bv[4];
-#pragma unroll
-      for (int p = 0; p < 4; ++p) av[p] = (i0 + p < b) ? A[(i0 + p) * b + k] : T(0);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) bv[q] = (j0 + q < b) ? B[k * b + j0 + q] : T(0);
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] += av[p] * bv[q];
+    for (int p = 0; p < 4; ++p) {
+      const T a = A[(i0 + p) * kTile + k];
+      c[p][0] += a * b0;
+      c[p][1] += a * b1;
     }
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (i0 + p < b && j0 + q < b) {
-          T *c = C + (i0 + p) * b + j0 + q;
-          *c = accumulate ? *c + alpha * acc[p][q] : alpha * acc[p][q];
-        }
-      }
   }
+  __syncthreads();   // C may alias nothing, but callers reuse A/B tiles next
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    T *cr = C + (i0 + p) * kTile + j0;
+    cr[0] = acc ? cr[0] + alpha * c[p][0] : alpha * c[p][0];
+    cr[1] = acc ? cr[1] + alpha * c[p][1] : alpha * c[p][1];
+  }
+  __syncthreads();
 }
 
+// One reduction level: every surviving slab k = 2*stride*i eliminates its
+// odd neighbours l = k - stride and r = k + stride:
+//   X = A_k B_l^{-1},  Y = C_k B_r^{-1}
+//   B_k -= X C_l + Y A_r,  A_k <- -X A_l,  C_k <- -Y C_r.
+// The CTA of k also writes B_r^{-1} (each odd slab has exactly one left
+// survivor at its level).  stride = 0: invert the root slab 0.
 template <typename T>
-__device__ void load_blk(T *dst, const T *src, int n) {
-  for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
-}
-template <typename T>
-__device__ void store_blk(T *dst, const T *src, int n) {
-  for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
-}
-
-// invert the pivot blocks of the slabs eliminated at this level
-// (k = stride*(2i+1)); with stride = 0 inverts slab 0 (the root).
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_bcr_inv(DeviceTables t, Workspace w, int stride) {
+__global__ void __launch_bounds__(kThreads) k_bcr_level(DeviceTables t, Workspace w, int stride,
+                                                       int lev) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  T *M = reinterpret_cast<T *>(smraw);
   __shared__ int bad;
   const RealInfo ri = t.real[blockIdx.y];
-  const int k = stride == 0 ? (blockIdx.x == 0 ? 0 : ri.nslab) : stride * (2 * blockIdx.x + 1);
-  if (k >= ri.nslab) return;
-  const int b = ri.bmax;
+  const int K = ri.nslab, b = ri.bmax;
   const int64_t bb = static_cast<int64_t>(b) * b;
-  T *B = static_cast<T *>(w.slabB) + ri.slab_off + k * bb;
-  if (threadIdx.x == 0) bad = 0;
-  load_blk(M, B, static_cast<int>(bb));
-  __syncthreads();
-  smem_gj_inverse(M, b, &bad);
-  store_blk(B, M, static_cast<int>(bb));
-  if (threadIdx.x == 0 && bad) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
-}
-
-// eliminate the odd neighbours of the surviving slabs k = 2*stride*i
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_bcr_update(DeviceTables t, Workspace w, int stride,
-                                                        int lev) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const RealInfo ri = t.real[blockIdx.y];
-  const int k = 2 * stride * blockIdx.x;
-  if (k >= ri.nslab) return;
-  const int b = ri.bmax;
-  const int bb = b * b;
-  T *M1 = reinterpret_cast<T *>(smraw);
-  T *M2 = M1 + bb;
-  T *M3 = M2 + bb;
-  T *M4 = M3 + bb;
   T *Bs = static_cast<T *>(w.slabB) + ri.slab_off;
   T *As = static_cast<T *>(w.slabA) + ri.slab_off;
   T *Cs = static_cast<T *>(w.slabC) + ri.slab_off;
-  T *X = static_cast<T *>(w.X) + ri.xy_off + (static_cast<int64_t>(lev) * ri.nslab + k) * bb;
-  T *Y = static_cast<T *>(w.Y) + ri.xy_off + (static_cast<int64_t>(lev) * ri.nslab + k) * bb;
-  const int l = k - stride, rt = k + stride;
-  load_blk(M4, Bs + static_cast<int64_t>(k) * bb, bb);
-  if (l >= 0) {
-    // X = A_k Binv_l ; B_k -= X C_l ; A_k <- -X A_l
-    load_blk(M1, As + static_cast<int64_t>(k) * bb, bb);
-    load_blk(M2, Bs + static_cast<int64_t>(l) * bb, bb);
+  T *Is = static_cast<T *>(w.slabI) + ri.slab_off;
+  T *tl = reinterpret_cast<T *>(smraw);
+  T *tr = tl + kTile * kTile;
+  T *tk = tr + kTile * kTile;
+  T *tx = tk + kTile * kTile;
+  T *tm = tx + kTile * kTile;
+  if (threadIdx.x == 0) bad = 0;
+  if (stride == 0) {
+    if (blockIdx.x != 0) return;
+    tile_load(tk, Bs, b);
     __syncthreads();
-    smem_gemm(M3, M1, M2, b, T(1), false);
-    __syncthreads();
-    store_blk(X, M3, bb);
-    load_blk(M1, Cs + static_cast<int64_t>(l) * bb, bb);
-    __syncthreads();
-    smem_gemm(M4, M3, M1, b, T(-1), true);
-    __syncthreads();
-    load_blk(M1, As + static_cast<int64_t>(l) * bb, bb);
-    __syncthreads();
-    smem_gemm(M2, M3, M1, b, T(-1), false);
-    __syncthreads();
-    store_blk(As + static_cast<int64_t>(k) * bb, M2, bb);
-    __syncthreads();
-  } else {
-    for (int e = threadIdx.x; e < bb; e += blockDim.x) X[e] = T(0);
+    tile_gj_inverse(tk, b, &bad);
+    tile_store(Is, tk, b);
+    if (threadIdx.x == 0 && bad) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
+    return;
   }
-  if (rt < ri.nslab) {
-    // Y = C_k Binv_rt ; B_k -= Y A_rt ; C_k <- -Y C_rt
-    load_blk(M1, Cs + static_cast<int64_t>(k) * bb, bb);
-    load_blk(M2, Bs + static_cast<int64_t>(rt) * bb, bb);
-    __syncthreads();
-    smem_gemm(M3, M1, M2, b, T(1), false);
-    __syncthreads();
-    store_blk(Y, M3, bb);
-    load_blk(M1, As + static_cast<int64_t>(rt) * bb, bb);
-    __syncthreads();
-    smem_gemm(M4, M3, M1, b, T(-1), true);
-    __syncthreads();
-    load_blk(M1, Cs + static_cast<int64_t>(rt) * bb, bb);
-    __syncthreads();
-    smem_gemm(M2, M3, M1, b, T(-1), false);
-    __syncthreads();
-    store_blk(Cs + static_cast<int64_t>(k) * bb, M2, bb);
-    __syncthreads();
-  } else {
-    for (int e = threadIdx.x; e < bb; e += blockDim.x) Y[e] = T(0);
-  }
+  const int k = 2 * stride * blockIdx.x;
+  if (k >= K) return;
+  const int l = k - stride, r = k + stride;
+  T *X = static_cast<T *>(w.X) + ri.xy_off + (static_cast<int64_t>(lev) * K + k) * bb;
+  T *Y = static_cast<T *>(w.Y) + ri.xy_off + (static_cast<int64_t>(lev) * K + k) * bb;
+  tile_load(tk, Bs + k * bb, b);
+  if (l >= 0) tile_load(tl, Bs + l * bb, b);
+  if (r < K) tile_load(tr, Bs + r * bb, b);
   __syncthreads();
-  store_blk(Bs + static_cast<int64_t>(k) * bb, M4, bb);
+  if (l >= 0) tile_gj_inverse(tl, b, &bad);
+  if (r < K) {
+    tile_gj_inverse(tr, b, &bad);
+    tile_store(Is + r * bb, tr, b);
+  }
+  if (l >= 0) {
+    tile_load(tm, As + k * bb, b);
+    __syncthreads();
+    tile_gemm(tx, tm, tl, b, T(1), false);          // X
+    tile_store(X, tx, b);
+    tile_load(tm, Cs + l * bb, b);
+    __syncthreads();
+    tile_gemm(tk, tx, tm, b, T(-1), true);          // B_k -= X C_l
+    tile_load(tm, As + l * bb, b);
+    __syncthreads();
+    tile_gemm(tl, tx, tm, b, T(-1), false);         // -X A_l
+    tile_store(As + k * bb, tl, b);
+  } else {
+    tile_zero_global(X, b);
+  }
+  if (r < K) {
+    tile_load(tm, Cs + k * bb, b);
+    __syncthreads();
+    tile_gemm(tx, tm, tr, b, T(1), false);          // Y
+    tile_store(Y, tx, b);
+    tile_load(tm, As + r * bb, b);
+    __syncthreads();
+    tile_gemm(tk, tx, tm, b, T(-1), true);          // B_k -= Y A_r
+    tile_load(tm, Cs + r * bb, b);
+    __syncthreads();
+    tile_gemm(tr, tx, tm, b, T(-1), false);         // -Y C_r
+    tile_store(Cs + k * bb, tr, b);
+  } else {
+    tile_zero_global(Y, b);
+  }
+  tile_store(Bs + k * bb, tk, b);
+  if (threadIdx.x == 0 && bad) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
 }
 
 // ------------------------------------------------------------ BCR solve
-// y = M_scaled^{-1} z for one realisation, by one CTA; z and y are
-// slab-padded vectors in shared memory (tmp: scratch of the same size).
+// y = Shat^{-1} z for one realisation, by one CTA; v holds z on entry and y
+// on exit (slab-padded, shared memory), tmp is scratch of the same size.
+// One warp per output row: coalesced row reads, shuffle reduction.
 template <typename T>
 __device__ void bcr_solve_cta(const DeviceTables &t, const Workspace &w, const RealInfo &ri, T *v,
                               T *tmp) {
   const int K = ri.nslab, b = ri.bmax;
   const int64_t bb = static_cast<int64_t>(b) * b;
-  const T *Bs = static_cast<const T *>(w.slabB) + ri.slab_off;
   const T *As = static_cast<const T *>(w.slabA) + ri.slab_off;
   const T *Cs = static_cast<const T *>(w.slabC) + ri.slab_off;
+  const T *Is = static_cast<const T *>(w.slabI) + ri.slab_off;
   const T *X = static_cast<const T *>(w.X) + ri.xy_off;
   const T *Y = static_cast<const T *>(w.Y) + ri.xy_off;
-  // forward: v_k -= X_lev(k) v_{k-stride} + Y_lev(k) v_{k+stride}
-  for (int lev = 0, stride = 1; lev < ri.nlev; ++lev, stride <<= 1) {
-    const int nk = (K + 2 * stride - 1) / (2 * stride);
-    for (int o = threadIdx.x; o < nk * b; o += blockDim.x) {
-      const int k = (o / b) * 2 * stride, i = o % b;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int j0 = lane, j1 = lane + 32;
+  // forward: v_k -= X_lev(k) v_{k-s} + Y_lev(k) v_{k+s}, k = 0 mod 2s
+  for (int lev = 0, s = 1; lev < ri.nlev; ++lev, s <<= 1) {
+    const int nk = (K + 2 * s - 1) / (2 * s);
+    for (int o = wid; o < nk * b; o += nw) {
+      const int k = (o / b) * 2 * s, i = o % b;
       T acc = T(0);
-      if (k - stride >= 0) {
-        const T *Xk = X + (static_cast<int64_t>(lev) * K + k) * bb + static_cast<int64_t>(i) * b;
-        const T *vl = v + (k - stride) * b;
-        for (int j = 0; j < b; ++j) acc += Xk[j] * vl[j];
+      if (k - s >= 0) {
+        const T *row = X + (static_cast<int64_t>(lev) * K + k) * bb + static_cast<int64_t>(i) * b;
+        const T *vl = v + (k - s) * b;
+        if (j0 < b) acc += row[j0] * vl[j0];
+        if (j1 < b) acc += row[j1] * vl[j1];
       }
-      if (k + stride < K) {
-        const T *Yk = Y + (static_cast<int64_t>(lev) * K + k) * bb + static_cast<int64_t>(i) * b;
-        const T *vr = v + (k + stride) * b;
-        for (int j = 0; j < b; ++j) acc += Yk[j] * vr[j];
+      if (k + s < K) {
+        const T *row = Y + (static_cast<int64_t>(lev) * K + k) * bb + static_cast<int64_t>(i) * b;
+        const T *vr = v + (k + s) * b;
+        if (j0 < b) acc += row[j0] * vr[j0];
+        if (j1 < b) acc += row[j1] * vr[j1];
       }
-      tmp[k * b + i] = v[k * b + i] - acc;
-    }
-    __syncthreads();
-    for (int o = threadIdx.x; o < nk * b; o += blockDim.x) {
-      const int k = (o / b) * 2 * stride, i = o % b;
-      v[k * b + i] = tmp[k * b + i];
+      acc = warp_sum(acc);
+      if (lane == 0) v[k * b + i] -= acc;
     }
     __syncthreads();
   }
   // root
-  for (int i = threadIdx.x; i < b; i += blockDim.x) {
-    const T *Bi = Bs + static_cast<int64_t>(i) * b;
+  for (int i = wid; i < b; i += nw) {
+    const T *row = Is + static_cast<int64_t>(i) * b;
     T acc = T(0);
-    for (int j = 0; j < b; ++j) acc += Bi[j] * v[j];
-    tmp[i] = acc;
+    if (j0 < b) acc += row[j0] * v[j0];
+    if (j1 < b) acc += row[j1] * v[j1];
+    acc = warp_sum(acc);
+    if (lane == 0) tmp[i] = acc;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < b; i += blockDim.x) v[i] = tmp[i];
   __syncthreads();
-  // backward: x_k = Binv_k (v_k - A_k x_{k-stride} - C_k x_{k+stride})
+  // backward: x_k = B_k^{-1} (v_k - A_k x_{k-s} - C_k x_{k+s}), k odd multiple of s
   for (int lev = ri.nlev - 1; lev >= 0; --lev) {
-    const int stride = 1 << lev;
-    const int nk = (K - stride + 2 * stride - 1) / (2 * stride);
-    for (int o = threadIdx.x; o < nk * b; o += blockDim.x) {
-      const int k = stride + (o / b) * 2 * stride, i = o % b;
-      if (k >= K) continue;
-      T acc = v[k * b + i];
-      const T *Ak = As + k * bb + static_cast<int64_t>(i) * b;
-      const T *xl = v + (k - stride) * b;
-      for (int j = 0; j < b; ++j) acc -= Ak[j] * xl[j];
-      if (k + stride < K) {
-        const T *Ck = Cs + k * bb + static_cast<int64_t>(i) * b;
-        const T *xr = v + (k + stride) * b;
-        for (int j = 0; j < b; ++j) acc -= Ck[j] * xr[j];
+    const int s = 1 << lev;
+    const int nk = (K - s + 2 * s - 1) / (2 * s);
+    for (int o = wid; o < nk * b; o += nw) {
+      const int k = s + (o / b) * 2 * s, i = o % b;
+      const T *ra = As + k * bb + static_cast<int64_t>(i) * b;
+      const T *xl = v + (k - s) * b;
+      T acc = T(0);
+      if (j0 < b) acc += ra[j0] * xl[j0];
+      if (j1 < b) acc += ra[j1] * xl[j1];
+      if (k + s < K) {
+        const T *rc = Cs + k * bb + static_cast<int64_t>(i) * b;
+        const T *xr = v + (k + s) * b;
+        if (j0 < b) acc += rc[j0] * xr[j0];
+        if (j1 < b) acc += rc[j1] * xr[j1];
       }
-      tmp[k * b + i] = acc;
+      acc = warp_sum(acc);
+      if (lane == 0) tmp[k * b + i] = v[k * b + i] - acc;
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < nk * b; o += blockDim.x) {
-      const int k = stride + (o / b) * 2 * stride, i = o % b;
-      if (k >= K) continue;
-      const T *Bk = Bs + k * bb + static_cast<int64_t>(i) * b;
+    for (int o = wid; o < nk * b; o += nw) {
+      const int k = s + (o / b) * 2 * s, i = o % b;
+      const T *ri_ = Is + k * bb + static_cast<int64_t>(i) * b;
       const T *tk = tmp + k * b;
       T acc = T(0);
-      for (int j = 0; j < b; ++j) acc += Bk[j] * tk[j];
-      v[k * b + i] = acc;
+      if (j0 < b) acc += ri_[j0] * tk[j0];
+      if (j1 < b) acc += ri_[j1] * tk[j1];
+      acc = warp_sum(acc);
+      if (lane == 0) v[k * b + i] = acc;
     }
     __syncthreads();
   }
@@ -629,20 +546,15 @@ cudaError_t launch_iface_assemble(const DeviceTables &t, const Workspace &w, int
 }
 
 template <typename T>
-static cudaError_t bcr_factor_t(const DeviceTables &t, const Workspace &w, int maxslab, int bmax,
-                                int nlev, int *nlaunch, cudaStream_t st) {
-  const size_t bb = static_cast<size_t>(bmax) * bmax * sizeof(T);
+static cudaError_t bcr_factor_t(const DeviceTables &t, const Workspace &w, int maxslab, int nlev,
+                                int *nlaunch, cudaStream_t st) {
+  const size_t smem = 5 * kTile * kTile * sizeof(T);
   for (int lev = 0, stride = 1; lev < nlev; ++lev, stride <<= 1) {
-    const int nodd = (maxslab + 2 * stride - 1 - stride) / (2 * stride);
-    if (nodd > 0) {
-      k_bcr_inv<T><<<dim3(nodd, t.n_real), kThreads, bb, st>>>(t, w, stride);
-      ++*nlaunch;
-    }
     const int neven = (maxslab + 2 * stride - 1) / (2 * stride);
-    k_bcr_update<T><<<dim3(neven, t.n_real), kThreads, 4 * bb, st>>>(t, w, stride, lev);
+    k_bcr_level<T><<<dim3(neven, t.n_real), kThreads, smem, st>>>(t, w, stride, lev);
     ++*nlaunch;
   }
-  k_bcr_inv<T><<<dim3(1, t.n_real), kThreads, bb, st>>>(t, w, 0);
+  k_bcr_level<T><<<dim3(1, t.n_real), kThreads, smem, st>>>(t, w, 0, 0);
   ++*nlaunch;
   return cudaGetLastError();
 }
@@ -656,8 +568,8 @@ cudaError_t launch_bcr_factor(const DeviceTables &t, const Workspace &w, int pre
     if (host_real[r].nlev > nlev) nlev = host_real[r].nlev;
   }
   if (bmax > kBmax) return cudaErrorInvalidValue;
-  if (prec == MRCM_PREC_FP64) return bcr_factor_t<double>(t, w, maxslab, bmax, nlev, nlaunch, st);
-  return bcr_factor_t<float>(t, w, maxslab, bmax, nlev, nlaunch, st);
+  if (prec == MRCM_PREC_FP64) return bcr_factor_t<double>(t, w, maxslab, nlev, nlaunch, st);
+  return bcr_factor_t<float>(t, w, maxslab, nlev, nlaunch, st);
 }
 
 template <typename T>
@@ -692,13 +604,10 @@ cudaError_t launch_iface_solve(const DeviceTables &t, const Workspace &w, int pr
 
 template <typename T>
 static cudaError_t init_iface_t(int bmax, int max_vec) {
-  const int bb = bmax * bmax * static_cast<int>(sizeof(T));
+  (void)bmax;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_bcr_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bb)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_bcr_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                4 * bb)) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(k_bcr_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(5 * kTile * kTile * sizeof(T)))) != cudaSuccess)
     return e;
   return cudaFuncSetAttribute(k_iface_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               2 * max_vec * static_cast<int>(sizeof(T)));

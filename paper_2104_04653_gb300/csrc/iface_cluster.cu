@@ -1,0 +1,511 @@
+// Step (d) of the MRCM solve (Eq. "mrc2") in ONE launch per realisation:
+// a thread-block cluster with one CTA per interface slab.
+//
+// The slabs make the interface matrix block tridiagonal (see iface.cu).  CTA
+// k of the cluster owns slab k: it computes the congruence scaling of its
+// interfaces, assembles its scaled diagonal block B_k and couplings A_k,
+// C_k, takes part in the block cyclic reduction (odd slabs invert their
+// pivot block, surviving slabs read the inverses and couplings of their
+// neighbours through distributed shared memory), and keeps its share of the
+// factorisation in shared memory for every refinement sweep.  A sweep is:
+//   A  x_g += T_g^T y_g            (previous correction, FP64 in global memory)
+//   B  r_g = f_g - (M x)_g (FP64), z_g = T_g (sign r_g)
+//   C  y = Shat^{-1} z by the cluster's cyclic reduction
+// with cluster barriers between the phases; realisations are independent
+// clusters, so no grid-wide synchronisation exists.
+#include "mrcm_internal.h"
+#include "../../include/mrcm.h"
+#include "iface_common.cuh"
+
+#include <cooperative_groups.h>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cg = cooperative_groups;
+
+namespace mrcm {
+namespace {
+
+constexpr int kCT = 512;        // threads per CTA
+constexpr int kCMaxB = 64;      // largest slab
+
+// Gauss-Jordan inverse of the b x b row-major (leading dimension b) shared
+// matrix M in place, no pivoting.  Thread t keeps column t%64 and rows
+// t/64 + 8q in registers; pivot row and column go through shared memory.
+template <typename T>
+__device__ void gj_inverse(T *M, int b, int *bad) {
+  __shared__ T colk[2][kCMaxB], rowk[2][kCMaxB];
+  const int t = threadIdx.x, j = t & 63, rg = t >> 6;
+  T R[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int i = rg + 8 * q;
+    R[q] = (i < b && j < b) ? M[i * b + j] : T(0);
+  }
+  __syncthreads();
+  for (int k = 0; k < b; ++k) {
+    const int buf = k & 1;
+    if (j == k) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) colk[buf][rg + 8 * q] = R[q];
+    }
+    if (rg == (k & 7)) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q == (k >> 3)) rowk[buf][j] = R[q];
+    }
+    __syncthreads();
+    const T piv = rowk[buf][k];
+    if (t == 0 && (!(piv != T(0)) || !isfinite(static_cast<double>(piv)))) *bad = 1;
+    const T ip = T(1) / piv;
+    const T rj = rowk[buf][j] * ip;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = rg + 8 * q;
+      const T ci = colk[buf][i];
+      if (i == k) R[q] = (j == k) ? ip : rj;
+      else if (j == k) R[q] = -ci * ip;
+      else R[q] -= ci * rj;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int i = rg + 8 * q;
+    if (i < b && j < b) M[i * b + j] = R[q];
+  }
+  __syncthreads();
+}
+
+// C = alpha A B (+ C), b x b row-major shared matrices; thread owns rows
+// 4*(t/32)..+3, columns 2*(t%32)..+1.  C must not alias A or B.
+template <typename T>
+__device__ void gemm(T *C, const T *A, const T *B, int b, T alpha, bool acc) {
+  const int t = threadIdx.x, j0 = 2 * (t & 31), i0 = 4 * (t >> 5);
+  if (i0 < b && j0 < b) {
+    const bool j1ok = j0 + 1 < b;
+    T c[4][2] = {};
+    for (int k = 0; k < b; ++k) {
+      const T b0 = B[k * b + j0];
+      const T b1 = j1ok ? B[k * b + j0 + 1] : T(0);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const T a = (i0 + p < b) ? A[(i0 + p) * b + k] : T(0);
+        c[p][0] += a * b0;
+        c[p][1] += a * b1;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      if (i0 + p >= b) continue;
+      T *cr = C + (i0 + p) * b + j0;
+      cr[0] = acc ? cr[0] + alpha * c[p][0] : alpha * c[p][0];
+      if (j1ok) cr[1] = acc ? cr[1] + alpha * c[p][1] : alpha * c[p][1];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void copy_in(T *dst, const T *src, int n) {
+  for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
+  __syncthreads();
+}
+
+// y = M x for a b x b shared matrix, warp per row
+template <typename T>
+__device__ void matvec_acc(T *y, const T *M, const T *x, int b, T alpha) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < b; i += nw) {
+    T a = T(0);
+    for (int j = lane; j < b; j += 32) a += M[i * b + j] * x[j];
+    a = warp_sum(a);
+    if (lane == 0) y[i] += alpha * a;
+  }
+}
+
+struct ClusterLayout {
+  int b, nlev, mmax;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kCT, 1)
+    k_iface_cluster(DeviceTables t, Workspace w, const int *slab_if, const int *slab_if_off,
+                    double tol, int max_solves) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int K = static_cast<int>(cluster.num_blocks());
+  const int k = static_cast<int>(cluster.block_rank());
+  const int r = blockIdx.x / K;
+  const RealInfo ri = t.real[r];
+  const int b = ri.bmax, nlev = ri.nlev;
+  const int bb = (b * b + 3) & ~3;   // tile stride (keeps later FP64 arrays aligned)
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = kCT / 32;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *tB = reinterpret_cast<T *>(smraw);
+  T *tA = tB + bb;
+  T *tC = tA + bb;
+  T *tW1 = tC + bb;
+  T *tW2 = tW1 + bb;
+  T *tX = tW2 + bb;             // nlev tiles
+  T *tY = tX + nlev * bb;       // nlev tiles
+  T *v = tY + nlev * bb;        // slab vector (z, then y)
+  T *vr1 = v + kCMaxB;
+  T *vr2 = vr1 + kCMaxB;
+  T *vt = vr2 + kCMaxB;
+  double *rl = reinterpret_cast<double *>(vt + kCMaxB);   // FP64 residual of the slab
+  double *part = rl + kCMaxB;                             // [2] partial sums
+  __shared__ int bad;
+  __shared__ double red[kCT / 32];
+  if (tid == 0) bad = 0;
+
+  const int if0 = slab_if_off[r * K + k], if1 = slab_if_off[r * K + k + 1];
+  const int nif = if1 - if0;
+
+  // ---- scaling of this slab's interfaces (scratch in the tile area)
+  {
+    const int mm = t.mmax;
+    const int ld = mm + 1;
+    const int per = 2 * mm * ld;                          // doubles per warp
+    const int avail = static_cast<int>((static_cast<size_t>(5 + 2 * nlev) * bb * sizeof(T)) /
+                                       (sizeof(double) * per));
+    const int np = avail < nw ? avail : nw;
+    double *scr = reinterpret_cast<double *>(smraw);
+    if (np < 1) {
+      if (tid == 0) atomicOr(&w.status[0], MRCM_FLAG_LAYOUT);
+    } else if (wid < np) {
+      for (int q = wid; q < nif; q += np) {
+        const int g = slab_if[if0 + q];
+        iface_scale_warp(t, w, g, scr + wid * per, scr + wid * per + mm * ld, ld);
+        const IfaceInfo fi = t.iface[g];
+        for (int i = lane; i < fi.nU + fi.nP; i += 32) w.x[fi.unk + i] = 0.0;
+      }
+    }
+  }
+  __threadfence();
+  cluster.sync();
+
+  // ---- assemble the scaled slab blocks: T_g S_{g g'} T_{g'}^T
+  for (int e = tid; e < 3 * bb; e += kCT) tB[e] = T(0);
+  __syncthreads();
+  // pairs (own interface g, neighbour g'): one warp each
+  {
+    const int mm = t.mmax;
+    // per-warp scratch after the first three tiles: S and X blocks (FP64)
+    double *scr = reinterpret_cast<double *>(tW1) + wid * 2 * mm * mm;
+    for (int q = wid; q < nif * 8; q += nw) {
+      const int g = slab_if[if0 + q / 8];
+      const int nbk = q % 8;
+      const IfaceInfo fi = t.iface[g];
+      const SubInfo &L = t.sub[fi.L];
+      const SubInfo &R = t.sub[fi.R];
+      const int gn = nbk < 4 ? L.edge_iface[nbk] : R.edge_iface[nbk - 4];
+      if (gn < 0) continue;
+      bool dup = false;
+      for (int qq = 0; qq < nbk; ++qq)
+        if ((qq < 4 ? L.edge_iface[qq] : R.edge_iface[qq - 4]) == gn) dup = true;
+      if (dup) continue;
+      const IfaceInfo fn = t.iface[gn];
+      const int m = fi.nU + fi.nP, mn = fn.nU + fn.nP;
+      int eL = -1, eR = -1;
+      for (int qq = 0; qq < 4; ++qq) {
+        if (L.edge_iface[qq] == gn) eL = qq;
+        if (R.edge_iface[qq] == gn) eR = qq;
+      }
+      double *Sb = scr, *Xb = scr + mm * mm;
+      for (int e = lane; e < m * mn; e += 32) {
+        const int i = e / mn, j = e % mn;
+        const RowRef rr = row_ref(t, w, fi, i);
+        double val = 0.0;
+        if (eL >= 0) val += rr.gL[L.edge_col[eL] + j];
+        if (eR >= 0) val += rr.gR[R.edge_col[eR] + j];
+        if (i >= fi.nU) val = -val;
+        if (fi.unk + i == ri.pin || fn.unk + j == ri.pin) val = 0.0;
+        Sb[i * mn + j] = val;
+      }
+      __syncwarp();
+      const double *Tg = w.tsc + fi.tsc_off;
+      const double *Tn = w.tsc + fn.tsc_off;
+      for (int e = lane; e < m * mn; e += 32) {
+        const int i = e / mn, j = e % mn;
+        double a = 0.0;
+        for (int qq = 0; qq <= i; ++qq) a += Tg[i * m + qq] * Sb[qq * mn + j];
+        Xb[i * mn + j] = a;
+      }
+      __syncwarp();
+      T *blk = fn.slab == k ? tB : (fn.slab == k - 1 ? tA : tC);
+      if (fn.slab < k - 1 || fn.slab > k + 1) {
+        if (lane == 0) atomicOr(&w.status[0], MRCM_FLAG_LAYOUT);
+        continue;
+      }
+      for (int e = lane; e < m * mn; e += 32) {
+        const int i = e / mn, j = e % mn;
+        double a = 0.0;
+        for (int qq = 0; qq <= j; ++qq) a += Xb[i * mn + qq] * Tn[j * mn + qq];
+        blk[(fi.pos + i) * b + fn.pos + j] = static_cast<T>(a);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // padded positions and the pinned unknown: identity (after the blocks,
+  // whose pinned row and column are zero)
+  {
+    const int *p2u = t.pos2unk + ri.vec_off + static_cast<int64_t>(k) * b;
+    for (int p = tid; p < b; p += kCT) {
+      const int u = p2u[p];
+      if (u < 0 || u == ri.pin) tB[p * b + p] = T(1);
+    }
+  }
+  __syncthreads();
+  cluster.sync();
+
+  // ---- block cyclic reduction
+  for (int lev = 0; lev < nlev; ++lev) {
+    const int s = 1 << lev;
+    if (k % (2 * s) == s) gj_inverse(tB, b, &bad);
+    cluster.sync();
+    if (k % (2 * s) == 0) {
+      const int l = k - s, rt = k + s;
+      T *X = tX + lev * bb;
+      T *Y = tY + lev * bb;
+      if (l >= 0) {
+        copy_in(tW1, cluster.map_shared_rank(tB, l), b * b);         // B_l^{-1}
+        gemm(X, tA, tW1, b, T(1), false);                          // X = A_k B_l^{-1}
+        copy_in(tW2, cluster.map_shared_rank(tC, l), b * b);
+        gemm(tB, X, tW2, b, T(-1), true);                          // B_k -= X C_l
+        copy_in(tW2, cluster.map_shared_rank(tA, l), b * b);
+        gemm(tW1, X, tW2, b, T(-1), false);                        // -X A_l
+        copy_in(tA, tW1, b * b);
+      } else {
+        for (int e = tid; e < b * b; e += kCT) X[e] = T(0);
+      }
+      if (rt < K) {
+        copy_in(tW1, cluster.map_shared_rank(tB, rt), b * b);        // B_r^{-1}
+        gemm(Y, tC, tW1, b, T(1), false);                          // Y = C_k B_r^{-1}
+        copy_in(tW2, cluster.map_shared_rank(tA, rt), b * b);
+        gemm(tB, Y, tW2, b, T(-1), true);                          // B_k -= Y A_r
+        copy_in(tW2, cluster.map_shared_rank(tC, rt), b * b);
+        gemm(tW1, Y, tW2, b, T(-1), false);                        // -Y C_r
+        copy_in(tC, tW1, b * b);
+      } else {
+        for (int e = tid; e < b * b; e += kCT) Y[e] = T(0);
+      }
+    }
+    cluster.sync();
+  }
+  if (k == 0) gj_inverse(tB, b, &bad);
+  if (tid == 0 && bad) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
+  cluster.sync();
+
+  // ---- refinement sweeps
+  // ||f||^2 of the realisation (every CTA computes the same total)
+  double fsq = 0.0;
+  for (int q = wid; q < nif; q += nw) {
+    const IfaceInfo fi = t.iface[slab_if[if0 + q]];
+    double a = 0.0;
+    for (int i = lane; i < fi.nU + fi.nP; i += 32) a += w.f[fi.unk + i] * w.f[fi.unk + i];
+    fsq += warp_sum(a);
+  }
+  if (lane == 0) red[wid] = fsq;
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0;
+    for (int q = 0; q < nw; ++q) a += red[q];
+    part[1] = a;
+  }
+  cluster.sync();
+  double fnorm2 = 0.0;
+  for (int q = 0; q < K; ++q) fnorm2 += *cluster.map_shared_rank(part + 1, q);
+
+  double prev = 1e300, rel = 0.0;
+  int nsolve = 0;
+  for (;;) {
+    // A: x += T^T y for this slab's interfaces
+    if (nsolve > 0) {
+      for (int q = wid; q < nif; q += nw) {
+        const IfaceInfo fi = t.iface[slab_if[if0 + q]];
+        const int m = fi.nU + fi.nP;
+        const double *Tg = w.tsc + fi.tsc_off;
+        for (int i = lane; i < m; i += 32) {
+          double d = 0.0;
+          for (int qq = i; qq < m; ++qq) d += Tg[qq * m + i] * static_cast<double>(v[fi.pos + qq]);
+          w.x[fi.unk + i] += d;
+        }
+      }
+      __threadfence();
+      cluster.sync();
+    }
+    // B: FP64 residual of this slab's rows, warp per row
+    double rsq = 0.0;
+    for (int q = wid; q < b; q += nw) {
+      const int u = t.pos2unk[ri.vec_off + static_cast<int64_t>(k) * b + q];
+      double sacc = 0.0;
+      if (u >= 0 && u != ri.pin) {
+        const IfaceInfo fi = t.iface[t.unk_iface[u]];
+        const RowRef rr = row_ref(t, w, fi, u - fi.unk);
+        for (int c = 1 + lane; c < rr.ncL; c += 32) sacc -= rr.gL[c] * w.x[t.col[rr.offL + c].unk];
+        for (int c = 1 + lane; c < rr.ncR; c += 32) sacc -= rr.gR[c] * w.x[t.col[rr.offR + c].unk];
+        sacc = warp_sum(sacc) + w.f[u];
+      }
+      // flux-continuity (P) rows carry the symmetrising sign
+      bool prow = false;
+      if (u >= 0) {
+        const IfaceInfo fi = t.iface[t.unk_iface[u]];
+        prow = (u - fi.unk) >= fi.nU;
+      }
+      if (lane == 0) rl[q] = prow ? -sacc : sacc;
+      rsq += sacc * sacc;
+    }
+    if (lane == 0) red[wid] = rsq;
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0;
+      for (int q = 0; q < nw; ++q) a += red[q];
+      part[0] = a;
+    }
+    // z = T (sign r) into v
+    for (int q = wid; q < nif; q += nw) {
+      const IfaceInfo fi = t.iface[slab_if[if0 + q]];
+      const int m = fi.nU + fi.nP;
+      const double *Tg = w.tsc + fi.tsc_off;
+      for (int i = lane; i < m; i += 32) {
+        double zv = 0.0;
+        for (int qq = 0; qq <= i; ++qq) zv += Tg[i * m + qq] * rl[fi.pos + qq];
+        v[fi.pos + i] = static_cast<T>(zv);
+      }
+    }
+    for (int p = tid; p < b; p += kCT) {
+      const int u = t.pos2unk[ri.vec_off + static_cast<int64_t>(k) * b + p];
+      if (u < 0 || u == ri.pin) v[p] = T(0);
+    }
+    cluster.sync();
+    double rn2 = 0.0;
+    for (int q = 0; q < K; ++q) rn2 += *cluster.map_shared_rank(part, q);
+    rel = fnorm2 > 0.0 ? sqrt(rn2 / fnorm2) : 0.0;
+    const bool stop = (rel <= tol) || (nsolve >= max_solves) || !(rel == rel) ||
+                      (nsolve >= 2 && rel > 0.5 * prev);
+    prev = rel;
+    if (stop) break;
+    // C: y = Shat^{-1} z, cluster-wide cyclic reduction
+    for (int lev = 0; lev < nlev; ++lev) {
+      const int s = 1 << lev;
+      if (k % (2 * s) == 0) {
+        const int l = k - s, rt = k + s;
+        if (l >= 0) copy_in(vr1, cluster.map_shared_rank(v, l), b);
+        if (rt < K) copy_in(vr2, cluster.map_shared_rank(v, rt), b);
+        if (l >= 0) matvec_acc(v, tX + lev * bb, vr1, b, T(-1));
+        __syncthreads();
+        if (rt < K) matvec_acc(v, tY + lev * bb, vr2, b, T(-1));
+      }
+      cluster.sync();
+    }
+    if (k == 0) {
+      copy_in(vr1, v, b);
+      for (int p = tid; p < b; p += kCT) v[p] = T(0);
+      __syncthreads();
+      matvec_acc(v, tB, vr1, b, T(1));
+    }
+    cluster.sync();
+    for (int lev = nlev - 1; lev >= 0; --lev) {
+      const int s = 1 << lev;
+      if (k % (2 * s) == s) {
+        const int l = k - s, rt = k + s;
+        copy_in(vr1, cluster.map_shared_rank(v, l), b);
+        if (rt < K) copy_in(vr2, cluster.map_shared_rank(v, rt), b);
+        copy_in(vt, v, b);
+        matvec_acc(vt, tA, vr1, b, T(-1));
+        __syncthreads();
+        if (rt < K) matvec_acc(vt, tC, vr2, b, T(-1));
+        __syncthreads();
+        for (int p = tid; p < b; p += kCT) v[p] = T(0);
+        __syncthreads();
+        matvec_acc(v, tB, vt, b, T(1));
+      }
+      cluster.sync();
+    }
+    ++nsolve;
+  }
+  if (k == 0 && tid == 0) {
+    w.done[r] = 1;
+    w.dstat[2 + r] = rel;
+    atomic_max_pos_double(&w.dstat[1], rel);
+    atomicMax(&w.status[2], nsolve > 0 ? nsolve - 1 : 0);
+    if (!(rel <= tol)) atomicOr(&w.status[0], MRCM_FLAG_IFACE_STALL);
+  }
+}
+
+template <typename T>
+size_t cluster_smem(int bmax, int nlev) {
+  const size_t bb = (static_cast<size_t>(bmax) * bmax + 3) & ~static_cast<size_t>(3);
+  return (5 + 2 * static_cast<size_t>(nlev)) * bb * sizeof(T) + 4 * kCMaxB * sizeof(T) +
+         (kCMaxB + 2) * sizeof(double) + 16;
+}
+
+}  // namespace
+
+// Can the one-launch cluster path run this problem?  Returns the cluster
+// size (0: no).
+int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int dev) {
+  if (prec != MRCM_PREC_FP32_IR) return 0;
+  if (nslab < 1 || nslab > 16 || bmax > kCMaxB) return 0;
+  const size_t smem = cluster_smem<float>(bmax, nlev);
+  // per-warp assembly scratch must fit behind the first three tiles
+  const size_t scr = static_cast<size_t>(kCT / 32) * 2 * mmax * mmax * sizeof(double);
+  const size_t behind = (2 + 2 * static_cast<size_t>(nlev)) *
+                        ((static_cast<size_t>(bmax) * bmax + 3) & ~static_cast<size_t>(3)) *
+                        sizeof(float);
+  // the scaling scratch of at least one warp must fit in the tile area
+  const size_t tiles = (5 + 2 * static_cast<size_t>(nlev)) *
+                       ((static_cast<size_t>(bmax) * bmax + 3) & ~static_cast<size_t>(3)) *
+                       sizeof(float);
+  if (2 * static_cast<size_t>(mmax) * (mmax + 1) * sizeof(double) > tiles) return 0;
+  if (scr > behind) return 0;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem > static_cast<size_t>(optin)) return 0;
+  if (cudaFuncSetAttribute(k_iface_cluster<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess)
+    return 0;
+  if (nslab > 8 &&
+      cudaFuncSetAttribute(k_iface_cluster<float>,
+                           cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nslab);
+  cfg.blockDim = dim3(kCT);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nslab;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_iface_cluster<float>, &cfg) != cudaSuccess)
+    return 0;
+  cudaGetLastError();
+  return nclusters > 0 ? nslab : 0;
+}
+
+cudaError_t launch_iface_cluster(const DeviceTables &t, const Workspace &w, const int *slab_if,
+                                 const int *slab_if_off, int nslab, int bmax, int nlev,
+                                 double tol, int max_solves, cudaStream_t st) {
+  const size_t smem = cluster_smem<float>(bmax, nlev);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nslab * t.n_real);
+  cfg.blockDim = dim3(kCT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nslab;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_iface_cluster<float>, t, w, slab_if, slab_if_off, tol,
+                            max_solves);
+}
+
+}  // namespace mrcm

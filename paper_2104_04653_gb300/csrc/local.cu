@@ -21,6 +21,9 @@ namespace {
 
 constexpr int kS = 16;      // subdomain edge handled by these kernels
 constexpr int kNC = 12;     // right-hand sides per CTA of the basis kernel
+// per-subdomain coefficient block: tW tE tS tN d kappa [S*S each], then
+// beta on the interface faces [4][S]
+constexpr int kCoefStride = 6 * kS * kS + 4 * kS;
 
 __device__ __forceinline__ void atomic_max_pos_double(double *addr, double v) {
   // valid for v >= 0: IEEE order of non-negative doubles matches their bits
@@ -90,11 +93,22 @@ __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, 
   face_T(t, sb, kap, a, b, T4);
   const double diag = T4[0] + T4[1] + T4[2] + T4[3];
   const double d = 1.0 / sqrt(diag);
-  double *coef = w.coef + static_cast<int64_t>(g) * 6 * N;
+  double *coef = w.coef + static_cast<int64_t>(g) * kCoefStride;
 #pragma unroll
   for (int k = 0; k < 4; ++k) coef[k * N + tid] = T4[k];
   coef[4 * N + tid] = d;
   coef[5 * N + tid] = kc;
+  // beta = alpha H / kappa on the interface faces of the cell (Eq. "beta")
+  {
+    const bool onface[4] = {a == 0, a == S - 1, b == 0, b == S - 1};
+#pragma unroll
+    for (int side = 0; side < 4; ++side) {
+      if (!onface[side] || sb.edge_iface[side] < 0) continue;
+      const int e = (side < 2) ? b : a;
+      const double al = t.alpha[t.iface[sb.edge_iface[side]].alpha_off + e];
+      coef[6 * N + side * S + e] = al * t.H / kc;
+    }
+  }
   dsc[tid] = d;
   tE[tid] = T4[1];
   tN[tid] = T4[3];
@@ -151,7 +165,9 @@ struct BasisSmem {
   T ec[kS * kS];            // scaled row couplings e_j[a]
   T z[kNC * kS * kS];       // scaled residual (input of the solve)
   T v[kNC * kS * kS];       // forward values, then the solution
-  double coef[6 * kS * kS]; // tW tE tS tN d kappa
+  double coef[kCoefStride]; // tW tE tS tN d kappa, edge beta
+  double su[4][kS][kNC];    // one-sided velocity traces on the four edges
+  double sp[4][kS][kNC];    // face-pressure traces
   double x[kNC * kS * kS];  // FP64 iterate
   double bb[kNC * kS * kS]; // FP64 right-hand sides
   double red[kNC][kS * kS / 32];
@@ -206,11 +222,14 @@ template <typename T>
 __device__ void column_sums(BasisSmem<T> &sm, const double *val, int nc, double *out) {
   constexpr int NW = kS * kS / 32;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int c = 0; c < nc; ++c) {
-    double s = val[c];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) sm.red[c][wid] = s;
+  for (int c = 0; c < kNC; ++c) {
+    if (c < nc) {
+      double s = val[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) sm.red[c][wid] = s;
+    }
   }
   __syncthreads();
   if (tid < nc) {
@@ -242,8 +261,8 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   {
     const T *Wg = static_cast<const T *>(w.W) + static_cast<int64_t>(g) * S * N;
     for (int k = tid; k < S * N; k += N) sm.Ws[k] = Wg[k];
-    const double *coef = w.coef + static_cast<int64_t>(g) * 6 * N;
-    for (int k = tid; k < 6 * N; k += N) sm.coef[k] = coef[k];
+    const double *coef = w.coef + static_cast<int64_t>(g) * kCoefStride;
+    for (int k = tid; k < kCoefStride; k += N) sm.coef[k] = coef[k];
     if (tid < nc) sm.col[tid] = t.col[sb.col_off + it.c0 + tid];
   }
   __syncthreads();
@@ -254,10 +273,12 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
 
   // right-hand sides (FP64)
   const double myT[4] = {tWs[tid], tEs[tid], tSs[tid], tNs[tid]};
-  const double kc = ks[tid];
   const int gi = sb.x0 + a, gj = sb.y0 + b;
   double bnl[kNC];
-  for (int c = 0; c < nc; ++c) {
+#pragma unroll
+  for (int c = 0; c < kNC; ++c) {
+    bnl[c] = 0.0;
+    if (c >= nc) continue;
     const ColInfo ci = sm.col[c];
     double val = 0.0;
     if (ci.unk < 0) {
@@ -285,8 +306,7 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
         const double fv = t.fnval[ci.fn * t.fn_stride + e];
         double gval;
         if (ci.is_u) {
-          const double al = t.alpha[t.iface[sb.edge_iface[side]].alpha_off + e];
-          const double beta = al * t.H / kc;
+          const double beta = sm.coef[6 * N + side * S + e];
           const double sigma = (side == kEdgeE || side == kEdgeN) ? 1.0 : -1.0;
           gval = -beta * sigma * fv;
         } else {
@@ -313,7 +333,10 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
     if (sweep >= ir_max) break;
     // FP64 residual r = b - A x
     double rn[kNC];
-    for (int c = 0; c < nc; ++c) {
+#pragma unroll
+    for (int c = 0; c < kNC; ++c) {
+      rn[c] = 0.0;
+      if (c >= nc) continue;
       const double *xc = sm.x + c * N;
       double ax = (myT[0] + myT[1] + myT[2] + myT[3]) * xc[tid];
       if (a > 0) ax -= myT[0] * xc[tid - 1];
@@ -352,10 +375,35 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   double *bas = w.basis + sb.basis_off;
   for (int c = 0; c < nc; ++c) bas[static_cast<int64_t>(it.c0 + c) * N + tid] = sm.x[c * N + tid];
 
-  // interface traces -> rows of G (Eq. "mrc2"):
+  // one-sided traces on every interface edge face, per column:
+  //   u(e) = T_R (p_c - g_e)/h,  p_face(e) = g_e + beta_e u(e)
+  const double inv_h = 1.0 / h;
+  for (int q = tid; q < 4 * S * nc; q += N) {
+    const int side = q / (S * nc), e = (q / nc) % S, c = q % nc;
+    if (sb.edge_iface[side] < 0) continue;
+    int la, lb;
+    if (side == kEdgeW) { la = 0; lb = e; }
+    else if (side == kEdgeE) { la = S - 1; lb = e; }
+    else if (side == kEdgeS) { la = e; lb = 0; }
+    else { la = e; lb = S - 1; }
+    const int cl = lb * S + la;
+    const double TR = sm.coef[side * N + cl];
+    const double beta = sm.coef[6 * N + side * S + e];
+    const ColInfo ci = sm.col[c];
+    double ge = 0.0;
+    if (ci.edge == side) {
+      const double fv = t.fnval[ci.fn * t.fn_stride + e];
+      const double sigma = (side == kEdgeE || side == kEdgeN) ? 1.0 : -1.0;
+      ge = ci.is_u ? -beta * sigma * fv : fv;
+    }
+    const double u = TR * inv_h * (sm.x[c * N + cl] - ge);
+    sm.su[side][e][c] = u;
+    sm.sp[side][e][c] = ge + beta * u;
+  }
+  __syncthreads();
+  // rows of G (Eq. "mrc2"), this side's share:
   //   U rows: sigma * sum_e h phi_k(e) p_face(e)    (pressure continuity)
   //   P rows: sum_e h psi_k(e) u(e)                 (flux continuity)
-  // with u(e) = T_R (p_c - g_e)/h and p_face = g_e + beta_e u(e).
   double *G = w.G + sb.g_off;
   const int nrow = sb.nrows;
   for (int pr = tid; pr < nrow * nc; pr += N) {
@@ -365,36 +413,18 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
                          row < sb.edge_row[side] + t.iface[sb.edge_iface[side]].nU +
                                    t.iface[sb.edge_iface[side]].nP))
       ++side;
-    const IfaceInfo fi = t.iface[sb.edge_iface[side]];
+    const int nU = t.iface[sb.edge_iface[side]].nU;
     const int k = row - sb.edge_row[side];
-    const double sigma = (side == kEdgeE || side == kEdgeN) ? 1.0 : -1.0;
-    const ColInfo ci = sm.col[c];
-    const bool own = (ci.edge == side);
-    const double *tside = sm.coef + side * N;
+    const bool urow = k < nU;
+    const double *fn = t.fnval + (urow ? k : k - nU) * t.fn_stride;
     double acc = 0.0;
-    for (int e = 0; e < S; ++e) {
-      int la, lb;
-      if (side == kEdgeW) { la = 0; lb = e; }
-      else if (side == kEdgeE) { la = S - 1; lb = e; }
-      else if (side == kEdgeS) { la = e; lb = 0; }
-      else { la = e; lb = S - 1; }
-      const int cl = lb * S + la;
-      const double TR = tside[cl];
-      const double beta = t.alpha[fi.alpha_off + e] * t.H / ks[cl];
-      double ge = 0.0;
-      if (own) {
-        const double fv = t.fnval[ci.fn * t.fn_stride + e];
-        ge = ci.is_u ? -beta * sigma * fv : fv;
-      }
-      const double u = TR * (sm.x[c * N + cl] - ge) / h;
-      if (k < fi.nU) {
-        const double pf = ge + beta * u;
-        acc += h * t.fnval[k * t.fn_stride + e] * pf;
-      } else {
-        acc += h * t.fnval[(k - fi.nU) * t.fn_stride + e] * u;
-      }
+    if (urow) {
+      for (int e = 0; e < S; ++e) acc += fn[e] * sm.sp[side][e][c];
+      acc *= (side == kEdgeE || side == kEdgeN) ? h : -h;
+    } else {
+      for (int e = 0; e < S; ++e) acc += fn[e] * sm.su[side][e][c];
+      acc *= h;
     }
-    if (k < fi.nU) acc *= sigma;
     G[static_cast<int64_t>(row) * sb.ncols + it.c0 + c] = acc;
   }
 }

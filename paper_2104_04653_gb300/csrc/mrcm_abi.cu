@@ -8,8 +8,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <string>
 #include <vector>
+#include <algorithm>
 
 #include <cuda_runtime.h>
 
@@ -31,6 +33,10 @@ struct mrcm_ctx {
   std::vector<RealInfo> real;
   std::vector<BasisItem> items;
   std::vector<int> unk_iface, unk_slabpos, pos2unk;
+  std::vector<int> slab_if, slab_if_off;   // interfaces of every (realisation, slab)
+  int mmax = 1, nslab_max = 0, bmax_max = 0, nlev_max = 0;
+  int cluster_k = 0;                       // > 0: one-launch cluster interface path
+  int *d_slab_if = nullptr, *d_slab_if_off = nullptr;
   std::vector<int64_t> pos_real_off;
   int64_t slab_elems = 0, xy_elems = 0, npos = 0, basis_elems = 0, g_elems = 0, gam_elems = 0;
   int64_t tsc_elems = 0;
@@ -244,6 +250,10 @@ static mrcm_status build_tables(mrcm_ctx *c) {
     }
     ri.bmax = 1;
     for (int k = 0; k < ri.nslab; ++k) {
+      c->slab_if_off.push_back(static_cast<int>(c->slab_if.size()));
+      for (int g : slabs[k]) c->slab_if.push_back(g);
+    }
+    for (int k = 0; k < ri.nslab; ++k) {
       int pos = 0;
       for (int g : slabs[k]) {
         IfaceInfo &fi = c->iface[g];
@@ -271,7 +281,14 @@ static mrcm_status build_tables(mrcm_ctx *c) {
     nsub_tot += ri.nsub;
     nif_tot += ri.niface;
   }
+  c->slab_if_off.push_back(static_cast<int>(c->slab_if.size()));
   c->nunk = unk_tot;
+  for (const IfaceInfo &fi : c->iface) c->mmax = std::max(c->mmax, fi.nU + fi.nP);
+  for (const RealInfo &ri : c->real) {
+    c->nslab_max = std::max(c->nslab_max, ri.nslab);
+    c->bmax_max = std::max(c->bmax_max, ri.bmax);
+    c->nlev_max = std::max(c->nlev_max, ri.nlev);
+  }
   c->unk_iface.assign(unk_tot, -1);
   c->unk_slabpos.assign(unk_tot, -1);
   c->pos2unk.assign(vec_off, -1);
@@ -365,12 +382,15 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                o_items = A.take<BasisItem>(c->items.size()),
                o_p2u = A.take<int>(c->npos ? c->npos : 1),
                o_pro = A.take<int64_t>(c->pos_real_off.size()),
-               o_coef = A.take<double>(static_cast<size_t>(nsub) * 6 * N),
+               o_sif = A.take<int>(c->slab_if.size() ? c->slab_if.size() : 1),
+               o_sio = A.take<int>(c->slab_if_off.size()),
+               o_coef = A.take<double>(static_cast<size_t>(nsub) * (6 * N + 4 * S)),
                o_W = A.take<char>(static_cast<size_t>(nsub) * S * N * esz),
                o_basis = A.take<double>(c->basis_elems), o_G = A.take<double>(c->g_elems ? c->g_elems : 1),
                o_sB = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
                o_sA = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
                o_sC = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
+               o_sI = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
                o_X = A.take<char>((c->xy_elems ? c->xy_elems : 1) * esz),
                o_Y = A.take<char>((c->xy_elems ? c->xy_elems : 1) * esz),
                o_ds = A.take<double>(c->tsc_elems ? c->tsc_elems : 1),
@@ -405,6 +425,8 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
       (e = up(o_p2u, c->pos2unk.data(), c->npos * sizeof(int))) != cudaSuccess ||
       (e = up(o_pro, c->pos_real_off.data(), c->pos_real_off.size() * sizeof(int64_t))) !=
           cudaSuccess ||
+      (e = up(o_sif, c->slab_if.data(), c->slab_if.size() * sizeof(int))) != cudaSuccess ||
+      (e = up(o_sio, c->slab_if_off.data(), c->slab_if_off.size() * sizeof(int))) != cudaSuccess ||
       (e = cudaMemset(base + o_st, 0, 4 * sizeof(int))) != cudaSuccess ||
       (e = cudaMemset(base + o_dst, 0, (2 + 2 * d.n_real) * sizeof(double))) != cudaSuccess) {
     cudaFree(c->arena);
@@ -436,6 +458,10 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   c->d_items = reinterpret_cast<BasisItem *>(base + o_items);
   c->d_pos2unk = reinterpret_cast<int *>(base + o_p2u);
   c->d_pos_real_off = reinterpret_cast<int64_t *>(base + o_pro);
+  c->d_slab_if = reinterpret_cast<int *>(base + o_sif);
+  c->d_slab_if_off = reinterpret_cast<int *>(base + o_sio);
+  t.pos2unk = c->d_pos2unk;
+  t.mmax = c->mmax;
   Workspace &w = c->w;
   w.coef = reinterpret_cast<double *>(base + o_coef);
   w.W = base + o_W;
@@ -444,6 +470,7 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   w.slabB = base + o_sB;
   w.slabA = base + o_sA;
   w.slabC = base + o_sC;
+  w.slabI = base + o_sI;
   w.X = base + o_X;
   w.Y = base + o_Y;
   w.tsc = reinterpret_cast<double *>(base + o_ds);
@@ -466,6 +493,9 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     return cuda_fail(nullptr, e, "kernel attributes");
   }
   c->solve_grid = iface_solve_grid(c->prec, c->dev, c->max_vec);
+  if (nunk > 0 && !getenv("MRCM_NO_CLUSTER"))
+    c->cluster_k = iface_cluster_plan(c->prec, c->nslab_max, c->bmax_max, c->nlev_max, c->mmax,
+                                      c->dev);
   if (nunk > 0 && (c->solve_grid < 1 || d.n_real > c->solve_grid)) {
     cudaFree(c->arena);
     delete c;
@@ -547,7 +577,13 @@ static mrcm_status read_info(mrcm_ctx *ctx, mrcm_info *info) {
 mrcm_status mrcm_solve_interface(mrcm_ctx *ctx, mrcm_info *info) {
   if (!ctx) return MRCM_EINVAL;
   if (ctx->state < 2) return fail(ctx, MRCM_EINVAL, "solve_interface before build_basis");
-  if (ctx->nunk > 0) {
+  if (ctx->nunk > 0 && ctx->cluster_k > 0) {
+    cudaError_t e = launch_iface_cluster(ctx->t, ctx->w, ctx->d_slab_if, ctx->d_slab_if_off,
+                                         ctx->cluster_k, ctx->bmax_max, ctx->nlev_max,
+                                         ctx->d.iface_tol, 1 + ctx->d.iface_ir_max, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "interface cluster launch");
+    ctx->launches += 1;
+  } else if (ctx->nunk > 0) {
     cudaError_t e = launch_iface_assemble(ctx->t, ctx->w, ctx->prec, ctx->slab_elems,
                                           ctx->d_pos2unk, ctx->npos, ctx->d_pos_real_off,
                                           ctx->stream);
@@ -558,6 +594,9 @@ mrcm_status mrcm_solve_interface(mrcm_ctx *ctx, mrcm_info *info) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "interface factor launch");
     ctx->launches += nl;
     const int max_solves = 1 + ctx->d.iface_ir_max;
+    if ((e = cudaMemsetAsync(ctx->w.dstat + 2, 0, sizeof(double) * ctx->d.n_real, ctx->stream)) !=
+        cudaSuccess)
+      return cuda_fail(ctx, e, "reset");
     e = launch_iface_solve(ctx->t, ctx->w, ctx->prec, ctx->d_pos2unk, ctx->d.iface_tol,
                            max_solves, ctx->solve_grid, ctx->max_vec, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "interface solve launch");

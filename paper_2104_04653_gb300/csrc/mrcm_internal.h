@@ -77,6 +77,8 @@ struct DeviceTables {
   const RealInfo *real;
   const int *unk_iface;     // global unknown -> interface id
   const int *unk_slabpos;   // global unknown -> slab*bmax + pos (within realisation)
+  const int *pos2unk;       // slab-padded position -> global unknown or -1
+  int mmax;                 // largest nU + nP over all interfaces
   const double *fnval;      // [kMaxFn][s] interface function values at midpoints
   int fn_stride;            // = s
   const double *alpha;      // per face
@@ -86,11 +88,13 @@ struct DeviceTables {
 
 // Workspace (device pointers), owned by the context.
 struct Workspace {
-  double *coef;       // [nsub][5][S*S]: tW, tE, tS, tN, d (=1/sqrt(diag))
+  double *coef;       // [nsub][6*S*S + 4*S]: tW, tE, tS, tN, d (=1/sqrt(diag)), kappa,
+                      // then beta on the four interface edges
   void *W;            // [nsub][S][S][S] inverse Schur blocks, prec-typed
   double *basis;      // basis columns (FP64)
   double *G;          // local interface contributions (FP64)
   void *slabB, *slabA, *slabC;  // [per real][nslab][bmax*bmax], prec-typed
+  void *slabI;        // inverses of the eliminated pivot blocks, same layout
   void *X, *Y;        // BCR forward multipliers, prec-typed
   double *tsc;        // per interface m x m congruence scaling T_g (FP64)
   double *f;          // [nunk] interface RHS
@@ -122,6 +126,10 @@ cudaError_t launch_iface_solve(const DeviceTables &t, const Workspace &w, int pr
 cudaError_t launch_reconstruct(const DeviceTables &t, const Workspace &w, double *p,
                                double *ux, double *uy, double *gam, cudaStream_t st);
 int iface_solve_grid(int prec, int dev, int max_vec);
+int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int dev);
+cudaError_t launch_iface_cluster(const DeviceTables &t, const Workspace &w, const int *slab_if,
+                                 const int *slab_if_off, int nslab, int bmax, int nlev,
+                                 double tol, int max_solves, cudaStream_t st);
 cudaError_t init_local_attributes();
 cudaError_t init_iface_attributes(int prec, int bmax, int max_vec);
 

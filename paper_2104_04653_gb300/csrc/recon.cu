@@ -35,9 +35,8 @@ __global__ void __launch_bounds__(kS *kS) k_recon_cells(DeviceTables t, Workspac
   for (int c = 0; c < sb.ncols; ++c) pc += coefc[c] * bas[static_cast<int64_t>(c) * N + tid];
   p[tid] = pc;
   __syncthreads();
-  const double *coef = w.coef + static_cast<int64_t>(g) * 6 * N;
+  const double *coef = w.coef + static_cast<int64_t>(g) * (6 * N + 4 * S);
   const double tW = coef[tid], tE = coef[N + tid], tS = coef[2 * N + tid], tN = coef[3 * N + tid];
-  const double kc = coef[5 * N + tid];
   const double h = t.h;
   const int gi = sb.x0 + a, gj = sb.y0 + b;
   const int nx = t.nx, ny = t.ny;
@@ -57,7 +56,7 @@ __global__ void __launch_bounds__(kS *kS) k_recon_cells(DeviceTables t, Workspac
     double un;  // outward normal velocity
     if (sb.edge_iface[side] >= 0) {
       const IfaceInfo fi = t.iface[sb.edge_iface[side]];
-      const double beta = t.alpha[fi.alpha_off + e] * t.H / kc;
+      const double beta = coef[6 * N + side * S + e];
       double UH = 0.0, PH = 0.0;
       for (int k = 0; k < fi.nU; ++k) UH += w.x[fi.unk + k] * t.fnval[k * t.fn_stride + e];
       for (int k = 0; k < fi.nP; ++k) PH += w.x[fi.unk + fi.nU + k] * t.fnval[k * t.fn_stride + e];

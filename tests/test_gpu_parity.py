@@ -246,3 +246,15 @@ def test_refinement_limit_reports_stall():
     info = s.mrcm_get_info(check=False)
     assert info["status"] == "MRCM_ENOCONV"
     s.close()
+
+
+@pytest.mark.parametrize("path", ["cluster", "multi-kernel"])
+def test_interface_paths_agree(path, monkeypatch):
+    """The one-launch cluster interface solve and the multi-kernel global
+    memory one both meet the tolerance on the bench workload."""
+    O, mrcm, W = _mods()
+    if path == "multi-kernel":
+        monkeypatch.setenv("MRCM_NO_CLUSTER", "1")
+    else:
+        monkeypatch.delenv("MRCM_NO_CLUSTER", raising=False)
+    _check(W.config2(), 1)
