@@ -157,49 +157,6 @@ __device__ void tile_zero_global(T *dst, int b) {
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) dst[e] = T(0);
 }
 
-// In-place Gauss-Jordan inverse of the b x b tile M, no pivoting (the
-// pivots of the scaled quasi-definite matrix are bounded away from zero).
-// Thread t keeps column j = t % 64, rows i = t/64 + 8q (q < 8) in registers;
-// only the pivot row and column go through shared memory (double buffer).
-template <typename T>
-__device__ void tile_gj_inverse(T *M, int b, int *bad) {
-  __shared__ T colk[2][kTile], rowk[2][kTile];
-  const int t = threadIdx.x, j = t & (kTile - 1), rg = t >> 6;
-  T R[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) R[q] = M[(rg + 8 * q) * kTile + j];
-  __syncthreads();
-  for (int k = 0; k < b; ++k) {
-    const int buf = k & 1;
-    if (j == k) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) colk[buf][rg + 8 * q] = R[q];
-    }
-    if (rg == (k & 7)) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q == (k >> 3)) rowk[buf][j] = R[q];
-    }
-    __syncthreads();
-    const T piv = rowk[buf][k];
-    if (t == 0 && (!(piv != T(0)) || !isfinite(static_cast<double>(piv)))) *bad = 1;
-    const T ip = T(1) / piv;
-    const T rj = rowk[buf][j] * ip;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int i = rg + 8 * q;
-      const T ci = colk[buf][i];
-      if (i == k) R[q] = (j == k) ? ip : rj;
-      else if (j == k) R[q] = -ci * ip;
-      else R[q] -= ci * rj;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 8; ++q) M[(rg + 8 * q) * kTile + j] = R[q];
-  __syncthreads();
-}
-
 // C = alpha * A B (+ C if acc), 64 x 64 tiles, k < b.  Thread t owns rows
 // 4*(t/32)..+3 and columns 2*(t%32)..+1.
 template <typename T>
@@ -251,12 +208,13 @@ __global__ void __launch_bounds__(kThreads) k_bcr_level(DeviceTables t, Workspac
   T *tk = tr + kTile * kTile;
   T *tx = tk + kTile * kTile;
   T *tm = tx + kTile * kTile;
+  T *gjs = tm + kTile * kTile;               // Gauss-Jordan scratch (64 + 1024)
   if (threadIdx.x == 0) bad = 0;
   if (stride == 0) {
     if (blockIdx.x != 0) return;
     tile_load(tk, Bs, b);
     __syncthreads();
-    tile_gj_inverse(tk, b, &bad);
+    gj_inverse_blocked<T, kThreads>(tk, b, kTile, gjs, &bad);
     tile_store(Is, tk, b);
     if (threadIdx.x == 0 && bad) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
     return;
@@ -270,9 +228,9 @@ __global__ void __launch_bounds__(kThreads) k_bcr_level(DeviceTables t, Workspac
   if (l >= 0) tile_load(tl, Bs + l * bb, b);
   if (r < K) tile_load(tr, Bs + r * bb, b);
   __syncthreads();
-  if (l >= 0) tile_gj_inverse(tl, b, &bad);
+  if (l >= 0) gj_inverse_blocked<T, kThreads>(tl, b, kTile, gjs, &bad);
   if (r < K) {
-    tile_gj_inverse(tr, b, &bad);
+    gj_inverse_blocked<T, kThreads>(tr, b, kTile, gjs, &bad);
     tile_store(Is + r * bb, tr, b);
   }
   if (l >= 0) {
@@ -548,7 +506,7 @@ cudaError_t launch_iface_assemble(const DeviceTables &t, const Workspace &w, int
 template <typename T>
 static cudaError_t bcr_factor_t(const DeviceTables &t, const Workspace &w, int maxslab, int nlev,
                                 int *nlaunch, cudaStream_t st) {
-  const size_t smem = 5 * kTile * kTile * sizeof(T);
+  const size_t smem = (5 * kTile * kTile + 64 + 1024) * sizeof(T);
   for (int lev = 0, stride = 1; lev < nlev; ++lev, stride <<= 1) {
     const int neven = (maxslab + 2 * stride - 1) / (2 * stride);
     k_bcr_level<T><<<dim3(neven, t.n_real), kThreads, smem, st>>>(t, w, stride, lev);
@@ -607,7 +565,8 @@ static cudaError_t init_iface_t(int bmax, int max_vec) {
   (void)bmax;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_bcr_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(5 * kTile * kTile * sizeof(T)))) != cudaSuccess)
+                                static_cast<int>((5 * kTile * kTile + 64 + 1024) * sizeof(T)))) !=
+      cudaSuccess)
     return e;
   return cudaFuncSetAttribute(k_iface_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               2 * max_vec * static_cast<int>(sizeof(T)));

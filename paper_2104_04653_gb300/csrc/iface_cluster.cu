@@ -28,54 +28,7 @@ namespace {
 
 constexpr int kCT = 512;        // threads per CTA
 constexpr int kCMaxB = 64;      // largest slab
-
-// Gauss-Jordan inverse of the b x b row-major (leading dimension b) shared
-// matrix M in place, no pivoting.  Thread t keeps column t%64 and rows
-// t/64 + 8q in registers; pivot row and column go through shared memory.
-template <typename T>
-__device__ void gj_inverse(T *M, int b, int *bad) {
-  __shared__ T colk[2][kCMaxB], rowk[2][kCMaxB];
-  const int t = threadIdx.x, j = t & 63, rg = t >> 6;
-  T R[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int i = rg + 8 * q;
-    R[q] = (i < b && j < b) ? M[i * b + j] : T(0);
-  }
-  __syncthreads();
-  for (int k = 0; k < b; ++k) {
-    const int buf = k & 1;
-    if (j == k) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) colk[buf][rg + 8 * q] = R[q];
-    }
-    if (rg == (k & 7)) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q == (k >> 3)) rowk[buf][j] = R[q];
-    }
-    __syncthreads();
-    const T piv = rowk[buf][k];
-    if (t == 0 && (!(piv != T(0)) || !isfinite(static_cast<double>(piv)))) *bad = 1;
-    const T ip = T(1) / piv;
-    const T rj = rowk[buf][j] * ip;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int i = rg + 8 * q;
-      const T ci = colk[buf][i];
-      if (i == k) R[q] = (j == k) ? ip : rj;
-      else if (j == k) R[q] = -ci * ip;
-      else R[q] -= ci * rj;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int i = rg + 8 * q;
-    if (i < b && j < b) M[i * b + j] = R[q];
-  }
-  __syncthreads();
-}
+constexpr int kGjScr = 64 + 2 * 512;   // blocked Gauss-Jordan scratch (elements)
 
 // C = alpha A B (+ C), b x b row-major shared matrices; thread owns rows
 // 4*(t/32)..+3, columns 2*(t%32)..+1.  C must not alias A or B.
@@ -124,9 +77,34 @@ __device__ void matvec_acc(T *y, const T *M, const T *x, int b, T alpha) {
   }
 }
 
-struct ClusterLayout {
-  int b, nlev, mmax;
-};
+// in-place transpose of a b x b shared tile
+template <typename T>
+__device__ void transpose_tile(T *M, int b) {
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e / b, j = e % b;
+    if (i < j) {
+      const T x = M[i * b + j];
+      M[i * b + j] = M[j * b + i];
+      M[j * b + i] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// sum_j M[i][j] x[j] with M stored transposed (Mt[j*b + i]); four chains
+template <typename T>
+__device__ __forceinline__ T rowdot_t(const T *Mt, const T *x, int b, int i) {
+  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+  int j = 0;
+  for (; j + 3 < b; j += 4) {
+    a0 += Mt[j * b + i] * x[j];
+    a1 += Mt[(j + 1) * b + i] * x[j + 1];
+    a2 += Mt[(j + 2) * b + i] * x[j + 2];
+    a3 += Mt[(j + 3) * b + i] * x[j + 3];
+  }
+  for (; j < b; ++j) a0 += Mt[j * b + i] * x[j];
+  return (a0 + a1) + (a2 + a3);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kCT, 1)
@@ -152,7 +130,8 @@ __global__ void __launch_bounds__(kCT, 1)
   T *vr1 = v + kCMaxB;
   T *vr2 = vr1 + kCMaxB;
   T *vt = vr2 + kCMaxB;
-  double *rl = reinterpret_cast<double *>(vt + kCMaxB);   // FP64 residual of the slab
+  T *gjs = vt + kCMaxB;                                   // Gauss-Jordan scratch
+  double *rl = reinterpret_cast<double *>(gjs + kGjScr);  // FP64 residual of the slab
   double *part = rl + kCMaxB;                             // [2] partial sums
   __shared__ int bad;
   __shared__ double red[kCT / 32];
@@ -211,6 +190,8 @@ __global__ void __launch_bounds__(kCT, 1)
         if (L.edge_iface[qq] == gn) eL = qq;
         if (R.edge_iface[qq] == gn) eR = qq;
       }
+      // S block and both products in FP64 (rounded once into the FP32
+      // tile): products in FP32 cost two extra refinement sweeps
       double *Sb = scr, *Xb = scr + mm * mm;
       for (int e = lane; e < m * mn; e += 32) {
         const int i = e / mn, j = e % mn;
@@ -262,7 +243,7 @@ __global__ void __launch_bounds__(kCT, 1)
   // ---- block cyclic reduction
   for (int lev = 0; lev < nlev; ++lev) {
     const int s = 1 << lev;
-    if (k % (2 * s) == s) gj_inverse(tB, b, &bad);
+    if (k % (2 * s) == s) gj_inverse_blocked<T, kCT>(tB, b, b, gjs, &bad);
     cluster.sync();
     if (k % (2 * s) == 0) {
       const int l = k - s, rt = k + s;
@@ -293,68 +274,132 @@ __global__ void __launch_bounds__(kCT, 1)
     }
     cluster.sync();
   }
-  if (k == 0) gj_inverse(tB, b, &bad);
+  if (k == 0) gj_inverse_blocked<T, kCT>(tB, b, b, gjs, &bad);
   if (tid == 0 && bad) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
   cluster.sync();
 
-  // ---- refinement sweeps
-  // ||f||^2 of the realisation (every CTA computes the same total)
-  double fsq = 0.0;
-  for (int q = wid; q < nif; q += nw) {
-    const IfaceInfo fi = t.iface[slab_if[if0 + q]];
-    double a = 0.0;
-    for (int i = lane; i < fi.nU + fi.nP; i += 32) a += w.f[fi.unk + i] * w.f[fi.unk + i];
-    fsq += warp_sum(a);
+  // ---- transposed copies of the tiles the solve reads (thread-per-row
+  // matrix-vector products with conflict-free shared loads)
+  transpose_tile(tA, b);
+  transpose_tile(tC, b);
+  transpose_tile(tB, b);
+  for (int lev = 0; lev < nlev; ++lev) {
+    transpose_tile(tX + lev * bb, b);
+    transpose_tile(tY + lev * bb, b);
   }
-  if (lane == 0) red[wid] = fsq;
+
+  // ---- refinement data, all in shared memory: x of this slab and of its two
+  // neighbours (FP64), f, the residual rows as (coefficient, position in xs)
+  // lists, and the scaling blocks in the working precision.
+  const int E = t.emax, mm = t.mmax;
+  double *xs = part + 2;                         // [3b]: slabs k-1, k, k+1
+  double *fs = xs + 3 * kCMaxB;                  // [b]
+  double *rowc = fs + kCMaxB;                    // [b][E]
+  short *rowi = reinterpret_cast<short *>(rowc + b * E);   // [b][E]
+  int *rowcnt = reinterpret_cast<int *>(rowi + ((b * E + 1) & ~1));   // [b]
+  int *posinf = rowcnt + kCMaxB;   // [b] first position << 16 | m << 8 | index
+  T *Trow = reinterpret_cast<T *>(posinf + kCMaxB);   // [b][mm]
+  const int *p2u = t.pos2unk + ri.vec_off + static_cast<int64_t>(k) * b;
+  for (int e = tid; e < 3 * kCMaxB; e += kCT) xs[e] = 0.0;
+  for (int pos = wid; pos < b; pos += nw) {
+    const int u = p2u[pos];
+    if (u < 0) {
+      if (lane == 0) {
+        rowcnt[pos] = 0;
+        posinf[pos] = -1;
+        fs[pos] = 0.0;
+      }
+      continue;
+    }
+    const IfaceInfo fi = t.iface[t.unk_iface[u]];
+    const int i = u - fi.unk, m = fi.nU + fi.nP;
+    const RowRef rr = row_ref(t, w, fi, i);
+    const bool pinned = (u == ri.pin);
+    const int nL = rr.ncL - 1, nR = rr.ncR - 1;
+    for (int e = lane; e < nL + nR; e += 32) {
+      const bool left = e < nL;
+      const int c = left ? e + 1 : e - nL + 1;
+      const int v_ = t.col[(left ? rr.offL : rr.offR) + c].unk;
+      const double g = left ? rr.gL[c] : rr.gR[c];
+      const int sp = t.unk_slabpos[v_];
+      const int ds = sp / b - k;
+      const bool use = !pinned && v_ != ri.pin && ds >= -1 && ds <= 1;
+      rowc[pos * E + e] = use ? g : 0.0;
+      rowi[pos * E + e] = static_cast<short>(use ? (ds + 1) * b + sp % b : 0);
+    }
+    const double *Tg = w.tsc + fi.tsc_off;
+    for (int j = lane; j < mm; j += 32) Trow[pos * mm + j] = j < m ? static_cast<T>(Tg[i * m + j]) : T(0);
+    if (lane == 0) {
+      rowcnt[pos] = pinned ? 0 : nL + nR;
+      posinf[pos] = (fi.pos << 16) | (m << 8) | i;
+      fs[pos] = pinned ? 0.0 : w.f[u];
+    }
+  }
   __syncthreads();
-  if (tid == 0) {
+  // ||f||^2 of the realisation (every CTA sums the K partials in the same order)
+  if (tid < 32) {
     double a = 0.0;
-    for (int q = 0; q < nw; ++q) a += red[q];
-    part[1] = a;
+    for (int q = tid; q < b; q += 32) a += fs[q] * fs[q];
+    a = warp_sum(a);
+    if (tid == 0) part[1] = a;
   }
   cluster.sync();
   double fnorm2 = 0.0;
-  for (int q = 0; q < K; ++q) fnorm2 += *cluster.map_shared_rank(part + 1, q);
+  if (tid < 32) {
+    double a = tid < K ? *cluster.map_shared_rank(part + 1, tid) : 0.0;
+    fnorm2 = warp_sum(a);
+  }
+  fnorm2 = __shfl_sync(0xffffffffu, fnorm2, 0);   // lanes of warp 0; others below
+  __shared__ double s_f2, s_r2;
+  if (tid == 0) s_f2 = fnorm2;
+  __syncthreads();
+  fnorm2 = s_f2;
+  const double tol2 = tol * tol;
 
-  double prev = 1e300, rel = 0.0;
+  double prev2 = 1e300, rn2 = 0.0;
   int nsolve = 0;
   for (;;) {
-    // A: x += T^T y for this slab's interfaces
+    // A: x += T^T y (working precision correction added in FP64)
     if (nsolve > 0) {
-      for (int q = wid; q < nif; q += nw) {
-        const IfaceInfo fi = t.iface[slab_if[if0 + q]];
-        const int m = fi.nU + fi.nP;
-        const double *Tg = w.tsc + fi.tsc_off;
-        for (int i = lane; i < m; i += 32) {
-          double d = 0.0;
-          for (int qq = i; qq < m; ++qq) d += Tg[qq * m + i] * static_cast<double>(v[fi.pos + qq]);
-          w.x[fi.unk + i] += d;
-        }
+      for (int pos = tid; pos < b; pos += kCT) {
+        const int pi_ = posinf[pos];
+        if (pi_ < 0) continue;
+        const int p0 = pi_ >> 16, m = (pi_ >> 8) & 255, i = pi_ & 255;
+        T d = T(0);
+        for (int q = i; q < m; ++q) d += Trow[(p0 + q) * mm + i] * v[p0 + q];
+        xs[kCMaxB + pos] += static_cast<double>(d);
       }
-      __threadfence();
       cluster.sync();
     }
-    // B: FP64 residual of this slab's rows, warp per row
+    // neighbours' x
+    if (k > 0)
+      for (int p = tid; p < b; p += kCT) xs[p] = cluster.map_shared_rank(xs, k - 1)[kCMaxB + p];
+    if (k + 1 < K)
+      for (int p = tid; p < b; p += kCT)
+        xs[2 * kCMaxB + p] = cluster.map_shared_rank(xs, k + 1)[kCMaxB + p];
+    __syncthreads();
+    // B: FP64 residual rows, warp per row
     double rsq = 0.0;
-    for (int q = wid; q < b; q += nw) {
-      const int u = t.pos2unk[ri.vec_off + static_cast<int64_t>(k) * b + q];
+    for (int pos = wid; pos < b; pos += nw) {
+      const int cnt = rowcnt[pos];
       double sacc = 0.0;
-      if (u >= 0 && u != ri.pin) {
-        const IfaceInfo fi = t.iface[t.unk_iface[u]];
-        const RowRef rr = row_ref(t, w, fi, u - fi.unk);
-        for (int c = 1 + lane; c < rr.ncL; c += 32) sacc -= rr.gL[c] * w.x[t.col[rr.offL + c].unk];
-        for (int c = 1 + lane; c < rr.ncR; c += 32) sacc -= rr.gR[c] * w.x[t.col[rr.offR + c].unk];
-        sacc = warp_sum(sacc) + w.f[u];
+      for (int e = lane; e < cnt; e += 32) {
+        const int xi = rowi[pos * E + e];
+        sacc = fma(rowc[pos * E + e], xs[(xi / b) * kCMaxB + xi % b], sacc);
       }
-      // flux-continuity (P) rows carry the symmetrising sign
-      bool prow = false;
-      if (u >= 0) {
-        const IfaceInfo fi = t.iface[t.unk_iface[u]];
-        prow = (u - fi.unk) >= fi.nU;
+      sacc = warp_sum(sacc);
+      const double rv = cnt > 0 ? fs[pos] - sacc : 0.0;
+      if (lane == 0) {
+        const int pi_ = posinf[pos];
+        bool prow = false;
+        if (pi_ >= 0) {
+          const int u = p2u[pos];
+          const IfaceInfo fi = t.iface[t.unk_iface[u]];
+          prow = (pi_ & 255) >= fi.nU;
+        }
+        rl[pos] = prow ? -rv : rv;
       }
-      if (lane == 0) rl[q] = prow ? -sacc : sacc;
-      rsq += sacc * sacc;
+      rsq += rv * rv;
     }
     if (lane == 0) red[wid] = rsq;
     __syncthreads();
@@ -363,69 +408,81 @@ __global__ void __launch_bounds__(kCT, 1)
       for (int q = 0; q < nw; ++q) a += red[q];
       part[0] = a;
     }
-    // z = T (sign r) into v
-    for (int q = wid; q < nif; q += nw) {
-      const IfaceInfo fi = t.iface[slab_if[if0 + q]];
-      const int m = fi.nU + fi.nP;
-      const double *Tg = w.tsc + fi.tsc_off;
-      for (int i = lane; i < m; i += 32) {
-        double zv = 0.0;
-        for (int qq = 0; qq <= i; ++qq) zv += Tg[i * m + qq] * rl[fi.pos + qq];
-        v[fi.pos + i] = static_cast<T>(zv);
+    // z = T (sign r) in the working precision
+    for (int pos = tid; pos < b; pos += kCT) {
+      const int pi_ = posinf[pos];
+      T z = T(0);
+      if (pi_ >= 0 && rowcnt[pos] > 0) {
+        const int p0 = pi_ >> 16, i = pi_ & 255;
+        for (int q = 0; q <= i; ++q) z += Trow[pos * mm + q] * static_cast<T>(rl[p0 + q]);
       }
-    }
-    for (int p = tid; p < b; p += kCT) {
-      const int u = t.pos2unk[ri.vec_off + static_cast<int64_t>(k) * b + p];
-      if (u < 0 || u == ri.pin) v[p] = T(0);
+      v[pos] = z;
     }
     cluster.sync();
-    double rn2 = 0.0;
-    for (int q = 0; q < K; ++q) rn2 += *cluster.map_shared_rank(part, q);
-    rel = fnorm2 > 0.0 ? sqrt(rn2 / fnorm2) : 0.0;
-    const bool stop = (rel <= tol) || (nsolve >= max_solves) || !(rel == rel) ||
-                      (nsolve >= 2 && rel > 0.5 * prev);
-    prev = rel;
+    if (tid < 32) {
+      double a = tid < K ? *cluster.map_shared_rank(part, tid) : 0.0;
+      a = warp_sum(a);
+      if (tid == 0) s_r2 = a;
+    }
+    __syncthreads();
+    rn2 = s_r2;
+    const bool stop = (rn2 <= tol2 * fnorm2) || (nsolve >= max_solves) || !(rn2 == rn2) ||
+                      (nsolve >= 2 && rn2 > 0.25 * prev2);
+    prev2 = rn2;
     if (stop) break;
-    // C: y = Shat^{-1} z, cluster-wide cyclic reduction
+    // C: y = Shat^{-1} z, cluster-wide cyclic reduction (transposed tiles)
     for (int lev = 0; lev < nlev; ++lev) {
       const int s = 1 << lev;
       if (k % (2 * s) == 0) {
         const int l = k - s, rt = k + s;
-        if (l >= 0) copy_in(vr1, cluster.map_shared_rank(v, l), b);
-        if (rt < K) copy_in(vr2, cluster.map_shared_rank(v, rt), b);
-        if (l >= 0) matvec_acc(v, tX + lev * bb, vr1, b, T(-1));
+        for (int p = tid; p < b; p += kCT) {
+          vr1[p] = l >= 0 ? cluster.map_shared_rank(v, l)[p] : T(0);
+          vr2[p] = rt < K ? cluster.map_shared_rank(v, rt)[p] : T(0);
+        }
         __syncthreads();
-        if (rt < K) matvec_acc(v, tY + lev * bb, vr2, b, T(-1));
+        if (tid < b) {
+          T acc = T(0);
+          if (l >= 0) acc += rowdot_t(tX + lev * bb, vr1, b, tid);
+          if (rt < K) acc += rowdot_t(tY + lev * bb, vr2, b, tid);
+          v[tid] -= acc;
+        }
       }
       cluster.sync();
     }
     if (k == 0) {
-      copy_in(vr1, v, b);
-      for (int p = tid; p < b; p += kCT) v[p] = T(0);
+      for (int p = tid; p < b; p += kCT) vr1[p] = v[p];
       __syncthreads();
-      matvec_acc(v, tB, vr1, b, T(1));
+      if (tid < b) v[tid] = rowdot_t(tB, vr1, b, tid);
     }
     cluster.sync();
     for (int lev = nlev - 1; lev >= 0; --lev) {
       const int s = 1 << lev;
       if (k % (2 * s) == s) {
         const int l = k - s, rt = k + s;
-        copy_in(vr1, cluster.map_shared_rank(v, l), b);
-        if (rt < K) copy_in(vr2, cluster.map_shared_rank(v, rt), b);
-        copy_in(vt, v, b);
-        matvec_acc(vt, tA, vr1, b, T(-1));
+        for (int p = tid; p < b; p += kCT) {
+          vr1[p] = cluster.map_shared_rank(v, l)[p];
+          vr2[p] = rt < K ? cluster.map_shared_rank(v, rt)[p] : T(0);
+        }
         __syncthreads();
-        if (rt < K) matvec_acc(vt, tC, vr2, b, T(-1));
+        if (tid < b) {
+          T acc = v[tid] - rowdot_t(tA, vr1, b, tid);
+          if (rt < K) acc -= rowdot_t(tC, vr2, b, tid);
+          vt[tid] = acc;
+        }
         __syncthreads();
-        for (int p = tid; p < b; p += kCT) v[p] = T(0);
-        __syncthreads();
-        matvec_acc(v, tB, vt, b, T(1));
+        if (tid < b) v[tid] = rowdot_t(tB, vt, b, tid);
       }
       cluster.sync();
     }
     ++nsolve;
   }
+  // the interface solution of this slab, for reconstruction
+  for (int pos = tid; pos < b; pos += kCT) {
+    const int u = p2u[pos];
+    if (u >= 0) w.x[u] = xs[kCMaxB + pos];
+  }
   if (k == 0 && tid == 0) {
+    const double rel = fnorm2 > 0.0 ? sqrt(rn2 / fnorm2) : 0.0;
     w.done[r] = 1;
     w.dstat[2 + r] = rel;
     atomic_max_pos_double(&w.dstat[1], rel);
@@ -435,20 +492,27 @@ __global__ void __launch_bounds__(kCT, 1)
 }
 
 template <typename T>
-size_t cluster_smem(int bmax, int nlev) {
+size_t cluster_smem(int bmax, int nlev, int emax, int mmax) {
   const size_t bb = (static_cast<size_t>(bmax) * bmax + 3) & ~static_cast<size_t>(3);
-  return (5 + 2 * static_cast<size_t>(nlev)) * bb * sizeof(T) + 4 * kCMaxB * sizeof(T) +
-         (kCMaxB + 2) * sizeof(double) + 16;
+  size_t n = (5 + 2 * static_cast<size_t>(nlev)) * bb * sizeof(T) +
+             (4 * kCMaxB + kGjScr) * sizeof(T) + (kCMaxB + 2) * sizeof(double);
+  n = (n + 7) & ~static_cast<size_t>(7);
+  n += (3 * kCMaxB + kCMaxB) * sizeof(double);                    // xs, fs
+  n += static_cast<size_t>(bmax) * emax * sizeof(double);         // rowc
+  n += ((static_cast<size_t>(bmax) * emax + 1) & ~static_cast<size_t>(1)) * sizeof(short);
+  n += 2 * kCMaxB * sizeof(int);                                  // rowcnt, posinf
+  n += static_cast<size_t>(bmax) * mmax * sizeof(T);              // Trow
+  return n + 64;
 }
 
 }  // namespace
 
 // Can the one-launch cluster path run this problem?  Returns the cluster
 // size (0: no).
-int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int dev) {
+int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int emax, int dev) {
   if (prec != MRCM_PREC_FP32_IR) return 0;
-  if (nslab < 1 || nslab > 16 || bmax > kCMaxB) return 0;
-  const size_t smem = cluster_smem<float>(bmax, nlev);
+  if (nslab < 1 || nslab > 16 || bmax > kCMaxB || 3 * kCMaxB > 32767) return 0;
+  const size_t smem = cluster_smem<float>(bmax, nlev, emax, mmax);
   // per-warp assembly scratch must fit behind the first three tiles
   const size_t scr = static_cast<size_t>(kCT / 32) * 2 * mmax * mmax * sizeof(double);
   const size_t behind = (2 + 2 * static_cast<size_t>(nlev)) *
@@ -491,7 +555,7 @@ int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int de
 cudaError_t launch_iface_cluster(const DeviceTables &t, const Workspace &w, const int *slab_if,
                                  const int *slab_if_off, int nslab, int bmax, int nlev,
                                  double tol, int max_solves, cudaStream_t st) {
-  const size_t smem = cluster_smem<float>(bmax, nlev);
+  const size_t smem = cluster_smem<float>(bmax, nlev, t.emax, t.mmax);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nslab * t.n_real);
   cfg.blockDim = dim3(kCT);

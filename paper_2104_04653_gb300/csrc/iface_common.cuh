@@ -75,6 +75,10 @@ __device__ void iface_scale_warp(const DeviceTables &t, const Workspace &w, int 
   }
   __syncwarp();
   // Cholesky of the two diagonal sub-blocks in place (lower), row i per lane
+  // (the reciprocal square roots come from rsqrtf plus one FP64 Newton step:
+  //  no FP64 divide or square root, which are very slow on this part; any
+  //  accurate scaling works, the same T is used everywhere)
+  const int dcol = ld - 1;                     // spare column: 1/L_kk
   for (int k = 0; k < m; ++k) {
     const int lo = k < fi.nU ? 0 : fi.nU;      // first index of k's sub-block
     const int hi = k < fi.nU ? fi.nU : m;
@@ -85,13 +89,16 @@ __device__ void iface_scale_warp(const DeviceTables &t, const Workspace &w, int 
         bad = 1;
         d = 1.0;
       }
-      Sd(k, k) = sqrt(d);
+      double y = static_cast<double>(rsqrtf(static_cast<float>(d)));
+      y = y * (1.5 - 0.5 * d * y * y);
+      Sd(k, k) = d * y;                        // sqrt(d)
+      Sd(k, dcol) = y;                         // 1/sqrt(d)
     }
     __syncwarp();
     if (i > k && i < hi) {
       double v = Sd(i, k);
       for (int q = lo; q < k; ++q) v -= Sd(i, q) * Sd(k, q);
-      Sd(i, k) = v / Sd(k, k);
+      Sd(i, k) = v * Sd(k, dcol);
     }
     __syncwarp();
   }
@@ -104,7 +111,7 @@ __device__ void iface_scale_warp(const DeviceTables &t, const Workspace &w, int 
       if (r < i) continue;
       double v = (r == i) ? 1.0 : 0.0;
       for (int q = i; q < r; ++q) v -= Sd(r, q) * Xd(q, i);
-      Xd(r, i) = v / Sd(r, r);
+      Xd(r, i) = v * Sd(r, dcol);
     }
   }
   __syncwarp();
@@ -115,7 +122,8 @@ __device__ void iface_scale_warp(const DeviceTables &t, const Workspace &w, int 
       // not quasi-definite: fall back to diagonal scaling
       const RowRef rr = row_ref(t, w, fi, i);
       const double dg = fabs(rr.gL[rr.colL] + rr.gR[rr.colR]);
-      for (int j = 0; j < m; ++j) T[i * m + j] = (i == j) ? (dg > 0.0 ? 1.0 / sqrt(dg) : 1.0) : 0.0;
+      const double sc = dg > 0.0 ? static_cast<double>(rsqrtf(static_cast<float>(dg))) : 1.0;
+      for (int j = 0; j < m; ++j) T[i * m + j] = (i == j) ? sc : 0.0;
     } else {
       for (int j = 0; j < m; ++j) T[i * m + j] = Xd(i, j);
     }
@@ -126,6 +134,99 @@ __device__ void iface_scale_warp(const DeviceTables &t, const Workspace &w, int 
 #undef Xd
 }
 
+
+
+__device__ __forceinline__ float fast_recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double fast_recip(double x) { return 1.0 / x; }
+
+// In-place Gauss-Jordan inverse of the b x b shared matrix M (row stride
+// ld, b <= 64), no pivoting, by NT threads, in blocks of 8 pivots: warp 0
+// inverts the 8 x 8 pivot block in registers (shuffles) while the others
+// copy the pivot column panel; then the pivot row panel is formed and the
+// rest of the matrix gets a rank-8 update.  scr: 64 + 2*512 elements of T.
+// The pivot rows are written in their own loop: fusing them into the update
+// loop was mis-compiled at -O3 (wrong results, correct at -G).
+template <typename T, int NT>
+__device__ void gj_inverse_blocked(T *M, int b, int ld, T *scr, int *bad) {
+  T *Pi = scr, *ColP = scr + 64, *RowP = ColP + 64 * 8;
+  const int t = threadIdx.x;
+  const int nblk = (b + 7) >> 3;
+  for (int K = 0; K < nblk; ++K) {
+    const int k0 = 8 * K, kb = (b - k0) < 8 ? (b - k0) : 8;
+    if (t < 32) {
+      const int r = t >> 3, c = t & 7;   // lane holds (r, c) and (r + 4, c)
+      T e0 = (r < kb && c < kb) ? M[(k0 + r) * ld + k0 + c] : T(r == c);
+      T e1 = (r + 4 < kb && c < kb) ? M[(k0 + r + 4) * ld + k0 + c] : T(r + 4 == c);
+      for (int p = 0; p < kb; ++p) {
+        const int src = (p & 3) * 8;
+        const T ro = __shfl_sync(0xffffffffu, p < 4 ? e0 : e1, src + c);
+        const T pv = __shfl_sync(0xffffffffu, p < 4 ? e0 : e1, src + p);
+        const T c0 = __shfl_sync(0xffffffffu, e0, r * 8 + p);
+        const T c1 = __shfl_sync(0xffffffffu, e1, r * 8 + p);
+        if (t == 0 && (!(pv != T(0)) || !isfinite(static_cast<double>(pv)))) *bad = 1;
+        const T ip = fast_recip(pv);
+        const T rv = ro * ip;
+        T n0 = e0 - c0 * rv, n1 = e1 - c1 * rv;
+        n0 = (c == p) ? -c0 * ip : n0;
+        n1 = (c == p) ? -c1 * ip : n1;
+        n0 = (r == p) ? ((c == p) ? ip : rv) : n0;
+        n1 = (r + 4 == p) ? ((c == p) ? ip : rv) : n1;
+        e0 = n0;
+        e1 = n1;
+      }
+      Pi[r * 8 + c] = e0;
+      Pi[(r + 4) * 8 + c] = e1;
+    } else {
+      for (int e = t - 32; e < 64 * 8; e += NT - 32) {
+        const int i = e >> 3, p = e & 7;
+        ColP[e] = (i < b && p < kb) ? M[i * ld + k0 + p] : T(0);
+      }
+    }
+    __syncthreads();
+    for (int e = t; e < 8 * 64; e += NT) {
+      const int q = e >> 6, j = e & 63;
+      T a = T(0);
+      if (q < kb && j < b) {
+#pragma unroll
+        for (int p = 0; p < 8; ++p)
+          if (p < kb) a += Pi[q * 8 + p] * M[(k0 + p) * ld + j];
+      }
+      RowP[e] = a;
+    }
+    __syncthreads();
+    // pivot rows: M[K, :] = RowP, M[K, K] = Pinv
+    for (int e = t; e < 8 * 64; e += NT) {
+      const int q = e >> 6, j = e & 63;
+      if (q < kb && j < b)
+        M[(k0 + q) * ld + j] = (j >= k0 && j < k0 + kb) ? Pi[q * 8 + (j - k0)] : RowP[e];
+    }
+    // other rows: rank-kb update, and -M[i,K] Pinv in the pivot columns
+    for (int i0 = 0; i0 < 64; i0 += NT >> 3) {
+      const int i = i0 + (t >> 3);
+      if (i >= b || (i >= k0 && i < k0 + kb)) continue;
+      T cp[8];
+#pragma unroll
+      for (int p = 0; p < 8; ++p) cp[p] = ColP[i * 8 + p];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int j = (t & 7) + 8 * c;
+        if (j >= b) continue;
+        T a;
+        if (c == K) {
+          a = T(0);
+#pragma unroll
+          for (int p = 0; p < 8; ++p) a -= cp[p] * Pi[p * 8 + (t & 7)];
+        } else {
+          a = M[i * ld + j];
+#pragma unroll
+          for (int p = 0; p < 8; ++p) a -= cp[p] * RowP[p * 64 + j];
+        }
+        M[i * ld + j] = a;
+      }
+    }
+    __syncthreads();
+  }
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

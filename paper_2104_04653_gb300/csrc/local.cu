@@ -67,7 +67,19 @@ __device__ void face_T(const DeviceTables &t, const SubInfo &sb, const double *k
 }
 
 // ---------------------------------------------------------------------------
-// (a)+(b): one CTA per subdomain, one thread per cell / per block element.
+// (a)+(b): one CTA per subdomain.  Stage 1 (all 256 threads, one cell each):
+// FP64 transmissibilities, Jacobi scaling and the scaled couplings.  Stage 2
+// (warp 0): the block LDL^T recursion S_j = D_j - E_{j-1} W_{j-1} E_{j-1} and
+// the Gauss-Jordan inverses W_j = S_j^{-1} in registers: lane l holds column
+// c = l % 16 and rows 8 (l / 16) + q, q < 8; pivots are exchanged with warp
+// shuffles, so the 256-step pivot chain has no block-wide barrier.
+template <typename T>
+__device__ __forceinline__ T shfl(T v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 template <typename T>
 __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, const double *K,
                                                    const double *lam) {
@@ -77,12 +89,8 @@ __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, 
   const int tid = threadIdx.x;
   const int a = tid % S, b = tid / S;
   __shared__ double kap[N];
-  __shared__ double dsc[N];
-  __shared__ double tE[N], tN[N];
-  __shared__ T M[N];
-  __shared__ T Wp[N];
-  __shared__ int bad;
-  if (tid == 0) bad = 0;
+  __shared__ T offx[N];   // scaled coupling of cell (a,b) to (a+1,b)
+  __shared__ T ecp[N];    // scaled coupling of cell (a,b) to (a,b+1)
 
   const int64_t cell = (static_cast<int64_t>(sb.r) * t.ny + sb.y0 + b) * t.nx + sb.x0 + a;
   const double kc = K[cell] * lam[cell];
@@ -91,15 +99,14 @@ __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, 
   __syncthreads();
   double T4[4];
   face_T(t, sb, kap, a, b, T4);
-  const double diag = T4[0] + T4[1] + T4[2] + T4[3];
-  const double d = 1.0 / sqrt(diag);
+  const double d = 1.0 / sqrt(T4[0] + T4[1] + T4[2] + T4[3]);
   double *coef = w.coef + static_cast<int64_t>(g) * kCoefStride;
 #pragma unroll
   for (int k = 0; k < 4; ++k) coef[k * N + tid] = T4[k];
   coef[4 * N + tid] = d;
   coef[5 * N + tid] = kc;
-  // beta = alpha H / kappa on the interface faces of the cell (Eq. "beta")
   {
+    // beta = alpha H / kappa on the interface faces of the cell (Eq. "beta")
     const bool onface[4] = {a == 0, a == S - 1, b == 0, b == S - 1};
 #pragma unroll
     for (int side = 0; side < 4; ++side) {
@@ -109,52 +116,53 @@ __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, 
       coef[6 * N + side * S + e] = al * t.H / kc;
     }
   }
-  dsc[tid] = d;
-  tE[tid] = T4[1];
-  tN[tid] = T4[3];
+  kap[tid] = d;                       // reuse: scaling factors
   __syncthreads();
-
-  // block element (ra, cb) of the current S x S Schur block
-  const int ra = tid / S, cb = tid % S;
+  offx[tid] = static_cast<T>(a < S - 1 ? -T4[1] * d * kap[tid + 1] : 0.0);
+  ecp[tid] = static_cast<T>(b < S - 1 ? -T4[3] * d * kap[tid + S] : 0.0);
+  __syncthreads();
+  if (tid >= 32) return;
+  const int lane = tid, c = lane & 15, h = lane >> 4;
+  T R[8];
   T *Wg = static_cast<T *>(w.W) + static_cast<int64_t>(g) * S * N;
+  bool bad = false;
+#pragma unroll 1
   for (int j = 0; j < S; ++j) {
-    double v = 0.0;
-    if (ra == cb) {
-      v = 1.0;
-    } else if (ra - cb == 1 || cb - ra == 1) {
-      const int lo = ra < cb ? ra : cb;
-      v = -tE[j * S + lo] * dsc[j * S + ra] * dsc[j * S + cb];
+    const T ec = j > 0 ? ecp[(j - 1) * S + c] : T(0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = 8 * h + q;
+      T v = T(0);
+      if (r == c) v = T(1);
+      else if (r - c == 1) v = offx[j * S + c];
+      else if (c - r == 1) v = offx[j * S + r];
+      if (j > 0) v -= ecp[(j - 1) * S + r] * ec * R[q];
+      R[q] = v;
     }
-    if (j > 0) {
-      const double ea = -tN[(j - 1) * S + ra] * dsc[(j - 1) * S + ra] * dsc[j * S + ra];
-      const double eb = -tN[(j - 1) * S + cb] * dsc[(j - 1) * S + cb] * dsc[j * S + cb];
-      v -= ea * eb * static_cast<double>(Wp[tid]);
-    }
-    M[tid] = static_cast<T>(v);
-    __syncthreads();
-    // in-place Gauss-Jordan inverse; no pivoting (the block is SPD)
-    for (int k = 0; k < S; ++k) {
-      const T piv = M[k * S + k];
-      const T mak = M[ra * S + k];
-      const T mkb = M[k * S + cb];
-      __syncthreads();
-      if (!(piv > T(0))) {
-        if (tid == 0) bad = 1;
+#pragma unroll
+    for (int p = 0; p < S; ++p) {
+      const int src = (p >> 3) << 4;
+      const T rowv = shfl(R[p & 7], src + c);
+      const T piv = shfl(R[p & 7], src + p);
+      T colv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) colv[q] = shfl(R[q], (h << 4) + p);
+      if (!(piv > T(0))) bad = true;
+      const T ip = recip(piv);
+      const T rv = rowv * ip;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = 8 * h + q;
+        T nv = R[q] - colv[q] * rv;
+        nv = (c == p) ? -colv[q] * ip : nv;
+        nv = (r == p) ? ((c == p) ? ip : rv) : nv;
+        R[q] = nv;
       }
-      const T ipiv = T(1) / piv;
-      T nv;
-      if (ra == k && cb == k) nv = ipiv;
-      else if (ra == k) nv = mkb * ipiv;
-      else if (cb == k) nv = -mak * ipiv;
-      else nv = M[tid] - mak * mkb * ipiv;
-      M[tid] = nv;
-      __syncthreads();
     }
-    Wg[j * N + tid] = M[tid];
-    Wp[tid] = M[tid];
-    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) Wg[j * N + (8 * h + q) * S + c] = R[q];
   }
-  if (tid == 0 && bad) atomicOr(&w.status[0], MRCM_FLAG_NOTSPD);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&w.status[0], MRCM_FLAG_NOTSPD);
 }
 
 // ---------------------------------------------------------------------------
@@ -170,9 +178,10 @@ struct BasisSmem {
   double sp[4][kS][kNC];    // face-pressure traces
   double x[kNC * kS * kS];  // FP64 iterate
   double bb[kNC * kS * kS]; // FP64 right-hand sides
-  double red[kNC][kS * kS / 32];
-  double bn[kNC];
-  double rel;
+  float redf[kNC][kS * kS / 32];
+  float bnf[kNC];
+  float rnf[kNC];
+  float rel2;
   ColInfo col[kNC];
 };
 
@@ -217,25 +226,25 @@ __device__ void block_solve(BasisSmem<T> &sm, int nc) {
   }
 }
 
-// per-column sum over the CTA of val[c] (c < nc), result in sm.red[c][0]
+// per-column sum over the CTA of val[c] (c < nc) into out[c]
 template <typename T>
-__device__ void column_sums(BasisSmem<T> &sm, const double *val, int nc, double *out) {
+__device__ void column_sums(BasisSmem<T> &sm, const float *val, int nc, float *out) {
   constexpr int NW = kS * kS / 32;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 #pragma unroll
   for (int c = 0; c < kNC; ++c) {
     if (c < nc) {
-      double s = val[c];
+      float s = val[c];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) sm.red[c][wid] = s;
+      if (lane == 0) sm.redf[c][wid] = s;
     }
   }
   __syncthreads();
   if (tid < nc) {
-    double s = 0.0;
+    float s = 0.0f;
 #pragma unroll
-    for (int k = 0; k < NW; ++k) s += sm.red[tid][k];
+    for (int k = 0; k < NW; ++k) s += sm.redf[tid][k];
     out[tid] = s;
   }
   __syncthreads();
@@ -248,7 +257,6 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   constexpr int S = kS, N = S * S;
   extern __shared__ __align__(16) unsigned char smraw[];
   BasisSmem<T> &sm = *reinterpret_cast<BasisSmem<T> *>(smraw);
-  __shared__ double colres[kNC];
   const BasisItem it = items[blockIdx.x];
   const int g = it.sub;
   const SubInfo sb = t.sub[g];
@@ -274,10 +282,13 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   // right-hand sides (FP64)
   const double myT[4] = {tWs[tid], tEs[tid], tSs[tid], tNs[tid]};
   const int gi = sb.x0 + a, gj = sb.y0 + b;
-  double bnl[kNC];
+  const double dsl = ds[tid];
+  const float dsf = static_cast<float>(dsl);
+  const double mydiag = myT[0] + myT[1] + myT[2] + myT[3];
+  float bnl[kNC];
 #pragma unroll
   for (int c = 0; c < kNC; ++c) {
-    bnl[c] = 0.0;
+    bnl[c] = 0.0f;
     if (c >= nc) continue;
     const ColInfo ci = sm.col[c];
     double val = 0.0;
@@ -294,7 +305,7 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
         else if (side == kEdgeE) k = t.ny + gj;
         else if (side == kEdgeS) k = 2 * t.ny + gi;
         else k = 2 * t.ny + t.nx + gi;
-        if (t.bc_type[k] == 1) val += myT[side] * t.bc_val[k];
+        if (t.bc_type[k] == 1) val += sm.coef[side * N + tid] * t.bc_val[k];
         else val -= t.bc_val[k] * h;
       }
     } else {
@@ -312,60 +323,69 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
         } else {
           gval = fv;
         }
-        val = myT[side] * gval;
+        val = sm.coef[side * N + tid] * gval;
       }
     }
     sm.bb[c * N + tid] = val;
     sm.x[c * N + tid] = 0.0;
-    sm.z[c * N + tid] = static_cast<T>(ds[tid] * val);
-    bnl[c] = val * val;
+    const T zv = static_cast<T>(dsl * val);
+    sm.z[c * N + tid] = zv;
+    bnl[c] = static_cast<float>(zv) * static_cast<float>(zv);
   }
-  column_sums(sm, bnl, nc, sm.bn);
+  column_sums(sm, bnl, nc, sm.bnf);
 
-  // refinement loop: z holds D r in the working precision
+  // refinement loop: z holds D r in the working precision.  Convergence is
+  // tested on the Jacobi-scaled residual, ||D r|| <= tol ||D b|| per column,
+  // with squared norms (no division on the FP64 pipe).
+  const float tol2 = static_cast<float>(tol) * static_cast<float>(tol);
   int sweep = 0;
-  double prev = 1e300, rel = 0.0;
+  float prev2 = 3e38f, rel2 = 0.0f;
   for (;;) {
     block_solve(sm, nc);
-    for (int c = 0; c < nc; ++c)
-      sm.x[c * N + tid] += ds[tid] * static_cast<double>(sm.v[c * N + tid]);
+    for (int c = 0; c < nc; ++c) {
+      if (sizeof(T) == sizeof(float))
+        sm.x[c * N + tid] += static_cast<double>(dsf * static_cast<float>(sm.v[c * N + tid]));
+      else
+        sm.x[c * N + tid] += dsl * static_cast<double>(sm.v[c * N + tid]);
+    }
     __syncthreads();
     if (sweep >= ir_max) break;
-    // FP64 residual r = b - A x
-    double rn[kNC];
+    // FP64 residual r = b - A x (five FP64 FMAs per cell and column)
+    float rn[kNC];
 #pragma unroll
     for (int c = 0; c < kNC; ++c) {
-      rn[c] = 0.0;
+      rn[c] = 0.0f;
       if (c >= nc) continue;
       const double *xc = sm.x + c * N;
-      double ax = (myT[0] + myT[1] + myT[2] + myT[3]) * xc[tid];
-      if (a > 0) ax -= myT[0] * xc[tid - 1];
-      if (a < S - 1) ax -= myT[1] * xc[tid + 1];
-      if (b > 0) ax -= myT[2] * xc[tid - S];
-      if (b < S - 1) ax -= myT[3] * xc[tid + S];
-      const double r = sm.bb[c * N + tid] - ax;
-      sm.z[c * N + tid] = static_cast<T>(ds[tid] * r);
-      rn[c] = r * r;
+      double r = fma(-mydiag, xc[tid], sm.bb[c * N + tid]);
+      if (a > 0) r = fma(myT[0], xc[tid - 1], r);
+      if (a < S - 1) r = fma(myT[1], xc[tid + 1], r);
+      if (b > 0) r = fma(myT[2], xc[tid - S], r);
+      if (b < S - 1) r = fma(myT[3], xc[tid + S], r);
+      T zv;
+      if (sizeof(T) == sizeof(float)) zv = static_cast<T>(static_cast<float>(r) * dsf);
+      else zv = static_cast<T>(dsl * r);
+      sm.z[c * N + tid] = zv;
+      rn[c] = static_cast<float>(zv) * static_cast<float>(zv);
     }
-    column_sums(sm, rn, nc, colres);
-    if (tid == 0) {
-      double m = 0.0;
-      for (int c = 0; c < nc; ++c) {
-        const double bnc = sm.bn[c];
-        const double rr = bnc > 0.0 ? sqrt(colres[c] / bnc) : 0.0;
-        m = (rr > m || rr != rr) ? rr : m;
-      }
-      sm.rel = m;
+    column_sums(sm, rn, nc, sm.rnf);
+    if (tid < 32) {
+      float rr = 0.0f;
+      if (tid < nc) rr = sm.bnf[tid] > 0.0f ? sm.rnf[tid] / sm.bnf[tid] : 0.0f;
+      if (rr != rr) rr = 3e38f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rr = fmaxf(rr, __shfl_xor_sync(0xffffffffu, rr, o));
+      if (tid == 0) sm.rel2 = rr;
     }
     __syncthreads();
-    rel = sm.rel;
+    rel2 = sm.rel2;
     ++sweep;
-    if (!(rel == rel)) break;
-    if (rel <= tol) break;
-    if (sweep > 2 && rel > 0.5 * prev) break;  // stalled
-    prev = rel;
+    if (rel2 <= tol2) break;
+    if (sweep > 2 && rel2 > 0.25f * prev2) break;  // stalled
+    prev2 = rel2;
   }
   if (tid == 0 && ir_max > 0) {
+    const double rel = sqrt(static_cast<double>(rel2));
     atomicMax(&w.status[1], sweep);
     atomic_max_pos_double(&w.dstat[0], rel);
     if (!(rel <= 1e3 * tol)) atomicOr(&w.status[0], MRCM_FLAG_LOCAL_STALL);
@@ -377,7 +397,7 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
 
   // one-sided traces on every interface edge face, per column:
   //   u(e) = T_R (p_c - g_e)/h,  p_face(e) = g_e + beta_e u(e)
-  const double inv_h = 1.0 / h;
+  const double inv_h = t.inv_h;
   for (int q = tid; q < 4 * S * nc; q += N) {
     const int side = q / (S * nc), e = (q / nc) % S, c = q % nc;
     if (sb.edge_iface[side] < 0) continue;

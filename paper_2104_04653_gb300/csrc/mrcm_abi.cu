@@ -444,6 +444,7 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   t.s = S;
   t.h = d.ly / d.ny;
   t.H = S * t.h;
+  t.inv_h = d.ny / d.ly;
   t.sub = reinterpret_cast<const SubInfo *>(base + o_sub);
   t.iface = reinterpret_cast<const IfaceInfo *>(base + o_if);
   t.col = reinterpret_cast<const ColInfo *>(base + o_col);
@@ -462,6 +463,9 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   c->d_slab_if_off = reinterpret_cast<int *>(base + o_sio);
   t.pos2unk = c->d_pos2unk;
   t.mmax = c->mmax;
+  t.emax = 1;
+  for (const IfaceInfo &fi : c->iface)
+    t.emax = std::max(t.emax, c->sub[fi.L].ncols - 1 + c->sub[fi.R].ncols - 1);
   Workspace &w = c->w;
   w.coef = reinterpret_cast<double *>(base + o_coef);
   w.W = base + o_W;
@@ -495,7 +499,7 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   c->solve_grid = iface_solve_grid(c->prec, c->dev, c->max_vec);
   if (nunk > 0 && !getenv("MRCM_NO_CLUSTER"))
     c->cluster_k = iface_cluster_plan(c->prec, c->nslab_max, c->bmax_max, c->nlev_max, c->mmax,
-                                      c->dev);
+                                      t.emax, c->dev);
   if (nunk > 0 && (c->solve_grid < 1 || d.n_real > c->solve_grid)) {
     cudaFree(c->arena);
     delete c;

@@ -70,7 +70,7 @@ struct DeviceTables {
   int nx, ny, n_real, nsub, niface, nunk;
   int pure_neumann;
   int s;             // subdomain edge (uniform across realisations for now)
-  double h, H;
+  double h, H, inv_h;
   const SubInfo *sub;
   const IfaceInfo *iface;
   const ColInfo *col;
@@ -79,6 +79,7 @@ struct DeviceTables {
   const int *unk_slabpos;   // global unknown -> slab*bmax + pos (within realisation)
   const int *pos2unk;       // slab-padded position -> global unknown or -1
   int mmax;                 // largest nU + nP over all interfaces
+  int emax;                 // largest number of terms of one interface row
   const double *fnval;      // [kMaxFn][s] interface function values at midpoints
   int fn_stride;            // = s
   const double *alpha;      // per face
@@ -126,7 +127,7 @@ cudaError_t launch_iface_solve(const DeviceTables &t, const Workspace &w, int pr
 cudaError_t launch_reconstruct(const DeviceTables &t, const Workspace &w, double *p,
                                double *ux, double *uy, double *gam, cudaStream_t st);
 int iface_solve_grid(int prec, int dev, int max_vec);
-int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int dev);
+int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int emax, int dev);
 cudaError_t launch_iface_cluster(const DeviceTables &t, const Workspace &w, const int *slab_if,
                                  const int *slab_if_off, int nslab, int bmax, int nlev,
                                  double tol, int max_solves, cudaStream_t st);
