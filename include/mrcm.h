@@ -187,6 +187,32 @@ void mrcm_destroy(mrcm_ctx *ctx);
 const char *mrcm_last_error(const mrcm_ctx *ctx);
 int32_t mrcm_version(void);
 
+/* Local subdomain solve that allocates nothing.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc, e.g. code running inside another runtime's memory pool, or a
+ * process whose device footprint must stay fixed after start-up.
+ *
+ * Solves A x = rhs for nsub independent 16 x 16-cell subdomains (1 <= nsub
+ * <= 64), where A is the local two-point operator of Eq. "mrc1": harmonic
+ * transmissibilities between cells and, on the 4 x 16 boundary faces, the
+ * given face transmissibilities (Robin T_R, 2 kappa for a prescribed
+ * pressure, 0 for a prescribed flux).  FP32 block factorisation, FP64
+ * refinement to ||D r|| <= 1e-13 ||D rhs|| (D = diag(A)^-1/2), at most 30
+ * sweeps.  Device arrays, FP64: d_kappa [nsub][16][16] (x fastest), d_tface
+ * [nsub][4][16] (W, E, S, N faces; along +y for W/E, +x for S/N), d_rhs and
+ * d_x [nsub][256].  Asynchronous on cuda_stream; numerical failures are not
+ * reported (check the output).
+ *
+ * Its only scratch is a fixed 1 MiB __device__ array in the library, held by
+ * every GPU that loads the library until the process exits.  The first call
+ * on a device looks up that array's device address, so make it before any
+ * stream capture.  Every call reuses the same array and overwrites what it
+ * reads, so calls whose kernels overlap on the GPU (e.g. on two streams)
+ * race: serialise them.  nsub outside 1..64 returns MRCM_EINVAL (message from
+ * mrcm_last_error(NULL)). */
+mrcm_status mrcm_local_solve_noalloc(int32_t nsub, const double *d_kappa, const double *d_tface,
+                                     const double *d_rhs, double *d_x, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,6 +65,8 @@ static mrcm_status fail(mrcm_ctx *c, mrcm_status s, const char *fmt, ...) {
   return s;
 }
 
+void mrcm::set_global_error(const char *msg) { g_setup_err = msg; }
+
 static mrcm_status cuda_fail(mrcm_ctx *c, cudaError_t e, const char *where) {
   return fail(c, MRCM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }

@@ -127,6 +127,8 @@ cudaError_t launch_iface_solve(const DeviceTables &t, const Workspace &w, int pr
 cudaError_t launch_reconstruct(const DeviceTables &t, const Workspace &w, double *p,
                                double *ux, double *uy, double *gam, cudaStream_t st);
 int iface_solve_grid(int prec, int dev, int max_vec);
+// message returned by mrcm_last_error(NULL) (thread-local)
+void set_global_error(const char *msg);
 int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int emax, int dev);
 cudaError_t launch_iface_cluster(const DeviceTables &t, const Workspace &w, const int *slab_if,
                                  const int *slab_if_off, int nslab, int bmax, int nlev,

@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "MRCM_OK", 1: "MRCM_EINVAL", 2: "MRCM_ENOMEM", 3: "MRCM_ECUDA
 EXPORTED = ["mrcm_setup", "mrcm_factor_local", "mrcm_build_basis", "mrcm_solve_interface",
             "mrcm_reconstruct", "mrcm_get_info", "mrcm_set_stream", "mrcm_launch_count",
             "mrcm_num_interface_unknowns", "mrcm_num_gamma_values",
-            "mrcm_copy_interface_solution", "mrcm_destroy", "mrcm_last_error", "mrcm_version"]
+            "mrcm_copy_interface_solution", "mrcm_destroy", "mrcm_last_error", "mrcm_version",
+            "mrcm_local_solve_noalloc"]
 
 
 class MrcmDesc(ctypes.Structure):
@@ -100,6 +101,8 @@ def lib(path: Optional[Path] = None):
     L.mrcm_last_error.restype = ctypes.c_char_p
     L.mrcm_version.argtypes = []
     L.mrcm_version.restype = i32
+    L.mrcm_local_solve_noalloc.argtypes = [i32, dp, dp, dp, dp, vp]
+    L.mrcm_local_solve_noalloc.restype = i32
     if path is None:
         _lib = L
     return L
@@ -248,6 +251,21 @@ class Mrcm:
             self.close()
         except Exception:
             pass
+
+
+def local_solve_noalloc(kappa, tface, rhs, x, stream=None):
+    """Local subdomain solve with no device allocation (see
+    mrcm_local_solve_noalloc in include/mrcm.h).  kappa [n,16,16], tface
+    [n,4,16], rhs and x [n,16,16]: contiguous FP64 CUDA tensors."""
+    import torch
+    L = lib()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    n = int(kappa.shape[0])
+    st = L.mrcm_local_solve_noalloc(n, _ptr(kappa), _ptr(tface), _ptr(rhs), _ptr(x),
+                                    ctypes.c_void_p(stream.cuda_stream))
+    if st != MRCM_OK:
+        raise MrcmError(st, L.mrcm_last_error(None).decode())
 
 
 def device_inputs(prob):
