@@ -310,6 +310,9 @@ def run_gpu(args):
     peaks, src = measured_peaks()
     dom = max(calls, key=calls.get)
     roof = roofline_entry(dom, calls[dom], prob, s, peaks, src, clocks)
+    all_roofs = {c: roofline_entry(c, calls[c], prob, s, peaks, src, clocks) for c in calls}
+    for v in all_roofs.values():
+        v.pop("algorithmic", None)
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -324,6 +327,7 @@ def run_gpu(args):
         "calls_ms": {k: v * 1e3 for k, v in calls.items()},
         "solver_info": {k: {kk: vv for kk, vv in r["info"].items()} for k, r in results.items()},
         "roofline": roof,
+        "calls_roofline": all_roofs,
         "e2e": {"value": cells * ws / e2e_t, "unit": "cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": results["fp32_ir"]["launches"] * args.steps,
@@ -332,6 +336,26 @@ def run_gpu(args):
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
+
+
+# DRAM traffic per launch from the committed ncu capture (profiles/
+# k_iface_cluster_channels-256x64.md), valid only while the kernel sources are
+# the ones that were profiled.
+TRAFFIC = {"k_iface_cluster": {"bytes": 636928.0, "sha": "e97789e3cdd20329",
+                               "sources": ["csrc/iface_cluster.cu", "csrc/iface_common.cuh"]},
+           "k_basis": {"bytes": 2120704.0, "sha": "bc135466061d3e78", "sources": ["csrc/local.cu"]},
+           "k_factor": {"bytes": 332288.0, "sha": "bc135466061d3e78", "sources": ["csrc/local.cu"]}}
+
+
+def _traffic(kernel):
+    import hashlib
+    e = TRAFFIC.get(kernel)
+    if not e or not e["sha"]:
+        return None
+    h = hashlib.sha256()
+    for rel in e["sources"]:
+        h.update((ROOT / "paper_2104_04653_gb300" / rel).read_bytes())
+    return e["bytes"] if h.hexdigest()[:16] == e["sha"] else None
 
 
 def roofline_entry(call, seconds, prob, solver, peaks, src, clocks):
@@ -352,7 +376,7 @@ def roofline_entry(call, seconds, prob, solver, peaks, src, clocks):
         unit = "TFLOP/s"
         note = f"FP32 SIMT peak at the sampled {sm_mhz:.0f} MHz (152 SMs x 128 lanes x 2)"
     return {"kernel": w["kernel"], "bound": w["bound"], "achieved": ach, "peak": peak,
-            "unit": unit, "frac": ach / peak, "traffic": None, "peak_source": note,
+            "unit": unit, "frac": ach / peak, "traffic": _traffic(w["kernel"]), "peak_source": note,
             "call_ms": seconds * 1e3, "algorithmic": w}
 
 

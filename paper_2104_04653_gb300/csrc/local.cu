@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, 
   const int tid = threadIdx.x;
   const int a = tid % S, b = tid / S;
   __shared__ double kap[N];
+  __shared__ double dsc[N];
   __shared__ T offx[N];   // scaled coupling of cell (a,b) to (a+1,b)
   __shared__ T ecp[N];    // scaled coupling of cell (a,b) to (a,b+1)
 
@@ -116,10 +117,10 @@ __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, 
       coef[6 * N + side * S + e] = al * t.H / kc;
     }
   }
-  kap[tid] = d;                       // reuse: scaling factors
+  dsc[tid] = d;
   __syncthreads();
-  offx[tid] = static_cast<T>(a < S - 1 ? -T4[1] * d * kap[tid + 1] : 0.0);
-  ecp[tid] = static_cast<T>(b < S - 1 ? -T4[3] * d * kap[tid + S] : 0.0);
+  offx[tid] = static_cast<T>(a < S - 1 ? -T4[1] * d * dsc[tid + 1] : 0.0);
+  ecp[tid] = static_cast<T>(b < S - 1 ? -T4[3] * d * dsc[tid + S] : 0.0);
   __syncthreads();
   if (tid >= 32) return;
   const int lane = tid, c = lane & 15, h = lane >> 4;
