@@ -59,9 +59,25 @@ __device__ void gemm(T *C, const T *A, const T *B, int b, T alpha, bool acc) {
   __syncthreads();
 }
 
+// dst[0..n) = src[0..n) (src may be another CTA's shared memory): every
+// thread issues its eight loads before storing, so a copy costs one
+// distributed-shared-memory latency, not eight
 template <typename T>
 __device__ void copy_in(T *dst, const T *src, int n) {
-  for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
+  constexpr int U = 8;
+  for (int base = threadIdx.x; base < n; base += blockDim.x * U) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * blockDim.x;
+      v[u] = e < n ? src[e] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * blockDim.x;
+      if (e < n) dst[e] = v[u];
+    }
+  }
   __syncthreads();
 }
 
@@ -131,98 +147,144 @@ __global__ void __launch_bounds__(kCT, 1)
   T *vr2 = vr1 + kCMaxB;
   T *vt = vr2 + kCMaxB;
   T *gjs = vt + kCMaxB;                                   // Gauss-Jordan scratch
+  const int E = t.emax, mm = t.mmax;
   double *rl = reinterpret_cast<double *>(gjs + kGjScr);  // FP64 residual of the slab
   double *part = rl + kCMaxB;                             // [2] partial sums
+  double *xs = part + 2;                                  // [3 kCMaxB]: x of slabs k-1, k, k+1
+  double *fs = xs + 3 * kCMaxB;                           // [kCMaxB] f of the slab rows
+  double *Td = fs + kCMaxB;                               // [b][mm] scaling rows (FP64)
+  double *rowc = Td + b * mm;                             // [b][E] row coefficients
+  short *rowi = reinterpret_cast<short *>(rowc + b * E);  // [b][E] term positions
+  int *rowcnt = reinterpret_cast<int *>(rowi + ((b * E + 1) & ~1));   // [kCMaxB]
+  int *posinf = rowcnt + kCMaxB;   // [kCMaxB] p0 << 16 | m << 8 | i, bit 30 P row, bit 29 pin
+  T *Trow = reinterpret_cast<T *>(posinf + kCMaxB);       // [b][mm] scaling rows (working prec.)
   __shared__ int bad;
   __shared__ double red[kCT / 32];
   if (tid == 0) bad = 0;
+  const int64_t P0 = ri.vec_off + static_cast<int64_t>(k) * b;   // first slab position
 
-  const int if0 = slab_if_off[r * K + k], if1 = slab_if_off[r * K + k + 1];
-  const int nif = if1 - if0;
+  // ---- the slab's interface rows from the precomputed plans: one gather of G
+  for (int p = tid; p < b; p += kCT) {
+    const int info = t.plan_info[P0 + p];
+    posinf[p] = info;
+    rowcnt[p] = t.plan_cnt[P0 + p];
+    const int f0 = t.plan_fgoff[2 * (P0 + p)], f1 = t.plan_fgoff[2 * (P0 + p) + 1];
+    fs[p] = (info >= 0 && f0 >= 0) ? -(w.G[f0] + w.G[f1]) : 0.0;
+  }
+  for (int e = tid; e < b * E; e += kCT) {
+    const int go = t.plan_goff[P0 * E + e];
+    rowc[e] = go >= 0 ? w.G[go] : 0.0;
+    rowi[e] = t.plan_xi[P0 * E + e];
+  }
+  for (int e = tid; e < 3 * kCMaxB; e += kCT) xs[e] = 0.0;
+  __syncthreads();
 
-  // ---- scaling of this slab's interfaces (scratch in the tile area)
+  // ---- scaling of this slab's interfaces from their diagonal blocks, one
+  // warp per interface, in FP32: any consistent scaling is valid (the same T
+  // scales the assembled blocks, the residuals and the corrections), and the
+  // FP64 pipe of this part is too slow for a warp-serial Cholesky
   {
-    const int mm = t.mmax;
     const int ld = mm + 1;
-    const int per = 2 * mm * ld;                          // doubles per warp
+    const int per = 2 * mm * ld + mm * mm;                   // floats per warp
     const int avail = static_cast<int>((static_cast<size_t>(5 + 2 * nlev) * bb * sizeof(T)) /
-                                       (sizeof(double) * per));
+                                       (sizeof(float) * per));
     const int np = avail < nw ? avail : nw;
-    double *scr = reinterpret_cast<double *>(smraw);
+    float *scr = reinterpret_cast<float *>(smraw);
+    const int pa0 = t.pair_off[r * K + k], pa1 = t.pair_off[r * K + k + 1];
     if (np < 1) {
       if (tid == 0) atomicOr(&w.status[0], MRCM_FLAG_LAYOUT);
     } else if (wid < np) {
-      for (int q = wid; q < nif; q += np) {
-        const int g = slab_if[if0 + q];
-        iface_scale_warp(t, w, g, scr + wid * per, scr + wid * per + mm * ld, ld);
-        const IfaceInfo fi = t.iface[g];
-        for (int i = lane; i < fi.nU + fi.nP; i += 32) w.x[fi.unk + i] = 0.0;
+      float *Sd = scr + wid * per, *Xd = Sd + mm * ld, *To = Xd + mm * ld;
+      int nth = 0;
+      for (int q = pa0; q < pa1; ++q) {
+        const PairPlan pp = t.pairs[q];
+        if (pp.ds != 0 || pp.pn0 != pp.p0) continue;        // the diagonal block
+        if ((nth++ % np) != wid) continue;
+        const int m = pp.m, nU = pp.nU, p0 = pp.p0;
+        // A = -M_UU, C = -M_PP; a pinned unknown gets a unit diagonal
+        for (int e = lane; e < m * m; e += 32) {
+          const int i = e / m, j = e % m;
+          const int g0 = t.pair_goff[pp.goff + 2 * e], g1 = t.pair_goff[pp.goff + 2 * e + 1];
+          const double val = (g0 >= 0 ? w.G[g0] : 0.0) + (g1 >= 0 ? w.G[g1] : 0.0);
+          float sv = ((i < nU) == (j < nU)) ? static_cast<float>(-val) : 0.0f;
+          if (((posinf[p0 + i] >> 29) & 1) || ((posinf[p0 + j] >> 29) & 1))
+            sv = (i == j) ? 1.0f : 0.0f;
+          Sd[i * ld + j] = sv;
+        }
+        const int bd = iface_scale_core(Sd, Xd, ld, m, nU, To);
+        if (lane < m) {
+          for (int j = 0; j < mm; ++j) {
+            float tv = j < m ? To[lane * m + j] : 0.0f;
+            if (bd && j < m) tv = (lane == j) ? 1.0f : 0.0f;
+            Td[(p0 + lane) * mm + j] = static_cast<double>(tv);
+            Trow[(p0 + lane) * mm + j] = static_cast<T>(tv);
+            if (j < m) w.tsc[pp.tsc + lane * m + j] = static_cast<double>(tv);
+          }
+        }
+        if (bd && lane == 0) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
+        __syncwarp();
       }
     }
   }
   __threadfence();
   cluster.sync();
 
-  // ---- assemble the scaled slab blocks: T_g S_{g g'} T_{g'}^T
+  // ---- assemble the scaled slab blocks: T_g S_{g g'} T_{g'}^T, one warp
+  // per (own, neighbour) interface pair, S from the precomputed G offsets
   for (int e = tid; e < 3 * bb; e += kCT) tB[e] = T(0);
   __syncthreads();
-  // pairs (own interface g, neighbour g'): one warp each
   {
-    const int mm = t.mmax;
-    // per-warp scratch after the first three tiles: S and X blocks (FP64)
+    const int pa0 = t.pair_off[r * K + k], pa1 = t.pair_off[r * K + k + 1];
     double *scr = reinterpret_cast<double *>(tW1) + wid * 2 * mm * mm;
-    for (int q = wid; q < nif * 8; q += nw) {
-      const int g = slab_if[if0 + q / 8];
-      const int nbk = q % 8;
-      const IfaceInfo fi = t.iface[g];
-      const SubInfo &L = t.sub[fi.L];
-      const SubInfo &R = t.sub[fi.R];
-      const int gn = nbk < 4 ? L.edge_iface[nbk] : R.edge_iface[nbk - 4];
-      if (gn < 0) continue;
-      bool dup = false;
-      for (int qq = 0; qq < nbk; ++qq)
-        if ((qq < 4 ? L.edge_iface[qq] : R.edge_iface[qq - 4]) == gn) dup = true;
-      if (dup) continue;
-      const IfaceInfo fn = t.iface[gn];
-      const int m = fi.nU + fi.nP, mn = fn.nU + fn.nP;
-      int eL = -1, eR = -1;
-      for (int qq = 0; qq < 4; ++qq) {
-        if (L.edge_iface[qq] == gn) eL = qq;
-        if (R.edge_iface[qq] == gn) eR = qq;
-      }
-      // S block and both products in FP64 (rounded once into the FP32
-      // tile): products in FP32 cost two extra refinement sweeps
+    for (int q = pa0 + wid; q < pa1; q += nw) {
+      const PairPlan pp = t.pairs[q];
+      const int m = pp.m, mn = pp.mn;
       double *Sb = scr, *Xb = scr + mm * mm;
       for (int e = lane; e < m * mn; e += 32) {
-        const int i = e / mn, j = e % mn;
-        const RowRef rr = row_ref(t, w, fi, i);
-        double val = 0.0;
-        if (eL >= 0) val += rr.gL[L.edge_col[eL] + j];
-        if (eR >= 0) val += rr.gR[R.edge_col[eR] + j];
-        if (i >= fi.nU) val = -val;
-        if (fi.unk + i == ri.pin || fn.unk + j == ri.pin) val = 0.0;
-        Sb[i * mn + j] = val;
+        const int i = e / mn;
+        const int g0 = t.pair_goff[pp.goff + 2 * e], g1 = t.pair_goff[pp.goff + 2 * e + 1];
+        double val = (g0 >= 0 ? w.G[g0] : 0.0) + (g1 >= 0 ? w.G[g1] : 0.0);
+        Sb[e] = (i >= pp.nU) ? -val : val;                 // symmetrising sign
       }
       __syncwarp();
-      const double *Tg = w.tsc + fi.tsc_off;
-      const double *Tn = w.tsc + fn.tsc_off;
-      for (int e = lane; e < m * mn; e += 32) {
-        const int i = e / mn, j = e % mn;
-        double a = 0.0;
-        for (int qq = 0; qq <= i; ++qq) a += Tg[i * m + qq] * Sb[qq * mn + j];
-        Xb[i * mn + j] = a;
-      }
-      __syncwarp();
-      T *blk = fn.slab == k ? tB : (fn.slab == k - 1 ? tA : tC);
-      if (fn.slab < k - 1 || fn.slab > k + 1) {
+      T *blk = pp.ds == 0 ? tB : (pp.ds == -1 ? tA : tC);
+      if (pp.ds < -1 || pp.ds > 1) {
         if (lane == 0) atomicOr(&w.status[0], MRCM_FLAG_LAYOUT);
         continue;
       }
-      for (int e = lane; e < m * mn; e += 32) {
-        const int i = e / mn, j = e % mn;
-        double a = 0.0;
-        for (int qq = 0; qq <= j; ++qq) a += Xb[i * mn + qq] * Tn[j * mn + qq];
-        blk[(fi.pos + i) * b + fn.pos + j] = static_cast<T>(a);
+      const bool own = pp.ds == 0;
+      const bool diag = own && pp.pn0 == pp.p0;
+      const double *Tn = own ? Td + pp.pn0 * mm : w.tsc + pp.tscn;
+      const int ldn = own ? mm : mn;
+      // X = T_g S in FP64 (rounding S or X T^T's left factor to the working
+      // precision first costs a refinement sweep); the diagonal block, whose
+      // T S T^T = [-I *; * I] cancels, also takes Y = X T^T in FP64, the
+      // other blocks in the working precision
+      {
+        const double *Tg = Td + pp.p0 * mm;
+        for (int e = lane; e < m * mn; e += 32) {
+          const int i = e / mn, j = e % mn;
+          double a = 0.0;
+          for (int qq = 0; qq <= i; ++qq) a += Tg[i * mm + qq] * Sb[qq * mn + j];
+          Xb[e] = a;
+        }
+      }
+      __syncwarp();
+      if (diag) {
+        for (int e = lane; e < m * mn; e += 32) {
+          const int i = e / mn, j = e % mn;
+          double a = 0.0;
+          for (int qq = 0; qq <= j; ++qq) a += Xb[i * mn + qq] * Tn[j * ldn + qq];
+          blk[(pp.p0 + i) * b + pp.pn0 + j] = static_cast<T>(a);
+        }
+      } else {
+        for (int e = lane; e < m * mn; e += 32) {
+          const int i = e / mn, j = e % mn;
+          T a = T(0);
+          for (int qq = 0; qq <= j; ++qq)
+            a += static_cast<T>(Xb[i * mn + qq]) * static_cast<T>(Tn[j * ldn + qq]);
+          blk[(pp.p0 + i) * b + pp.pn0 + j] = a;
+        }
       }
       __syncwarp();
     }
@@ -230,12 +292,9 @@ __global__ void __launch_bounds__(kCT, 1)
   __syncthreads();
   // padded positions and the pinned unknown: identity (after the blocks,
   // whose pinned row and column are zero)
-  {
-    const int *p2u = t.pos2unk + ri.vec_off + static_cast<int64_t>(k) * b;
-    for (int p = tid; p < b; p += kCT) {
-      const int u = p2u[p];
-      if (u < 0 || u == ri.pin) tB[p * b + p] = T(1);
-    }
+  for (int p = tid; p < b; p += kCT) {
+    const int info = posinf[p];
+    if (info < 0 || ((info >> 29) & 1)) tB[p * b + p] = T(1);
   }
   __syncthreads();
   cluster.sync();
@@ -288,54 +347,9 @@ __global__ void __launch_bounds__(kCT, 1)
     transpose_tile(tY + lev * bb, b);
   }
 
-  // ---- refinement data, all in shared memory: x of this slab and of its two
-  // neighbours (FP64), f, the residual rows as (coefficient, position in xs)
-  // lists, and the scaling blocks in the working precision.
-  const int E = t.emax, mm = t.mmax;
-  double *xs = part + 2;                         // [3b]: slabs k-1, k, k+1
-  double *fs = xs + 3 * kCMaxB;                  // [b]
-  double *rowc = fs + kCMaxB;                    // [b][E]
-  short *rowi = reinterpret_cast<short *>(rowc + b * E);   // [b][E]
-  int *rowcnt = reinterpret_cast<int *>(rowi + ((b * E + 1) & ~1));   // [b]
-  int *posinf = rowcnt + kCMaxB;   // [b] first position << 16 | m << 8 | index
-  T *Trow = reinterpret_cast<T *>(posinf + kCMaxB);   // [b][mm]
-  const int *p2u = t.pos2unk + ri.vec_off + static_cast<int64_t>(k) * b;
-  for (int e = tid; e < 3 * kCMaxB; e += kCT) xs[e] = 0.0;
-  for (int pos = wid; pos < b; pos += nw) {
-    const int u = p2u[pos];
-    if (u < 0) {
-      if (lane == 0) {
-        rowcnt[pos] = 0;
-        posinf[pos] = -1;
-        fs[pos] = 0.0;
-      }
-      continue;
-    }
-    const IfaceInfo fi = t.iface[t.unk_iface[u]];
-    const int i = u - fi.unk, m = fi.nU + fi.nP;
-    const RowRef rr = row_ref(t, w, fi, i);
-    const bool pinned = (u == ri.pin);
-    const int nL = rr.ncL - 1, nR = rr.ncR - 1;
-    for (int e = lane; e < nL + nR; e += 32) {
-      const bool left = e < nL;
-      const int c = left ? e + 1 : e - nL + 1;
-      const int v_ = t.col[(left ? rr.offL : rr.offR) + c].unk;
-      const double g = left ? rr.gL[c] : rr.gR[c];
-      const int sp = t.unk_slabpos[v_];
-      const int ds = sp / b - k;
-      const bool use = !pinned && v_ != ri.pin && ds >= -1 && ds <= 1;
-      rowc[pos * E + e] = use ? g : 0.0;
-      rowi[pos * E + e] = static_cast<short>(use ? (ds + 1) * b + sp % b : 0);
-    }
-    const double *Tg = w.tsc + fi.tsc_off;
-    for (int j = lane; j < mm; j += 32) Trow[pos * mm + j] = j < m ? static_cast<T>(Tg[i * m + j]) : T(0);
-    if (lane == 0) {
-      rowcnt[pos] = pinned ? 0 : nL + nR;
-      posinf[pos] = (fi.pos << 16) | (m << 8) | i;
-      fs[pos] = pinned ? 0.0 : w.f[u];
-    }
-  }
-  __syncthreads();
+  // ---- refinement: x of this slab and of its two neighbours (xs, FP64),
+  // the residual rows (rowc/rowi), f and the scaling rows are all in shared
+  // memory from here on; global memory is written once at the end.
   // ||f||^2 of the realisation (every CTA sums the K partials in the same order)
   if (tid < 32) {
     double a = 0.0;
@@ -364,7 +378,7 @@ __global__ void __launch_bounds__(kCT, 1)
       for (int pos = tid; pos < b; pos += kCT) {
         const int pi_ = posinf[pos];
         if (pi_ < 0) continue;
-        const int p0 = pi_ >> 16, m = (pi_ >> 8) & 255, i = pi_ & 255;
+        const int p0 = (pi_ >> 16) & 255, m = (pi_ >> 8) & 255, i = pi_ & 255;
         T d = T(0);
         for (int q = i; q < m; ++q) d += Trow[(p0 + q) * mm + i] * v[p0 + q];
         xs[kCMaxB + pos] += static_cast<double>(d);
@@ -378,34 +392,44 @@ __global__ void __launch_bounds__(kCT, 1)
       for (int p = tid; p < b; p += kCT)
         xs[2 * kCMaxB + p] = cluster.map_shared_rank(xs, k + 1)[kCMaxB + p];
     __syncthreads();
-    // B: FP64 residual rows, warp per row
+    // B: FP64 residual, one thread per row with four independent chains (no
+    // FP64 warp reductions: every FP64 warp instruction costs the FP64 pipe
+    // ~19 clocks on this part)
     double rsq = 0.0;
-    for (int pos = wid; pos < b; pos += nw) {
-      const int cnt = rowcnt[pos];
-      double sacc = 0.0;
-      for (int e = lane; e < cnt; e += 32) {
-        const int xi = rowi[pos * E + e];
-        sacc = fma(rowc[pos * E + e], xs[(xi / b) * kCMaxB + xi % b], sacc);
+    if (tid < b) {
+      const int pos = tid, cnt = rowcnt[pos];
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      const double *rc = rowc + pos * E;
+      const short *ri_ = rowi + pos * E;
+      int e = 0;
+      for (; e + 3 < cnt; e += 4) {
+        int x0 = ri_[e], x1 = ri_[e + 1], x2 = ri_[e + 2], x3 = ri_[e + 3];
+        x0 += (x0 >= b ? (x0 >= 2 * b ? 2 : 1) : 0) * (kCMaxB - b);
+        x1 += (x1 >= b ? (x1 >= 2 * b ? 2 : 1) : 0) * (kCMaxB - b);
+        x2 += (x2 >= b ? (x2 >= 2 * b ? 2 : 1) : 0) * (kCMaxB - b);
+        x3 += (x3 >= b ? (x3 >= 2 * b ? 2 : 1) : 0) * (kCMaxB - b);
+        a0 = fma(rc[e], xs[x0], a0);
+        a1 = fma(rc[e + 1], xs[x1], a1);
+        a2 = fma(rc[e + 2], xs[x2], a2);
+        a3 = fma(rc[e + 3], xs[x3], a3);
       }
-      sacc = warp_sum(sacc);
-      const double rv = cnt > 0 ? fs[pos] - sacc : 0.0;
-      if (lane == 0) {
-        const int pi_ = posinf[pos];
-        bool prow = false;
-        if (pi_ >= 0) {
-          const int u = p2u[pos];
-          const IfaceInfo fi = t.iface[t.unk_iface[u]];
-          prow = (pi_ & 255) >= fi.nU;
-        }
-        rl[pos] = prow ? -rv : rv;
+      for (; e < cnt; ++e) {
+        int x0 = ri_[e];
+        x0 += (x0 >= b ? (x0 >= 2 * b ? 2 : 1) : 0) * (kCMaxB - b);
+        a0 = fma(rc[e], xs[x0], a0);
       }
-      rsq += rv * rv;
+      const double rv = cnt > 0 ? fs[pos] - ((a0 + a1) + (a2 + a3)) : 0.0;
+      rl[pos] = ((posinf[pos] >> 30) & 1) ? -rv : rv;
+      rsq = rv * rv;
     }
-    if (lane == 0) red[wid] = rsq;
+    if (tid < ((b + 31) & ~31)) {
+      rsq = warp_sum(rsq);
+      if (lane == 0) red[wid] = rsq;
+    }
     __syncthreads();
     if (tid == 0) {
       double a = 0.0;
-      for (int q = 0; q < nw; ++q) a += red[q];
+      for (int q = 0; q < (b + 31) / 32; ++q) a += red[q];
       part[0] = a;
     }
     // z = T (sign r) in the working precision
@@ -413,7 +437,7 @@ __global__ void __launch_bounds__(kCT, 1)
       const int pi_ = posinf[pos];
       T z = T(0);
       if (pi_ >= 0 && rowcnt[pos] > 0) {
-        const int p0 = pi_ >> 16, i = pi_ & 255;
+        const int p0 = (pi_ >> 16) & 255, i = pi_ & 255;
         for (int q = 0; q <= i; ++q) z += Trow[pos * mm + q] * static_cast<T>(rl[p0 + q]);
       }
       v[pos] = z;
@@ -478,7 +502,7 @@ __global__ void __launch_bounds__(kCT, 1)
   }
   // the interface solution of this slab, for reconstruction
   for (int pos = tid; pos < b; pos += kCT) {
-    const int u = p2u[pos];
+    const int u = t.pos2unk[P0 + pos];
     if (u >= 0) w.x[u] = xs[kCMaxB + pos];
   }
   if (k == 0 && tid == 0) {
@@ -495,9 +519,10 @@ template <typename T>
 size_t cluster_smem(int bmax, int nlev, int emax, int mmax) {
   const size_t bb = (static_cast<size_t>(bmax) * bmax + 3) & ~static_cast<size_t>(3);
   size_t n = (5 + 2 * static_cast<size_t>(nlev)) * bb * sizeof(T) +
-             (4 * kCMaxB + kGjScr) * sizeof(T) + (kCMaxB + 2) * sizeof(double);
+             (4 * kCMaxB + kGjScr) * sizeof(T);
   n = (n + 7) & ~static_cast<size_t>(7);
-  n += (3 * kCMaxB + kCMaxB) * sizeof(double);                    // xs, fs
+  n += (kCMaxB + 2 + 3 * kCMaxB + kCMaxB) * sizeof(double);      // rl, part, xs, fs
+  n += static_cast<size_t>(bmax) * mmax * sizeof(double);         // Td
   n += static_cast<size_t>(bmax) * emax * sizeof(double);         // rowc
   n += ((static_cast<size_t>(bmax) * emax + 1) & ~static_cast<size_t>(1)) * sizeof(short);
   n += 2 * kCMaxB * sizeof(int);                                  // rowcnt, posinf

@@ -47,18 +47,81 @@ __device__ __forceinline__ RowRef row_ref(const DeviceTables &t, const Workspace
 // on every interface block, A and C SPD.  T = blockdiag(L_A^{-1}, L_C^{-1})
 // from the Cholesky factors of the interface's own A and C makes the
 // diagonal blocks of T S T^T equal to -I and +I, which removes the
-// contrast-driven spread of the interface matrix.  Also writes f.
-// Executed by one full warp; Sd, Xd: shared scratch of m rows with leading
-// dimension ld (>= m + 1).
+// contrast-driven spread of the interface matrix.
+//
+// iface_scale_core: executed by one full warp.  On entry Sd (m rows, leading
+// dimension ld >= m + 1) holds A in [0,nU)^2 and C in [nU,m)^2 (zero
+// elsewhere; a pinned unknown has a unit diagonal and a zero row and
+// column).  Writes T (m x m, row-major) to Tout; returns nonzero if a pivot
+// was not positive (T is then left for the caller to replace).  The
+// reciprocal square roots come from rsqrtf plus one FP64 Newton step: no
+// FP64 divide or square root, which are very slow on this part; any accurate
+// scaling works, the same T is used everywhere.
+__device__ __forceinline__ double rsqrt_accurate(double d) {
+  double y = static_cast<double>(rsqrtf(static_cast<float>(d)));
+  return y * (1.5 - 0.5 * d * y * y);
+}
+__device__ __forceinline__ float rsqrt_accurate(float d) { return rsqrtf(d); }
+
+template <typename R>
+__device__ int iface_scale_core(R *Sd_, R *Xd_, int ld, int m, int nU, R *Tout) {
+  const int i = threadIdx.x & 31;
+  int bad = 0;
+#define Sd(r_, c_) Sd_[(r_) * ld + (c_)]
+#define Xd(r_, c_) Xd_[(r_) * ld + (c_)]
+  __syncwarp();
+  const int dcol = ld - 1;                     // spare column: 1/L_kk
+  for (int k = 0; k < m; ++k) {
+    const int lo = k < nU ? 0 : nU;            // first index of k's sub-block
+    const int hi = k < nU ? nU : m;
+    if (i == k) {
+      R d = Sd(k, k);
+      for (int q = lo; q < k; ++q) d -= Sd(k, q) * Sd(k, q);
+      if (!(d > R(0)) || !isfinite(static_cast<double>(d))) {
+        bad = 1;
+        d = R(1);
+      }
+      const R y = rsqrt_accurate(d);
+      Sd(k, k) = d * y;                        // sqrt(d)
+      Sd(k, dcol) = y;                         // 1/sqrt(d)
+    }
+    __syncwarp();
+    if (i > k && i < hi) {
+      R v = Sd(i, k);
+      for (int q = lo; q < k; ++q) v -= Sd(i, q) * Sd(k, q);
+      Sd(i, k) = v * Sd(k, dcol);
+    }
+    __syncwarp();
+  }
+  // X = L^{-1} (block lower triangular), column j per lane
+  if (i < m) {
+    const int lo = i < nU ? 0 : nU;
+    const int hi = i < nU ? nU : m;
+    for (int r = 0; r < m; ++r) Xd(r, i) = R(0);
+    for (int r = lo; r < hi; ++r) {
+      if (r < i) continue;
+      R v = (r == i) ? R(1) : R(0);
+      for (int q = i; q < r; ++q) v -= Sd(r, q) * Xd(q, i);
+      Xd(r, i) = v * Sd(r, dcol);
+    }
+  }
+  __syncwarp();
+  bad = __any_sync(0xffffffffu, bad);
+  if (i < m)
+    for (int j = 0; j < m; ++j) Tout[i * m + j] = Xd(i, j);
+  __syncwarp();
+#undef Sd
+#undef Xd
+  return bad;
+}
+
+// Scaling of interface g from its G rows (multi-kernel path); also writes f.
 __device__ void iface_scale_warp(const DeviceTables &t, const Workspace &w, int g, double *Sd_,
                                  double *Xd_, int ld) {
   const IfaceInfo fi = t.iface[g];
   const RealInfo &ri = t.real[fi.r];
   const int m = fi.nU + fi.nP;
   const int i = threadIdx.x & 31;
-  int bad = 0;
-#define Sd(r_, c_) Sd_[(r_) * ld + (c_)]
-#define Xd(r_, c_) Xd_[(r_) * ld + (c_)]
   if (i < m) {
     const RowRef rr = row_ref(t, w, fi, i);
     const bool pin_i = (fi.unk + i == ri.pin);
@@ -69,72 +132,24 @@ __device__ void iface_scale_warp(const DeviceTables &t, const Workspace &w, int 
       const bool same = (i < fi.nU) == (j < fi.nU);
       v = same ? -v : 0.0;
       if (pin_i || pin_j) v = (i == j) ? 1.0 : 0.0;
-      Sd(i, j) = v;
+      Sd_[i * ld + j] = v;
     }
     w.f[fi.unk + i] = pin_i ? 0.0 : -(rr.gL[0] + rr.gR[0]);
   }
-  __syncwarp();
-  // Cholesky of the two diagonal sub-blocks in place (lower), row i per lane
-  // (the reciprocal square roots come from rsqrtf plus one FP64 Newton step:
-  //  no FP64 divide or square root, which are very slow on this part; any
-  //  accurate scaling works, the same T is used everywhere)
-  const int dcol = ld - 1;                     // spare column: 1/L_kk
-  for (int k = 0; k < m; ++k) {
-    const int lo = k < fi.nU ? 0 : fi.nU;      // first index of k's sub-block
-    const int hi = k < fi.nU ? fi.nU : m;
-    if (i == k) {
-      double d = Sd(k, k);
-      for (int q = lo; q < k; ++q) d -= Sd(k, q) * Sd(k, q);
-      if (!(d > 0.0) || !isfinite(d)) {
-        bad = 1;
-        d = 1.0;
-      }
-      double y = static_cast<double>(rsqrtf(static_cast<float>(d)));
-      y = y * (1.5 - 0.5 * d * y * y);
-      Sd(k, k) = d * y;                        // sqrt(d)
-      Sd(k, dcol) = y;                         // 1/sqrt(d)
-    }
-    __syncwarp();
-    if (i > k && i < hi) {
-      double v = Sd(i, k);
-      for (int q = lo; q < k; ++q) v -= Sd(i, q) * Sd(k, q);
-      Sd(i, k) = v * Sd(k, dcol);
-    }
-    __syncwarp();
-  }
-  // X = L^{-1} (block lower triangular), column j per lane
-  if (i < m) {
-    const int lo = i < fi.nU ? 0 : fi.nU;
-    const int hi = i < fi.nU ? fi.nU : m;
-    for (int r = 0; r < m; ++r) Xd(r, i) = 0.0;
-    for (int r = lo; r < hi; ++r) {
-      if (r < i) continue;
-      double v = (r == i) ? 1.0 : 0.0;
-      for (int q = i; q < r; ++q) v -= Sd(r, q) * Xd(q, i);
-      Xd(r, i) = v * Sd(r, dcol);
-    }
-  }
-  __syncwarp();
-  bad = __any_sync(0xffffffffu, bad);
   double *T = w.tsc + fi.tsc_off;
-  if (i < m) {
-    if (bad) {
-      // not quasi-definite: fall back to diagonal scaling
+  const int bad = iface_scale_core(Sd_, Xd_, ld, m, fi.nU, T);
+  if (bad) {
+    // not quasi-definite: fall back to diagonal scaling
+    if (i < m) {
       const RowRef rr = row_ref(t, w, fi, i);
       const double dg = fabs(rr.gL[rr.colL] + rr.gR[rr.colR]);
       const double sc = dg > 0.0 ? static_cast<double>(rsqrtf(static_cast<float>(dg))) : 1.0;
       for (int j = 0; j < m; ++j) T[i * m + j] = (i == j) ? sc : 0.0;
-    } else {
-      for (int j = 0; j < m; ++j) T[i * m + j] = Xd(i, j);
     }
+    if (i == 0) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
   }
-  if (i == 0 && bad) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
   __syncwarp();
-#undef Sd
-#undef Xd
 }
-
-
 
 __device__ __forceinline__ float fast_recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double fast_recip(double x) { return 1.0 / x; }

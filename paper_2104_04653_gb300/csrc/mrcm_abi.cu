@@ -37,6 +37,12 @@ struct mrcm_ctx {
   int mmax = 1, nslab_max = 0, bmax_max = 0, nlev_max = 0;
   int cluster_k = 0;                       // > 0: one-launch cluster interface path
   int *d_slab_if = nullptr, *d_slab_if_off = nullptr;
+  // cluster interface plans (see DeviceTables)
+  std::vector<int> plan_info, plan_cnt, plan_goff, plan_fgoff, plan_tsc, pair_off, pair_goff;
+  std::vector<short> plan_xi;
+  std::vector<PairPlan> pairs;
+  int emax = 1;
+  bool plans_ok = false;
   std::vector<int64_t> pos_real_off;
   int64_t slab_elems = 0, xy_elems = 0, npos = 0, basis_elems = 0, g_elems = 0, gam_elems = 0;
   int64_t tsc_elems = 0;
@@ -314,6 +320,130 @@ static mrcm_status build_tables(mrcm_ctx *c) {
   return MRCM_OK;
 }
 
+// Per-slab plans of the one-launch cluster interface path: for every slab
+// position the G offsets and slab positions of its row's terms, and for
+// every (own interface, neighbour interface) block the G offsets of its
+// entries.  Everything the kernel would otherwise chase through the tables.
+static void build_plans(mrcm_ctx *c) {
+  c->emax = 1;
+  for (const IfaceInfo &fi : c->iface)
+    c->emax = std::max(c->emax, c->sub[fi.L].ncols - 1 + c->sub[fi.R].ncols - 1);
+  const int E = c->emax;
+  const int64_t npos = c->npos;
+  if (c->g_elems >= (int64_t(1) << 31) || npos * E >= (int64_t(1) << 31)) {
+    c->plans_ok = false;
+    return;
+  }
+  c->plan_info.assign(npos, -1);
+  c->plan_cnt.assign(npos, 0);
+  c->plan_goff.assign(npos * E, -1);
+  c->plan_xi.assign(npos * E, 0);
+  c->plan_fgoff.assign(npos * 2, -1);
+  c->plan_tsc.assign(npos, 0);
+  c->pairs.clear();
+  c->pair_off.clear();
+  c->pair_goff.clear();
+  auto rows_of = [&](const IfaceInfo &fi, int i, int64_t &goffL, int64_t &goffR, const SubInfo *&L,
+                     const SubInfo *&R, int &eL, int &eR) {
+    L = &c->sub[fi.L];
+    R = &c->sub[fi.R];
+    eL = fi.kind == 0 ? kEdgeE : kEdgeN;
+    eR = fi.kind == 0 ? kEdgeW : kEdgeS;
+    goffL = L->g_off + static_cast<int64_t>(L->edge_row[eL] + i) * L->ncols;
+    goffR = R->g_off + static_cast<int64_t>(R->edge_row[eR] + i) * R->ncols;
+  };
+  int slab_base = 0;   // global index of the realisation's first slab
+  for (size_t r = 0; r < c->real.size(); ++r) {
+    const RealInfo &ri = c->real[r];
+    const int b = ri.bmax;
+    for (int k = 0; k < ri.nslab; ++k) {
+      // rows
+      for (int p = 0; p < b; ++p) {
+        const int64_t P = ri.vec_off + static_cast<int64_t>(k) * b + p;
+        const int u = c->pos2unk[P];
+        if (u < 0) continue;
+        const IfaceInfo &fi = c->iface[c->unk_iface[u]];
+        const int i = u - fi.unk, m = fi.nU + fi.nP;
+        const bool pinned = (u == ri.pin);
+        c->plan_info[P] = (fi.pos << 16) | (m << 8) | i | (i >= fi.nU ? (1 << 30) : 0) |
+                          (pinned ? (1 << 29) : 0);
+        c->plan_tsc[P] = static_cast<int>(fi.tsc_off);
+        int64_t gL, gR;
+        const SubInfo *L, *R;
+        int eL, eR;
+        rows_of(fi, i, gL, gR, L, R, eL, eR);
+        if (pinned) continue;
+        c->plan_fgoff[2 * P] = static_cast<int>(gL);
+        c->plan_fgoff[2 * P + 1] = static_cast<int>(gR);
+        int e = 0;
+        for (int side = 0; side < 2; ++side) {
+          const SubInfo *S = side == 0 ? L : R;
+          const int64_t g0 = side == 0 ? gL : gR;
+          for (int cc = 1; cc < S->ncols; ++cc, ++e) {
+            const int v = c->col[S->col_off + cc].unk;
+            if (v == ri.pin) continue;
+            const int sp = c->unk_slabpos[v];
+            const int ds = sp / b - k;
+            c->plan_goff[P * E + e] = static_cast<int>(g0 + cc);
+            c->plan_xi[P * E + e] = static_cast<short>((ds + 1) * b + sp % b);
+          }
+        }
+        c->plan_cnt[P] = e;
+      }
+      // pairs of this slab
+      c->pair_off.push_back(static_cast<int>(c->pairs.size()));
+      const int s0 = c->slab_if_off[slab_base + k];
+      const int s1 = c->slab_if_off[slab_base + k + 1];
+      for (int q = s0; q < s1; ++q) {
+        const IfaceInfo &fi = c->iface[c->slab_if[q]];
+        const SubInfo &L = c->sub[fi.L], &R = c->sub[fi.R];
+        std::vector<int> nb;
+        for (int e = 0; e < 4; ++e) {
+          if (L.edge_iface[e] >= 0) nb.push_back(L.edge_iface[e]);
+          if (R.edge_iface[e] >= 0) nb.push_back(R.edge_iface[e]);
+        }
+        std::sort(nb.begin(), nb.end());
+        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        const int m = fi.nU + fi.nP;
+        for (int gn : nb) {
+          const IfaceInfo &fn = c->iface[gn];
+          const int mn = fn.nU + fn.nP;
+          PairPlan pp;
+          pp.p0 = fi.pos;
+          pp.m = m;
+          pp.nU = fi.nU;
+          pp.tsc = static_cast<int>(fi.tsc_off);
+          pp.pn0 = fn.pos;
+          pp.mn = mn;
+          pp.tscn = static_cast<int>(fn.tsc_off);
+          pp.ds = fn.slab - fi.slab;
+          pp.goff = static_cast<int>(c->pair_goff.size());
+          int eLn = -1, eRn = -1;
+          for (int e = 0; e < 4; ++e) {
+            if (L.edge_iface[e] == gn) eLn = e;
+            if (R.edge_iface[e] == gn) eRn = e;
+          }
+          for (int i = 0; i < m; ++i) {
+            int64_t gL, gR;
+            const SubInfo *Lp, *Rp;
+            int eL, eR;
+            rows_of(fi, i, gL, gR, Lp, Rp, eL, eR);
+            for (int j = 0; j < mn; ++j) {
+              const bool pin = (fi.unk + i == ri.pin) || (fn.unk + j == ri.pin);
+              c->pair_goff.push_back(!pin && eLn >= 0 ? static_cast<int>(gL + L.edge_col[eLn] + j) : -1);
+              c->pair_goff.push_back(!pin && eRn >= 0 ? static_cast<int>(gR + R.edge_col[eRn] + j) : -1);
+            }
+          }
+          c->pairs.push_back(pp);
+        }
+      }
+    }
+    slab_base += ri.nslab;
+  }
+  c->pair_off.push_back(static_cast<int>(c->pairs.size()));
+  c->plans_ok = true;
+}
+
 namespace {
 struct Arena {
   size_t off = 0;
@@ -349,6 +479,7 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     delete c;
     return st;
   }
+  build_plans(c);
   cudaError_t e = cudaGetDevice(&c->dev);
   if (e != cudaSuccess) {
     delete c;
@@ -386,6 +517,15 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                o_pro = A.take<int64_t>(c->pos_real_off.size()),
                o_sif = A.take<int>(c->slab_if.size() ? c->slab_if.size() : 1),
                o_sio = A.take<int>(c->slab_if_off.size()),
+               o_pinfo = A.take<int>(c->plan_info.size() + 1),
+               o_pcnt = A.take<int>(c->plan_cnt.size() + 1),
+               o_pgoff = A.take<int>(c->plan_goff.size() + 1),
+               o_pxi = A.take<short>(c->plan_xi.size() + 1),
+               o_pfg = A.take<int>(c->plan_fgoff.size() + 1),
+               o_ptsc = A.take<int>(c->plan_tsc.size() + 1),
+               o_pairs = A.take<PairPlan>(c->pairs.size() + 1),
+               o_paoff = A.take<int>(c->pair_off.size() + 1),
+               o_pagoff = A.take<int>(c->pair_goff.size() + 1),
                o_coef = A.take<double>(static_cast<size_t>(nsub) * (6 * N + 4 * S)),
                o_W = A.take<char>(static_cast<size_t>(nsub) * S * N * esz),
                o_basis = A.take<double>(c->basis_elems), o_G = A.take<double>(c->g_elems ? c->g_elems : 1),
@@ -429,6 +569,15 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
           cudaSuccess ||
       (e = up(o_sif, c->slab_if.data(), c->slab_if.size() * sizeof(int))) != cudaSuccess ||
       (e = up(o_sio, c->slab_if_off.data(), c->slab_if_off.size() * sizeof(int))) != cudaSuccess ||
+      (e = up(o_pinfo, c->plan_info.data(), c->plan_info.size() * sizeof(int))) != cudaSuccess ||
+      (e = up(o_pcnt, c->plan_cnt.data(), c->plan_cnt.size() * sizeof(int))) != cudaSuccess ||
+      (e = up(o_pgoff, c->plan_goff.data(), c->plan_goff.size() * sizeof(int))) != cudaSuccess ||
+      (e = up(o_pxi, c->plan_xi.data(), c->plan_xi.size() * sizeof(short))) != cudaSuccess ||
+      (e = up(o_pfg, c->plan_fgoff.data(), c->plan_fgoff.size() * sizeof(int))) != cudaSuccess ||
+      (e = up(o_ptsc, c->plan_tsc.data(), c->plan_tsc.size() * sizeof(int))) != cudaSuccess ||
+      (e = up(o_pairs, c->pairs.data(), c->pairs.size() * sizeof(PairPlan))) != cudaSuccess ||
+      (e = up(o_paoff, c->pair_off.data(), c->pair_off.size() * sizeof(int))) != cudaSuccess ||
+      (e = up(o_pagoff, c->pair_goff.data(), c->pair_goff.size() * sizeof(int))) != cudaSuccess ||
       (e = cudaMemset(base + o_st, 0, 4 * sizeof(int))) != cudaSuccess ||
       (e = cudaMemset(base + o_dst, 0, (2 + 2 * d.n_real) * sizeof(double))) != cudaSuccess) {
     cudaFree(c->arena);
@@ -465,9 +614,16 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   c->d_slab_if_off = reinterpret_cast<int *>(base + o_sio);
   t.pos2unk = c->d_pos2unk;
   t.mmax = c->mmax;
-  t.emax = 1;
-  for (const IfaceInfo &fi : c->iface)
-    t.emax = std::max(t.emax, c->sub[fi.L].ncols - 1 + c->sub[fi.R].ncols - 1);
+  t.emax = c->emax;
+  t.plan_info = reinterpret_cast<const int *>(base + o_pinfo);
+  t.plan_cnt = reinterpret_cast<const int *>(base + o_pcnt);
+  t.plan_goff = reinterpret_cast<const int *>(base + o_pgoff);
+  t.plan_xi = reinterpret_cast<const short *>(base + o_pxi);
+  t.plan_fgoff = reinterpret_cast<const int *>(base + o_pfg);
+  t.plan_tsc = reinterpret_cast<const int *>(base + o_ptsc);
+  t.pairs = reinterpret_cast<const PairPlan *>(base + o_pairs);
+  t.pair_off = reinterpret_cast<const int *>(base + o_paoff);
+  t.pair_goff = reinterpret_cast<const int *>(base + o_pagoff);
   Workspace &w = c->w;
   w.coef = reinterpret_cast<double *>(base + o_coef);
   w.W = base + o_W;
@@ -499,7 +655,7 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     return cuda_fail(nullptr, e, "kernel attributes");
   }
   c->solve_grid = iface_solve_grid(c->prec, c->dev, c->max_vec);
-  if (nunk > 0 && !getenv("MRCM_NO_CLUSTER"))
+  if (nunk > 0 && c->plans_ok && !getenv("MRCM_NO_CLUSTER"))
     c->cluster_k = iface_cluster_plan(c->prec, c->nslab_max, c->bmax_max, c->nlev_max, c->mmax,
                                       t.emax, c->dev);
   if (nunk > 0 && (c->solve_grid < 1 || d.n_real > c->solve_grid)) {

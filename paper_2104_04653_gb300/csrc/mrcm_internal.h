@@ -60,6 +60,14 @@ struct RealInfo {
   double h, H;
 };
 
+// One (own interface, neighbour interface) block of a slab's rows, for the
+// cluster interface path.  goff indexes pair_goff (m*mn*2 G offsets).
+struct PairPlan {
+  int p0, m, nU, tsc;      // own interface: first slab position, size, flux size, T offset
+  int pn0, mn, tscn, ds;   // neighbour: first position in its slab, size, T offset, slab - own
+  int goff;
+};
+
 struct BasisItem {   // one CTA of the basis kernel
   int sub;
   int c0, nc;        // column range
@@ -79,6 +87,16 @@ struct DeviceTables {
   const int *unk_slabpos;   // global unknown -> slab*bmax + pos (within realisation)
   const int *pos2unk;       // slab-padded position -> global unknown or -1
   int mmax;                 // largest nU + nP over all interfaces
+  // cluster interface path: per slab position (realisations concatenated)
+  const int *plan_info;     // p0 << 16 | m << 8 | i, bit 30 P row, bit 29 pinned; -1 padding
+  const int *plan_cnt;      // terms of the position's row
+  const int *plan_goff;     // [npos][emax] G offset of each term (-1: none)
+  const short *plan_xi;     // [npos][emax] position of the term's unknown in slabs k-1..k+1
+  const int *plan_fgoff;    // [npos][2] G offsets of the row's source/BC entries
+  const int *plan_tsc;      // [npos] offset of the position's interface scaling block
+  const PairPlan *pairs;    // per slab, realisations concatenated
+  const int *pair_off;      // [n_real * nslab + 1]
+  const int *pair_goff;     // G offsets of every pair entry (2 per entry, -1: none)
   int emax;                 // largest number of terms of one interface row
   const double *fnval;      // [kMaxFn][s] interface function values at midpoints
   int fn_stride;            // = s
