@@ -76,6 +76,9 @@ typedef enum {
 #define MRCM_FLAG_NAN         0x8
 #define MRCM_FLAG_IFACE_PIVOT 0x10
 #define MRCM_FLAG_LAYOUT      0x20  /* internal table inconsistency (a bug) */
+#define MRCM_FLAG_PRECOND_FALLBACK 0x40  /* informational: the caller-supplied   */
+                                         /* preconditioner stalled and GMRES was */
+                                         /* rerun with block-Jacobi              */
 
 typedef enum {
   MRCM_PREC_FP64 = 0,     /* plain path: FP64 factors and solves            */
@@ -86,6 +89,20 @@ typedef enum {
   MRCM_BASIS_LEGENDRE = 0,  /* P_k(t), Legendre polynomials                 */
   MRCM_BASIS_MONOMIAL = 1   /* t^k (same spans; for invariance checks)      */
 } mrcm_basis_family;
+
+typedef enum {
+  MRCM_IFACE_AUTO = 0,    /* direct when every slab has <= 64 unknowns, else GMRES */
+  MRCM_IFACE_DIRECT = 1,  /* block cyclic reduction over slabs + refinement  */
+  MRCM_IFACE_GMRES = 2    /* restarted FP64 GMRES, right-preconditioned      */
+} mrcm_iface_solver;
+
+typedef enum {
+  MRCM_PRECOND_BLOCK_JACOBI = 0,  /* P_g = (M_gg)^-1 per interface g          */
+  MRCM_PRECOND_USER = 1,          /* blocks from mrcm_set_precond_blocks (the  */
+                                  /* learned preconditioner); block-Jacobi    */
+                                  /* takes over if the residual stalls        */
+  MRCM_PRECOND_NONE = 2
+} mrcm_precond;
 
 typedef struct mrcm_ctx mrcm_ctx;   /* opaque, owned by the library */
 
@@ -115,13 +132,20 @@ typedef struct {
   double  iface_tol;         /* interface refinement tolerance (relative)     */
   int32_t iface_ir_max;      /* max interface refinement sweeps after the     */
                              /* first solve                                   */
+  int32_t iface_solver;      /* a mrcm_iface_solver value, 0 = auto           */
+  int32_t precond;           /* mrcm_precond, GMRES only (0 = block-Jacobi)   */
+  int32_t gmres_restart;     /* Krylov steps before a restart, 1..64 (0: 40)  */
+  int32_t gmres_max;         /* max GMRES steps in total (0: 5000)            */
+  double  gmres_tol;         /* stop at ||f - M x|| <= tol ||f||, the TRUE    */
+                             /* residual (0: iface_tol)                       */
 } mrcm_desc;
 
 typedef struct {
   int32_t flags;             /* OR of MRCM_FLAG_*                              */
   int32_t local_sweeps_max;  /* most local refinement sweeps any RHS took      */
   int32_t iface_sweeps;      /* interface refinement sweeps (max over real.)   */
-  int32_t reserved;
+  int32_t gmres_iters;       /* GMRES steps (max over realisations, including  */
+                             /* a block-Jacobi rerun); 0 on the direct path    */
   double  local_resid_max;   /* max ||b - A x|| / ||b|| over local solves      */
   double  iface_resid;       /* max over realisations ||f - M x|| / ||f||      */
 } mrcm_info;
@@ -148,11 +172,14 @@ mrcm_status mrcm_factor_local(mrcm_ctx *ctx, const double *d_K, const double *d_
  * its interface traces to workspace.  Text after Eq. "beta". */
 mrcm_status mrcm_build_basis(mrcm_ctx *ctx, const double *d_q);
 
-/* Step (d).  Assembles the interface system (Eq. "mrc2") from the basis
- * traces, factors it (FP64, or FP32 with FP64 refinement) and solves for
- * (U_H, P_H).  info: NULL = fully asynchronous; else the stream is
- * synchronised and *info filled (and the return value reflects device
- * flags). */
+/* Step (d).  Solves the interface system (Eq. "mrc2"), whose rows are the
+ * traces of the basis, for (U_H, P_H).  Direct path: assembles the slab
+ * blocks, factors them by block cyclic reduction (FP64, or FP32 with FP64
+ * refinement).  GMRES path: restarted FP64 GMRES on the unassembled rows,
+ * right-preconditioned by one m x m block per interface, until the true
+ * relative residual is <= gmres_tol or gmres_max steps.  info: NULL = fully
+ * asynchronous; else the stream is synchronised and *info filled (and the
+ * return value reflects device flags). */
 mrcm_status mrcm_solve_interface(mrcm_ctx *ctx, mrcm_info *info);
 
 /* Step (e).  Writes p [n_real][ny][nx], ux [n_real][ny][nx+1],
@@ -182,6 +209,23 @@ int64_t mrcm_num_gamma_values(const mrcm_ctx *ctx);
 /* Copy the interface solution (U_H, P_H), realisations concatenated in
  * canonical order, to the device buffer d_x (FP64). */
 mrcm_status mrcm_copy_interface_solution(mrcm_ctx *ctx, double *d_x);
+
+/* 1 if step (d) runs the GMRES path, 0 for the direct path. */
+int32_t mrcm_uses_gmres(const mrcm_ctx *ctx);
+
+/* Length of the preconditioner-block array: for every interface in
+ * canonical order (realisations concatenated) an m x m row-major block,
+ * m = nU + nP. */
+int64_t mrcm_num_precond_values(const mrcm_ctx *ctx);
+
+/* Preconditioner blocks for precond = MRCM_PRECOND_USER (the learned
+ * preconditioner).  d_blocks: device FP64, mrcm_num_precond_values()
+ * entries in the layout above; copied (stream-ordered) into the context, so
+ * the caller may reuse the buffer after the stream reaches this point.  Each
+ * block approximates the inverse of its interface's diagonal block; the
+ * GMRES path applies P = blockdiag(blocks) on the right.  EINVAL if the
+ * context does not use the GMRES path with precond = MRCM_PRECOND_USER. */
+mrcm_status mrcm_set_precond_blocks(mrcm_ctx *ctx, const double *d_blocks);
 
 void mrcm_destroy(mrcm_ctx *ctx);
 const char *mrcm_last_error(const mrcm_ctx *ctx);

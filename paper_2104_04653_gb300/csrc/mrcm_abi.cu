@@ -56,9 +56,20 @@ struct mrcm_ctx {
   int *d_pos2unk = nullptr;
   int64_t *d_pos_real_off = nullptr;
   int solve_grid = 1;
+  // GMRES interface path
+  bool use_gmres = false;
+  int gm_K = 40, gm_maxit = 5000, gm_precond = 0, gm_nblk = 0;
+  double gm_tol = 1e-13;
+  bool gm_user_set = false;
+  std::vector<GmRow> gm_rows;
+  std::vector<GmBlock> gm_blocks;
+  GmArgs gm{};
+  double *gm_Pbj = nullptr, *gm_Pid = nullptr, *gm_Puser = nullptr;
 };
 
 static thread_local std::string g_setup_err;
+
+static int d_nreal(const mrcm_ctx *c) { return c->d.n_real; }
 
 static mrcm_status fail(mrcm_ctx *c, mrcm_status s, const char *fmt, ...) {
   char buf[512];
@@ -113,6 +124,14 @@ static mrcm_status validate(const mrcm_desc *d) {
     return fail(nullptr, MRCM_EINVAL, "tolerances must be > 0 and sweep limits >= 0");
   if (d->ir_max > 1000 || d->iface_ir_max > 1000)
     return fail(nullptr, MRCM_EINVAL, "sweep limits above 1000");
+  if (d->iface_solver < MRCM_IFACE_AUTO || d->iface_solver > MRCM_IFACE_GMRES)
+    return fail(nullptr, MRCM_EINVAL, "unknown interface solver %d", d->iface_solver);
+  if (d->precond < MRCM_PRECOND_BLOCK_JACOBI || d->precond > MRCM_PRECOND_NONE)
+    return fail(nullptr, MRCM_EINVAL, "unknown preconditioner %d", d->precond);
+  if (d->gmres_restart < 0 || d->gmres_restart > kGmKmax)
+    return fail(nullptr, MRCM_EINVAL, "gmres_restart must be in 0..%d", kGmKmax);
+  if (d->gmres_max < 0 || !(d->gmres_tol >= 0.0))
+    return fail(nullptr, MRCM_EINVAL, "gmres_max and gmres_tol must be >= 0");
   const int s0 = d->sub_size[0];
   for (int r = 0; r < d->n_real; ++r) {
     const int s = d->sub_size[r];
@@ -271,9 +290,13 @@ static mrcm_status build_tables(mrcm_ctx *c) {
       }
       if (pos > ri.bmax) ri.bmax = pos;
     }
-    if (ri.bmax > 64)
-      return fail(nullptr, MRCM_EINVAL,
-                  "interface slab of %d unknowns exceeds the supported 64 (grid too wide)", ri.bmax);
+    if (ri.bmax > 64) {
+      if (d.iface_solver == MRCM_IFACE_DIRECT)
+        return fail(nullptr, MRCM_EINVAL,
+                    "interface slab of %d unknowns exceeds the direct solver's 64 (use GMRES)",
+                    ri.bmax);
+      c->use_gmres = true;
+    }
     int nlev = 0;
     while ((1 << nlev) < ri.nslab) ++nlev;
     ri.nlev = nlev;
@@ -291,6 +314,13 @@ static mrcm_status build_tables(mrcm_ctx *c) {
   }
   c->slab_if_off.push_back(static_cast<int>(c->slab_if.size()));
   c->nunk = unk_tot;
+  if (d.iface_solver == MRCM_IFACE_GMRES) c->use_gmres = true;
+  if (c->use_gmres) {
+    // no slab blocks on the GMRES path
+    slab_off = 0;
+    xy_off = 0;
+    for (RealInfo &ri : c->real) ri.slab_off = ri.xy_off = 0;
+  }
   for (const IfaceInfo &fi : c->iface) c->mmax = std::max(c->mmax, fi.nU + fi.nP);
   for (const RealInfo &ri : c->real) {
     c->nslab_max = std::max(c->nslab_max, ri.nslab);
@@ -326,6 +356,10 @@ static mrcm_status build_tables(mrcm_ctx *c) {
 // entries.  Everything the kernel would otherwise chase through the tables.
 static void build_plans(mrcm_ctx *c) {
   c->emax = 1;
+  if (c->use_gmres) {
+    c->plans_ok = false;
+    return;
+  }
   for (const IfaceInfo &fi : c->iface)
     c->emax = std::max(c->emax, c->sub[fi.L].ncols - 1 + c->sub[fi.R].ncols - 1);
   const int E = c->emax;
@@ -444,6 +478,70 @@ static void build_plans(mrcm_ctx *c) {
   c->plans_ok = true;
 }
 
+// GMRES path: one row descriptor per interface unknown, and the CTA plan of
+// the cooperative kernel (each realisation gets CTAs in proportion to its
+// unknowns, about 128 rows each, within the co-resident limit cap).
+static void build_gmres_rows(mrcm_ctx *c) {
+  c->gm_rows.assign(c->nunk, GmRow{});
+  for (const IfaceInfo &fi : c->iface) {
+    const SubInfo &L = c->sub[fi.L], &R = c->sub[fi.R];
+    const int eL = fi.kind == 0 ? kEdgeE : kEdgeN, eR = fi.kind == 0 ? kEdgeW : kEdgeS;
+    for (int i = 0; i < fi.nU + fi.nP; ++i) {
+      GmRow gr;
+      gr.gL = L.g_off + static_cast<int64_t>(L.edge_row[eL] + i) * L.ncols + 1;
+      gr.gR = R.g_off + static_cast<int64_t>(R.edge_row[eR] + i) * R.ncols + 1;
+      gr.cL = L.col_off + 1;
+      gr.cR = R.col_off + 1;
+      gr.nL = L.ncols - 1;
+      gr.nR = R.ncols - 1;
+      c->gm_rows[fi.unk + i] = gr;
+    }
+  }
+}
+
+static bool plan_gmres_blocks(mrcm_ctx *c, int cap) {
+  const int R = static_cast<int>(c->real.size());
+  if (cap < R) return false;
+  std::vector<int64_t> want(R);
+  int64_t tot = 0;
+  for (int r = 0; r < R; ++r) {
+    want[r] = std::max<int64_t>(1, (c->real[r].nunk + 127) / 128);
+    tot += want[r];
+  }
+  std::vector<int> nb(R);
+  if (tot <= cap) {
+    for (int r = 0; r < R; ++r) nb[r] = static_cast<int>(want[r]);
+  } else {
+    // scale down, at least one CTA each, never above cap in total
+    int64_t used = 0;
+    for (int r = 0; r < R; ++r) {
+      nb[r] = static_cast<int>(std::max<int64_t>(1, want[r] * (cap - R) / tot));
+      used += nb[r];
+    }
+    for (int r = 0; used < cap && r < R; ++r)
+      if (nb[r] < want[r]) {
+        ++nb[r];
+        ++used;
+      }
+  }
+  c->gm_blocks.clear();
+  for (int r = 0; r < R; ++r) {
+    const RealInfo &ri = c->real[r];
+    const int blk0 = static_cast<int>(c->gm_blocks.size());
+    for (int b = 0; b < nb[r]; ++b) {
+      GmBlock gb;
+      gb.r = r;
+      gb.row0 = ri.unk0 + static_cast<int>(static_cast<int64_t>(ri.nunk) * b / nb[r]);
+      gb.row1 = ri.unk0 + static_cast<int>(static_cast<int64_t>(ri.nunk) * (b + 1) / nb[r]);
+      gb.blk0 = blk0;
+      gb.nblk = nb[r];
+      c->gm_blocks.push_back(gb);
+    }
+  }
+  c->gm_nblk = static_cast<int>(c->gm_blocks.size());
+  return c->gm_nblk <= cap;
+}
+
 namespace {
 struct Arena {
   size_t off = 0;
@@ -480,10 +578,30 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     return st;
   }
   build_plans(c);
+  if (c->use_gmres) {
+    if (c->mmax > kGmMmax) {
+      delete c;
+      return fail(nullptr, MRCM_EINVAL, "GMRES path: interface size %d above %d", c->mmax,
+                  kGmMmax);
+    }
+    c->gm_K = desc->gmres_restart > 0 ? desc->gmres_restart : 40;
+    c->gm_maxit = desc->gmres_max > 0 ? desc->gmres_max : 5000;
+    c->gm_tol = desc->gmres_tol > 0.0 ? desc->gmres_tol : desc->iface_tol;
+    c->gm_precond = desc->precond;
+    build_gmres_rows(c);
+  }
   cudaError_t e = cudaGetDevice(&c->dev);
   if (e != cudaSuccess) {
     delete c;
     return cuda_fail(nullptr, e, "cudaGetDevice");
+  }
+  if (c->use_gmres) {
+    const int cap = gmres_max_blocks(c->gm_K, c->dev);
+    if (!plan_gmres_blocks(c, cap)) {
+      delete c;
+      return fail(nullptr, MRCM_EINVAL, "GMRES path: %d realisations exceed the %d co-resident CTAs",
+                  d_nreal(c), cap);
+    }
   }
   const mrcm_desc &d = c->d;
   const int S = c->S;
@@ -542,6 +660,19 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                o_ps = A.take<double>(nsub), o_gt = A.take<double>(c->gam_elems ? c->gam_elems : 1),
                o_st = A.take<int>(4), o_dst = A.take<double>(2 + 2 * d.n_real),
                o_done = A.take<int>(d.n_real + 1);
+  const bool G = c->use_gmres;
+  const int64_t Kp = c->gm_K;
+  const size_t o_gmrow = A.take<GmRow>(G ? c->gm_rows.size() + 1 : 0),
+               o_gmblk = A.take<GmBlock>(G ? c->gm_blocks.size() : 0),
+               o_gmGp = A.take<double>(G ? (c->g_elems ? c->g_elems : 1) : 0),
+               o_gmPbj = A.take<double>(G ? c->tsc_elems + 1 : 0),
+               o_gmPid = A.take<double>(G ? c->tsc_elems + 1 : 0),
+               o_gmPus = A.take<double>(G ? c->tsc_elems + 1 : 0),
+               o_gmV = A.take<double>(G ? (Kp + 1) * (nunk + 1) : 0),
+               o_gmW = A.take<double>(G ? nunk + 1 : 0), o_gmY = A.take<double>(G ? nunk + 1 : 0),
+               o_gmpart = A.take<double>(G ? static_cast<int64_t>(c->gm_nblk) * (Kp + 2) : 0),
+               o_gmres = A.take<double>(G ? d.n_real : 0),
+               o_gmint = A.take<int>(G ? 3 * d.n_real : 0);
   e = cudaMalloc(&c->arena, A.off);
   if (e != cudaSuccess) {
     delete c;
@@ -578,6 +709,10 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
       (e = up(o_pairs, c->pairs.data(), c->pairs.size() * sizeof(PairPlan))) != cudaSuccess ||
       (e = up(o_paoff, c->pair_off.data(), c->pair_off.size() * sizeof(int))) != cudaSuccess ||
       (e = up(o_pagoff, c->pair_goff.data(), c->pair_goff.size() * sizeof(int))) != cudaSuccess ||
+      (G && (e = up(o_gmrow, c->gm_rows.data(), c->gm_rows.size() * sizeof(GmRow))) !=
+                cudaSuccess) ||
+      (G && (e = up(o_gmblk, c->gm_blocks.data(), c->gm_blocks.size() * sizeof(GmBlock))) !=
+                cudaSuccess) ||
       (e = cudaMemset(base + o_st, 0, 4 * sizeof(int))) != cudaSuccess ||
       (e = cudaMemset(base + o_dst, 0, (2 + 2 * d.n_real) * sizeof(double))) != cudaSuccess) {
     cudaFree(c->arena);
@@ -646,19 +781,51 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   w.dstat = reinterpret_cast<double *>(base + o_dst);
   w.ifnorm = nullptr;
   w.done = reinterpret_cast<int *>(base + o_done);
+  if (G) {
+    GmArgs &a = c->gm;
+    a.row = reinterpret_cast<const GmRow *>(base + o_gmrow);
+    a.blk = reinterpret_cast<const GmBlock *>(base + o_gmblk);
+    a.Gp = reinterpret_cast<double *>(base + o_gmGp);
+    c->gm_Pbj = reinterpret_cast<double *>(base + o_gmPbj);
+    c->gm_Pid = reinterpret_cast<double *>(base + o_gmPid);
+    c->gm_Puser = reinterpret_cast<double *>(base + o_gmPus);
+    a.V = reinterpret_cast<double *>(base + o_gmV);
+    a.Wv = reinterpret_cast<double *>(base + o_gmW);
+    a.Y = reinterpret_cast<double *>(base + o_gmY);
+    a.part = reinterpret_cast<double *>(base + o_gmpart);
+    a.resid = reinterpret_cast<double *>(base + o_gmres);
+    a.done = reinterpret_cast<int *>(base + o_gmint);
+    a.fallback = a.done + d.n_real;
+    a.iters = a.fallback + d.n_real;
+    a.K = c->gm_K;
+    a.maxit = c->gm_maxit;
+    a.tol = c->gm_tol;
+    // identity blocks (no preconditioner)
+    std::vector<double> id(c->tsc_elems + 1, 0.0);
+    for (const IfaceInfo &fi : c->iface) {
+      const int m = fi.nU + fi.nP;
+      for (int k = 0; k < m; ++k) id[fi.tsc_off + k * m + k] = 1.0;
+    }
+    if ((e = cudaMemcpy(c->gm_Pid, id.data(), id.size() * sizeof(double),
+                        cudaMemcpyHostToDevice)) != cudaSuccess) {
+      cudaFree(c->arena);
+      delete c;
+      return cuda_fail(nullptr, e, "mrcm_setup upload");
+    }
+  }
   int bmax = 1;
   for (const RealInfo &ri : c->real) bmax = ri.bmax > bmax ? ri.bmax : bmax;
   if ((e = init_local_attributes()) != cudaSuccess ||
-      (e = init_iface_attributes(c->prec, bmax, c->max_vec)) != cudaSuccess) {
+      (e = init_iface_attributes(c->prec, bmax, c->use_gmres ? 0 : c->max_vec)) != cudaSuccess) {
     cudaFree(c->arena);
     delete c;
     return cuda_fail(nullptr, e, "kernel attributes");
   }
-  c->solve_grid = iface_solve_grid(c->prec, c->dev, c->max_vec);
-  if (nunk > 0 && c->plans_ok && !getenv("MRCM_NO_CLUSTER"))
+  c->solve_grid = c->use_gmres ? 0 : iface_solve_grid(c->prec, c->dev, c->max_vec);
+  if (nunk > 0 && c->plans_ok && !c->use_gmres && !getenv("MRCM_NO_CLUSTER"))
     c->cluster_k = iface_cluster_plan(c->prec, c->nslab_max, c->bmax_max, c->nlev_max, c->mmax,
                                       t.emax, c->dev);
-  if (nunk > 0 && (c->solve_grid < 1 || d.n_real > c->solve_grid)) {
+  if (nunk > 0 && !c->use_gmres && (c->solve_grid < 1 || d.n_real > c->solve_grid)) {
     cudaFree(c->arena);
     delete c;
     return fail(nullptr, MRCM_EINVAL,
@@ -721,7 +888,7 @@ static mrcm_status read_info(mrcm_ctx *ctx, mrcm_info *info) {
   info->flags = st[0];
   info->local_sweeps_max = st[1];
   info->iface_sweeps = st[2];
-  info->reserved = 0;
+  info->gmres_iters = st[3];
   info->local_resid_max = ds[0];
   info->iface_resid = ds[1];
   if (st[0] & MRCM_FLAG_LAYOUT) return fail(ctx, MRCM_EINVAL, "internal slab layout error");
@@ -736,10 +903,53 @@ static mrcm_status read_info(mrcm_ctx *ctx, mrcm_info *info) {
   return MRCM_OK;
 }
 
+// GMRES path of step (d): preconditioner blocks, G' = G P, the cooperative
+// solve; with caller-supplied blocks a second, gated pass reruns the
+// stalled realisations with block-Jacobi.
+static mrcm_status solve_gmres(mrcm_ctx *ctx) {
+  const int R = ctx->d.n_real;
+  cudaStream_t st = ctx->stream;
+  GmArgs a = ctx->gm;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(a.done, 0, sizeof(int) * 3 * R, st)) != cudaSuccess)
+    return cuda_fail(ctx, e, "reset");
+  const int pc = ctx->gm_precond;
+  if (pc == MRCM_PRECOND_USER && !ctx->gm_user_set)
+    return fail(ctx, MRCM_EINVAL, "precond = MRCM_PRECOND_USER but no blocks were set");
+  a.P = pc == MRCM_PRECOND_BLOCK_JACOBI ? ctx->gm_Pbj
+        : pc == MRCM_PRECOND_USER       ? ctx->gm_Puser
+                                        : ctx->gm_Pid;
+  a.stall = pc == MRCM_PRECOND_USER ? 1 : 0;
+  a.gate = 0;
+  if ((e = launch_gmres_precond(ctx->t, ctx->w, a, ctx->gm_Pbj, pc == MRCM_PRECOND_BLOCK_JACOBI,
+                                st)) != cudaSuccess)
+    return cuda_fail(ctx, e, "GMRES preconditioner launch");
+  ctx->launches += pc == MRCM_PRECOND_BLOCK_JACOBI ? 2 : 1;
+  if ((e = launch_gmres(ctx->t, ctx->w, a, ctx->gm_nblk, st)) != cudaSuccess)
+    return cuda_fail(ctx, e, "GMRES launch");
+  ctx->launches += 1;
+  if (pc == MRCM_PRECOND_USER) {
+    if ((e = cudaMemsetAsync(a.done, 0, sizeof(int) * R, st)) != cudaSuccess)
+      return cuda_fail(ctx, e, "reset");
+    a.P = ctx->gm_Pbj;
+    a.stall = 0;
+    a.gate = 1;
+    if ((e = launch_gmres_precond(ctx->t, ctx->w, a, ctx->gm_Pbj, true, st)) != cudaSuccess)
+      return cuda_fail(ctx, e, "GMRES preconditioner launch");
+    if ((e = launch_gmres(ctx->t, ctx->w, a, ctx->gm_nblk, st)) != cudaSuccess)
+      return cuda_fail(ctx, e, "GMRES launch");
+    ctx->launches += 3;
+  }
+  return MRCM_OK;
+}
+
 mrcm_status mrcm_solve_interface(mrcm_ctx *ctx, mrcm_info *info) {
   if (!ctx) return MRCM_EINVAL;
   if (ctx->state < 2) return fail(ctx, MRCM_EINVAL, "solve_interface before build_basis");
-  if (ctx->nunk > 0 && ctx->cluster_k > 0) {
+  if (ctx->nunk > 0 && ctx->use_gmres) {
+    mrcm_status gs = solve_gmres(ctx);
+    if (gs != MRCM_OK) return gs;
+  } else if (ctx->nunk > 0 && ctx->cluster_k > 0) {
     cudaError_t e = launch_iface_cluster(ctx->t, ctx->w, ctx->d_slab_if, ctx->d_slab_if_off,
                                          ctx->cluster_k, ctx->bmax_max, ctx->nlev_max,
                                          ctx->d.iface_tol, 1 + ctx->d.iface_ir_max, ctx->stream);
@@ -790,6 +1000,26 @@ int32_t mrcm_launch_count(const mrcm_ctx *ctx) { return ctx ? ctx->launches : 0;
 int64_t mrcm_num_interface_unknowns(const mrcm_ctx *ctx) { return ctx ? ctx->nunk : 0; }
 
 int64_t mrcm_num_gamma_values(const mrcm_ctx *ctx) { return ctx ? ctx->gam_elems : 0; }
+
+int32_t mrcm_uses_gmres(const mrcm_ctx *ctx) { return ctx && ctx->use_gmres ? 1 : 0; }
+
+int64_t mrcm_num_precond_values(const mrcm_ctx *ctx) { return ctx ? ctx->tsc_elems : 0; }
+
+mrcm_status mrcm_set_precond_blocks(mrcm_ctx *ctx, const double *d_blocks) {
+  if (!ctx) return MRCM_EINVAL;
+  if (!ctx->use_gmres || ctx->gm_precond != MRCM_PRECOND_USER)
+    return fail(ctx, MRCM_EINVAL, "preconditioner blocks need the GMRES path with MRCM_PRECOND_USER");
+  if (ctx->tsc_elems == 0) {
+    ctx->gm_user_set = true;
+    return MRCM_OK;
+  }
+  if (!d_blocks) return fail(ctx, MRCM_EINVAL, "d_blocks must be a device pointer");
+  cudaError_t e = cudaMemcpyAsync(ctx->gm_Puser, d_blocks, sizeof(double) * ctx->tsc_elems,
+                                  cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "copy preconditioner blocks");
+  ctx->gm_user_set = true;
+  return MRCM_OK;
+}
 
 mrcm_status mrcm_copy_interface_solution(mrcm_ctx *ctx, double *d_x) {
   if (!ctx) return MRCM_EINVAL;

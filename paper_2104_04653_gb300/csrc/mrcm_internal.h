@@ -68,6 +68,41 @@ struct PairPlan {
   int goff;
 };
 
+// GMRES interface path (iface_gmres.cu)
+constexpr int kGmThreads = 256;
+constexpr int kGmKmax = 64;   // largest restart length
+constexpr int kGmMmax = 32;   // largest interface size nU + nP
+
+struct GmRow {       // one interface unknown = one row of the interface system
+  int64_t gL, gR;    // G offsets of the row's basis-column-1 entry, L and R side
+  int cL, cR;        // column-table offsets of basis column 1 on each side
+  int nL, nR;        // basis columns on each side (ncols - 1)
+};
+
+struct GmBlock {     // one CTA of the GMRES kernel
+  int r;             // realisation
+  int row0, row1;    // global unknowns [row0, row1) owned by the CTA
+  int blk0, nblk;    // the realisation's CTAs
+};
+
+struct GmArgs {
+  const GmRow *row;
+  const GmBlock *blk;
+  const double *P;   // preconditioner blocks (m x m per interface, at tsc_off)
+  double *Gp;        // G P, same layout as G
+  double *V;         // Krylov slots: per realisation (K + 1) x nunk
+  double *Wv, *Y;    // work vector and iterate of the preconditioned system
+  double *part;      // [CTAs][K + 2] partial sums
+  double *resid;     // [n_real] final relative residual
+  int *done;         // [n_real]
+  int *fallback;     // [n_real] 1: rerun with block-Jacobi
+  int *iters;        // [n_real] GMRES steps, accumulated over launches
+  int K, maxit;
+  int stall;         // 1: stop on a stalled residual and request the rerun
+  int gate;          // 1: run only the realisations whose fallback flag is set
+  double tol;
+};
+
 struct BasisItem {   // one CTA of the basis kernel
   int sub;
   int c0, nc;        // column range
@@ -151,6 +186,12 @@ int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int em
 cudaError_t launch_iface_cluster(const DeviceTables &t, const Workspace &w, const int *slab_if,
                                  const int *slab_if_off, int nslab, int bmax, int nlev,
                                  double tol, int max_solves, cudaStream_t st);
+size_t gmres_smem_bytes(int K);
+int gmres_max_blocks(int K, int dev);
+cudaError_t launch_gmres_precond(const DeviceTables &t, const Workspace &w, const GmArgs &a,
+                                 double *Pbj, bool build_bj, cudaStream_t st);
+cudaError_t launch_gmres(const DeviceTables &t, const Workspace &w, const GmArgs &a, int nblk,
+                         cudaStream_t st);
 cudaError_t init_local_attributes();
 cudaError_t init_iface_attributes(int prec, int bmax, int max_vec);
 

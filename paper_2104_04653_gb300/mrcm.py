@@ -21,6 +21,9 @@ MRCM_OK, MRCM_EINVAL, MRCM_ENOMEM, MRCM_ECUDA, MRCM_ENOTSPD = 0, 1, 2, 3, 4
 MRCM_EIRSTALL, MRCM_ENOCONV, MRCM_ENAN, MRCM_ETIMEOUT = 5, 6, 7, 8
 PREC_FP64, PREC_FP32_IR = 0, 1
 BASIS_LEGENDRE, BASIS_MONOMIAL = 0, 1
+IFACE_AUTO, IFACE_DIRECT, IFACE_GMRES = 0, 1, 2
+PRECOND_BLOCK_JACOBI, PRECOND_USER, PRECOND_NONE = 0, 1, 2
+FLAG_PRECOND_FALLBACK = 0x40
 STATUS_NAMES = {0: "MRCM_OK", 1: "MRCM_EINVAL", 2: "MRCM_ENOMEM", 3: "MRCM_ECUDA",
                 4: "MRCM_ENOTSPD", 5: "MRCM_EIRSTALL", 6: "MRCM_ENOCONV", 7: "MRCM_ENAN",
                 8: "MRCM_ETIMEOUT"}
@@ -29,7 +32,8 @@ EXPORTED = ["mrcm_setup", "mrcm_factor_local", "mrcm_build_basis", "mrcm_solve_i
             "mrcm_reconstruct", "mrcm_get_info", "mrcm_set_stream", "mrcm_launch_count",
             "mrcm_num_interface_unknowns", "mrcm_num_gamma_values",
             "mrcm_copy_interface_solution", "mrcm_destroy", "mrcm_last_error", "mrcm_version",
-            "mrcm_local_solve_noalloc"]
+            "mrcm_local_solve_noalloc", "mrcm_uses_gmres", "mrcm_num_precond_values",
+            "mrcm_set_precond_blocks"]
 
 
 class MrcmDesc(ctypes.Structure):
@@ -47,16 +51,19 @@ class MrcmDesc(ctypes.Structure):
         ("prec", ctypes.c_int32),
         ("ir_tol", ctypes.c_double), ("ir_max", ctypes.c_int32),
         ("iface_tol", ctypes.c_double), ("iface_ir_max", ctypes.c_int32),
+        ("iface_solver", ctypes.c_int32), ("precond", ctypes.c_int32),
+        ("gmres_restart", ctypes.c_int32), ("gmres_max", ctypes.c_int32),
+        ("gmres_tol", ctypes.c_double),
     ]
 
 
 class MrcmInfo(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_int32), ("local_sweeps_max", ctypes.c_int32),
-                ("iface_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("iface_sweeps", ctypes.c_int32), ("gmres_iters", ctypes.c_int32),
                 ("local_resid_max", ctypes.c_double), ("iface_resid", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -103,6 +110,12 @@ def lib(path: Optional[Path] = None):
     L.mrcm_version.restype = i32
     L.mrcm_local_solve_noalloc.argtypes = [i32, dp, dp, dp, dp, vp]
     L.mrcm_local_solve_noalloc.restype = i32
+    L.mrcm_uses_gmres.argtypes = [vp]
+    L.mrcm_uses_gmres.restype = i32
+    L.mrcm_num_precond_values.argtypes = [vp]
+    L.mrcm_num_precond_values.restype = i64
+    L.mrcm_set_precond_blocks.argtypes = [vp, dp]
+    L.mrcm_set_precond_blocks.restype = i32
     if path is None:
         _lib = L
     return L
@@ -131,6 +144,11 @@ class SolverOptions:
     ir_max: int = 30
     iface_tol: float = 1e-13
     iface_ir_max: int = 40
+    iface_solver: int = IFACE_AUTO
+    precond: int = PRECOND_BLOCK_JACOBI
+    gmres_restart: int = 40
+    gmres_max: int = 5000
+    gmres_tol: float = 0.0          # 0: iface_tol
 
 
 class Mrcm:
@@ -165,6 +183,9 @@ class Mrcm:
         d.prec = opts.prec
         d.ir_tol, d.ir_max = opts.ir_tol, opts.ir_max
         d.iface_tol, d.iface_ir_max = opts.iface_tol, opts.iface_ir_max
+        d.iface_solver, d.precond = opts.iface_solver, opts.precond
+        d.gmres_restart, d.gmres_max = opts.gmres_restart, opts.gmres_max
+        d.gmres_tol = opts.gmres_tol
         self.desc = d
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -216,6 +237,17 @@ class Mrcm:
 
     def num_gamma_values(self) -> int:
         return int(self.L.mrcm_num_gamma_values(self.ctx))
+
+    def uses_gmres(self) -> bool:
+        return bool(self.L.mrcm_uses_gmres(self.ctx))
+
+    def num_precond_values(self) -> int:
+        return int(self.L.mrcm_num_precond_values(self.ctx))
+
+    def mrcm_set_precond_blocks(self, blocks):
+        """Caller-supplied (learned) preconditioner blocks: contiguous FP64
+        CUDA tensor of num_precond_values() entries."""
+        self._check(self.L.mrcm_set_precond_blocks(self.ctx, _ptr(blocks)))
 
     def interface_solution(self):
         import torch

@@ -48,7 +48,8 @@ def _desc(mrcm, nx=64, ny=32, sub=16, prec=1, nU=2, nP=2, pure=0, bct=None):
     return d, keep
 
 
-@pytest.mark.parametrize("bad", ["nx", "sub", "prec", "nU", "pure_dirichlet", "null"])
+@pytest.mark.parametrize("bad", ["nx", "sub", "prec", "nU", "pure_dirichlet", "null", "solver",
+                                 "precond", "restart"])
 def test_setup_rejects_bad_descriptors(L, bad):
     from paper_2104_04653_gb300 import mrcm
     kw = {}
@@ -65,10 +66,14 @@ def test_setup_rejects_bad_descriptors(L, bad):
         bt[0] = 1
         kw = dict(pure=1, bct=bt)
     ctx = ctypes.c_void_p()
+    field = {"solver": ("iface_solver", 3), "precond": ("precond", -1),
+             "restart": ("gmres_restart", 65)}.get(bad)
     if bad == "null":
         st = L.mrcm_setup(None, None, ctypes.byref(ctx))
     else:
         d, keep = _desc(mrcm, **kw)
+        if field:
+            setattr(d, *field)
         st = L.mrcm_setup(ctypes.byref(d), None, ctypes.byref(ctx))
     assert st == mrcm.MRCM_EINVAL
     assert not ctx.value
