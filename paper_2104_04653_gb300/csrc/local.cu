@@ -19,11 +19,17 @@
 namespace mrcm {
 namespace {
 
-constexpr int kS = 16;      // subdomain edge handled by these kernels
-constexpr int kNC = 12;     // right-hand sides per CTA of the basis kernel
-// per-subdomain coefficient block: tW tE tS tN d kappa [S*S each], then
-// beta on the interface faces [4][S]
+constexpr int kS = 16;      // subdomain edge of the shared-memory-resident kernels
+constexpr int kNC = kNC16;  // right-hand sides per CTA of the basis kernel
+// per-subdomain coefficient block (at SubInfo::coef_off): tW tE tS tN d
+// kappa [S*S each], then beta on the interface faces [4][S]
 constexpr int kCoefStride = 6 * kS * kS + 4 * kS;
+
+// interface-function table of subdomain size S (RealInfo::fn_off)
+template <int S>
+__device__ __forceinline__ const double *fn_table(const DeviceTables &t) {
+  return t.fnval + (S == 16 ? 0 : 16 * 16);
+}
 
 __device__ __forceinline__ void atomic_max_pos_double(double *addr, double v) {
   // valid for v >= 0: IEEE order of non-negative doubles matches their bits
@@ -35,24 +41,24 @@ __device__ __forceinline__ void atomic_max_pos_double(double *addr, double v) {
 // Transmissibilities of the four faces of local cell (a, b) of subdomain sb,
 // in the order W, E, S, N.  Two-point fluxes on square cells: harmonic mean
 // between cells, kappa/(alpha H/h + 1/2) on a Robin face, 2 kappa on a
-// Dirichlet face, 0 on a Neumann face.
-__device__ void face_T(const DeviceTables &t, const SubInfo &sb, const double *kap, int a,
-                       int b, double out[4]) {
-  const int S = kS;
-  const double kc = kap[b * S + a];
+// Dirichlet face, 0 on a Neumann face.  kn[side]: kappa of the neighbour
+// cell on that side when it lies inside the subdomain.
+template <int S>
+__device__ void face_T(const DeviceTables &t, const SubInfo &sb, double kc, const double kn[4],
+                       int a, int b, double out[4]) {
   const int nb_a[4] = {a - 1, a + 1, a, a};
   const int nb_b[4] = {b, b, b - 1, b + 1};
+  const double HoverH = static_cast<double>(S);   // H / h
 #pragma unroll
   for (int side = 0; side < 4; ++side) {
     const int na = nb_a[side], nbb = nb_b[side];
     double T;
     if (na >= 0 && na < S && nbb >= 0 && nbb < S) {
-      const double kn = kap[nbb * S + na];
-      T = 2.0 * kc * kn / (kc + kn);
+      T = 2.0 * kc * kn[side] / (kc + kn[side]);
     } else if (sb.edge_iface[side] >= 0) {
       const int e = (side < 2) ? b : a;
       const double al = t.alpha[t.iface[sb.edge_iface[side]].alpha_off + e];
-      T = kc / (al * t.H / t.h + 0.5);
+      T = kc / (al * HoverH + 0.5);
     } else {
       const int gi = sb.x0 + a, gj = sb.y0 + b;
       int k;
@@ -67,12 +73,13 @@ __device__ void face_T(const DeviceTables &t, const SubInfo &sb, const double *k
 }
 
 // ---------------------------------------------------------------------------
-// (a)+(b): one CTA per subdomain.  Stage 1 (all 256 threads, one cell each):
-// FP64 transmissibilities, Jacobi scaling and the scaled couplings.  Stage 2
-// (warp 0): the block LDL^T recursion S_j = D_j - E_{j-1} W_{j-1} E_{j-1} and
-// the Gauss-Jordan inverses W_j = S_j^{-1} in registers: lane l holds column
-// c = l % 16 and rows 8 (l / 16) + q, q < 8; pivots are exchanged with warp
-// shuffles, so the 256-step pivot chain has no block-wide barrier.
+// (a)+(b).  Stage 1 (one thread per cell): FP64 transmissibilities, Jacobi
+// scaling and the scaled couplings.  Stage 2 (one warp per subdomain): the
+// block LDL^T recursion S_j = D_j - E_{j-1} W_{j-1} E_{j-1} and the
+// Gauss-Jordan inverses W_j = S_j^{-1} in registers.  Lane l holds column
+// c = l % S and rows HL (l / S) .. + RPL - 1 of the current block (HL = 32/S
+// lanes per column, RPL = S / HL rows per lane); pivots are exchanged with
+// warp shuffles, so the S^2-step pivot chain has no block-wide barrier.
 template <typename T>
 __device__ __forceinline__ T shfl(T v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
@@ -80,11 +87,76 @@ __device__ __forceinline__ T shfl(T v, int src) {
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
+// Stage 2 for one subdomain, executed by one whole warp.  offx[cell]: scaled
+// coupling of (a,b) to (a+1,b); ecp[cell]: to (a,b+1).  Writes W_j to Wg.
+template <typename T, int S>
+__device__ __forceinline__ bool schur_inverses(int lane, const T *offx, const T *ecp, T *Wg) {
+  constexpr int N = S * S, HL = 32 / S, RPL = S / HL;
+  static_assert(HL * S == 32, "S must divide 32 lanes");
+  const int c = lane % S, h = lane / S;
+  T R[RPL];
+  bool bad = false;
+#pragma unroll 1
+  for (int j = 0; j < S; ++j) {
+    const T ec = j > 0 ? ecp[(j - 1) * S + c] : T(0);
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int r = RPL * h + q;
+      T v = T(0);
+      if (r == c) v = T(1);
+      else if (r - c == 1) v = offx[j * S + c];
+      else if (c - r == 1) v = offx[j * S + r];
+      if (j > 0) v -= ecp[(j - 1) * S + r] * ec * R[q];
+      R[q] = v;
+    }
+#pragma unroll
+    for (int p = 0; p < S; ++p) {
+      const int src = (p / RPL) * S;
+      const T rowv = shfl(R[p % RPL], src + c);
+      const T piv = shfl(R[p % RPL], src + p);
+      T colv[RPL];
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) colv[q] = shfl(R[q], h * S + p);
+      if (!(piv > T(0))) bad = true;
+      const T ip = recip(piv);
+      const T rv = rowv * ip;
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        const int r = RPL * h + q;
+        T nv = R[q] - colv[q] * rv;
+        nv = (c == p) ? -colv[q] * ip : nv;
+        nv = (r == p) ? ((c == p) ? ip : rv) : nv;
+        R[q] = nv;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) Wg[j * N + (RPL * h + q) * S + c] = R[q];
+  }
+  return bad;
+}
+
+// beta = alpha H / kappa on the interface faces of cell (a, b) (Eq. "beta")
+template <int S>
+__device__ __forceinline__ void write_beta(const DeviceTables &t, const SubInfo &sb, double kc,
+                                           int a, int b, double *coef) {
+  constexpr int N = S * S;
+  const bool onface[4] = {a == 0, a == S - 1, b == 0, b == S - 1};
+  const double H = S * t.h;
+#pragma unroll
+  for (int side = 0; side < 4; ++side) {
+    if (!onface[side] || sb.edge_iface[side] < 0) continue;
+    const int e = (side < 2) ? b : a;
+    const double al = t.alpha[t.iface[sb.edge_iface[side]].alpha_off + e];
+    coef[6 * N + side * S + e] = al * H / kc;
+  }
+}
+
+// s = 16: one CTA of 256 threads per subdomain.
 template <typename T>
 __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, const double *K,
                                                    const double *lam) {
   constexpr int S = kS, N = S * S;
-  const int g = blockIdx.x;
+  const int g = t.sub_by_size[blockIdx.x];
   const SubInfo sb = t.sub[g];
   const int tid = threadIdx.x;
   const int a = tid % S, b = tid / S;
@@ -98,72 +170,207 @@ __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, 
   if (!(kc > 0.0) || !isfinite(kc)) atomicOr(&w.status[0], MRCM_FLAG_NAN);
   kap[tid] = kc;
   __syncthreads();
+  double kn[4];
+  kn[0] = a > 0 ? kap[tid - 1] : 0.0;
+  kn[1] = a < S - 1 ? kap[tid + 1] : 0.0;
+  kn[2] = b > 0 ? kap[tid - S] : 0.0;
+  kn[3] = b < S - 1 ? kap[tid + S] : 0.0;
   double T4[4];
-  face_T(t, sb, kap, a, b, T4);
+  face_T<S>(t, sb, kc, kn, a, b, T4);
   const double d = 1.0 / sqrt(T4[0] + T4[1] + T4[2] + T4[3]);
-  double *coef = w.coef + static_cast<int64_t>(g) * kCoefStride;
+  double *coef = w.coef + sb.coef_off;
 #pragma unroll
   for (int k = 0; k < 4; ++k) coef[k * N + tid] = T4[k];
   coef[4 * N + tid] = d;
   coef[5 * N + tid] = kc;
-  {
-    // beta = alpha H / kappa on the interface faces of the cell (Eq. "beta")
-    const bool onface[4] = {a == 0, a == S - 1, b == 0, b == S - 1};
-#pragma unroll
-    for (int side = 0; side < 4; ++side) {
-      if (!onface[side] || sb.edge_iface[side] < 0) continue;
-      const int e = (side < 2) ? b : a;
-      const double al = t.alpha[t.iface[sb.edge_iface[side]].alpha_off + e];
-      coef[6 * N + side * S + e] = al * t.H / kc;
-    }
-  }
+  write_beta<S>(t, sb, kc, a, b, coef);
   dsc[tid] = d;
   __syncthreads();
   offx[tid] = static_cast<T>(a < S - 1 ? -T4[1] * d * dsc[tid + 1] : 0.0);
   ecp[tid] = static_cast<T>(b < S - 1 ? -T4[3] * d * dsc[tid + S] : 0.0);
   __syncthreads();
   if (tid >= 32) return;
-  const int lane = tid, c = lane & 15, h = lane >> 4;
-  T R[8];
-  T *Wg = static_cast<T *>(w.W) + static_cast<int64_t>(g) * S * N;
-  bool bad = false;
-#pragma unroll 1
-  for (int j = 0; j < S; ++j) {
-    const T ec = j > 0 ? ecp[(j - 1) * S + c] : T(0);
+  T *Wg = static_cast<T *>(w.W) + sb.w_off;
+  const bool bad = schur_inverses<T, S>(tid, offx, ecp, Wg);
+  if (__any_sync(0xffffffffu, bad) && tid == 0) atomicOr(&w.status[0], MRCM_FLAG_NOTSPD);
+}
+
+// s = 32: one WARP per subdomain (kFW subdomains per CTA), stage 1 with
+// N / 32 cells per lane, so that every resident warp works in stage 2.
+constexpr int kFW = 4;
+
+template <typename T, int S>
+struct FactorWarpSmem {
+  double dsc[S * S];
+  T offx[S * S];
+  T ecp[S * S];
+};
+
+template <typename T, int S>
+__global__ void __launch_bounds__(32 * kFW) k_factor_warp(DeviceTables t, Workspace w,
+                                                          const double *K, const double *lam,
+                                                          int first, int count) {
+  constexpr int N = S * S, CPL = N / 32;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int idx = blockIdx.x * kFW + wid;
+  if (idx >= count) return;     // whole warp; no CTA-wide barrier follows
+  FactorWarpSmem<T, S> &sm = reinterpret_cast<FactorWarpSmem<T, S> *>(smraw)[wid];
+  const int g = t.sub_by_size[first + idx];
+  const SubInfo sb = t.sub[g];
+  double *coef = w.coef + sb.coef_off;
+  const int64_t row0 = static_cast<int64_t>(sb.r) * t.ny + sb.y0;
+  auto kappa = [&](int a, int b) {
+    const int64_t cc = (row0 + b) * t.nx + sb.x0 + a;
+    return K[cc] * lam[cc];
+  };
+  bool nan = false;
+  for (int k = 0; k < CPL; ++k) {
+    const int cell = lane + 32 * k, a = cell % S, b = cell / S;
+    const double kc = kappa(a, b);
+    if (!(kc > 0.0) || !isfinite(kc)) nan = true;
+    double kn[4];
+    kn[0] = a > 0 ? kappa(a - 1, b) : 0.0;
+    kn[1] = a < S - 1 ? kappa(a + 1, b) : 0.0;
+    kn[2] = b > 0 ? kappa(a, b - 1) : 0.0;
+    kn[3] = b < S - 1 ? kappa(a, b + 1) : 0.0;
+    double T4[4];
+    face_T<S>(t, sb, kc, kn, a, b, T4);
+    const double d = 1.0 / sqrt(T4[0] + T4[1] + T4[2] + T4[3]);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int r = 8 * h + q;
-      T v = T(0);
-      if (r == c) v = T(1);
-      else if (r - c == 1) v = offx[j * S + c];
-      else if (c - r == 1) v = offx[j * S + r];
-      if (j > 0) v -= ecp[(j - 1) * S + r] * ec * R[q];
-      R[q] = v;
-    }
-#pragma unroll
-    for (int p = 0; p < S; ++p) {
-      const int src = (p >> 3) << 4;
-      const T rowv = shfl(R[p & 7], src + c);
-      const T piv = shfl(R[p & 7], src + p);
-      T colv[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) colv[q] = shfl(R[q], (h << 4) + p);
-      if (!(piv > T(0))) bad = true;
-      const T ip = recip(piv);
-      const T rv = rowv * ip;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int r = 8 * h + q;
-        T nv = R[q] - colv[q] * rv;
-        nv = (c == p) ? -colv[q] * ip : nv;
-        nv = (r == p) ? ((c == p) ? ip : rv) : nv;
-        R[q] = nv;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) Wg[j * N + (8 * h + q) * S + c] = R[q];
+    for (int q = 0; q < 4; ++q) coef[q * N + cell] = T4[q];
+    coef[4 * N + cell] = d;
+    coef[5 * N + cell] = kc;
+    write_beta<S>(t, sb, kc, a, b, coef);
+    sm.dsc[cell] = d;
   }
+  if (__any_sync(0xffffffffu, nan) && lane == 0) atomicOr(&w.status[0], MRCM_FLAG_NAN);
+  __syncwarp();
+  for (int k = 0; k < CPL; ++k) {
+    const int cell = lane + 32 * k, a = cell % S, b = cell / S;
+    const double d = sm.dsc[cell];
+    sm.offx[cell] = static_cast<T>(a < S - 1 ? -coef[N + cell] * d * sm.dsc[cell + 1] : 0.0);
+    sm.ecp[cell] = static_cast<T>(b < S - 1 ? -coef[3 * N + cell] * d * sm.dsc[cell + S] : 0.0);
+  }
+  __syncwarp();
+  T *Wg = static_cast<T *>(w.W) + sb.w_off;
+  const bool bad = schur_inverses<T, S>(lane, sm.offx, sm.ecp, Wg);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&w.status[0], MRCM_FLAG_NOTSPD);
+}
+
+
+// Right-hand side of one basis column at cell (a, b), FP64: the particular
+// column carries the sources q h^2 and the physical boundary data (2 kappa
+// p_b on a Dirichlet face, -u_b h on a Neumann face); a basis column carries
+// T_R g on its own edge, g = -beta sigma phi_k(e) for a flux function and
+// psi_k(e) for a pressure function (Eq. "mrc1").
+template <int S>
+__device__ __forceinline__ double rhs_value(const DeviceTables &t, const SubInfo &sb,
+                                            const double *coef, const double *q,
+                                            const ColInfo &ci, int a, int b) {
+  constexpr int N = S * S;
+  const int tid = b * S + a;
+  const int gi = sb.x0 + a, gj = sb.y0 + b;
+  const double h = t.h;
+  double val = 0.0;
+  if (ci.unk < 0) {
+    const int64_t cell = (static_cast<int64_t>(sb.r) * t.ny + gj) * t.nx + gi;
+    val = q[cell] * h * h;
+    const bool onface[4] = {a == 0, a == S - 1, b == 0, b == S - 1};
+#pragma unroll
+    for (int side = 0; side < 4; ++side) {
+      if (!onface[side] || sb.edge_iface[side] >= 0) continue;
+      int k;
+      if (side == kEdgeW) k = gj;
+      else if (side == kEdgeE) k = t.ny + gj;
+      else if (side == kEdgeS) k = 2 * t.ny + gi;
+      else k = 2 * t.ny + t.nx + gi;
+      if (t.bc_type[k] == 1) val += coef[side * N + tid] * t.bc_val[k];
+      else val -= t.bc_val[k] * h;
+    }
+  } else {
+    const int side = ci.edge;
+    const bool adj = (side == kEdgeW && a == 0) || (side == kEdgeE && a == S - 1) ||
+                     (side == kEdgeS && b == 0) || (side == kEdgeN && b == S - 1);
+    if (adj) {
+      const int e = (side < 2) ? b : a;
+      const double fv = fn_table<S>(t)[ci.fn * S + e];
+      double gval;
+      if (ci.is_u) {
+        const double beta = coef[6 * N + side * S + e];
+        const double sigma = (side == kEdgeE || side == kEdgeN) ? 1.0 : -1.0;
+        gval = -beta * sigma * fv;
+      } else {
+        gval = fv;
+      }
+      val = coef[side * N + tid] * gval;
+    }
+  }
+  return val;
+}
+
+// One-sided traces of the finished columns on every interface edge face,
+//   u(e) = T_R (p_c - g_e)/h,  p_face(e) = g_e + beta_e u(e),
+// then this side's share of the rows of G (Eq. "mrc2"):
+//   U rows: sigma * sum_e h phi_k(e) p_face(e)    (pressure continuity)
+//   P rows: sum_e h psi_k(e) u(e)                 (flux continuity)
+// x: column c of the CTA at x + c S^2 (FP64).  All threads of the CTA.
+template <int S, int NCMAX>
+__device__ __forceinline__ void traces_and_rows(const DeviceTables &t, const Workspace &w,
+                                                const SubInfo &sb, const double *coef,
+                                                const ColInfo *col, const double *x, int c0,
+                                                int nc, double (*su)[S][NCMAX],
+                                                double (*sp)[S][NCMAX]) {
+  constexpr int N = S * S;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const double h = t.h, inv_h = t.inv_h;
+  const double *fnt = fn_table<S>(t);
+  for (int q = tid; q < 4 * S * nc; q += nthr) {
+    const int side = q / (S * nc), e = (q / nc) % S, c = q % nc;
+    if (sb.edge_iface[side] < 0) continue;
+    int la, lb;
+    if (side == kEdgeW) { la = 0; lb = e; }
+    else if (side == kEdgeE) { la = S - 1; lb = e; }
+    else if (side == kEdgeS) { la = e; lb = 0; }
+    else { la = e; lb = S - 1; }
+    const int cl = lb * S + la;
+    const double TR = coef[side * N + cl];
+    const double beta = coef[6 * N + side * S + e];
+    const ColInfo ci = col[c];
+    double ge = 0.0;
+    if (ci.edge == side) {
+      const double fv = fnt[ci.fn * S + e];
+      const double sigma = (side == kEdgeE || side == kEdgeN) ? 1.0 : -1.0;
+      ge = ci.is_u ? -beta * sigma * fv : fv;
+    }
+    const double u = TR * inv_h * (x[c * N + cl] - ge);
+    su[side][e][c] = u;
+    sp[side][e][c] = ge + beta * u;
+  }
+  __syncthreads();
+  double *G = w.G + sb.g_off;
+  const int nrow = sb.nrows;
+  for (int pr = tid; pr < nrow * nc; pr += nthr) {
+    const int row = pr / nc, c = pr % nc;
+    int side = 0;
+    while (side < 3 && !(sb.edge_iface[side] >= 0 && row >= sb.edge_row[side] &&
+                         row < sb.edge_row[side] + t.iface[sb.edge_iface[side]].nU +
+                                   t.iface[sb.edge_iface[side]].nP))
+      ++side;
+    const int nU = t.iface[sb.edge_iface[side]].nU;
+    const int k = row - sb.edge_row[side];
+    const bool urow = k < nU;
+    const double *fn = fnt + (urow ? k : k - nU) * S;
+    double acc = 0.0;
+    if (urow) {
+      for (int e = 0; e < S; ++e) acc += fn[e] * sp[side][e][c];
+      acc *= (side == kEdgeE || side == kEdgeN) ? h : -h;
+    } else {
+      for (int e = 0; e < S; ++e) acc += fn[e] * su[side][e][c];
+      acc *= h;
+    }
+    G[static_cast<int64_t>(row) * sb.ncols + c0 + c] = acc;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -268,9 +475,9 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
 
   // stage W_j, the coefficients and the column descriptors
   {
-    const T *Wg = static_cast<const T *>(w.W) + static_cast<int64_t>(g) * S * N;
+    const T *Wg = static_cast<const T *>(w.W) + sb.w_off;
     for (int k = tid; k < S * N; k += N) sm.Ws[k] = Wg[k];
-    const double *coef = w.coef + static_cast<int64_t>(g) * kCoefStride;
+    const double *coef = w.coef + sb.coef_off;
     for (int k = tid; k < kCoefStride; k += N) sm.coef[k] = coef[k];
     if (tid < nc) sm.col[tid] = t.col[sb.col_off + it.c0 + tid];
   }
@@ -282,7 +489,6 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
 
   // right-hand sides (FP64)
   const double myT[4] = {tWs[tid], tEs[tid], tSs[tid], tNs[tid]};
-  const int gi = sb.x0 + a, gj = sb.y0 + b;
   const double dsl = ds[tid];
   const float dsf = static_cast<float>(dsl);
   const double mydiag = myT[0] + myT[1] + myT[2] + myT[3];
@@ -291,42 +497,7 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   for (int c = 0; c < kNC; ++c) {
     bnl[c] = 0.0f;
     if (c >= nc) continue;
-    const ColInfo ci = sm.col[c];
-    double val = 0.0;
-    if (ci.unk < 0) {
-      const int64_t cell = (static_cast<int64_t>(sb.r) * t.ny + gj) * t.nx + gi;
-      val = q[cell] * h * h;
-      // physical faces of this cell
-      const bool onface[4] = {a == 0, a == S - 1, b == 0, b == S - 1};
-#pragma unroll
-      for (int side = 0; side < 4; ++side) {
-        if (!onface[side] || sb.edge_iface[side] >= 0) continue;
-        int k;
-        if (side == kEdgeW) k = gj;
-        else if (side == kEdgeE) k = t.ny + gj;
-        else if (side == kEdgeS) k = 2 * t.ny + gi;
-        else k = 2 * t.ny + t.nx + gi;
-        if (t.bc_type[k] == 1) val += sm.coef[side * N + tid] * t.bc_val[k];
-        else val -= t.bc_val[k] * h;
-      }
-    } else {
-      const int side = ci.edge;
-      const bool adj = (side == kEdgeW && a == 0) || (side == kEdgeE && a == S - 1) ||
-                       (side == kEdgeS && b == 0) || (side == kEdgeN && b == S - 1);
-      if (adj) {
-        const int e = (side < 2) ? b : a;
-        const double fv = t.fnval[ci.fn * t.fn_stride + e];
-        double gval;
-        if (ci.is_u) {
-          const double beta = sm.coef[6 * N + side * S + e];
-          const double sigma = (side == kEdgeE || side == kEdgeN) ? 1.0 : -1.0;
-          gval = -beta * sigma * fv;
-        } else {
-          gval = fv;
-        }
-        val = sm.coef[side * N + tid] * gval;
-      }
-    }
+    const double val = rhs_value<S>(t, sb, sm.coef, q, sm.col[c], a, b);
     sm.bb[c * N + tid] = val;
     sm.x[c * N + tid] = 0.0;
     const T zv = static_cast<T>(dsl * val);
@@ -396,94 +567,272 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   double *bas = w.basis + sb.basis_off;
   for (int c = 0; c < nc; ++c) bas[static_cast<int64_t>(it.c0 + c) * N + tid] = sm.x[c * N + tid];
 
-  // one-sided traces on every interface edge face, per column:
-  //   u(e) = T_R (p_c - g_e)/h,  p_face(e) = g_e + beta_e u(e)
-  const double inv_h = t.inv_h;
-  for (int q = tid; q < 4 * S * nc; q += N) {
-    const int side = q / (S * nc), e = (q / nc) % S, c = q % nc;
-    if (sb.edge_iface[side] < 0) continue;
-    int la, lb;
-    if (side == kEdgeW) { la = 0; lb = e; }
-    else if (side == kEdgeE) { la = S - 1; lb = e; }
-    else if (side == kEdgeS) { la = e; lb = 0; }
-    else { la = e; lb = S - 1; }
-    const int cl = lb * S + la;
-    const double TR = sm.coef[side * N + cl];
-    const double beta = sm.coef[6 * N + side * S + e];
-    const ColInfo ci = sm.col[c];
-    double ge = 0.0;
-    if (ci.edge == side) {
-      const double fv = t.fnval[ci.fn * t.fn_stride + e];
-      const double sigma = (side == kEdgeE || side == kEdgeN) ? 1.0 : -1.0;
-      ge = ci.is_u ? -beta * sigma * fv : fv;
-    }
-    const double u = TR * inv_h * (sm.x[c * N + cl] - ge);
-    sm.su[side][e][c] = u;
-    sm.sp[side][e][c] = ge + beta * u;
-  }
+  traces_and_rows<S, kNC>(t, w, sb, sm.coef, sm.col, sm.x, it.c0, nc, sm.su, sm.sp);
+}
+
+// ---------------------------------------------------------------------------
+// (c) for s = 32.  The S inverse Schur blocks (S^3 values) do not fit in
+// shared memory next to the right-hand sides, so W_j is streamed through a
+// double buffer, one block per solve step (prefetched during the step
+// before), and the FP64 iterate lives in the basis array itself: each
+// thread owns one cell of every column of the CTA.  Each 32-term row of a
+// W_j product is split over kKS threads and summed with shuffles.
+constexpr int kS32 = 32, kKS = 4;
+constexpr int kWst = kS32 + kKS;     // padded W row stride: conflict-free reads
+static_assert(kKS * kS32 * kNC32 == kS32 * kS32, "one thread per (split, row, column)");
+
+template <typename T>
+struct BasisSmem32 {
+  T Wb[2][kS32 * kWst];
+  T ec[kS32 * kS32];
+  T z[kNC32 * kS32 * kS32];
+  T v[kNC32 * kS32 * kS32];
+  double su[4][kS32][kNC32];
+  double sp[4][kS32][kNC32];
+  float redf[kNC32][kS32 * kS32 / 32];
+  float bnf[kNC32];
+  float rnf[kNC32];
+  float rel2;
+  ColInfo col[kNC32];
+};
+
+template <typename T>
+__device__ void block_solve32(BasisSmem32<T> &sm, const T *Wg, int nc) {
+  constexpr int S = kS32, N = S * S, NSTEP = 2 * S - 1;
+  const int tid = threadIdx.x;
+  const int ks = tid % kKS, o = tid / kKS, a = o % S, c = o / S;
+  const bool act = c < nc;            // uniform over a warp (c = tid / 128)
+  const int wrow = (tid / S) * kWst + tid % S;
+  sm.Wb[0][wrow] = Wg[tid];
   __syncthreads();
-  // rows of G (Eq. "mrc2"), this side's share:
-  //   U rows: sigma * sum_e h phi_k(e) p_face(e)    (pressure continuity)
-  //   P rows: sum_e h psi_k(e) u(e)                 (flux continuity)
-  double *G = w.G + sb.g_off;
-  const int nrow = sb.nrows;
-  for (int pr = tid; pr < nrow * nc; pr += N) {
-    const int row = pr / nc, c = pr % nc;
-    int side = 0;
-    while (side < 3 && !(sb.edge_iface[side] >= 0 && row >= sb.edge_row[side] &&
-                         row < sb.edge_row[side] + t.iface[sb.edge_iface[side]].nU +
-                                   t.iface[sb.edge_iface[side]].nP))
-      ++side;
-    const int nU = t.iface[sb.edge_iface[side]].nU;
-    const int k = row - sb.edge_row[side];
-    const bool urow = k < nU;
-    const double *fn = t.fnval + (urow ? k : k - nU) * t.fn_stride;
-    double acc = 0.0;
-    if (urow) {
-      for (int e = 0; e < S; ++e) acc += fn[e] * sm.sp[side][e][c];
-      acc *= (side == kEdgeE || side == kEdgeN) ? h : -h;
-    } else {
-      for (int e = 0; e < S; ++e) acc += fn[e] * sm.su[side][e][c];
-      acc *= h;
+  int buf = 0;
+  for (int k = 0; k < NSTEP; ++k) {
+    const int j = k < S ? k : 2 * S - 2 - k;
+    T nextw = T(0);
+    if (k + 1 < NSTEP) {
+      const int jn = k + 1 < S ? k + 1 : 2 * S - 3 - k;
+      nextw = Wg[static_cast<int64_t>(jn) * N + tid];
     }
-    G[static_cast<int64_t>(row) * sb.ncols + it.c0 + c] = acc;
+    const T *Wj = sm.Wb[buf] + a * kWst;
+    T acc = T(0);
+    if (act) {
+      if (k < S) {
+        // forward: v_j = W_j (z_j - e_{j-1} v_{j-1})
+        const T *zj = sm.z + c * N + j * S;
+        if (j == 0) {
+#pragma unroll
+          for (int q = 0; q < S / kKS; ++q) {
+            const int bq = ks + kKS * q;
+            acc += Wj[bq] * zj[bq];
+          }
+        } else {
+          const T *vp = sm.v + c * N + (j - 1) * S;
+          const T *ep = sm.ec + (j - 1) * S;
+#pragma unroll
+          for (int q = 0; q < S / kKS; ++q) {
+            const int bq = ks + kKS * q;
+            acc += Wj[bq] * (zj[bq] - ep[bq] * vp[bq]);
+          }
+        }
+      } else {
+        // backward: y_j = v_j - W_j (e_j y_{j+1})
+        const T *yn = sm.v + c * N + (j + 1) * S;
+        const T *ep = sm.ec + j * S;
+#pragma unroll
+        for (int q = 0; q < S / kKS; ++q) {
+          const int bq = ks + kKS * q;
+          acc += Wj[bq] * (ep[bq] * yn[bq]);
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 1; m < kKS; m <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+    if (act && ks == 0) {
+      if (k < S) sm.v[c * N + j * S + a] = acc;
+      else sm.v[c * N + j * S + a] -= acc;
+    }
+    if (k + 1 < NSTEP) sm.Wb[buf ^ 1][wrow] = nextw;
+    __syncthreads();
+    buf ^= 1;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kS32 *kS32, 1) k_basis32(DeviceTables t, Workspace w,
+                                                           const BasisItem *items,
+                                                           const double *q, double tol,
+                                                           int ir_max) {
+  constexpr int S = kS32, N = S * S, NC = kNC32, NW = N / 32;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  BasisSmem32<T> &sm = *reinterpret_cast<BasisSmem32<T> *>(smraw);
+  const BasisItem it = items[blockIdx.x];
+  const SubInfo sb = t.sub[it.sub];
+  const int nc = it.nc;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int a = tid % S, b = tid / S;
+  const T *Wg = static_cast<const T *>(w.W) + sb.w_off;
+  const double *coef = w.coef + sb.coef_off;
+  double *X = w.basis + sb.basis_off + static_cast<int64_t>(it.c0) * N;
+  if (tid < nc) sm.col[tid] = t.col[sb.col_off + it.c0 + tid];
+  const double myT[4] = {coef[tid], coef[N + tid], coef[2 * N + tid], coef[3 * N + tid]};
+  const double dsl = coef[4 * N + tid];
+  const float dsf = static_cast<float>(dsl);
+  const double mydiag = myT[0] + myT[1] + myT[2] + myT[3];
+  sm.ec[tid] = b < S - 1 ? static_cast<T>(-myT[3] * dsl * coef[4 * N + tid + S]) : T(0);
+  __syncthreads();
+
+  auto col_sums = [&](const float *val, float *out) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (c < nc) {
+        float s2 = val[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        if (lane == 0) sm.redf[c][wid] = s2;
+      }
+    }
+    __syncthreads();
+    if (tid < nc) {
+      float s2 = 0.0f;
+      for (int k = 0; k < NW; ++k) s2 += sm.redf[tid][k];
+      out[tid] = s2;
+    }
+    __syncthreads();
+  };
+
+  double bb[NC];
+  float bnl[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    bb[c] = 0.0;
+    bnl[c] = 0.0f;
+    if (c >= nc) continue;
+    const double val = rhs_value<S>(t, sb, coef, q, sm.col[c], a, b);
+    bb[c] = val;
+    X[c * N + tid] = 0.0;
+    const T zv = static_cast<T>(dsl * val);
+    sm.z[c * N + tid] = zv;
+    bnl[c] = static_cast<float>(zv) * static_cast<float>(zv);
+  }
+  col_sums(bnl, sm.bnf);
+
+  const float tol2 = static_cast<float>(tol) * static_cast<float>(tol);
+  int sweep = 0;
+  float prev2 = 3e38f, rel2 = 0.0f;
+  for (;;) {
+    block_solve32(sm, Wg, nc);
+    for (int c = 0; c < nc; ++c) {
+      if (sizeof(T) == sizeof(float))
+        X[c * N + tid] += static_cast<double>(dsf * static_cast<float>(sm.v[c * N + tid]));
+      else
+        X[c * N + tid] += dsl * static_cast<double>(sm.v[c * N + tid]);
+    }
+    __syncthreads();
+    if (sweep >= ir_max) break;
+    // FP64 residual r = b - A x, the neighbours' x from the basis array
+    float rn[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      rn[c] = 0.0f;
+      if (c >= nc) continue;
+      const double *xc = X + c * N;
+      double r = fma(-mydiag, xc[tid], bb[c]);
+      if (a > 0) r = fma(myT[0], xc[tid - 1], r);
+      if (a < S - 1) r = fma(myT[1], xc[tid + 1], r);
+      if (b > 0) r = fma(myT[2], xc[tid - S], r);
+      if (b < S - 1) r = fma(myT[3], xc[tid + S], r);
+      T zv;
+      if (sizeof(T) == sizeof(float)) zv = static_cast<T>(static_cast<float>(r) * dsf);
+      else zv = static_cast<T>(dsl * r);
+      sm.z[c * N + tid] = zv;
+      rn[c] = static_cast<float>(zv) * static_cast<float>(zv);
+    }
+    col_sums(rn, sm.rnf);
+    if (tid < 32) {
+      float rr = 0.0f;
+      if (tid < nc) rr = sm.bnf[tid] > 0.0f ? sm.rnf[tid] / sm.bnf[tid] : 0.0f;
+      if (rr != rr) rr = 3e38f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rr = fmaxf(rr, __shfl_xor_sync(0xffffffffu, rr, o));
+      if (tid == 0) sm.rel2 = rr;
+    }
+    __syncthreads();
+    rel2 = sm.rel2;
+    ++sweep;
+    if (rel2 <= tol2) break;
+    if (sweep > 2 && rel2 > 0.25f * prev2) break;  // stalled
+    prev2 = rel2;
+  }
+  if (tid == 0 && ir_max > 0) {
+    const double rel = sqrt(static_cast<double>(rel2));
+    atomicMax(&w.status[1], sweep);
+    atomic_max_pos_double(&w.dstat[0], rel);
+    if (!(rel <= 1e3 * tol)) atomicOr(&w.status[0], MRCM_FLAG_LOCAL_STALL);
+  }
+  traces_and_rows<S, NC>(t, w, sb, coef, sm.col, X, it.c0, nc, sm.su, sm.sp);
 }
 
 }  // namespace
 
 cudaError_t launch_factor(const DeviceTables &t, const Workspace &w, int prec, const double *K,
                           const double *lam, cudaStream_t st) {
-  if (t.s != kS) return cudaErrorInvalidValue;
-  if (prec == MRCM_PREC_FP64)
-    k_factor<double><<<t.nsub, kS * kS, 0, st>>>(t, w, K, lam);
-  else
-    k_factor<float><<<t.nsub, kS * kS, 0, st>>>(t, w, K, lam);
+  const int n16 = t.nsub16, n32 = t.nsub - t.nsub16;
+  if (n16 > 0) {
+    if (prec == MRCM_PREC_FP64)
+      k_factor<double><<<n16, kS * kS, 0, st>>>(t, w, K, lam);
+    else
+      k_factor<float><<<n16, kS * kS, 0, st>>>(t, w, K, lam);
+  }
+  if (n32 > 0) {
+    const int grid = (n32 + kFW - 1) / kFW;
+    if (prec == MRCM_PREC_FP64)
+      k_factor_warp<double, 32><<<grid, 32 * kFW, kFW * sizeof(FactorWarpSmem<double, 32>), st>>>(
+          t, w, K, lam, n16, n32);
+    else
+      k_factor_warp<float, 32><<<grid, 32 * kFW, kFW * sizeof(FactorWarpSmem<float, 32>), st>>>(
+          t, w, K, lam, n16, n32);
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t launch_basis_t(const DeviceTables &t, const Workspace &w,
-                                  const BasisItem *items, int nitems, const double *q,
+                                  const BasisItem *items, int n16, int n32, const double *q,
                                   double tol, int ir_max, cudaStream_t st) {
-  k_basis<T><<<nitems, kS * kS, sizeof(BasisSmem<T>), st>>>(t, w, items, q, tol, ir_max);
+  if (n16 > 0)
+    k_basis<T><<<n16, kS * kS, sizeof(BasisSmem<T>), st>>>(t, w, items, q, tol, ir_max);
+  if (n32 > 0)
+    k_basis32<T><<<n32, kS32 * kS32, sizeof(BasisSmem32<T>), st>>>(t, w, items + n16, q, tol,
+                                                                    ir_max);
   return cudaGetLastError();
 }
 
 cudaError_t init_local_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_basis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(sizeof(BasisSmem<float>)));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_basis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(sizeof(BasisSmem<double>)));
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_basis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(sizeof(BasisSmem<float>)))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_basis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(sizeof(BasisSmem<double>)))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_basis32<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(sizeof(BasisSmem32<float>)))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_basis32<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(sizeof(BasisSmem32<double>)))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_factor_warp<float, 32>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kFW * sizeof(FactorWarpSmem<float, 32>)))) !=
+          cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_factor_warp<double, 32>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kFW * sizeof(FactorWarpSmem<double, 32>)));
 }
 
 cudaError_t launch_basis(const DeviceTables &t, const Workspace &w, int prec,
-                         const BasisItem *items, int nitems, const double *q, double ir_tol,
-                         int ir_max, cudaStream_t st) {
-  if (t.s != kS) return cudaErrorInvalidValue;
-  if (prec == MRCM_PREC_FP64) return launch_basis_t<double>(t, w, items, nitems, q, ir_tol, 0, st);
-  return launch_basis_t<float>(t, w, items, nitems, q, ir_tol, ir_max, st);
+                         const BasisItem *items, int nitems16, int nitems32, const double *q,
+                         double ir_tol, int ir_max, cudaStream_t st) {
+  if (prec == MRCM_PREC_FP64)
+    return launch_basis_t<double>(t, w, items, nitems16, nitems32, q, ir_tol, 0, st);
+  return launch_basis_t<float>(t, w, items, nitems16, nitems32, q, ir_tol, ir_max, st);
 }
 
 }  // namespace mrcm

@@ -22,7 +22,6 @@ struct mrcm_ctx {
   int dev = 0;
   cudaStream_t stream = nullptr;
   int prec = 0;
-  int S = 16;
   int state = 0;           // 0 set up, 1 factored, 2 basis, 3 interface solved
   int launches = 0;
   std::string err;
@@ -31,7 +30,11 @@ struct mrcm_ctx {
   std::vector<IfaceInfo> iface;
   std::vector<ColInfo> col;
   std::vector<RealInfo> real;
-  std::vector<BasisItem> items;
+  std::vector<BasisItem> items;            // s = 16 subdomains' CTAs first
+  int nitems16 = 0;
+  std::vector<int> sub_by_size;
+  int nsub16 = 0, smax = 16;
+  int64_t coef_elems = 0, w_elems = 0, alpha_elems = 0;
   std::vector<int> unk_iface, unk_slabpos, pos2unk;
   std::vector<int> slab_if, slab_if_off;   // interfaces of every (realisation, slab)
   int mmax = 1, nslab_max = 0, bmax_max = 0, nlev_max = 0;
@@ -70,6 +73,11 @@ struct mrcm_ctx {
 static thread_local std::string g_setup_err;
 
 static int d_nreal(const mrcm_ctx *c) { return c->d.n_real; }
+
+// subdomain sizes present (one launch each for factor, basis, reconstruct)
+static int n_sizes(const mrcm_ctx *c) {
+  return (c->nsub16 > 0 ? 1 : 0) + (static_cast<int>(c->sub.size()) > c->nsub16 ? 1 : 0);
+}
 
 static mrcm_status fail(mrcm_ctx *c, mrcm_status s, const char *fmt, ...) {
   char buf[512];
@@ -132,13 +140,10 @@ static mrcm_status validate(const mrcm_desc *d) {
     return fail(nullptr, MRCM_EINVAL, "gmres_restart must be in 0..%d", kGmKmax);
   if (d->gmres_max < 0 || !(d->gmres_tol >= 0.0))
     return fail(nullptr, MRCM_EINVAL, "gmres_max and gmres_tol must be >= 0");
-  const int s0 = d->sub_size[0];
   for (int r = 0; r < d->n_real; ++r) {
     const int s = d->sub_size[r];
-    if (s != 16)
-      return fail(nullptr, MRCM_EINVAL, "subdomain size %d not supported (16 only)", s);
-    if (s != s0)
-      return fail(nullptr, MRCM_EINVAL, "mixed subdomain sizes across realisations not supported");
+    if (s != 16 && s != 32)
+      return fail(nullptr, MRCM_EINVAL, "subdomain size %d not supported (16 or 32)", s);
     if (d->nx % s || d->ny % s)
       return fail(nullptr, MRCM_EINVAL, "grid %dx%d not divisible by subdomain size %d", d->nx,
                   d->ny, s);
@@ -156,15 +161,24 @@ static mrcm_status validate(const mrcm_desc *d) {
 
 static mrcm_status build_tables(mrcm_ctx *c) {
   const mrcm_desc &d = c->d;
-  const int S = c->S;
   const double h = d.ly / d.ny;
   int nsub_tot = 0, nif_tot = 0, unk_tot = 0;
   int64_t alpha_off = 0, gam_off = 0, slab_off = 0, xy_off = 0, vec_off = 0;
-  int64_t basis_off = 0, g_off = 0, tsc_off = 0;
+  int64_t basis_off = 0, g_off = 0, tsc_off = 0, coef_off = 0, w_off = 0;
   int col_off = 0;
+  std::vector<BasisItem> items32;
+  std::vector<int> subs32;
+  int nslab_all = 1;   // slabs run along the longer side (the same for every s)
   for (int r = 0; r < d.n_real; ++r) {
+    const int sx = d.nx / d.sub_size[r], sy = d.ny / d.sub_size[r];
+    nslab_all = std::max(nslab_all, sx >= sy ? sx : sy);
+  }
+  for (int r = 0; r < d.n_real; ++r) {
+    const int S = d.sub_size[r];
+    c->smax = std::max(c->smax, S);
     RealInfo ri{};
     ri.s = S;
+    ri.fn_off = S == 16 ? 0 : 16 * 16;
     ri.Sx = d.nx / S;
     ri.Sy = d.ny / S;
     ri.sub0 = nsub_tot;
@@ -202,6 +216,7 @@ static mrcm_status build_tables(mrcm_ctx *c) {
                     nif_tot + g, S);
       if (d.pure_neumann && fi.nP < 1)
         return fail(nullptr, MRCM_EINVAL, "pure_neumann needs nP >= 1 on every interface");
+      fi.s = S;
       fi.unk = unk_tot;
       unk_tot += fi.nU + fi.nP;
       fi.alpha_off = alpha_off;
@@ -227,6 +242,7 @@ static mrcm_status build_tables(mrcm_ctx *c) {
         sb.J = J;
         sb.x0 = I * S;
         sb.y0 = J * S;
+        sb.s = S;
         const int ifW = (I > 0) ? ri.iface0 + J * (ri.Sx - 1) + (I - 1) : -1;
         const int ifE = (I < ri.Sx - 1) ? ri.iface0 + J * (ri.Sx - 1) + I : -1;
         const int ifS = (J > 0) ? ri.iface0 + nV + (J - 1) * ri.Sx + I : -1;
@@ -255,16 +271,35 @@ static mrcm_status build_tables(mrcm_ctx *c) {
         basis_off += static_cast<int64_t>(ncol) * S * S;
         sb.g_off = g_off;
         g_off += static_cast<int64_t>(nrow) * ncol;
+        sb.coef_off = coef_off;
+        coef_off += 6 * S * S + 4 * S;
+        sb.w_off = w_off;
+        w_off += static_cast<int64_t>(S) * S * S;
         const int gid = static_cast<int>(c->sub.size());
-        for (int c0 = 0; c0 < ncol; c0 += 12)
-          c->items.push_back(BasisItem{gid, c0, (ncol - c0) < 12 ? (ncol - c0) : 12});
+        if (S == 16) {
+          for (int c0 = 0; c0 < ncol; c0 += kNC16)
+            c->items.push_back(BasisItem{gid, c0, (ncol - c0) < kNC16 ? (ncol - c0) : kNC16});
+          c->sub_by_size.push_back(gid);
+        } else {
+          // balanced chunks of at most kNC32 columns
+          const int nch = (ncol + kNC32 - 1) / kNC32;
+          for (int k = 0; k < nch; ++k) {
+            const int c0 = ncol * k / nch, c1 = ncol * (k + 1) / nch;
+            items32.push_back(BasisItem{gid, c0, c1 - c0});
+          }
+          subs32.push_back(gid);
+        }
         c->sub.push_back(sb);
       }
     // slabs: block-tridiagonal grouping of the interfaces
+    // Every realisation gets the batch's largest slab count (the direct
+    // interface kernels take one slab count per launch); slabs past the
+    // realisation's own count are empty: identity rows, no coupling.
     const bool xdir = ri.Sx >= ri.Sy;
-    ri.nslab = xdir ? ri.Sx : ri.Sy;
+    const int nat = xdir ? ri.Sx : ri.Sy;
+    ri.nslab = nslab_all;
     std::vector<std::vector<int>> slabs(ri.nslab);
-    for (int k = 0; k < ri.nslab; ++k) {
+    for (int k = 0; k < nat; ++k) {
       if (xdir) {
         for (int J = 0; J < ri.Sy - 1; ++J) slabs[k].push_back(ri.iface0 + nV + J * ri.Sx + k);
         if (k < ri.Sx - 1)
@@ -314,6 +349,13 @@ static mrcm_status build_tables(mrcm_ctx *c) {
   }
   c->slab_if_off.push_back(static_cast<int>(c->slab_if.size()));
   c->nunk = unk_tot;
+  c->nitems16 = static_cast<int>(c->items.size());
+  c->items.insert(c->items.end(), items32.begin(), items32.end());
+  c->nsub16 = static_cast<int>(c->sub_by_size.size());
+  c->sub_by_size.insert(c->sub_by_size.end(), subs32.begin(), subs32.end());
+  c->coef_elems = coef_off;
+  c->w_elems = w_off;
+  c->alpha_elems = alpha_off;
   if (d.iface_solver == MRCM_IFACE_GMRES) c->use_gmres = true;
   if (c->use_gmres) {
     // no slab blocks on the GMRES path
@@ -570,7 +612,6 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   mrcm_ctx *c = new mrcm_ctx();
   c->d = *desc;
   c->prec = desc->prec;
-  c->S = desc->sub_size[0];
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   st = build_tables(c);
   if (st != MRCM_OK) {
@@ -604,16 +645,17 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     }
   }
   const mrcm_desc &d = c->d;
-  const int S = c->S;
-  const int N = S * S;
   const size_t esz = c->prec == MRCM_PREC_FP64 ? sizeof(double) : sizeof(float);
   const int nsub = static_cast<int>(c->sub.size());
   const int nif = static_cast<int>(c->iface.size());
   const int nunk = c->nunk;
   const int nb = 2 * d.nx + 2 * d.ny;
-  std::vector<double> fnv;
-  fn_table(d.basis_family, S, fnv);
-  std::vector<double> alpha(static_cast<size_t>(nif) * S, 1.0);
+  // interface-function tables for s = 16 (offset 0) and s = 32 (offset 256)
+  std::vector<double> fnv, fn32;
+  fn_table(d.basis_family, 16, fnv);
+  fn_table(d.basis_family, 32, fn32);
+  fnv.insert(fnv.end(), fn32.begin(), fn32.end());
+  std::vector<double> alpha(static_cast<size_t>(c->alpha_elems), 1.0);
   if (d.alpha) {
     for (size_t k = 0; k < alpha.size(); ++k) {
       alpha[k] = d.alpha[k];
@@ -644,8 +686,9 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                o_pairs = A.take<PairPlan>(c->pairs.size() + 1),
                o_paoff = A.take<int>(c->pair_off.size() + 1),
                o_pagoff = A.take<int>(c->pair_goff.size() + 1),
-               o_coef = A.take<double>(static_cast<size_t>(nsub) * (6 * N + 4 * S)),
-               o_W = A.take<char>(static_cast<size_t>(nsub) * S * N * esz),
+               o_sbs = A.take<int>(c->sub_by_size.size()),
+               o_coef = A.take<double>(static_cast<size_t>(c->coef_elems)),
+               o_W = A.take<char>(static_cast<size_t>(c->w_elems) * esz),
                o_basis = A.take<double>(c->basis_elems), o_G = A.take<double>(c->g_elems ? c->g_elems : 1),
                o_sB = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
                o_sA = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
@@ -695,6 +738,8 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
       (e = up(o_bt, d.bc_type, nb * sizeof(int8_t))) != cudaSuccess ||
       (e = up(o_bv, d.bc_val, nb * sizeof(double))) != cudaSuccess ||
       (e = up(o_items, c->items.data(), c->items.size() * sizeof(BasisItem))) != cudaSuccess ||
+      (e = up(o_sbs, c->sub_by_size.data(), c->sub_by_size.size() * sizeof(int))) !=
+          cudaSuccess ||
       (e = up(o_p2u, c->pos2unk.data(), c->npos * sizeof(int))) != cudaSuccess ||
       (e = up(o_pro, c->pos_real_off.data(), c->pos_real_off.size() * sizeof(int64_t))) !=
           cudaSuccess ||
@@ -727,10 +772,11 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   t.niface = nif;
   t.nunk = nunk;
   t.pure_neumann = d.pure_neumann ? 1 : 0;
-  t.s = S;
+  t.smax = c->smax;
   t.h = d.ly / d.ny;
-  t.H = S * t.h;
   t.inv_h = d.ny / d.ly;
+  t.sub_by_size = reinterpret_cast<const int *>(base + o_sbs);
+  t.nsub16 = c->nsub16;
   t.sub = reinterpret_cast<const SubInfo *>(base + o_sub);
   t.iface = reinterpret_cast<const IfaceInfo *>(base + o_if);
   t.col = reinterpret_cast<const ColInfo *>(base + o_col);
@@ -738,7 +784,6 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   t.unk_iface = reinterpret_cast<const int *>(base + o_ui);
   t.unk_slabpos = reinterpret_cast<const int *>(base + o_usp);
   t.fnval = reinterpret_cast<const double *>(base + o_fn);
-  t.fn_stride = S;
   t.alpha = reinterpret_cast<const double *>(base + o_al);
   t.bc_type = reinterpret_cast<const int8_t *>(base + o_bt);
   t.bc_val = reinterpret_cast<const double *>(base + o_bv);
@@ -859,7 +904,7 @@ mrcm_status mrcm_factor_local(mrcm_ctx *ctx, const double *d_K, const double *d_
     return cuda_fail(ctx, e, "reset status");
   e = launch_factor(ctx->t, ctx->w, ctx->prec, d_K, d_lambda, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "factor_local launch");
-  ctx->launches = 1;
+  ctx->launches = n_sizes(ctx);
   ctx->state = 1;
   return MRCM_OK;
 }
@@ -868,11 +913,11 @@ mrcm_status mrcm_build_basis(mrcm_ctx *ctx, const double *d_q) {
   if (!ctx) return MRCM_EINVAL;
   if (ctx->state < 1) return fail(ctx, MRCM_EINVAL, "build_basis before factor_local");
   if (!d_q) return fail(ctx, MRCM_EINVAL, "q must be a device pointer");
-  cudaError_t e = launch_basis(ctx->t, ctx->w, ctx->prec, ctx->d_items,
-                               static_cast<int>(ctx->items.size()), d_q, ctx->d.ir_tol,
-                               ctx->d.ir_max, ctx->stream);
+  cudaError_t e = launch_basis(ctx->t, ctx->w, ctx->prec, ctx->d_items, ctx->nitems16,
+                               static_cast<int>(ctx->items.size()) - ctx->nitems16, d_q,
+                               ctx->d.ir_tol, ctx->d.ir_max, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "build_basis launch");
-  ctx->launches += 1;
+  ctx->launches += n_sizes(ctx);
   ctx->state = 2;
   return MRCM_OK;
 }
@@ -986,7 +1031,7 @@ mrcm_status mrcm_reconstruct(mrcm_ctx *ctx, double *d_p, double *d_ux, double *d
   if (!d_p || !d_ux || !d_uy) return fail(ctx, MRCM_EINVAL, "p, ux, uy must be device pointers");
   cudaError_t e = launch_reconstruct(ctx->t, ctx->w, d_p, d_ux, d_uy, d_gamma_u, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reconstruct launch");
-  ctx->launches += ctx->d.pure_neumann ? 3 : 2;
+  ctx->launches += n_sizes(ctx) + (ctx->d.pure_neumann ? 2 : 1);
   return MRCM_OK;
 }
 

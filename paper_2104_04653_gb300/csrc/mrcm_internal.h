@@ -20,8 +20,11 @@ struct SubInfo {
   int edge_col[4];   // first basis column of the edge's functions
   int edge_row[4];   // first row of the edge in G
   int col_off;       // offset into the column table (ncols entries)
+  int s;             // subdomain edge in cells (16 or 32)
   int64_t basis_off; // offset (doubles) of basis [ncols][S*S]
   int64_t g_off;     // offset (doubles) of G [nrows][ncols]
+  int64_t coef_off;  // offset (doubles) of the coefficient block (6 S*S + 4 S)
+  int64_t w_off;     // offset (elements) of the inverse Schur blocks [S][S][S]
 };
 
 // One interface (all realisations concatenated, canonical order).
@@ -30,6 +33,7 @@ struct IfaceInfo {
   int kind;          // 0 vertical (normal +x), 1 horizontal (normal +y)
   int L, R;          // global subdomain ids, L < R
   int nU, nP;
+  int s;             // faces along the interface
   int unk;           // global unknown offset of U_0
   int slab, pos;     // BCR slab index (within realisation), row offset in slab
   int64_t alpha_off; // offset into the per-face alpha array (s values)
@@ -52,6 +56,7 @@ struct RealInfo {
   int iface0, niface;
   int unk0, nunk;
   int pin;           // pinned global unknown (pure Neumann) or -1
+  int fn_off;        // offset of the interface-function table for s (stride s)
   int nslab, bmax;   // BCR slabs and padded slab size
   int nlev;          // BCR reduction levels
   int64_t slab_off;  // offset (elements) of this realisation's slab blocks
@@ -103,6 +108,9 @@ struct GmArgs {
   double tol;
 };
 
+constexpr int kNC16 = 12;     // basis columns per CTA, s = 16
+constexpr int kNC32 = 8;      // basis columns per CTA, s = 32
+
 struct BasisItem {   // one CTA of the basis kernel
   int sub;
   int c0, nc;        // column range
@@ -112,9 +120,11 @@ struct BasisItem {   // one CTA of the basis kernel
 struct DeviceTables {
   int nx, ny, n_real, nsub, niface, nunk;
   int pure_neumann;
-  int s;             // subdomain edge (uniform across realisations for now)
-  double h, H, inv_h;
+  int smax;          // largest subdomain edge
+  double h, inv_h;   // cell size (shared by all realisations)
   const SubInfo *sub;
+  const int *sub_by_size;   // subdomain ids: the s = 16 ones first, then s = 32
+  int nsub16;               // how many of them have s = 16
   const IfaceInfo *iface;
   const ColInfo *col;
   const RealInfo *real;
@@ -133,8 +143,8 @@ struct DeviceTables {
   const int *pair_off;      // [n_real * nslab + 1]
   const int *pair_goff;     // G offsets of every pair entry (2 per entry, -1: none)
   int emax;                 // largest number of terms of one interface row
-  const double *fnval;      // [kMaxFn][s] interface function values at midpoints
-  int fn_stride;            // = s
+  const double *fnval;      // per subdomain size s (RealInfo::fn_off): [s][s]
+                            // interface function k at face midpoint e
   const double *alpha;      // per face
   const int8_t *bc_type;
   const double *bc_val;
@@ -166,8 +176,9 @@ struct Workspace {
 // Launch wrappers (return cudaGetLastError()).
 cudaError_t launch_factor(const DeviceTables &t, const Workspace &w, int prec,
                           const double *K, const double *lam, cudaStream_t st);
+// items: the s = 16 subdomains' CTAs first (nitems16), then the s = 32 ones
 cudaError_t launch_basis(const DeviceTables &t, const Workspace &w, int prec,
-                         const BasisItem *items, int nitems, const double *q,
+                         const BasisItem *items, int nitems16, int nitems32, const double *q,
                          double ir_tol, int ir_max, cudaStream_t st);
 cudaError_t launch_iface_assemble(const DeviceTables &t, const Workspace &w, int prec,
                                   int64_t slab_elems, const int *pos2unk, int64_t npos,

@@ -14,16 +14,18 @@
 namespace mrcm {
 namespace {
 
-constexpr int kS = 16;
-
-__global__ void __launch_bounds__(kS *kS) k_recon_cells(DeviceTables t, Workspace w, double *P,
-                                                        double *UX, double *UY, double *GAM) {
-  constexpr int S = kS, N = S * S;
-  const int g = blockIdx.x;
+// One CTA of S*S threads per subdomain of size S (ids from first on).
+template <int S>
+__global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace w, double *P,
+                                                      double *UX, double *UY, double *GAM,
+                                                      int first) {
+  constexpr int N = S * S;
+  const int g = t.sub_by_size[first + blockIdx.x];
   const SubInfo sb = t.sub[g];
   const int tid = threadIdx.x, a = tid % S, b = tid / S;
+  const double *fnt = t.fnval + (S == 16 ? 0 : 16 * 16);
   __shared__ double p[N];
-  __shared__ double coefc[160];
+  __shared__ double coefc[1 + 8 * S];
   __shared__ double red[N / 32];
   for (int c = tid; c < sb.ncols; c += N) {
     const int u = t.col[sb.col_off + c].unk;
@@ -35,7 +37,7 @@ __global__ void __launch_bounds__(kS *kS) k_recon_cells(DeviceTables t, Workspac
   for (int c = 0; c < sb.ncols; ++c) pc += coefc[c] * bas[static_cast<int64_t>(c) * N + tid];
   p[tid] = pc;
   __syncthreads();
-  const double *coef = w.coef + static_cast<int64_t>(g) * (6 * N + 4 * S);
+  const double *coef = w.coef + sb.coef_off;
   const double tW = coef[tid], tE = coef[N + tid], tS = coef[2 * N + tid], tN = coef[3 * N + tid];
   const double h = t.h;
   const int gi = sb.x0 + a, gj = sb.y0 + b;
@@ -58,8 +60,8 @@ __global__ void __launch_bounds__(kS *kS) k_recon_cells(DeviceTables t, Workspac
       const IfaceInfo fi = t.iface[sb.edge_iface[side]];
       const double beta = coef[6 * N + side * S + e];
       double UH = 0.0, PH = 0.0;
-      for (int k = 0; k < fi.nU; ++k) UH += w.x[fi.unk + k] * t.fnval[k * t.fn_stride + e];
-      for (int k = 0; k < fi.nP; ++k) PH += w.x[fi.unk + fi.nU + k] * t.fnval[k * t.fn_stride + e];
+      for (int k = 0; k < fi.nU; ++k) UH += w.x[fi.unk + k] * fnt[k * S + e];
+      for (int k = 0; k < fi.nP; ++k) PH += w.x[fi.unk + fi.nU + k] * fnt[k * S + e];
       const double gval = -beta * sgn * UH + PH;
       un = Tf[side] * (pc - gval) / h;
       GAM[fi.gam_off + (sgn > 0 ? 0 : S) + e] = un;
@@ -108,12 +110,14 @@ __global__ void k_recon_mean(DeviceTables t, Workspace w, double *pmean) {
 __global__ void k_recon_final(DeviceTables t, Workspace w, double *P, double *UX, double *UY,
                               const double *GAM, const double *pmean, int64_t ncells,
                               int64_t nfaces) {
-  const int S = t.s;
+  const int SM = t.smax;   // faces enumerated as (interface, e < smax)
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < nfaces;
        k += stride) {
-    const int gi = static_cast<int>(k / S), e = static_cast<int>(k % S);
+    const int gi = static_cast<int>(k / SM), e = static_cast<int>(k % SM);
     const IfaceInfo fi = t.iface[gi];
+    const int S = fi.s;
+    if (e >= S) continue;
     const SubInfo L = t.sub[fi.L];
     const double v = 0.5 * (GAM[fi.gam_off + e] - GAM[fi.gam_off + S + e]);
     if (fi.kind == 0) {
@@ -136,13 +140,14 @@ __global__ void k_recon_final(DeviceTables t, Workspace w, double *P, double *UX
 
 cudaError_t launch_reconstruct(const DeviceTables &t, const Workspace &w, double *p, double *ux,
                                double *uy, double *gam, cudaStream_t st) {
-  if (t.s != kS) return cudaErrorInvalidValue;
   double *G = gam ? gam : w.gamma_tmp;
-  k_recon_cells<<<t.nsub, kS * kS, 0, st>>>(t, w, p, ux, uy, G);
+  if (t.nsub16 > 0) k_recon_cells<16><<<t.nsub16, 256, 0, st>>>(t, w, p, ux, uy, G, 0);
+  if (t.nsub > t.nsub16)
+    k_recon_cells<32><<<t.nsub - t.nsub16, 1024, 0, st>>>(t, w, p, ux, uy, G, t.nsub16);
   double *pmean = w.dstat + 2 + t.n_real;
   if (t.pure_neumann) k_recon_mean<<<t.n_real, 256, 0, st>>>(t, w, pmean);
   const int64_t ncells = static_cast<int64_t>(t.n_real) * t.nx * t.ny;
-  const int64_t nfaces = static_cast<int64_t>(t.niface) * t.s;
+  const int64_t nfaces = static_cast<int64_t>(t.niface) * t.smax;
   const int64_t work = nfaces > ncells ? nfaces : ncells;
   int blocks = static_cast<int>((work + 255) / 256);
   if (blocks > 4096) blocks = 4096;

@@ -225,7 +225,8 @@ def uniform_spaces(nx: int, ny: int, s: int, n_u: int, n_p: int):
 def make_problem(nx, ny, s, K, lam=None, q=None, bc=None, n_u=2, n_p=2,
                  pure_neumann=False, ly=1.0, alpha=None, basis="legendre",
                  name="custom") -> Problem:
-    """Single-realisation (or stacked) problem with uniform spaces."""
+    """Single-realisation (or stacked) problem with uniform spaces; s is one
+    subdomain size for every realisation or a list with one per realisation."""
     K = np.asarray(K, dtype=np.float64)
     if K.ndim == 2:
         K = K[None]
@@ -234,10 +235,11 @@ def make_problem(nx, ny, s, K, lam=None, q=None, bc=None, n_u=2, n_p=2,
     q = np.zeros_like(K) if q is None else np.asarray(q, np.float64).reshape(K.shape)
     if bc is None:
         bc = bc_no_flow(nx, ny)
-    nu, npp = uniform_spaces(nx, ny, s, n_u, n_p)
-    return Problem(nx=nx, ny=ny, ly=ly, sub_size=[s] * R, K=K, lam=lam, q=q,
+    sizes = [int(s)] * R if np.ndim(s) == 0 else [int(v) for v in s]
+    spaces = [uniform_spaces(nx, ny, sz, n_u, n_p) for sz in sizes]
+    return Problem(nx=nx, ny=ny, ly=ly, sub_size=sizes, K=K, lam=lam, q=q,
                    bc_type=np.asarray(bc[0], np.int8), bc_val=np.asarray(bc[1], np.float64),
-                   iface_nU=[nu.copy() for _ in range(R)], iface_nP=[npp.copy() for _ in range(R)],
+                   iface_nU=[sp[0] for sp in spaces], iface_nP=[sp[1] for sp in spaces],
                    alpha=alpha, pure_neumann=pure_neumann, basis=basis, name=name)
 
 

@@ -54,6 +54,21 @@ def test_linear_pressure_exact():
         np.testing.assert_allclose(sol["uy"][0], 0.0, atol=1e-11)
 
 
+def test_linear_pressure_exact_mixed_subdomain_sizes():
+    """The same closed form with 16 x 16 and 32 x 32 subdomains in one batch
+    (one realisation each)."""
+    nx, ny = 64, 64
+    h = 1.0 / ny
+    prob = W.make_problem(nx, ny, [16, 32], np.full((2, ny, nx), 0.7),
+                          bc=W.bc_linear_pressure(nx, ny, h), n_u=2, n_p=2)
+    sol = O.mrcm_solve(prob)
+    xc = (np.arange(nx) + 0.5) * h
+    for r in range(2):
+        np.testing.assert_allclose(sol["p"][r], np.broadcast_to(1.0 - xc, (ny, nx)), atol=1e-12)
+        np.testing.assert_allclose(sol["ux"][r], 0.7, rtol=1e-12)
+        np.testing.assert_allclose(sol["uy"][r], 0.0, atol=1e-11)
+
+
 # ------------------------------------------------------------------ (ii) special case
 @pytest.mark.parametrize("pure_neumann", [False, True])
 @pytest.mark.parametrize("alpha", [0.05, 1.0, 20.0])
@@ -130,9 +145,9 @@ def _cell_outflow(prob, r, sol, lay):
     return out
 
 
-@pytest.mark.parametrize("pure_neumann", [False, True])
-def test_mass_balance_and_interface_balance(pure_neumann):
-    prob = _random_problem(32, 32, 8, 2, 3, seed=5, pure_neumann=pure_neumann)
+@pytest.mark.parametrize("pure_neumann,n,s", [(False, 32, 8), (True, 32, 8), (False, 64, 32)])
+def test_mass_balance_and_interface_balance(pure_neumann, n, s):
+    prob = _random_problem(n, n, s, 2, 3, seed=5, pure_neumann=pure_neumann)
     sol = O.mrcm_solve(prob)
     lay = O.Layout(prob, 0)
     h = prob.h
