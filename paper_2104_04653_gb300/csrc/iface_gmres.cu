@@ -475,6 +475,13 @@ int gmres_max_blocks(int K, int dev) {
   return nsm * per;
 }
 
+cudaError_t launch_gmres_bj(const DeviceTables &t, const Workspace &w, const GmArgs &a, double *Pbj,
+                            cudaStream_t st) {
+  if (t.niface == 0) return cudaSuccess;
+  k_gm_bj<<<(t.niface + kBjWarps - 1) / kBjWarps, 32 * kBjWarps, 0, st>>>(t, w, a, Pbj);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gmres_precond(const DeviceTables &t, const Workspace &w, const GmArgs &a,
                                  double *Pbj, bool build_bj, cudaStream_t st) {
   if (build_bj && t.niface > 0) {

@@ -471,7 +471,6 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   const int nc = it.nc;
   const int tid = threadIdx.x;
   const int a = tid % S, b = tid / S;
-  const double h = t.h;
 
   // stage W_j, the coefficients and the column descriptors
   {

@@ -3,6 +3,7 @@
 // the launch sequence of the five hot-path calls.
 #include "mrcm_internal.h"
 #include "../../include/mrcm.h"
+#include "../../include/mrcm_learned.h"
 
 #include <cmath>
 #include <cstdarg>
@@ -68,6 +69,10 @@ struct mrcm_ctx {
   std::vector<GmBlock> gm_blocks;
   GmArgs gm{};
   double *gm_Pbj = nullptr, *gm_Pid = nullptr, *gm_Puser = nullptr;
+  // learned preconditioner: interface neighbourhoods of the training target
+  std::vector<int> nb_off, nb_list;
+  int nb_max = 0, nloc_max = 0, m_uniform = 0, s_uniform = 0;
+  int *d_nb_off = nullptr, *d_nb_list = nullptr;
 };
 
 static thread_local std::string g_setup_err;
@@ -541,6 +546,41 @@ static void build_gmres_rows(mrcm_ctx *c) {
   }
 }
 
+// Neighbourhood of interface g: every interface with a subdomain within
+// Chebyshev distance 1 of one of g's two subdomains (ascending ids).
+static void build_neighbourhoods(mrcm_ctx *c) {
+  c->nb_off.assign(1, 0);
+  c->nb_list.clear();
+  c->nb_max = c->nloc_max = 0;
+  std::vector<int> nb;
+  for (const IfaceInfo &fi : c->iface) {
+    const RealInfo &ri = c->real[fi.r];
+    const SubInfo &L = c->sub[fi.L], &R = c->sub[fi.R];
+    nb.clear();
+    for (int J = std::min(L.J, R.J) - 1; J <= std::max(L.J, R.J) + 1; ++J)
+      for (int I = std::min(L.I, R.I) - 1; I <= std::max(L.I, R.I) + 1; ++I) {
+        if (I < 0 || J < 0 || I >= ri.Sx || J >= ri.Sy) continue;
+        const SubInfo &sb = c->sub[ri.sub0 + J * ri.Sx + I];
+        for (int e = 0; e < 4; ++e)
+          if (sb.edge_iface[e] >= 0) nb.push_back(sb.edge_iface[e]);
+      }
+    std::sort(nb.begin(), nb.end());
+    nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+    int nloc = 0;
+    for (int h : nb) nloc += c->iface[h].nU + c->iface[h].nP;
+    c->nb_max = std::max(c->nb_max, static_cast<int>(nb.size()));
+    c->nloc_max = std::max(c->nloc_max, nloc);
+    c->nb_list.insert(c->nb_list.end(), nb.begin(), nb.end());
+    c->nb_off.push_back(static_cast<int>(c->nb_list.size()));
+  }
+  c->m_uniform = c->iface.empty() ? 0 : c->iface[0].nU + c->iface[0].nP;
+  for (const IfaceInfo &fi : c->iface)
+    if (fi.nU + fi.nP != c->m_uniform) c->m_uniform = 0;
+  c->s_uniform = c->real[0].s;
+  for (const RealInfo &ri : c->real)
+    if (ri.s != c->s_uniform) c->s_uniform = 0;
+}
+
 static bool plan_gmres_blocks(mrcm_ctx *c, int cap) {
   const int R = static_cast<int>(c->real.size());
   if (cap < R) return false;
@@ -630,6 +670,7 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     c->gm_tol = desc->gmres_tol > 0.0 ? desc->gmres_tol : desc->iface_tol;
     c->gm_precond = desc->precond;
     build_gmres_rows(c);
+    build_neighbourhoods(c);
   }
   cudaError_t e = cudaGetDevice(&c->dev);
   if (e != cudaSuccess) {
@@ -715,7 +756,9 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                o_gmW = A.take<double>(G ? nunk + 1 : 0), o_gmY = A.take<double>(G ? nunk + 1 : 0),
                o_gmpart = A.take<double>(G ? static_cast<int64_t>(c->gm_nblk) * (Kp + 2) : 0),
                o_gmres = A.take<double>(G ? d.n_real : 0),
-               o_gmint = A.take<int>(G ? 3 * d.n_real : 0);
+               o_gmint = A.take<int>(G ? 3 * d.n_real : 0),
+               o_nboff = A.take<int>(G ? c->nb_off.size() : 0),
+               o_nblist = A.take<int>(G ? c->nb_list.size() + 1 : 0);
   e = cudaMalloc(&c->arena, A.off);
   if (e != cudaSuccess) {
     delete c;
@@ -757,6 +800,9 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
       (G && (e = up(o_gmrow, c->gm_rows.data(), c->gm_rows.size() * sizeof(GmRow))) !=
                 cudaSuccess) ||
       (G && (e = up(o_gmblk, c->gm_blocks.data(), c->gm_blocks.size() * sizeof(GmBlock))) !=
+                cudaSuccess) ||
+      (G && (e = up(o_nboff, c->nb_off.data(), c->nb_off.size() * sizeof(int))) != cudaSuccess) ||
+      (G && (e = up(o_nblist, c->nb_list.data(), c->nb_list.size() * sizeof(int))) !=
                 cudaSuccess) ||
       (e = cudaMemset(base + o_st, 0, 4 * sizeof(int))) != cudaSuccess ||
       (e = cudaMemset(base + o_dst, 0, (2 + 2 * d.n_real) * sizeof(double))) != cudaSuccess) {
@@ -842,6 +888,8 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     a.done = reinterpret_cast<int *>(base + o_gmint);
     a.fallback = a.done + d.n_real;
     a.iters = a.fallback + d.n_real;
+    c->d_nb_off = reinterpret_cast<int *>(base + o_nboff);
+    c->d_nb_list = reinterpret_cast<int *>(base + o_nblist);
     a.K = c->gm_K;
     a.maxit = c->gm_maxit;
     a.tol = c->gm_tol;
@@ -1062,6 +1110,79 @@ mrcm_status mrcm_set_precond_blocks(mrcm_ctx *ctx, const double *d_blocks) {
   cudaError_t e = cudaMemcpyAsync(ctx->gm_Puser, d_blocks, sizeof(double) * ctx->tsc_elems,
                                   cudaMemcpyDeviceToDevice, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "copy preconditioner blocks");
+  ctx->gm_user_set = true;
+  return MRCM_OK;
+}
+
+int64_t mrcm_lp_num_samples(const mrcm_ctx *ctx) {
+  return ctx ? static_cast<int64_t>(ctx->iface.size()) : 0;
+}
+
+mrcm_status mrcm_lp_windows(mrcm_ctx *ctx, const double *d_K, const double *d_lambda,
+                            int64_t first, int32_t count, void *d_x) {
+  if (!ctx) return MRCM_EINVAL;
+  if (!d_K || !d_lambda || !d_x) return fail(ctx, MRCM_EINVAL, "NULL device pointer");
+  if (!ctx->s_uniform) return fail(ctx, MRCM_EINVAL, "learned preconditioner: mixed subdomain sizes");
+  const int64_t nif = static_cast<int64_t>(ctx->iface.size());
+  if (first < 0 || count < 0 || first + count > nif)
+    return fail(ctx, MRCM_EINVAL, "interface range outside 0..%lld", static_cast<long long>(nif));
+  cudaError_t e = lp_windows(ctx->t, d_K, d_lambda, d_x, ctx->s_uniform, static_cast<int>(first),
+                             count, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "window launch");
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_lp_targets(mrcm_ctx *ctx, float *d_target) {
+  if (!ctx) return MRCM_EINVAL;
+  if (!d_target) return fail(ctx, MRCM_EINVAL, "d_target must be a device pointer");
+  if (!ctx->use_gmres) return fail(ctx, MRCM_EINVAL, "targets need the GMRES path");
+  if (ctx->state < 2) return fail(ctx, MRCM_EINVAL, "targets before build_basis");
+  if (!ctx->m_uniform) return fail(ctx, MRCM_EINVAL, "targets need one interface size m");
+  if (ctx->nb_max > kLpMaxNb || ctx->nloc_max > kLpMaxLoc)
+    return fail(ctx, MRCM_EINVAL, "neighbourhood of %d unknowns above %d", ctx->nloc_max,
+                kLpMaxLoc);
+  cudaError_t e = lp_targets(ctx->t, ctx->w, ctx->gm, ctx->d_nb_off, ctx->d_nb_list,
+                             ctx->nloc_max, ctx->m_uniform, 0.5, d_target, &ctx->w.status[0],
+                             ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "target launch");
+  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "stream synchronize");
+  int st0 = 0;
+  if ((e = cudaMemcpy(&st0, ctx->w.status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(ctx, e, "status read");
+  if (st0 & MRCM_FLAG_IFACE_PIVOT) return fail(ctx, MRCM_ENOTSPD, "singular neighbourhood matrix");
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_lp_apply(mrcm_ctx *ctx, mrcm_lp *lp, const double *d_K, const double *d_lambda) {
+  if (!ctx || !lp) return MRCM_EINVAL;
+  if (!ctx->use_gmres || ctx->gm_precond != MRCM_PRECOND_USER)
+    return fail(ctx, MRCM_EINVAL, "the learned preconditioner needs GMRES with MRCM_PRECOND_USER");
+  if (ctx->state < 2) return fail(ctx, MRCM_EINVAL, "lp_apply before build_basis");
+  if (ctx->s_uniform != lp_s(lp) || ctx->m_uniform != lp_m(lp))
+    return fail(ctx, MRCM_EINVAL, "network (s %d, m %d) does not match the problem", lp_s(lp),
+                lp_m(lp));
+  if (!d_K || !d_lambda) return fail(ctx, MRCM_EINVAL, "NULL device pointer");
+  cudaError_t e;
+  if ((e = launch_gmres_bj(ctx->t, ctx->w, ctx->gm, ctx->gm_Pbj, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "block-Jacobi launch");
+  ctx->launches += 1;
+  const cudaStream_t keep = lp_stream(lp);
+  mrcm_lp_set_stream(lp, ctx->stream);
+  const int nif = static_cast<int>(ctx->iface.size()), mb = lp_maxb(lp);
+  for (int g0 = 0; g0 < nif; g0 += mb) {
+    const int cnt = nif - g0 < mb ? nif - g0 : mb;
+    if ((e = lp_windows(ctx->t, d_K, d_lambda, lp_xbuf(lp), ctx->s_uniform, g0, cnt,
+                        ctx->stream)) != cudaSuccess ||
+        (e = lp_forward(lp, lp_xbuf(lp), cnt, lp_deltabuf(lp))) != cudaSuccess ||
+        (e = lp_blocks(ctx->t, ctx->gm_Pbj, lp_deltabuf(lp), ctx->gm_Puser, g0, cnt,
+                       ctx->m_uniform, ctx->stream)) != cudaSuccess) {
+      mrcm_lp_set_stream(lp, keep);
+      return cuda_fail(ctx, e, "learned preconditioner launch");
+    }
+    ctx->launches += 6;
+  }
+  mrcm_lp_set_stream(lp, keep);
   ctx->gm_user_set = true;
   return MRCM_OK;
 }

@@ -108,6 +108,13 @@ struct GmArgs {
   double tol;
 };
 
+// learned interface preconditioner (learned.cu)
+constexpr int kLpChannels = 32;   // channels of every convolution
+constexpr int kLpMaxM = 8;        // largest interface size it serves
+constexpr int kLpMaxNb = 64;      // largest neighbourhood (interfaces) of a target
+constexpr int kLpMaxLoc = 160;    // largest neighbourhood (unknowns) of a target
+constexpr double kLpClip = 2.0;   // entrywise bound of a target
+
 constexpr int kNC16 = 12;     // basis columns per CTA, s = 16
 constexpr int kNC32 = 8;      // basis columns per CTA, s = 32
 
@@ -204,6 +211,29 @@ cudaError_t launch_gmres_precond(const DeviceTables &t, const Workspace &w, cons
 cudaError_t launch_gmres(const DeviceTables &t, const Workspace &w, const GmArgs &a, int nblk,
                          cudaStream_t st);
 cudaError_t init_local_attributes();
+// learned preconditioner: window gather, blocks, targets, inference
+cudaError_t lp_windows(const DeviceTables &t, const double *K, const double *lam, void *x, int s,
+                       int g0, int count, cudaStream_t st);
+cudaError_t lp_blocks(const DeviceTables &t, const double *Pbj, const float *delta, double *Puser,
+                      int g0, int count, int m, cudaStream_t st);
+size_t lp_targets_smem(int nloc, int m);
+cudaError_t launch_gmres_bj(const DeviceTables &t, const Workspace &w, const GmArgs &a, double *Pbj,
+                            cudaStream_t st);
+cudaError_t lp_targets(const DeviceTables &t, const Workspace &w, const GmArgs &a,
+                       const int *nb_off, const int *nb_list, int nloc_max, int m, double theta,
+                       float *target, int *bad, cudaStream_t st);
 cudaError_t init_iface_attributes(int prec, int bmax, int max_vec);
 
+}  // namespace mrcm
+
+// network object of the learned preconditioner (learned.cu)
+struct mrcm_lp;
+namespace mrcm {
+cudaError_t lp_forward(mrcm_lp *lp, const void *x, int B, float *delta);
+int lp_s(const mrcm_lp *lp);
+int lp_m(const mrcm_lp *lp);
+int lp_maxb(const mrcm_lp *lp);
+void *lp_xbuf(mrcm_lp *lp);
+float *lp_deltabuf(mrcm_lp *lp);
+cudaStream_t lp_stream(const mrcm_lp *lp);
 }  // namespace mrcm

@@ -9,7 +9,7 @@ from oracle import cnn as C
 
 def _tiny(seed=0, B=3, s=4, m=2):
     rng = np.random.default_rng(seed)
-    p = C.init_params(m, seed)
+    p = C.init_params(m, seed, s)
     p["wh"] = 0.3 * rng.standard_normal(p["wh"].shape)
     p["bh"] = 0.1 * rng.standard_normal(p["bh"].shape)
     for l in (1, 2, 3):
@@ -41,8 +41,8 @@ def test_conv_matches_direct_sum():
     np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12)
 
 
-def _fd_check(p, x, t, n_probe=6, h=1e-6):
-    loss, g = C.loss_and_grad(p, x, t)
+def _fd_check(p, x, t, n_probe=6, h=1e-6, wk=None):
+    loss, g = C.loss_and_grad(p, x, t, wk)
     rng = np.random.default_rng(5)
     for k in p:
         flat = p[k].reshape(-1)
@@ -50,9 +50,9 @@ def _fd_check(p, x, t, n_probe=6, h=1e-6):
         for idx in rng.choice(flat.size, size=min(n_probe, flat.size), replace=False):
             old = flat[idx]
             flat[idx] = old + h
-            lp, _ = C.loss_and_grad(p, x, t)
+            lp, _ = C.loss_and_grad(p, x, t, wk)
             flat[idx] = old - h
-            lm, _ = C.loss_and_grad(p, x, t)
+            lm, _ = C.loss_and_grad(p, x, t, wk)
             flat[idx] = old
             fd = (lp - lm) / (2 * h)
             assert abs(fd - gk[idx]) <= 1e-6 * max(1.0, abs(fd)), (k, idx, fd, gk[idx])
@@ -62,6 +62,11 @@ def _fd_check(p, x, t, n_probe=6, h=1e-6):
 def test_gradient_matches_finite_differences():
     p, x, t = _tiny()
     _fd_check(p, x, t)
+
+
+def test_weighted_gradient_matches_finite_differences():
+    p, x, t = _tiny()
+    _fd_check(p, x, t, wk=np.array([0.5, 3.0, 0.01, 10.0]))
 
 
 def test_planted_bias_gradient_mistake_is_caught(monkeypatch):
@@ -77,7 +82,7 @@ def test_planted_bias_gradient_mistake_is_caught(monkeypatch):
 
 
 def test_zero_head_is_block_jacobi():
-    p = C.init_params(4, 3)
+    p = C.init_params(4, 3, 4)
     x = np.random.default_rng(2).standard_normal((5, 2, 8, 12))
     delta, _ = C.forward(p, x)
     assert np.all(delta == 0.0)
@@ -123,10 +128,10 @@ def test_target_with_whole_domain_neighbourhood():
     # 2 x 2 subdomains: every neighbourhood is the whole interface set, so
     # the restricted inverse is the inverse of M itself
     prob, M, lay = _system(n=32, s=16)
-    T = C.targets(M, lay, theta=1.0)
+    T = C.targets(M, lay, theta=1.0, clip=np.inf)
     Minv = np.linalg.inv(M)
     for g, f in enumerate(lay.ifaces):
         off, m = f["off"], f["nU"] + f["nP"]
         ref = M[off:off + m, off:off + m] @ Minv[off:off + m, off:off + m] - np.eye(m)
         np.testing.assert_allclose(T[g], ref, atol=1e-10)
-    assert np.allclose(C.targets(M, lay), 0.5 * T)
+    assert np.allclose(C.targets(M, lay), np.clip(0.5 * T, -2.0, 2.0))
