@@ -380,6 +380,62 @@ def roofline_entry(call, seconds, prob, solver, peaks, src, clocks):
             "call_ms": seconds * 1e3, "algorithmic": w}
 
 
+# --------------------------------------------------------- workload suite
+def _global_balance(prob, p, ux, uy):
+    """max over realisations |sum q h^2 - boundary outflow| / sum |q h^2|,
+    or over the boundary flux when there are no sources."""
+    h = prob.h
+    worst = 0.0
+    for r in range(prob.n_real):
+        src = float(prob.q[r].sum()) * h * h
+        out = (ux[r][:, -1].sum() - ux[r][:, 0].sum() + uy[r][-1, :].sum() - uy[r][0, :].sum()) * h
+        scale = max(abs(src), float(np.abs(ux[r][:, 0]).sum() * h), 1e-300)
+        worst = max(worst, abs(src - out) / scale)
+    return worst
+
+
+def run_suite(args):
+    """The large workloads at full size (one line each): per-call device
+    times, interface solver, GMRES steps, the solver's own FP64 residuals and
+    the global mass balance.  Not the headline line."""
+    import torch
+    from paper_2104_04653_gb300 import build, learned as LP, mrcm, workloads as W
+    build.build()
+    global np
+    import numpy as np
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    cases = []
+    if "resolve" in args.suite:
+        cases.append(("bl-front-512x512-s16-m4 (step 5)", W.config5(5, n=512), {}))
+    if "channels" in args.suite:
+        cases.append(("channels-2048x2048-s32-m4", W.config4(n=2048, s=32, n_ch=64), {}))
+    if "batch" in args.suite:
+        cases.append(("lognormal-32x1024x1024-s16/32-m2..8", W.config3(), {}))
+    for name, prob, extra in cases:
+        for prec in (mrcm.PREC_FP32_IR, mrcm.PREC_FP64):
+            opts = mrcm.SolverOptions(prec=prec, gmres_tol=1e-12, gmres_max=6000, **extra)
+            s = mrcm.Mrcm(prob, opts)
+            K, L, Q = mrcm.device_inputs(prob)
+            out = s.alloc_outputs()
+            s.solve(K, L, Q, out=out)
+            info = s.mrcm_get_info(check=False)
+            calls = _time_calls(s, K, L, Q, out, args.suite_steps, flush, torch)
+            tot = sum(calls.values())
+            p, ux, uy = (t.cpu().numpy() for t in out)
+            line = {"suite": name, "prec": "fp32_ir" if prec else "fp64",
+                    "cells": prob.cells(), "interface_solver": "gmres" if s.uses_gmres() else "direct",
+                    "ms_per_step": tot * 1e3, "cells_per_s": prob.cells() / tot,
+                    "calls_ms": {k: v * 1e3 for k, v in calls.items()},
+                    "gmres_iters": info["gmres_iters"], "iface_resid": info["iface_resid"],
+                    "local_resid_max": info["local_resid_max"], "status": info["status"],
+                    "global_balance": _global_balance(prob, p, ux, uy),
+                    "interface_unknowns": s.num_interface_unknowns()}
+            s.close()
+            print(json.dumps(line), flush=True)
+            del K, L, Q, out
+            torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,10 +444,15 @@ def main():
     ap.add_argument("--impl", default="mrcm", choices=["mrcm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--suite", default="", help="comma list of resolve,channels,batch: the "
+                    "large workloads at full size instead of the headline line")
+    ap.add_argument("--suite-steps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.suite:
+        run_suite(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
