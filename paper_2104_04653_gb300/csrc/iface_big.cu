@@ -1,0 +1,516 @@
+// Step (d), direct path for slabs larger than one CTA's tiles (b > 64): the
+// same block cyclic reduction over slabs as iface.cu (Eq. "mrc2", slab
+// ordering, congruence scaling, FP64 refinement), with every dense block
+// operation spread over the GPU:
+//
+//  * inverses of the eliminated pivot blocks by batched blocked Gauss-Jordan
+//    (no pivoting: the scaled slab blocks are symmetric quasi-definite), one
+//    panel of 64 pivots at a time: k_gj_panel inverts the 64 x 64 diagonal
+//    tile and forms the pivot row panel, k_gj_trail applies the rank-64
+//    update to every other tile and forms the new pivot column panel;
+//  * the six block products of every surviving slab per level by a batched
+//    128 x 128-tile SIMT GEMM over job descriptors (k_bgemm), two products
+//    accumulated in one job for B_k -= X C_l + Y A_r;
+//  * the refinement loop in one cooperative kernel (k_big_solve): FP64
+//    residual from G, scaling, stop test, then the reduction solve with one
+//    warp per block row and grid barriers between levels.
+#include "mrcm_internal.h"
+#include "iface_common.cuh"
+#include "../../include/mrcm.h"
+
+#include <cooperative_groups.h>
+#include <cstdint>
+
+namespace cg = cooperative_groups;
+
+namespace mrcm {
+namespace {
+
+constexpr int kGjNb = 64;       // panel width of the blocked Gauss-Jordan
+constexpr int kGjThreads = 256;
+
+// ---------------------------------------------------------------- inverse
+// Panel step p of the in-place Gauss-Jordan inverse of every matrix of the
+// batch (one CTA per matrix): D = A[p.., p..]^{-1} into the matrix and into
+// job.dinv, the old pivot column panel (rows outside the panel) into
+// job.cpan, and the pivot row panel R = D A[p.., :] (columns outside the
+// panel) back into the matrix.
+constexpr size_t kGjPanelElems = 2 * kGjNb * kGjNb + 64 + 2 * 512;
+constexpr size_t kGjTrailElems = 2 * kGjNb * kGjNb;
+
+template <typename T>
+__global__ void __launch_bounds__(kGjThreads) k_gj_panel(const InvJob *jobs, int p,
+                                                         int *status) {
+  extern __shared__ __align__(16) unsigned char gsmraw[];
+  T *D = reinterpret_cast<T *>(gsmraw);
+  T *tile = D + kGjNb * kGjNb;
+  T *scr = tile + kGjNb * kGjNb;
+  __shared__ int bad;
+  const InvJob jb = jobs[blockIdx.x];
+  const int n = jb.n;
+  if (p >= n) return;
+  T *A = static_cast<T *>(jb.a);
+  T *Dout = static_cast<T *>(jb.dinv);
+  T *Cp = static_cast<T *>(jb.cpan);
+  const int w = n - p < kGjNb ? n - p : kGjNb;
+  const int t = threadIdx.x;
+  if (t == 0) bad = 0;
+  for (int e = t; e < kGjNb * kGjNb; e += kGjThreads) {
+    const int i = e / kGjNb, j = e % kGjNb;
+    D[e] = (i < w && j < w) ? A[static_cast<int64_t>(p + i) * n + p + j] : T(i == j);
+  }
+  // old column panel, rows outside the panel
+  for (int64_t e = t; e < static_cast<int64_t>(n) * w; e += kGjThreads) {
+    const int i = static_cast<int>(e / w), c = static_cast<int>(e % w);
+    if (i >= p && i < p + w) continue;
+    Cp[e] = A[static_cast<int64_t>(i) * n + p + c];
+  }
+  __syncthreads();
+  gj_inverse_blocked<T, kGjThreads>(D, kGjNb, kGjNb, scr, &bad);
+  __syncthreads();
+  for (int e = t; e < w * w; e += kGjThreads) {
+    const int i = e / w, j = e % w;
+    const T v = D[i * kGjNb + j];
+    Dout[e] = v;
+    A[static_cast<int64_t>(p + i) * n + p + j] = v;
+  }
+  // row panel, 64 columns at a time
+  for (int j0 = 0; j0 < n; j0 += kGjNb) {
+    if (j0 == p) continue;                      // panels are 64-aligned
+    const int wj = n - j0 < kGjNb ? n - j0 : kGjNb;
+    __syncthreads();
+    for (int e = t; e < kGjNb * kGjNb; e += kGjThreads) {
+      const int c = e / kGjNb, j = e % kGjNb;
+      tile[e] = (c < w && j < wj) ? A[static_cast<int64_t>(p + c) * n + j0 + j] : T(0);
+    }
+    __syncthreads();
+    for (int e = t; e < w * wj; e += kGjThreads) {
+      const int r = e / wj, j = e % wj;
+      T acc = T(0);
+      for (int c = 0; c < w; ++c) acc += D[r * kGjNb + c] * tile[c * kGjNb + j];
+      A[static_cast<int64_t>(p + r) * n + j0 + j] = acc;
+    }
+  }
+  if (t == 0 && bad) atomicOr(status, MRCM_FLAG_IFACE_PIVOT);
+}
+
+// Rank-w update of panel step p: for rows i outside the panel,
+//   A[i, j] -= Cp[i, :] R[:, j]   (j outside the panel columns)
+//   A[i, panel] = -Cp[i, :] D
+// One CTA per (64 x 64 output tile, matrix).
+template <typename T>
+__global__ void __launch_bounds__(kGjThreads) k_gj_trail(const InvJob *jobs, int p) {
+  extern __shared__ __align__(16) unsigned char gsmraw[];
+  T *Cs = reinterpret_cast<T *>(gsmraw);   // [row][c]
+  T *Rs = Cs + kGjNb * kGjNb;              // [c][col]
+  const InvJob jb = jobs[blockIdx.y];
+  const int n = jb.n;
+  if (p >= n) return;
+  const int nt = (n + kGjNb - 1) / kGjNb;
+  const int ti = blockIdx.x / nt, tj = blockIdx.x % nt;
+  if (ti >= nt) return;
+  const int i0 = ti * kGjNb, j0 = tj * kGjNb;
+  if (i0 == p) return;                          // the pivot rows are final
+  T *A = static_cast<T *>(jb.a);
+  const T *Dv = static_cast<const T *>(jb.dinv);
+  const T *Cp = static_cast<const T *>(jb.cpan);
+  const int w = n - p < kGjNb ? n - p : kGjNb;
+  const int hi = n - i0 < kGjNb ? n - i0 : kGjNb, wj = n - j0 < kGjNb ? n - j0 : kGjNb;
+  const bool pcol = (j0 == p);
+  const int t = threadIdx.x;
+  for (int e = t; e < kGjNb * kGjNb; e += kGjThreads) {
+    const int a = e / kGjNb, b = e % kGjNb;
+    Cs[e] = (a < hi && b < w) ? Cp[static_cast<int64_t>(i0 + a) * w + b] : T(0);
+    T r = T(0);
+    if (a < w && b < wj) r = pcol ? Dv[a * w + b] : A[static_cast<int64_t>(p + a) * n + j0 + b];
+    Rs[e] = r;
+  }
+  __syncthreads();
+  // thread: 4 rows x 4 columns
+  const int tr = (t / 16) * 4, tc = (t % 16) * 4;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int c = 0; c < w; ++c) {
+    T ca[4], rb[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) ca[a] = Cs[(tr + a) * kGjNb + c];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) rb[b] = Rs[c * kGjNb + tc + b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] += ca[a] * rb[b];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (tr + a >= hi) continue;
+    T *row = A + static_cast<int64_t>(i0 + tr + a) * n + j0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if (tc + b >= wj) continue;
+      row[tc + b] = pcol ? -acc[a][b] : row[tc + b] - acc[a][b];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- GEMM
+// C = alpha (A1 B1 + A2 B2) (+ C if acc), all n x n row-major.  128 x 128
+// output tile per CTA, 256 threads with 8 x 8 outputs each, k-steps of 8
+// staged in shared memory (A transposed so both operands are read as
+// broadcast-free row vectors).
+constexpr int kBM = 128, kBK = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bgemm(const GemmJob *jobs) {
+  __shared__ T As[kBK][kBM];
+  __shared__ T Bs[kBK][kBM];
+  const GemmJob jb = jobs[blockIdx.y];
+  const int n = jb.n;
+  const int nt = (n + kBM - 1) / kBM;
+  const int ti = blockIdx.x / nt, tj = blockIdx.x % nt;
+  if (ti >= nt) return;
+  const int i0 = ti * kBM, j0 = tj * kBM;
+  const int t = threadIdx.x, ty = t / 16, tx = t % 16;
+  T acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = T(0);
+  for (int prod = 0; prod < 2; ++prod) {
+    const T *A = static_cast<const T *>(prod == 0 ? jb.a1 : jb.a2);
+    const T *B = static_cast<const T *>(prod == 0 ? jb.b1 : jb.b2);
+    if (!A || !B) continue;
+    for (int k0 = 0; k0 < n; k0 += kBK) {
+      // A tile [128 rows][8 k] -> As[k][row]; B tile [8 k][128 cols]
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = t + 256 * q;
+        const int ar = e / kBK, ak = e % kBK;
+        const int gi = i0 + ar, gk = k0 + ak;
+        As[ak][ar] = (gi < n && gk < n) ? A[static_cast<int64_t>(gi) * n + gk] : T(0);
+        const int bk = e / kBM, bc = e % kBM;
+        const int gk2 = k0 + bk, gj = j0 + bc;
+        Bs[bk][bc] = (gk2 < n && gj < n) ? B[static_cast<int64_t>(gk2) * n + gj] : T(0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < kBK; ++kk) {
+        T a[8], b[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = As[kk][ty * 8 + q];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) b[q] = Bs[kk][tx * 8 + q];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+          for (int r = 0; r < 8; ++r) acc[q][r] += a[q] * b[r];
+      }
+      __syncthreads();
+    }
+  }
+  T *C = static_cast<T *>(jb.c);
+  const T alpha = static_cast<T>(jb.alpha);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int gi = i0 + ty * 8 + q;
+    if (gi >= n) continue;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int gj = j0 + tx * 8 + r;
+      if (gj >= n) continue;
+      const int64_t o = static_cast<int64_t>(gi) * n + gj;
+      C[o] = jb.acc ? C[o] + alpha * acc[q][r] : alpha * acc[q][r];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- solve
+// warp-level dot product of a matrix row with a vector (length n)
+template <typename T>
+__device__ __forceinline__ T row_dot(const T *row, const T *x, int n) {
+  const int lane = threadIdx.x & 31;
+  T acc = T(0);
+  for (int j = lane; j < n; j += 32) acc += row[j] * x[j];
+  return warp_sum(acc);
+}
+
+// Refinement with the big-slab reduction solve, all realisations in one
+// cooperative launch.  Each sweep: x += T^T y; r = f - M x (FP64), z = T
+// (sign r); stop test per realisation; y = Shat^{-1} z by cyclic reduction
+// (forward levels, root, backward levels), one warp per block row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_big_solve(DeviceTables t, Workspace w, BigPlan bp,
+                                                   double tol, int max_solves) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double red[8];
+  __shared__ double s_rel;
+  __shared__ double wbuf[8][kMmax];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gwarp = blockIdx.x * 8 + wid;
+  const int nwarps = gridDim.x * 8;
+  T *vec = static_cast<T *>(w.vec);
+  T *tmp = static_cast<T *>(bp.vec2);
+  const int K = bp.K, R = t.n_real, B = bp.bmax;
+  int nsolve = 0;
+  for (int sweep = 0;; ++sweep) {
+    // A: x += T^T y
+    if (sweep > 0) {
+      for (int g = gwarp; g < t.niface; g += nwarps) {
+        const IfaceInfo fi = t.iface[g];
+        if (__ldcg(w.done + fi.r)) continue;
+        const RealInfo &ri = t.real[fi.r];
+        const int m = fi.nU + fi.nP;
+        const T *yv = vec + ri.vec_off + static_cast<int64_t>(fi.slab) * ri.bmax + fi.pos;
+        const double *Tg = w.tsc + fi.tsc_off;
+        if (lane < m) {
+          double d = 0.0;
+          for (int q = lane; q < m; ++q) d += Tg[q * m + lane] * static_cast<double>(__ldcg(yv + q));
+          w.x[fi.unk + lane] += d;
+        }
+      }
+      grid.sync();
+    }
+    // B: FP64 residual, scaled into the slab vector
+    for (int g = gwarp; g < t.niface; g += nwarps) {
+      const IfaceInfo fi = t.iface[g];
+      if (__ldcg(w.done + fi.r)) continue;
+      const RealInfo &ri = t.real[fi.r];
+      const int m = fi.nU + fi.nP;
+      double rv = 0.0;
+      if (lane < m && fi.unk + lane != ri.pin) {
+        const RowRef rr = row_ref(t, w, fi, lane);
+        double sacc = w.f[fi.unk + lane];
+        for (int c = 1; c < rr.ncL; ++c) sacc -= rr.gL[c] * __ldcg(w.x + t.col[rr.offL + c].unk);
+        for (int c = 1; c < rr.ncR; ++c) sacc -= rr.gR[c] * __ldcg(w.x + t.col[rr.offR + c].unk);
+        rv = sacc;
+      }
+      double sq = rv * rv;
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if (lane == 0) w.r[g] = sq;
+      wbuf[wid][lane] = (lane >= fi.nU) ? -rv : rv;
+      __syncwarp();
+      if (lane < m) {
+        const double *Tg = w.tsc + fi.tsc_off;
+        double zv = 0.0;
+        for (int q = 0; q <= lane; ++q) zv += Tg[lane * m + q] * wbuf[wid][q];
+        vec[ri.vec_off + static_cast<int64_t>(fi.slab) * ri.bmax + fi.pos + lane] =
+            static_cast<T>(zv);
+      }
+      __syncwarp();
+    }
+    grid.sync();
+    // C: stop test, one CTA per realisation
+    for (int r = blockIdx.x; r < R; r += gridDim.x) {
+      if (__ldcg(w.done + r)) continue;
+      const RealInfo ri = t.real[r];
+      double rn = 0.0, fn = 0.0;
+      for (int g = ri.iface0 + threadIdx.x; g < ri.iface0 + ri.niface; g += blockDim.x)
+        rn += __ldcg(w.r + g);
+      for (int u = ri.unk0 + threadIdx.x; u < ri.unk0 + ri.nunk; u += blockDim.x)
+        fn += w.f[u] * w.f[u];
+      for (int pass = 0; pass < 2; ++pass) {
+        double v = pass == 0 ? rn : fn;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double sacc = 0.0;
+          for (int k = 0; k < 8; ++k) sacc += red[k];
+          if (pass == 0) s_rel = sacc;
+          else s_rel = sacc > 0.0 ? sqrt(s_rel / sacc) : 0.0;
+        }
+        __syncthreads();
+      }
+      const double rel = s_rel;
+      const double prev = w.dstat[2 + r];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        w.dstat[2 + r] = rel;
+        const bool stop = (rel <= tol) || (nsolve >= max_solves) || !(rel == rel) ||
+                          (nsolve >= 2 && rel > 0.5 * prev);
+        if (stop) {
+          atomic_max_pos_double(&w.dstat[1], rel);
+          atomicMax(&w.status[2], nsolve > 0 ? nsolve - 1 : 0);
+          if (!(rel <= tol)) atomicOr(&w.status[0], MRCM_FLAG_IFACE_STALL);
+          __threadfence();
+          atomicExch(w.done + r, 1);
+        }
+      }
+    }
+    grid.sync();
+    {
+      int all = 1;
+      for (int r = 0; r < R; ++r) all &= __ldcg(w.done + r);
+      if (all) break;
+    }
+    // D: y = Shat^{-1} z.  Forward: v_k -= X v_{k-s} + Y v_{k+s} (survivors)
+    for (int lev = 0, s = 1; lev < bp.nlev; ++lev, s <<= 1) {
+      const int nsv = (K + 2 * s - 1) / (2 * s);
+      const int64_t items = static_cast<int64_t>(R) * nsv * B;
+      for (int64_t q = gwarp; q < items; q += nwarps) {
+        const int r = static_cast<int>(q / (static_cast<int64_t>(nsv) * B));
+        const int rem = static_cast<int>(q % (static_cast<int64_t>(nsv) * B));
+        const int ki = rem / B, i = rem % B;
+        if (__ldcg(w.done + r)) continue;
+        const RealInfo &ri = t.real[r];
+        const int b = ri.bmax;
+        if (i >= b) continue;
+        const int k = ki * 2 * s;
+        const int64_t bb = static_cast<int64_t>(b) * b;
+        const T *Xs = static_cast<const T *>(w.X) + ri.xy_off +
+                      (static_cast<int64_t>(bp.lev_off[lev]) + ki) * bb;
+        const T *Ys = static_cast<const T *>(w.Y) + ri.xy_off +
+                      (static_cast<int64_t>(bp.lev_off[lev]) + ki) * bb;
+        T *v = vec + ri.vec_off;
+        T acc = T(0);
+        if (k - s >= 0) acc += row_dot(Xs + static_cast<int64_t>(i) * b, v + (k - s) * b, b);
+        if (k + s < K) acc += row_dot(Ys + static_cast<int64_t>(i) * b, v + (k + s) * b, b);
+        if (lane == 0) v[k * b + i] -= acc;
+      }
+      grid.sync();
+    }
+    // root: slab 0 (its block holds the inverse)
+    for (int64_t q = gwarp; q < static_cast<int64_t>(R) * B; q += nwarps) {
+      const int r = static_cast<int>(q / B), i = static_cast<int>(q % B);
+      if (__ldcg(w.done + r)) continue;
+      const RealInfo &ri = t.real[r];
+      const int b = ri.bmax;
+      if (i >= b) continue;
+      const T *I0 = static_cast<const T *>(w.slabB) + ri.slab_off;
+      const T acc = row_dot(I0 + static_cast<int64_t>(i) * b, vec + ri.vec_off, b);
+      if (lane == 0) tmp[ri.vec_off + i] = acc;
+    }
+    grid.sync();
+    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+         q < static_cast<int64_t>(R) * B; q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+      const int r = static_cast<int>(q / B), i = static_cast<int>(q % B);
+      if (__ldcg(w.done + r) || i >= t.real[r].bmax) continue;
+      vec[t.real[r].vec_off + i] = tmp[t.real[r].vec_off + i];
+    }
+    grid.sync();
+    // backward: y_k = B_k^{-1} (v_k - A_k y_{k-s} - C_k y_{k+s}), eliminated k
+    for (int lev = bp.nlev - 1; lev >= 0; --lev) {
+      const int s = 1 << lev;
+      const int nel = (K - s + 2 * s - 1) / (2 * s);
+      const int64_t items = static_cast<int64_t>(R) * nel * B;
+      for (int64_t q = gwarp; q < items; q += nwarps) {
+        const int r = static_cast<int>(q / (static_cast<int64_t>(nel) * B));
+        const int rem = static_cast<int>(q % (static_cast<int64_t>(nel) * B));
+        const int ki = rem / B, i = rem % B;
+        if (__ldcg(w.done + r)) continue;
+        const RealInfo &ri = t.real[r];
+        const int b = ri.bmax;
+        if (i >= b) continue;
+        const int k = s + ki * 2 * s;
+        const int64_t bb = static_cast<int64_t>(b) * b;
+        const T *As = static_cast<const T *>(w.slabA) + ri.slab_off + k * bb;
+        const T *Cs = static_cast<const T *>(w.slabC) + ri.slab_off + k * bb;
+        T *v = vec + ri.vec_off;
+        T acc = row_dot(As + static_cast<int64_t>(i) * b, v + (k - s) * b, b);
+        if (k + s < K) acc += row_dot(Cs + static_cast<int64_t>(i) * b, v + (k + s) * b, b);
+        if (lane == 0) tmp[ri.vec_off + k * b + i] = v[k * b + i] - acc;
+      }
+      grid.sync();
+      for (int64_t q = gwarp; q < items; q += nwarps) {
+        const int r = static_cast<int>(q / (static_cast<int64_t>(nel) * B));
+        const int rem = static_cast<int>(q % (static_cast<int64_t>(nel) * B));
+        const int ki = rem / B, i = rem % B;
+        if (__ldcg(w.done + r)) continue;
+        const RealInfo &ri = t.real[r];
+        const int b = ri.bmax;
+        if (i >= b) continue;
+        const int k = s + ki * 2 * s;
+        const int64_t bb = static_cast<int64_t>(b) * b;
+        const T *Is = static_cast<const T *>(w.slabB) + ri.slab_off + k * bb;
+        const T acc = row_dot(Is + static_cast<int64_t>(i) * b, tmp + ri.vec_off + k * b, b);
+        if (lane == 0) vec[ri.vec_off + k * b + i] = acc;
+      }
+      grid.sync();
+    }
+    ++nsolve;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host launch
+template <typename T>
+static cudaError_t big_factor_t(const BigPlan &bp, int *status, int *nlaunch, cudaStream_t st) {
+  for (int lev = 0; lev <= bp.nlev; ++lev) {
+    // inverses of this level's eliminated slabs (the root at lev == nlev)
+    const int i0 = bp.inv_off[lev], ni = bp.inv_off[lev + 1] - i0;
+    if (ni > 0) {
+      const int tiles = (bp.bmax + kGjNb - 1) / kGjNb;
+      for (int p = 0; p < bp.bmax; p += kGjNb) {
+        k_gj_panel<T><<<ni, kGjThreads, kGjPanelElems * sizeof(T), st>>>(bp.inv + i0, p, status);
+        k_gj_trail<T><<<dim3(tiles * tiles, ni), kGjThreads, kGjTrailElems * sizeof(T), st>>>(
+            bp.inv + i0, p);
+        *nlaunch += 2;
+      }
+    }
+    if (lev == bp.nlev) break;
+    const int tiles = (bp.bmax + kBM - 1) / kBM;
+    for (int set = 0; set < 2; ++set) {
+      const int g0 = bp.gemm_off[2 * lev + set], ng = bp.gemm_off[2 * lev + set + 1] - g0;
+      if (ng == 0) continue;
+      k_bgemm<T><<<dim3(tiles * tiles, ng), 256, 0, st>>>(bp.gemm + g0);
+      ++*nlaunch;
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t init_big_attributes() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_gj_panel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kGjPanelElems * sizeof(float)))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_gj_panel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kGjPanelElems * sizeof(double)))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_gj_trail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kGjTrailElems * sizeof(float)))) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_gj_trail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kGjTrailElems * sizeof(double)));
+}
+
+cudaError_t launch_big_factor(const BigPlan &bp, int prec, int *status, int *nlaunch,
+                              cudaStream_t st) {
+  if (prec == MRCM_PREC_FP64) return big_factor_t<double>(bp, status, nlaunch, st);
+  return big_factor_t<float>(bp, status, nlaunch, st);
+}
+
+int big_solve_grid(int prec, int dev) {
+  int nsm = 0, per = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (prec == MRCM_PREC_FP64)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_big_solve<double>, 256, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_big_solve<float>, 256, 0);
+  return nsm * (per < 4 ? per : 4);
+}
+
+cudaError_t launch_big_solve(const DeviceTables &t, const Workspace &w, const BigPlan &bp, int prec,
+                             double tol, int max_solves, int grid, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(w.x, 0, sizeof(double) * t.nunk, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(w.dstat + 2, 0, sizeof(double) * t.n_real, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(w.done, 0, sizeof(int) * (t.n_real + 1), st)) != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (prec == MRCM_PREC_FP64)
+    return cudaLaunchKernelEx(&cfg, k_big_solve<double>, t, w, bp, tol, max_solves);
+  return cudaLaunchKernelEx(&cfg, k_big_solve<float>, t, w, bp, tol, max_solves);
+}
+
+}  // namespace mrcm

@@ -62,6 +62,13 @@ struct mrcm_ctx {
   int solve_grid = 1;
   // GMRES interface path
   bool use_gmres = false;
+  // direct path with slabs above 64 unknowns
+  bool use_big = false;
+  std::vector<int> big_lev_off;
+  std::vector<InvJob> big_inv;
+  std::vector<GemmJob> big_gemm;
+  BigPlan bp{};
+  int big_grid = 0;
   int gm_K = 40, gm_maxit = 5000, gm_precond = 0, gm_nblk = 0;
   double gm_tol = 1e-13;
   bool gm_user_set = false;
@@ -330,13 +337,7 @@ static mrcm_status build_tables(mrcm_ctx *c) {
       }
       if (pos > ri.bmax) ri.bmax = pos;
     }
-    if (ri.bmax > 64) {
-      if (d.iface_solver == MRCM_IFACE_DIRECT)
-        return fail(nullptr, MRCM_EINVAL,
-                    "interface slab of %d unknowns exceeds the direct solver's 64 (use GMRES)",
-                    ri.bmax);
-      c->use_gmres = true;
-    }
+    if (ri.bmax > 64) c->use_big = true;
     int nlev = 0;
     while ((1 << nlev) < ri.nslab) ++nlev;
     ri.nlev = nlev;
@@ -364,9 +365,24 @@ static mrcm_status build_tables(mrcm_ctx *c) {
   if (d.iface_solver == MRCM_IFACE_GMRES) c->use_gmres = true;
   if (c->use_gmres) {
     // no slab blocks on the GMRES path
+    c->use_big = false;
     slab_off = 0;
     xy_off = 0;
     for (RealInfo &ri : c->real) ri.slab_off = ri.xy_off = 0;
+  } else if (c->use_big) {
+    // big slabs: one multiplier slot per surviving slab and level (compact)
+    const int K = c->real.empty() ? 1 : c->real[0].nslab;
+    int nlev = 0;
+    while ((1 << nlev) < K) ++nlev;
+    c->big_lev_off.assign(1, 0);
+    for (int lev = 0, st = 1; lev < nlev; ++lev, st <<= 1)
+      c->big_lev_off.push_back(c->big_lev_off.back() + (K + 2 * st - 1) / (2 * st));
+    xy_off = 0;
+    for (RealInfo &ri : c->real) {
+      ri.xy_off = xy_off;
+      xy_off += static_cast<int64_t>(c->big_lev_off.back()) * ri.bmax * ri.bmax;
+    }
+    if (nlev > kBigMaxLev) return fail(nullptr, MRCM_EINVAL, "too many slabs (%d)", K);
   }
   for (const IfaceInfo &fi : c->iface) c->mmax = std::max(c->mmax, fi.nU + fi.nP);
   for (const RealInfo &ri : c->real) {
@@ -403,7 +419,7 @@ static mrcm_status build_tables(mrcm_ctx *c) {
 // entries.  Everything the kernel would otherwise chase through the tables.
 static void build_plans(mrcm_ctx *c) {
   c->emax = 1;
-  if (c->use_gmres) {
+  if (c->use_gmres || c->use_big) {
     c->plans_ok = false;
     return;
   }
@@ -659,6 +675,10 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     return st;
   }
   build_plans(c);
+  if (c->mmax > kGmMmax) {
+    delete c;
+    return fail(nullptr, MRCM_EINVAL, "interface size nU + nP = %d above %d", c->mmax, kGmMmax);
+  }
   if (c->use_gmres) {
     if (c->mmax > kGmMmax) {
       delete c;
@@ -734,7 +754,7 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                o_sB = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
                o_sA = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
                o_sC = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
-               o_sI = A.take<char>((c->slab_elems ? c->slab_elems : 1) * esz),
+               o_sI = A.take<char>((c->slab_elems && !c->use_big ? c->slab_elems : 1) * esz),
                o_X = A.take<char>((c->xy_elems ? c->xy_elems : 1) * esz),
                o_Y = A.take<char>((c->xy_elems ? c->xy_elems : 1) * esz),
                o_ds = A.take<double>(c->tsc_elems ? c->tsc_elems : 1),
@@ -759,6 +779,26 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                o_gmint = A.take<int>(G ? 3 * d.n_real : 0),
                o_nboff = A.take<int>(G ? c->nb_off.size() : 0),
                o_nblist = A.take<int>(G ? c->nb_list.size() + 1 : 0);
+  // big-slab direct path: second slab vector, inverse scratch, job lists
+  const bool BG = c->use_big;
+  const int bigK = c->real.empty() ? 1 : c->real[0].nslab;
+  const int bigLev = static_cast<int>(c->big_lev_off.size()) - 1;
+  int64_t n_inv = 0, n_gemm = 0, inv_slots = 0;
+  if (BG) {
+    for (int lev = 0, st = 1; lev < bigLev; ++lev, st <<= 1) {
+      const int nel = (bigK - st + 2 * st - 1) / (2 * st), nsv = (bigK + 2 * st - 1) / (2 * st);
+      n_inv += static_cast<int64_t>(nel) * d.n_real;
+      inv_slots = std::max<int64_t>(inv_slots, static_cast<int64_t>(nel) * d.n_real);
+      n_gemm += static_cast<int64_t>(5) * nsv * d.n_real;
+    }
+    n_inv += d.n_real;                                   // the roots
+    inv_slots = std::max<int64_t>(inv_slots, d.n_real);
+  }
+  const int64_t slot_elems = 64 * 64 + static_cast<int64_t>(c->bmax_max) * 64;
+  const size_t o_vec2 = A.take<char>(BG ? (c->npos ? c->npos : 1) * esz : 0),
+               o_iscr = A.take<char>(BG ? inv_slots * slot_elems * esz : 0),
+               o_ijob = A.take<InvJob>(BG ? n_inv : 0), o_gjob = A.take<GemmJob>(BG ? n_gemm : 0),
+               o_levo = A.take<int>(BG ? c->big_lev_off.size() : 0);
   e = cudaMalloc(&c->arena, A.off);
   if (e != cudaSuccess) {
     delete c;
@@ -906,19 +946,104 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
       return cuda_fail(nullptr, e, "mrcm_setup upload");
     }
   }
+  if (BG) {
+    // jobs: level by level, the eliminated slabs' inverses (in place in the
+    // B blocks), then for the survivors X = A_k I_l, Y = C_k I_r and
+    // B_k -= X C_l + Y A_r, A_k = -X A_l, C_k = -Y C_r; the roots last
+    BigPlan &bp = c->bp;
+    bp.K = bigK;
+    bp.nlev = bigLev;
+    bp.bmax = c->bmax_max;
+    const size_t es = esz;
+    char *sB = static_cast<char *>(w.slabB), *sA = static_cast<char *>(w.slabA),
+         *sC = static_cast<char *>(w.slabC), *sX = static_cast<char *>(w.X),
+         *sY = static_cast<char *>(w.Y);
+    char *iscr = base + o_iscr;
+    auto blk = [&](char *b0, const RealInfo &ri, int k) {
+      return static_cast<void *>(b0 + (ri.slab_off + static_cast<int64_t>(k) * ri.bmax * ri.bmax) * es);
+    };
+    auto xy = [&](char *b0, const RealInfo &ri, int lev, int ki) {
+      return static_cast<void *>(b0 + (ri.xy_off + (static_cast<int64_t>(c->big_lev_off[lev]) + ki) *
+                                                       ri.bmax * ri.bmax) * es);
+    };
+    c->big_inv.clear();
+    c->big_gemm.clear();
+    for (int lev = 0, st = 1; lev <= bigLev; ++lev, st <<= 1) {
+      bp.inv_off[lev] = static_cast<int>(c->big_inv.size());
+      int slot = 0;
+      for (const RealInfo &ri : c->real) {
+        if (lev == bigLev) {
+          c->big_inv.push_back(InvJob{blk(sB, ri, 0), iscr + slot * slot_elems * es,
+                                      iscr + (slot * slot_elems + 4096) * es, ri.bmax, 0});
+          ++slot;
+          continue;
+        }
+        for (int k = st; k < bigK; k += 2 * st, ++slot)
+          c->big_inv.push_back(InvJob{blk(sB, ri, k), iscr + slot * slot_elems * es,
+                                      iscr + (slot * slot_elems + 4096) * es, ri.bmax, 0});
+      }
+      if (lev == bigLev) break;
+      for (int set = 0; set < 2; ++set) {
+        bp.gemm_off[2 * lev + set] = static_cast<int>(c->big_gemm.size());
+        for (const RealInfo &ri : c->real)
+          for (int k = 0, ki = 0; k < bigK; k += 2 * st, ++ki) {
+            const bool hl = k - st >= 0, hr = k + st < bigK;
+            void *X = xy(sX, ri, lev, ki), *Y = xy(sY, ri, lev, ki);
+            if (set == 0) {
+              if (hl) c->big_gemm.push_back(GemmJob{blk(sA, ri, k), blk(sB, ri, k - st), nullptr,
+                                                    nullptr, X, ri.bmax, 0, 1.0});
+              if (hr) c->big_gemm.push_back(GemmJob{blk(sC, ri, k), blk(sB, ri, k + st), nullptr,
+                                                    nullptr, Y, ri.bmax, 0, 1.0});
+            } else {
+              if (hl || hr)
+                c->big_gemm.push_back(GemmJob{hl ? X : nullptr, hl ? blk(sC, ri, k - st) : nullptr,
+                                              hr ? Y : nullptr, hr ? blk(sA, ri, k + st) : nullptr,
+                                              blk(sB, ri, k), ri.bmax, 1, -1.0});
+              if (hl) c->big_gemm.push_back(GemmJob{X, blk(sA, ri, k - st), nullptr, nullptr,
+                                                    blk(sA, ri, k), ri.bmax, 0, -1.0});
+              if (hr) c->big_gemm.push_back(GemmJob{Y, blk(sC, ri, k + st), nullptr, nullptr,
+                                                    blk(sC, ri, k), ri.bmax, 0, -1.0});
+            }
+          }
+        bp.gemm_off[2 * lev + set + 1] = static_cast<int>(c->big_gemm.size());
+      }
+    }
+    bp.inv_off[bigLev + 1] = static_cast<int>(c->big_inv.size());
+    bp.inv = reinterpret_cast<const InvJob *>(base + o_ijob);
+    bp.gemm = reinterpret_cast<const GemmJob *>(base + o_gjob);
+    bp.lev_off = reinterpret_cast<const int *>(base + o_levo);
+    bp.vec2 = base + o_vec2;
+    if (static_cast<int64_t>(c->big_inv.size()) > n_inv ||
+        static_cast<int64_t>(c->big_gemm.size()) > n_gemm ||
+        (e = up(o_ijob, c->big_inv.data(), c->big_inv.size() * sizeof(InvJob))) != cudaSuccess ||
+        (e = up(o_gjob, c->big_gemm.data(), c->big_gemm.size() * sizeof(GemmJob))) != cudaSuccess ||
+        (e = up(o_levo, c->big_lev_off.data(), c->big_lev_off.size() * sizeof(int))) !=
+            cudaSuccess) {
+      cudaFree(c->arena);
+      delete c;
+      return cuda_fail(nullptr, e == cudaSuccess ? cudaErrorInvalidValue : e, "big-slab plan");
+    }
+  }
   int bmax = 1;
   for (const RealInfo &ri : c->real) bmax = ri.bmax > bmax ? ri.bmax : bmax;
-  if ((e = init_local_attributes()) != cudaSuccess ||
-      (e = init_iface_attributes(c->prec, bmax, c->use_gmres ? 0 : c->max_vec)) != cudaSuccess) {
+  if ((e = init_local_attributes()) != cudaSuccess || (e = init_big_attributes()) != cudaSuccess ||
+      (e = init_iface_attributes(c->prec, bmax, c->use_gmres || BG ? 0 : c->max_vec)) !=
+          cudaSuccess) {
     cudaFree(c->arena);
     delete c;
     return cuda_fail(nullptr, e, "kernel attributes");
   }
-  c->solve_grid = c->use_gmres ? 0 : iface_solve_grid(c->prec, c->dev, c->max_vec);
+  c->solve_grid = c->use_gmres || BG ? 0 : iface_solve_grid(c->prec, c->dev, c->max_vec);
+  if (BG) c->big_grid = big_solve_grid(c->prec, c->dev);
   if (nunk > 0 && c->plans_ok && !c->use_gmres && !getenv("MRCM_NO_CLUSTER"))
     c->cluster_k = iface_cluster_plan(c->prec, c->nslab_max, c->bmax_max, c->nlev_max, c->mmax,
                                       t.emax, c->dev);
-  if (nunk > 0 && !c->use_gmres && (c->solve_grid < 1 || d.n_real > c->solve_grid)) {
+  if (nunk > 0 && BG && c->big_grid < 1) {
+    cudaFree(c->arena);
+    delete c;
+    return fail(nullptr, MRCM_ECUDA, "no co-resident grid for the interface solve");
+  }
+  if (nunk > 0 && !c->use_gmres && !BG && (c->solve_grid < 1 || d.n_real > c->solve_grid)) {
     cudaFree(c->arena);
     delete c;
     return fail(nullptr, MRCM_EINVAL,
@@ -1042,6 +1167,21 @@ mrcm_status mrcm_solve_interface(mrcm_ctx *ctx, mrcm_info *info) {
   if (ctx->nunk > 0 && ctx->use_gmres) {
     mrcm_status gs = solve_gmres(ctx);
     if (gs != MRCM_OK) return gs;
+  } else if (ctx->nunk > 0 && ctx->use_big) {
+    cudaError_t e = launch_iface_assemble(ctx->t, ctx->w, ctx->prec, ctx->slab_elems,
+                                          ctx->d_pos2unk, ctx->npos, ctx->d_pos_real_off,
+                                          ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "interface assembly launch");
+    ctx->launches += 3;
+    int nl = 0;
+    if ((e = launch_big_factor(ctx->bp, ctx->prec, ctx->w.status, &nl, ctx->stream)) !=
+        cudaSuccess)
+      return cuda_fail(ctx, e, "interface factor launch");
+    ctx->launches += nl;
+    if ((e = launch_big_solve(ctx->t, ctx->w, ctx->bp, ctx->prec, ctx->d.iface_tol,
+                              1 + ctx->d.iface_ir_max, ctx->big_grid, ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "interface solve launch");
+    ctx->launches += 1;
   } else if (ctx->nunk > 0 && ctx->cluster_k > 0) {
     cudaError_t e = launch_iface_cluster(ctx->t, ctx->w, ctx->d_slab_if, ctx->d_slab_if_off,
                                          ctx->cluster_k, ctx->bmax_max, ctx->nlev_max,

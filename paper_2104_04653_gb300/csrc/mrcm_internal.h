@@ -118,6 +118,33 @@ constexpr double kLpClip = 2.0;   // entrywise bound of a target
 constexpr int kNC16 = 12;     // basis columns per CTA, s = 16
 constexpr int kNC32 = 8;      // basis columns per CTA, s = 32
 
+// Direct interface path for slabs above 64 unknowns (iface_big.cu)
+constexpr int kBigMaxLev = 20;
+
+struct InvJob {      // in-place inverse of one n x n block
+  void *a;           // the block (row-major)
+  void *dinv;        // 64 x 64 scratch
+  void *cpan;        // n x 64 scratch
+  int n, pad;
+};
+
+struct GemmJob {     // C = alpha (A1 B1 + A2 B2) (+ C if acc), n x n row-major
+  const void *a1, *b1, *a2, *b2;   // a2/b2 may be null
+  void *c;
+  int n, acc;
+  double alpha;
+};
+
+struct BigPlan {
+  int K, nlev, bmax;             // slabs, levels, largest slab
+  const int *lev_off;            // device [nlev + 1]: first multiplier slot of each level
+  void *vec2;                    // second slab-ordered vector
+  const InvJob *inv;             // device jobs, level by level, the root last
+  const GemmJob *gemm;           // device jobs, two sets per level
+  int inv_off[kBigMaxLev + 2];   // host: job ranges per level (nlev + 1 ranges)
+  int gemm_off[2 * kBigMaxLev + 1];
+};
+
 struct BasisItem {   // one CTA of the basis kernel
   int sub;
   int c0, nc;        // column range
@@ -204,6 +231,12 @@ int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int em
 cudaError_t launch_iface_cluster(const DeviceTables &t, const Workspace &w, const int *slab_if,
                                  const int *slab_if_off, int nslab, int bmax, int nlev,
                                  double tol, int max_solves, cudaStream_t st);
+cudaError_t init_big_attributes();
+cudaError_t launch_big_factor(const BigPlan &bp, int prec, int *status, int *nlaunch,
+                              cudaStream_t st);
+int big_solve_grid(int prec, int dev);
+cudaError_t launch_big_solve(const DeviceTables &t, const Workspace &w, const BigPlan &bp, int prec,
+                             double tol, int max_solves, int grid, cudaStream_t st);
 size_t gmres_smem_bytes(int K);
 int gmres_max_blocks(int K, int dev);
 cudaError_t launch_gmres_precond(const DeviceTables &t, const Workspace &w, const GmArgs &a,

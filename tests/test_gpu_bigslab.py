@@ -1,0 +1,105 @@
+"""GPU parity of the direct interface path for slabs above 64 unknowns
+(batched blocked Gauss-Jordan, batched GEMMs, cooperative refinement)
+against the FP64 oracle (relative L2 <= 1e-8)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_04653_gb300 import build
+    build.build()
+
+
+def _mods():
+    from oracle import mrcm_oracle as O
+    from paper_2104_04653_gb300 import mrcm, workloads as W
+    return O, mrcm, W
+
+
+def _check(prob, opts, ref=None):
+    O, mrcm, W = _mods()
+    ref = ref if ref is not None else O.mrcm_solve(prob)
+    s = mrcm.Mrcm(prob, opts)
+    K, L, Q = mrcm.device_inputs(prob)
+    p, ux, uy = s.solve(K, L, Q)
+    info = s.mrcm_get_info()
+    assert not s.uses_gmres()
+    got = dict(p=p.cpu().numpy(), ux=ux.cpu().numpy(), uy=uy.cpu().numpy())
+    s.close()
+    worst = 0.0
+    for r in range(prob.n_real):
+        one = {k: v[r:r + 1] for k, v in got.items()}
+        rr = {k: ref[k][r:r + 1] for k in ("p", "ux", "uy")}
+        worst = max(worst, *O.errors(one, rr))
+    assert worst <= TOL, (prob.name, worst, info)
+    assert info["gmres_iters"] == 0 and info["iface_resid"] <= opts.iface_tol
+    return info
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_wide_slabs_lognormal_resolve(prec):
+    """256^2 lognormal K with Buckley-Leverett mobility, 16x16 subdomains,
+    m = 4: slabs of 124 unknowns, chosen automatically."""
+    O, mrcm, W = _mods()
+    _check(W.config5(4, n=256), mrcm.SolverOptions(prec=prec))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_wide_slabs_channels_s32(prec):
+    """512^2 channels, contrast 1e6, 16x16 subdomains of 32x32 cells: slabs
+    of 124 unknowns."""
+    O, mrcm, W = _mods()
+    _check(W.config4(n=512, s=32, n_ch=16), mrcm.SolverOptions(prec=prec))
+
+
+def test_wide_slabs_mixed_sizes_ragged():
+    """Two realisations (16x16 and 32x32 subdomains) of the 1024^2 batch's
+    generator at 256^2: interface sizes drawn from {2,4,6,8}, slabs of
+    different widths (above 64) in one batch."""
+    O, mrcm, W = _mods()
+    prob = W.config3(n_real=2, n=256)
+    _check(prob, mrcm.SolverOptions(prec=1, iface_solver=mrcm.IFACE_DIRECT))
+
+
+def test_wide_slabs_pure_neumann():
+    O, mrcm, W = _mods()
+    n = 256
+    rng = np.random.default_rng(31)
+    K = np.exp(rng.standard_normal((n, n)))
+    prob = W.make_problem(n, n, 16, K, q=W.five_spot_sources(n, n, 1.0 / n),
+                          bc=W.bc_no_flow(n, n), n_u=2, n_p=2, pure_neumann=True)
+    _check(prob, mrcm.SolverOptions(prec=1))
+
+
+def test_wide_slabs_graph_replay():
+    import torch
+    O, mrcm, W = _mods()
+    prob = W.config5(2, n=256)
+    s = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=1))
+    K, L, Q = mrcm.device_inputs(prob)
+    eager = [t.clone() for t in s.solve(K, L, Q)]
+    out = s.alloc_outputs()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        s.solve(K, L, Q, out=out)
+    torch.cuda.current_stream().wait_stream(side)
+    with torch.cuda.graph(g):
+        s.L.mrcm_set_stream(s.ctx, torch.cuda.current_stream().cuda_stream)
+        s.solve(K, L, Q, out=out)
+    for t in out:
+        t.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for x, y in zip(eager, out):
+        assert torch.equal(x, y)
+    s.close()

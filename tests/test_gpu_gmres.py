@@ -94,20 +94,11 @@ def test_gmres_multi_realisation_ragged():
     _check(prob, _opts(1, gmres_restart=16))
 
 
-def test_auto_selects_gmres_for_wide_slabs():
+def test_gmres_for_wide_slabs():
     """256x256 lognormal K with Buckley-Leverett mobility, 16x16 subdomains,
-    m = 4: slabs of 124 unknowns exceed the direct solver, so the automatic
-    choice is GMRES."""
+    m = 4 (slabs of 124 unknowns) on the GMRES path."""
     _, _, mrcm, W = _mods()
-    prob = W.config5(4, n=256)
-    _check(prob, mrcm.SolverOptions(prec=1))
-
-
-def test_direct_solver_rejects_wide_slabs():
-    _, _, mrcm, W = _mods()
-    with pytest.raises(mrcm.MrcmError) as e:
-        mrcm.Mrcm(W.config5(4, n=256), mrcm.SolverOptions(prec=1, iface_solver=mrcm.IFACE_DIRECT))
-    assert e.value.status == mrcm.MRCM_EINVAL
+    _check(W.config5(4, n=256), _opts(1))
 
 
 def _oracle_system(prob):
