@@ -413,7 +413,7 @@ def run_suite(args):
         cases.append(("lognormal-32x1024x1024-s16/32-m2..8", W.config3(), {}))
     for name, prob, extra in cases:
         for prec in (mrcm.PREC_FP32_IR, mrcm.PREC_FP64):
-            opts = mrcm.SolverOptions(prec=prec, iface_tol=1e-12, gmres_tol=1e-12, gmres_max=6000,
+            opts = mrcm.SolverOptions(prec=prec, iface_tol=1e-11, gmres_tol=1e-11, gmres_max=6000,
                                       **extra)
             s = mrcm.Mrcm(prob, opts)
             K, L, Q = mrcm.device_inputs(prob)

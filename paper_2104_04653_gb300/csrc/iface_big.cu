@@ -31,11 +31,13 @@ constexpr int kGjThreads = 256;
 
 // ---------------------------------------------------------------- inverse
 // Panel step p of the in-place Gauss-Jordan inverse of every matrix of the
-// batch (one CTA per matrix): D = A[p.., p..]^{-1} into the matrix and into
-// job.dinv, the old pivot column panel (rows outside the panel) into
-// job.cpan, and the pivot row panel R = D A[p.., :] (columns outside the
-// panel) back into the matrix.
-constexpr size_t kGjPanelElems = 2 * kGjNb * kGjNb + 64 + 2 * 512;
+// batch, in three launches:
+//   k_gj_panel (one CTA per matrix): D = A[p.., p..]^{-1} into job.dinv;
+//   k_gj_rowpanel (one CTA per matrix and 64-column tile): the old pivot
+//     column panel rows of that tile into job.cpan, and the pivot row panel
+//     R = D A[p.., tile] back into the matrix (D itself for the panel tile);
+//   k_gj_trail (below): the rank-64 update of every other row tile.
+constexpr size_t kGjPanelElems = kGjNb * kGjNb + 64 + 2 * 512;
 constexpr size_t kGjTrailElems = 2 * kGjNb * kGjNb;
 
 template <typename T>
@@ -43,55 +45,94 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_panel(const InvJob *jobs, int
                                                          int *status) {
   extern __shared__ __align__(16) unsigned char gsmraw[];
   T *D = reinterpret_cast<T *>(gsmraw);
-  T *tile = D + kGjNb * kGjNb;
-  T *scr = tile + kGjNb * kGjNb;
+  T *scr = D + kGjNb * kGjNb;
   __shared__ int bad;
   const InvJob jb = jobs[blockIdx.x];
   const int n = jb.n;
   if (p >= n) return;
-  T *A = static_cast<T *>(jb.a);
+  const T *A = static_cast<const T *>(jb.a);
   T *Dout = static_cast<T *>(jb.dinv);
-  T *Cp = static_cast<T *>(jb.cpan);
   const int w = n - p < kGjNb ? n - p : kGjNb;
   const int t = threadIdx.x;
   if (t == 0) bad = 0;
+#pragma unroll 4
   for (int e = t; e < kGjNb * kGjNb; e += kGjThreads) {
     const int i = e / kGjNb, j = e % kGjNb;
     D[e] = (i < w && j < w) ? A[static_cast<int64_t>(p + i) * n + p + j] : T(i == j);
   }
-  // old column panel, rows outside the panel
-  for (int64_t e = t; e < static_cast<int64_t>(n) * w; e += kGjThreads) {
-    const int i = static_cast<int>(e / w), c = static_cast<int>(e % w);
-    if (i >= p && i < p + w) continue;
-    Cp[e] = A[static_cast<int64_t>(i) * n + p + c];
-  }
   __syncthreads();
   gj_inverse_blocked<T, kGjThreads>(D, kGjNb, kGjNb, scr, &bad);
   __syncthreads();
-  for (int e = t; e < w * w; e += kGjThreads) {
-    const int i = e / w, j = e % w;
-    const T v = D[i * kGjNb + j];
-    Dout[e] = v;
-    A[static_cast<int64_t>(p + i) * n + p + j] = v;
-  }
-  // row panel, 64 columns at a time
-  for (int j0 = 0; j0 < n; j0 += kGjNb) {
-    if (j0 == p) continue;                      // panels are 64-aligned
-    const int wj = n - j0 < kGjNb ? n - j0 : kGjNb;
-    __syncthreads();
-    for (int e = t; e < kGjNb * kGjNb; e += kGjThreads) {
-      const int c = e / kGjNb, j = e % kGjNb;
-      tile[e] = (c < w && j < wj) ? A[static_cast<int64_t>(p + c) * n + j0 + j] : T(0);
-    }
-    __syncthreads();
-    for (int e = t; e < w * wj; e += kGjThreads) {
-      const int r = e / wj, j = e % wj;
-      T acc = T(0);
-      for (int c = 0; c < w; ++c) acc += D[r * kGjNb + c] * tile[c * kGjNb + j];
-      A[static_cast<int64_t>(p + r) * n + j0 + j] = acc;
-    }
-  }
+#pragma unroll 4
+  for (int e = t; e < kGjNb * kGjNb; e += kGjThreads) Dout[e] = D[e];
   if (t == 0 && bad) atomicOr(status, MRCM_FLAG_IFACE_PIVOT);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGjThreads) k_gj_rowpanel(const InvJob *jobs, int p) {
+  extern __shared__ __align__(16) unsigned char gsmraw[];
+  T *D = reinterpret_cast<T *>(gsmraw);
+  T *tile = D + kGjNb * kGjNb;
+  const InvJob jb = jobs[blockIdx.y];
+  const int n = jb.n;
+  if (p >= n) return;
+  const int nt = (n + kGjNb - 1) / kGjNb;
+  if (static_cast<int>(blockIdx.x) >= nt) return;
+  const int j0 = blockIdx.x * kGjNb;
+  T *A = static_cast<T *>(jb.a);
+  const T *Dv = static_cast<const T *>(jb.dinv);
+  T *Cp = static_cast<T *>(jb.cpan);
+  const int w = n - p < kGjNb ? n - p : kGjNb;
+  const int wj = n - j0 < kGjNb ? n - j0 : kGjNb;
+  const int t = threadIdx.x;
+  if (j0 == p) {
+    // the panel tile: rows [p, p+w) become D
+#pragma unroll 4
+    for (int e = t; e < kGjNb * kGjNb; e += kGjThreads) {
+      const int i = e / kGjNb, j = e % kGjNb;
+      if (i < w && j < w) A[static_cast<int64_t>(p + i) * n + p + j] = Dv[e];
+    }
+    return;
+  }
+  // old column panel of the rows of this tile (rows j0 .. j0+wj)
+#pragma unroll 4
+  for (int e = t; e < kGjNb * kGjNb; e += kGjThreads) {
+    const int i = e / kGjNb, c = e % kGjNb;
+    if (i < wj && c < w) Cp[static_cast<int64_t>(j0 + i) * w + c] =
+        A[static_cast<int64_t>(j0 + i) * n + p + c];
+  }
+#pragma unroll 4
+  for (int e = t; e < kGjNb * kGjNb; e += kGjThreads) {
+    D[e] = Dv[e];
+    const int c = e / kGjNb, j = e % kGjNb;
+    tile[e] = (c < w && j < wj) ? A[static_cast<int64_t>(p + c) * n + j0 + j] : T(0);
+  }
+  __syncthreads();
+  // R = D tile: thread owns 4 rows x 4 columns
+  const int tr = (t / 16) * 4, tc = (t % 16) * 4;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int c = 0; c < w; ++c) {
+    T da[4], tb[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) da[a] = D[(tr + a) * kGjNb + c];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) tb[b] = tile[c * kGjNb + tc + b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] += da[a] * tb[b];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (tr + a >= w) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (tc + b < wj) A[static_cast<int64_t>(p + tr + a) * n + j0 + tc + b] = acc[a][b];
+  }
 }
 
 // Rank-w update of panel step p: for rows i outside the panel,
@@ -122,7 +163,7 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_trail(const InvJob *jobs, int
     const int a = e / kGjNb, b = e % kGjNb;
     Cs[e] = (a < hi && b < w) ? Cp[static_cast<int64_t>(i0 + a) * w + b] : T(0);
     T r = T(0);
-    if (a < w && b < wj) r = pcol ? Dv[a * w + b] : A[static_cast<int64_t>(p + a) * n + j0 + b];
+    if (a < w && b < wj) r = pcol ? Dv[a * kGjNb + b] : A[static_cast<int64_t>(p + a) * n + j0 + b];
     Rs[e] = r;
   }
   __syncthreads();
@@ -158,15 +199,48 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_trail(const InvJob *jobs, int
 
 // ---------------------------------------------------------------- GEMM
 // C = alpha (A1 B1 + A2 B2) (+ C if acc), all n x n row-major.  128 x 128
-// output tile per CTA, 256 threads with 8 x 8 outputs each, k-steps of 8
-// staged in shared memory (A transposed so both operands are read as
-// broadcast-free row vectors).
+// output tile per CTA and 256 threads; each thread owns the 8 x 8 outputs
+// at rows {4ty.., 64+4ty..} and columns {4tx.., 64+4tx..}, read from
+// shared memory as 4-wide vectors (conflict-free).  k-steps of 8 are
+// double-buffered: the next step's operands are loaded into registers
+// while the current one is multiplied.
 constexpr int kBM = 128, kBK = 8;
 
 template <typename T>
+struct Vec4 {
+  static __device__ __forceinline__ void ld(const T *p, T v[4]) {
+    v[0] = p[0];
+    v[1] = p[1];
+    v[2] = p[2];
+    v[3] = p[3];
+  }
+};
+template <>
+struct Vec4<float> {
+  static __device__ __forceinline__ void ld(const float *p, float v[4]) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  static __device__ __forceinline__ void ld(const double *p, double v[4]) {
+    const double2 q0 = *reinterpret_cast<const double2 *>(p);
+    const double2 q1 = *reinterpret_cast<const double2 *>(p + 2);
+    v[0] = q0.x;
+    v[1] = q0.y;
+    v[2] = q1.x;
+    v[3] = q1.y;
+  }
+};
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_bgemm(const GemmJob *jobs) {
-  __shared__ T As[kBK][kBM];
-  __shared__ T Bs[kBK][kBM];
+  __shared__ __align__(16) T As[2][kBK][kBM];
+  __shared__ __align__(16) T Bs[2][kBK][kBM];
   const GemmJob jb = jobs[blockIdx.y];
   const int n = jb.n;
   const int nt = (n + kBM - 1) / kBM;
@@ -174,52 +248,74 @@ __global__ void __launch_bounds__(256) k_bgemm(const GemmJob *jobs) {
   if (ti >= nt) return;
   const int i0 = ti * kBM, j0 = tj * kBM;
   const int t = threadIdx.x, ty = t / 16, tx = t % 16;
+  const int ar = t >> 1, ak = (t & 1) * 4;          // loader: A rows, 4 k each
+  const int bk = t >> 5, bc = (t & 31) * 4;         // loader: B k, 4 columns each
+  const T *A1 = static_cast<const T *>(jb.a1), *A2 = static_cast<const T *>(jb.a2);
+  const T *B1 = static_cast<const T *>(jb.b1), *B2 = static_cast<const T *>(jb.b2);
+  const int nk = (n + kBK - 1) / kBK;
+  const int np = (A1 && B1 ? 1 : 0) + (A2 && B2 ? 1 : 0);
+  const int first = (A1 && B1) ? 0 : 1;
+  const int total = np * nk;
+  T ra[4], rb[4];
+  auto load = [&](int step) {
+    const int prod = first + step / nk, k0 = (step % nk) * kBK;
+    const T *Ap = prod == 0 ? A1 : A2, *Bp = prod == 0 ? B1 : B2;
+    const int gi = i0 + ar;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gk = k0 + ak + q;
+      ra[q] = (gi < n && gk < n) ? Ap[static_cast<int64_t>(gi) * n + gk] : T(0);
+    }
+    const int gk = k0 + bk;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gj = j0 + bc + q;
+      rb[q] = (gk < n && gj < n) ? Bp[static_cast<int64_t>(gk) * n + gj] : T(0);
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) As[buf][ak + q][ar] = ra[q];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Bs[buf][bk][bc + q] = rb[q];
+  };
   T acc[8][8];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int b = 0; b < 8; ++b) acc[a][b] = T(0);
-  for (int prod = 0; prod < 2; ++prod) {
-    const T *A = static_cast<const T *>(prod == 0 ? jb.a1 : jb.a2);
-    const T *B = static_cast<const T *>(prod == 0 ? jb.b1 : jb.b2);
-    if (!A || !B) continue;
-    for (int k0 = 0; k0 < n; k0 += kBK) {
-      // A tile [128 rows][8 k] -> As[k][row]; B tile [8 k][128 cols]
+  if (total > 0) {
+    load(0);
+    store(0);
+    __syncthreads();
+  }
+  for (int step = 0; step < total; ++step) {
+    const int buf = step & 1;
+    if (step + 1 < total) load(step + 1);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = t + 256 * q;
-        const int ar = e / kBK, ak = e % kBK;
-        const int gi = i0 + ar, gk = k0 + ak;
-        As[ak][ar] = (gi < n && gk < n) ? A[static_cast<int64_t>(gi) * n + gk] : T(0);
-        const int bk = e / kBM, bc = e % kBM;
-        const int gk2 = k0 + bk, gj = j0 + bc;
-        Bs[bk][bc] = (gk2 < n && gj < n) ? B[static_cast<int64_t>(gk2) * n + gj] : T(0);
-      }
-      __syncthreads();
+    for (int kk = 0; kk < kBK; ++kk) {
+      T a[8], b[8];
+      Vec4<T>::ld(&As[buf][kk][ty * 4], a);
+      Vec4<T>::ld(&As[buf][kk][64 + ty * 4], a + 4);
+      Vec4<T>::ld(&Bs[buf][kk][tx * 4], b);
+      Vec4<T>::ld(&Bs[buf][kk][64 + tx * 4], b + 4);
 #pragma unroll
-      for (int kk = 0; kk < kBK; ++kk) {
-        T a[8], b[8];
+      for (int q = 0; q < 8; ++q)
 #pragma unroll
-        for (int q = 0; q < 8; ++q) a[q] = As[kk][ty * 8 + q];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) b[q] = Bs[kk][tx * 8 + q];
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-#pragma unroll
-          for (int r = 0; r < 8; ++r) acc[q][r] += a[q] * b[r];
-      }
-      __syncthreads();
+        for (int r = 0; r < 8; ++r) acc[q][r] += a[q] * b[r];
     }
+    if (step + 1 < total) store(buf ^ 1);
+    __syncthreads();
   }
   T *C = static_cast<T *>(jb.c);
   const T alpha = static_cast<T>(jb.alpha);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const int gi = i0 + ty * 8 + q;
+    const int gi = i0 + (q < 4 ? ty * 4 + q : 64 + ty * 4 + q - 4);
     if (gi >= n) continue;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      const int gj = j0 + tx * 8 + r;
+      const int gj = j0 + (r < 4 ? tx * 4 + r : 64 + tx * 4 + r - 4);
       if (gj >= n) continue;
       const int64_t o = static_cast<int64_t>(gi) * n + gj;
       C[o] = jb.acc ? C[o] + alpha * acc[q][r] : alpha * acc[q][r];
@@ -446,9 +542,11 @@ static cudaError_t big_factor_t(const BigPlan &bp, int *status, int *nlaunch, cu
       const int tiles = (bp.bmax + kGjNb - 1) / kGjNb;
       for (int p = 0; p < bp.bmax; p += kGjNb) {
         k_gj_panel<T><<<ni, kGjThreads, kGjPanelElems * sizeof(T), st>>>(bp.inv + i0, p, status);
+        k_gj_rowpanel<T><<<dim3(tiles, ni), kGjThreads, kGjTrailElems * sizeof(T), st>>>(
+            bp.inv + i0, p);
         k_gj_trail<T><<<dim3(tiles * tiles, ni), kGjThreads, kGjTrailElems * sizeof(T), st>>>(
             bp.inv + i0, p);
-        *nlaunch += 2;
+        *nlaunch += 3;
       }
     }
     if (lev == bp.nlev) break;
@@ -470,7 +568,11 @@ cudaError_t init_big_attributes() {
       (e = cudaFuncSetAttribute(k_gj_panel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kGjPanelElems * sizeof(double)))) != cudaSuccess ||
       (e = cudaFuncSetAttribute(k_gj_trail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(kGjTrailElems * sizeof(float)))) != cudaSuccess)
+                                static_cast<int>(kGjTrailElems * sizeof(float)))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_gj_rowpanel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kGjTrailElems * sizeof(float)))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_gj_rowpanel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kGjTrailElems * sizeof(double)))) != cudaSuccess)
     return e;
   return cudaFuncSetAttribute(k_gj_trail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(kGjTrailElems * sizeof(double)));
