@@ -554,7 +554,18 @@ static cudaError_t big_factor_t(const BigPlan &bp, int *status, int *nlaunch, cu
     for (int set = 0; set < 2; ++set) {
       const int g0 = bp.gemm_off[2 * lev + set], ng = bp.gemm_off[2 * lev + set + 1] - g0;
       if (ng == 0) continue;
-      k_bgemm<T><<<dim3(tiles * tiles, ng), 256, 0, st>>>(bp.gemm + g0);
+      if (sizeof(T) == sizeof(float) && bp.tensor_cores) {
+        for (int c0 = 0; c0 < ng; c0 += bp.tc_chunk) {
+          const int cnt = ng - c0 < bp.tc_chunk ? ng - c0 : bp.tc_chunk;
+          cudaError_t e = launch_tc_chunk(
+              bp.gemm + g0 + c0, static_cast<const char *>(bp.tc_maps) + (g0 + c0) * 8 * 128, cnt,
+              bp.bmax, bp.tc_planes, bp.tc_plane_elems, status, st);
+          if (e != cudaSuccess) return e;
+          ++*nlaunch;
+        }
+      } else {
+        k_bgemm<T><<<dim3(tiles * tiles, ng), 256, 0, st>>>(bp.gemm + g0);
+      }
       ++*nlaunch;
     }
   }
@@ -582,6 +593,13 @@ cudaError_t launch_big_factor(const BigPlan &bp, int prec, int *status, int *nla
                               cudaStream_t st) {
   if (prec == MRCM_PREC_FP64) return big_factor_t<double>(bp, status, nlaunch, st);
   return big_factor_t<float>(bp, status, nlaunch, st);
+}
+
+cudaError_t launch_simt_gemm(const GemmJob *jobs, int njobs, int nmax, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  const int tiles = (nmax + kBM - 1) / kBM;
+  k_bgemm<float><<<dim3(tiles * tiles, njobs), 256, 0, st>>>(jobs);
+  return cudaGetLastError();
 }
 
 int big_solve_grid(int prec, int dev) {

@@ -795,6 +795,13 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     inv_slots = std::max<int64_t>(inv_slots, d.n_real);
   }
   const int64_t slot_elems = 64 * 64 + static_cast<int64_t>(c->bmax_max) * 64;
+  // tensor-core products (FP32 path): packed planes for one chunk of jobs and
+  // 8 tensor maps (128 bytes each) per job
+  const bool TC = BG && c->prec != MRCM_PREC_FP64 && !getenv("MRCM_NO_TENSOR_CORES");
+  const int tc_chunk = 64;
+  const int64_t tc_pe = static_cast<int64_t>(c->bmax_max) * tc_pack_ldp(c->bmax_max);
+  const size_t o_tcp = A.take<float>(TC ? static_cast<int64_t>(tc_chunk) * 8 * tc_pe : 0),
+               o_tcm = A.take<char>(TC ? n_gemm * 8 * 128 : 0);
   const size_t o_vec2 = A.take<char>(BG ? (c->npos ? c->npos : 1) * esz : 0),
                o_iscr = A.take<char>(BG ? inv_slots * slot_elems * esz : 0),
                o_ijob = A.take<InvJob>(BG ? n_inv : 0), o_gjob = A.take<GemmJob>(BG ? n_gemm : 0),
@@ -954,6 +961,11 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     bp.K = bigK;
     bp.nlev = bigLev;
     bp.bmax = c->bmax_max;
+    bp.tensor_cores = TC ? 1 : 0;
+    bp.tc_chunk = tc_chunk;
+    bp.tc_planes = base + o_tcp;
+    bp.tc_plane_elems = tc_pe;
+    bp.tc_maps = base + o_tcm;
     const size_t es = esz;
     char *sB = static_cast<char *>(w.slabB), *sA = static_cast<char *>(w.slabA),
          *sC = static_cast<char *>(w.slabC), *sX = static_cast<char *>(w.X),
@@ -1009,6 +1021,16 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
       }
     }
     bp.inv_off[bigLev + 1] = static_cast<int>(c->big_inv.size());
+    std::vector<char> maps;
+    bool maps_ok = true;
+    if (TC) {
+      // job j of a set uses plane slot (j - set start) mod chunk
+      maps.assign(c->big_gemm.size() * 8 * 128, 0);
+      for (int sidx = 0; sidx < 2 * bigLev; ++sidx)
+        for (int j = bp.gemm_off[sidx]; j < bp.gemm_off[sidx + 1]; ++j)
+          maps_ok = maps_ok && tc_encode_maps(bp.tc_planes, tc_pe, (j - bp.gemm_off[sidx]) % tc_chunk,
+                                              c->big_gemm[j].n, maps.data() + static_cast<size_t>(j) * 8 * 128);
+    }
     bp.inv = reinterpret_cast<const InvJob *>(base + o_ijob);
     bp.gemm = reinterpret_cast<const GemmJob *>(base + o_gjob);
     bp.lev_off = reinterpret_cast<const int *>(base + o_levo);
@@ -1018,7 +1040,8 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
         (e = up(o_ijob, c->big_inv.data(), c->big_inv.size() * sizeof(InvJob))) != cudaSuccess ||
         (e = up(o_gjob, c->big_gemm.data(), c->big_gemm.size() * sizeof(GemmJob))) != cudaSuccess ||
         (e = up(o_levo, c->big_lev_off.data(), c->big_lev_off.size() * sizeof(int))) !=
-            cudaSuccess) {
+            cudaSuccess ||
+        !maps_ok || (TC && (e = up(o_tcm, maps.data(), maps.size())) != cudaSuccess)) {
       cudaFree(c->arena);
       delete c;
       return cuda_fail(nullptr, e == cudaSuccess ? cudaErrorInvalidValue : e, "big-slab plan");
@@ -1027,6 +1050,7 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   int bmax = 1;
   for (const RealInfo &ri : c->real) bmax = ri.bmax > bmax ? ri.bmax : bmax;
   if ((e = init_local_attributes()) != cudaSuccess || (e = init_big_attributes()) != cudaSuccess ||
+      (e = init_tc_attributes()) != cudaSuccess ||
       (e = init_iface_attributes(c->prec, bmax, c->use_gmres || BG ? 0 : c->max_vec)) !=
           cudaSuccess) {
     cudaFree(c->arena);

@@ -103,3 +103,39 @@ def test_wide_slabs_graph_replay():
     for x, y in zip(eager, out):
         assert torch.equal(x, y)
     s.close()
+
+
+@pytest.mark.parametrize("impl", [0, 1, 2])
+@pytest.mark.parametrize("n", [64, 100, 128, 252, 300])
+def test_batched_gemm_kernels(impl, n):
+    """C = alpha (A1 B1 + A2 B2) + C of the large-slab factor: the SIMT
+    kernel (impl 0), the tcgen05 kernel with 3 x TF32 split products (impl
+    1: operands staged through registers; impl 2: packed head/tail planes
+    streamed by TMA through a 3-stage pipeline) against an FP64 product, in
+    both forms (one or two products, accumulate or not)."""
+    import ctypes
+    import torch
+    from paper_2104_04653_gb300 import mrcm
+    L = mrcm.lib()
+    L.mrcm_test_gemm.argtypes = [ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 5 + \
+        [ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    L.mrcm_test_gemm.restype = ctypes.c_int32
+    rng = np.random.default_rng(n + 7 * impl)
+    mats = [rng.standard_normal((n, n)).astype(np.float32) for _ in range(5)]
+    dev = [torch.as_tensor(m, device="cuda") for m in mats]
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for two, acc, alpha in ((True, True, -1.0), (False, False, 1.0)):
+        c = dev[4].clone()
+        r = L.mrcm_test_gemm(impl, n, dev[0].data_ptr(), dev[1].data_ptr(),
+                             dev[2].data_ptr() if two else None, dev[3].data_ptr() if two else None,
+                             c.data_ptr(), alpha, 1 if acc else 0, st.data_ptr(),
+                             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert r == mrcm.MRCM_OK
+        m64 = [m.astype(np.float64) for m in mats]
+        ref = m64[0] @ m64[1] + (m64[2] @ m64[3] if two else 0.0)
+        ref = alpha * ref + (m64[4] if acc else 0.0)
+        err = np.linalg.norm(c.cpu().numpy() - ref) / np.linalg.norm(ref)
+        # FP32 accumulation (SIMT) vs 3 x TF32 products: the dropped tail
+        # product and the TF32 tail truncation grow as sqrt(K) 2^-22
+        assert err <= (2e-6 if impl == 0 else 1e-5), (impl, n, two, err)
+    assert int(st.item()) == 0
