@@ -341,10 +341,10 @@ def run_gpu(args):
 # DRAM traffic per launch from the committed ncu capture (profiles/
 # k_iface_cluster_channels-256x64.md), valid only while the kernel sources are
 # the ones that were profiled.
-TRAFFIC = {"k_iface_cluster": {"bytes": 636928.0, "sha": "e97789e3cdd20329",
+TRAFFIC = {"k_iface_cluster": {"bytes": 1303296.0, "sha": "d587cc1406d9d325",
                                "sources": ["csrc/iface_cluster.cu", "csrc/iface_common.cuh"]},
-           "k_basis": {"bytes": 2120704.0, "sha": "bc135466061d3e78", "sources": ["csrc/local.cu"]},
-           "k_factor": {"bytes": 332288.0, "sha": "bc135466061d3e78", "sources": ["csrc/local.cu"]}}
+           "k_basis": {"bytes": 2124800.0, "sha": "b1411998d5e2eebc", "sources": ["csrc/local.cu"]},
+           "k_factor": {"bytes": 331264.0, "sha": "b1411998d5e2eebc", "sources": ["csrc/local.cu"]}}
 
 
 def _traffic(kernel):
@@ -405,14 +405,21 @@ def run_suite(args):
     import numpy as np
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     cases = []
-    if "resolve" in args.suite:
+    if "resolve" in args.suite.split(","):
         cases.append(("bl-front-512x512-s16-m4 (step 5)", W.config5(5, n=512), {}))
-    if "channels" in args.suite:
+    if "channels" in args.suite.split(","):
         cases.append(("channels-2048x2048-s32-m4", W.config4(n=2048, s=32, n_ch=64), {}))
-    if "batch" in args.suite:
+    if "batch" in args.suite.split(","):
         cases.append(("lognormal-32x1024x1024-s16/32-m2..8", W.config3(), {}))
+    # profiling-size cases of the same generators
+    if "batch4" in args.suite.split(","):
+        cases.append(("lognormal-4x1024x1024-s16/32-m2..8", W.config3(n_real=4), {}))
+    if "channels1024" in args.suite.split(","):
+        cases.append(("channels-1024x1024-s32-m4", W.config4(n=1024, s=32, n_ch=32), {}))
+    precs = {"both": (mrcm.PREC_FP32_IR, mrcm.PREC_FP64), "fp32_ir": (mrcm.PREC_FP32_IR,),
+             "fp64": (mrcm.PREC_FP64,)}[args.suite_prec]
     for name, prob, extra in cases:
-        for prec in (mrcm.PREC_FP32_IR, mrcm.PREC_FP64):
+        for prec in precs:
             opts = mrcm.SolverOptions(prec=prec, iface_tol=1e-11, gmres_tol=1e-11, gmres_max=6000,
                                       **extra)
             s = mrcm.Mrcm(prob, opts)
@@ -448,6 +455,7 @@ def main():
     ap.add_argument("--suite", default="", help="comma list of resolve,channels,batch: the "
                     "large workloads at full size instead of the headline line")
     ap.add_argument("--suite-steps", type=int, default=3)
+    ap.add_argument("--suite-prec", default="both", choices=["both", "fp32_ir", "fp64"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
