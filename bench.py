@@ -235,8 +235,10 @@ def run_gpu(args):
             "fp64": mrcm.SolverOptions(prec=mrcm.PREC_FP64)}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     results = {}
+    widths = {}
     for name, o in opts.items():
         s = mrcm.Mrcm(prob, o)
+        widths[name] = s.mrcm_autotune(K, L, Q, reps=5)
         out = s.alloc_outputs()
         s.solve(K, L, Q, out=out)
         info = s.mrcm_get_info()
@@ -319,7 +321,8 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32+f64-refine", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": "FP32 factors/solves, FP64 refinement",
                    "parallelism": f"replicas x{ws}", "l2": "flushed (256 MB write) before each step",
-                   "graph": "CUDA graph replay"},
+                   "graph": "CUDA graph replay",
+                   "basis_width_autotuned": {k: {"s16": v[0], "s32": v[1]} for k, v in widths.items()}},
         "fp64_path": {"value": cells * ws / (fp64_ms * 1e-3), "ms_per_step": fp64_ms,
                       "calls_ms": {k: v * 1e3 for k, v in calls64.items()}},
         "speedup_vs_fp64": fp64_ms / ms,
@@ -424,6 +427,7 @@ def run_suite(args):
                                       **extra)
             s = mrcm.Mrcm(prob, opts)
             K, L, Q = mrcm.device_inputs(prob)
+            tuned = s.mrcm_autotune(K, L, Q, reps=2)
             out = s.alloc_outputs()
             s.solve(K, L, Q, out=out)
             info = s.mrcm_get_info(check=False)
@@ -437,7 +441,8 @@ def run_suite(args):
                     "gmres_iters": info["gmres_iters"], "iface_resid": info["iface_resid"],
                     "local_resid_max": info["local_resid_max"], "status": info["status"],
                     "global_balance": _global_balance(prob, p, ux, uy),
-                    "interface_unknowns": s.num_interface_unknowns()}
+                    "interface_unknowns": s.num_interface_unknowns(),
+                    "basis_width_autotuned": {"s16": tuned[0], "s32": tuned[1]}}
             s.close()
             print(json.dumps(line), flush=True)
             del K, L, Q, out

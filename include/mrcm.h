@@ -210,6 +210,22 @@ int64_t mrcm_num_gamma_values(const mrcm_ctx *ctx);
  * canonical order, to the device buffer d_x (FP64). */
 mrcm_status mrcm_copy_interface_solution(mrcm_ctx *ctx, double *d_x);
 
+/* Tile width of the basis kernels (step c): right-hand-side columns per CTA,
+ * one of 4, 8, 12, 16 for 16 x 16-cell subdomains and 4, 8 for 32 x 32.
+ * Results do not depend on it; the time does.  Synchronises the stream; call
+ * it before capturing the calls in a CUDA graph. */
+mrcm_status mrcm_set_basis_width(mrcm_ctx *ctx, int32_t nc16, int32_t nc32);
+
+/* Autotuner of the tile widths above: factors the problem once (as
+ * mrcm_factor_local), times mrcm_build_basis with every candidate width on
+ * the caller's inputs (device K, lambda, q as in the calls above; reps timed
+ * runs after one warm-up, median, CUDA events on the context's stream),
+ * keeps the fastest and writes it to chosen[0..1] (host, may be NULL).
+ * Leaves the context factored (call mrcm_build_basis next).  Synchronises;
+ * call it before graph capture. */
+mrcm_status mrcm_autotune(mrcm_ctx *ctx, const double *d_K, const double *d_lambda,
+                          const double *d_q, int32_t reps, int32_t *chosen);
+
 /* 1 if step (d) runs the GMRES path, 0 for the direct path. */
 int32_t mrcm_uses_gmres(const mrcm_ctx *ctx);
 

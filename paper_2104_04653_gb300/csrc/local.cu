@@ -20,7 +20,6 @@ namespace mrcm {
 namespace {
 
 constexpr int kS = 16;      // subdomain edge of the shared-memory-resident kernels
-constexpr int kNC = kNC16;  // right-hand sides per CTA of the basis kernel
 // per-subdomain coefficient block (at SubInfo::coef_off): tW tE tS tN d
 // kappa [S*S each], then beta on the interface faces [4][S]
 constexpr int kCoefStride = 6 * kS * kS + 4 * kS;
@@ -374,27 +373,28 @@ __device__ __forceinline__ void traces_and_rows(const DeviceTables &t, const Wor
 }
 
 // ---------------------------------------------------------------------------
-// (c): one CTA per (subdomain, block of up to kNC basis columns).
-template <typename T>
+// (c): one CTA per (subdomain, block of up to NC <= 16 basis columns; NC is
+// the tile width the autotuner chooses).
+template <typename T, int NC>
 struct BasisSmem {
   T Ws[kS * kS * kS];       // W_j, j = 0..S-1 (symmetric)
   T ec[kS * kS];            // scaled row couplings e_j[a]
-  T z[kNC * kS * kS];       // scaled residual (input of the solve)
-  T v[kNC * kS * kS];       // forward values, then the solution
+  T z[NC * kS * kS];       // scaled residual (input of the solve)
+  T v[NC * kS * kS];       // forward values, then the solution
   double coef[kCoefStride]; // tW tE tS tN d kappa, edge beta
-  double su[4][kS][kNC];    // one-sided velocity traces on the four edges
-  double sp[4][kS][kNC];    // face-pressure traces
-  double x[kNC * kS * kS];  // FP64 iterate
-  double bb[kNC * kS * kS]; // FP64 right-hand sides
-  float redf[kNC][kS * kS / 32];
-  float bnf[kNC];
-  float rnf[kNC];
+  double su[4][kS][NC];    // one-sided velocity traces on the four edges
+  double sp[4][kS][NC];    // face-pressure traces
+  double x[NC * kS * kS];  // FP64 iterate
+  double bb[NC * kS * kS]; // FP64 right-hand sides
+  float redf[NC][kS * kS / 32];
+  float bnf[NC];
+  float rnf[NC];
   float rel2;
-  ColInfo col[kNC];
+  ColInfo col[NC];
 };
 
-template <typename T>
-__device__ void block_solve(BasisSmem<T> &sm, int nc) {
+template <typename T, int NC>
+__device__ void block_solve(BasisSmem<T, NC> &sm, int nc) {
   // y = L^{-T} D^{-1} L^{-1} z for the block LDL^T of the scaled operator
   constexpr int S = kS, N = S * S;
   const int tid = threadIdx.x;
@@ -435,12 +435,12 @@ __device__ void block_solve(BasisSmem<T> &sm, int nc) {
 }
 
 // per-column sum over the CTA of val[c] (c < nc) into out[c]
-template <typename T>
-__device__ void column_sums(BasisSmem<T> &sm, const float *val, int nc, float *out) {
+template <typename T, int NC>
+__device__ void column_sums(BasisSmem<T, NC> &sm, const float *val, int nc, float *out) {
   constexpr int NW = kS * kS / 32;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 #pragma unroll
-  for (int c = 0; c < kNC; ++c) {
+  for (int c = 0; c < NC; ++c) {
     if (c < nc) {
       float s = val[c];
 #pragma unroll
@@ -458,13 +458,13 @@ __device__ void column_sums(BasisSmem<T> &sm, const float *val, int nc, float *o
   __syncthreads();
 }
 
-template <typename T>
+template <typename T, int NC>
 __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
                                                   const BasisItem *items, const double *q,
                                                   double tol, int ir_max) {
   constexpr int S = kS, N = S * S;
   extern __shared__ __align__(16) unsigned char smraw[];
-  BasisSmem<T> &sm = *reinterpret_cast<BasisSmem<T> *>(smraw);
+  BasisSmem<T, NC> &sm = *reinterpret_cast<BasisSmem<T, NC> *>(smraw);
   const BasisItem it = items[blockIdx.x];
   const int g = it.sub;
   const SubInfo sb = t.sub[g];
@@ -491,9 +491,9 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   const double dsl = ds[tid];
   const float dsf = static_cast<float>(dsl);
   const double mydiag = myT[0] + myT[1] + myT[2] + myT[3];
-  float bnl[kNC];
+  float bnl[NC];
 #pragma unroll
-  for (int c = 0; c < kNC; ++c) {
+  for (int c = 0; c < NC; ++c) {
     bnl[c] = 0.0f;
     if (c >= nc) continue;
     const double val = rhs_value<S>(t, sb, sm.coef, q, sm.col[c], a, b);
@@ -522,9 +522,9 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
     __syncthreads();
     if (sweep >= ir_max) break;
     // FP64 residual r = b - A x (five FP64 FMAs per cell and column)
-    float rn[kNC];
+    float rn[NC];
 #pragma unroll
-    for (int c = 0; c < kNC; ++c) {
+    for (int c = 0; c < NC; ++c) {
       rn[c] = 0.0f;
       if (c >= nc) continue;
       const double *xc = sm.x + c * N;
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   double *bas = w.basis + sb.basis_off;
   for (int c = 0; c < nc; ++c) bas[static_cast<int64_t>(it.c0 + c) * N + tid] = sm.x[c * N + tid];
 
-  traces_and_rows<S, kNC>(t, w, sb, sm.coef, sm.col, sm.x, it.c0, nc, sm.su, sm.sp);
+  traces_and_rows<S, NC>(t, w, sb, sm.coef, sm.col, sm.x, it.c0, nc, sm.su, sm.sp);
 }
 
 // ---------------------------------------------------------------------------
@@ -576,28 +576,35 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
 // before), and the FP64 iterate lives in the basis array itself: each
 // thread owns one cell of every column of the CTA.  Each 32-term row of a
 // W_j product is split over kKS threads and summed with shuffles.
-constexpr int kS32 = 32, kKS = 4;
-constexpr int kWst = kS32 + kKS;     // padded W row stride: conflict-free reads
-static_assert(kKS * kS32 * kNC32 == kS32 * kS32, "one thread per (split, row, column)");
-
-template <typename T>
-struct BasisSmem32 {
-  T Wb[2][kS32 * kWst];
-  T ec[kS32 * kS32];
-  T z[kNC32 * kS32 * kS32];
-  T v[kNC32 * kS32 * kS32];
-  double su[4][kS32][kNC32];
-  double sp[4][kS32][kNC32];
-  float redf[kNC32][kS32 * kS32 / 32];
-  float bnf[kNC32];
-  float rnf[kNC32];
-  float rel2;
-  ColInfo col[kNC32];
+constexpr int kS32 = 32;
+// NC columns per CTA (4 or 8), KS = 32 / NC threads per W row, W rows padded to
+// 32 + KS floats so the split reads are bank-conflict free
+template <int NC>
+struct Split32 {
+  static constexpr int KS = kS32 / NC;
+  static constexpr int Wst = kS32 + KS;
+  static_assert(KS * kS32 * NC == kS32 * kS32, "one thread per (split, row, column)");
 };
 
-template <typename T>
-__device__ void block_solve32(BasisSmem32<T> &sm, const T *Wg, int nc) {
+template <typename T, int NC>
+struct BasisSmem32 {
+  T Wb[2][kS32 * Split32<NC>::Wst];
+  T ec[kS32 * kS32];
+  T z[NC * kS32 * kS32];
+  T v[NC * kS32 * kS32];
+  double su[4][kS32][NC];
+  double sp[4][kS32][NC];
+  float redf[NC][kS32 * kS32 / 32];
+  float bnf[NC];
+  float rnf[NC];
+  float rel2;
+  ColInfo col[NC];
+};
+
+template <typename T, int NC>
+__device__ void block_solve32(BasisSmem32<T, NC> &sm, const T *Wg, int nc) {
   constexpr int S = kS32, N = S * S, NSTEP = 2 * S - 1;
+  constexpr int kKS = Split32<NC>::KS, kWst = Split32<NC>::Wst;
   const int tid = threadIdx.x;
   const int ks = tid % kKS, o = tid / kKS, a = o % S, c = o / S;
   const bool act = c < nc;            // uniform over a warp (c = tid / 128)
@@ -656,14 +663,14 @@ __device__ void block_solve32(BasisSmem32<T> &sm, const T *Wg, int nc) {
   }
 }
 
-template <typename T>
+template <typename T, int NC>
 __global__ void __launch_bounds__(kS32 *kS32, 1) k_basis32(DeviceTables t, Workspace w,
                                                            const BasisItem *items,
                                                            const double *q, double tol,
                                                            int ir_max) {
-  constexpr int S = kS32, N = S * S, NC = kNC32, NW = N / 32;
+  constexpr int S = kS32, N = S * S, NW = N / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
-  BasisSmem32<T> &sm = *reinterpret_cast<BasisSmem32<T> *>(smraw);
+  BasisSmem32<T, NC> &sm = *reinterpret_cast<BasisSmem32<T, NC> *>(smraw);
   const BasisItem it = items[blockIdx.x];
   const SubInfo sb = t.sub[it.sub];
   const int nc = it.nc;
@@ -794,32 +801,70 @@ cudaError_t launch_factor(const DeviceTables &t, const Workspace &w, int prec, c
   return cudaGetLastError();
 }
 
+template <typename T, int NC>
+static cudaError_t basis16(const DeviceTables &t, const Workspace &w, const BasisItem *items, int n,
+                           const double *q, double tol, int ir_max, cudaStream_t st) {
+  k_basis<T, NC><<<n, kS * kS, sizeof(BasisSmem<T, NC>), st>>>(t, w, items, q, tol, ir_max);
+  return cudaGetLastError();
+}
+template <typename T, int NC>
+static cudaError_t basis32(const DeviceTables &t, const Workspace &w, const BasisItem *items, int n,
+                           const double *q, double tol, int ir_max, cudaStream_t st) {
+  k_basis32<T, NC><<<n, kS32 * kS32, sizeof(BasisSmem32<T, NC>), st>>>(t, w, items, q, tol,
+                                                                       ir_max);
+  return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t launch_basis_t(const DeviceTables &t, const Workspace &w,
-                                  const BasisItem *items, int n16, int n32, const double *q,
-                                  double tol, int ir_max, cudaStream_t st) {
-  if (n16 > 0)
-    k_basis<T><<<n16, kS * kS, sizeof(BasisSmem<T>), st>>>(t, w, items, q, tol, ir_max);
-  if (n32 > 0)
-    k_basis32<T><<<n32, kS32 * kS32, sizeof(BasisSmem32<T>), st>>>(t, w, items + n16, q, tol,
-                                                                    ir_max);
-  return cudaGetLastError();
+                                  const BasisItem *items, int n16, int n32, int nc16, int nc32,
+                                  const double *q, double tol, int ir_max, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (n16 > 0) {
+    switch (nc16) {
+      case 4: e = basis16<T, 4>(t, w, items, n16, q, tol, ir_max, st); break;
+      case 8: e = basis16<T, 8>(t, w, items, n16, q, tol, ir_max, st); break;
+      case 12: e = basis16<T, 12>(t, w, items, n16, q, tol, ir_max, st); break;
+      case 16: e = basis16<T, 16>(t, w, items, n16, q, tol, ir_max, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  if (n32 > 0) {
+    switch (nc32) {
+      case 4: e = basis32<T, 4>(t, w, items + n16, n32, q, tol, ir_max, st); break;
+      case 8: e = basis32<T, 8>(t, w, items + n16, n32, q, tol, ir_max, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return e;
+}
+
+template <typename K, typename S>
+static cudaError_t smem_attr(K kern) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(sizeof(S)));
 }
 
 cudaError_t init_local_attributes() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_basis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(sizeof(BasisSmem<float>)))) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_basis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(sizeof(BasisSmem<double>)))) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_basis32<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(sizeof(BasisSmem32<float>)))) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_basis32<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(sizeof(BasisSmem32<double>)))) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_factor_warp<float, 32>,
+  if ((e = smem_attr<decltype(&k_basis<float, 4>), BasisSmem<float, 4>>(k_basis<float, 4>)) ||
+      (e = smem_attr<decltype(&k_basis<float, 8>), BasisSmem<float, 8>>(k_basis<float, 8>)) ||
+      (e = smem_attr<decltype(&k_basis<float, 12>), BasisSmem<float, 12>>(k_basis<float, 12>)) ||
+      (e = smem_attr<decltype(&k_basis<float, 16>), BasisSmem<float, 16>>(k_basis<float, 16>)) ||
+      (e = smem_attr<decltype(&k_basis<double, 4>), BasisSmem<double, 4>>(k_basis<double, 4>)) ||
+      (e = smem_attr<decltype(&k_basis<double, 8>), BasisSmem<double, 8>>(k_basis<double, 8>)) ||
+      (e = smem_attr<decltype(&k_basis<double, 12>), BasisSmem<double, 12>>(k_basis<double, 12>)) ||
+      (e = smem_attr<decltype(&k_basis<double, 16>), BasisSmem<double, 16>>(k_basis<double, 16>)) ||
+      (e = smem_attr<decltype(&k_basis32<float, 4>), BasisSmem32<float, 4>>(k_basis32<float, 4>)) ||
+      (e = smem_attr<decltype(&k_basis32<float, 8>), BasisSmem32<float, 8>>(k_basis32<float, 8>)) ||
+      (e = smem_attr<decltype(&k_basis32<double, 4>), BasisSmem32<double, 4>>(k_basis32<double, 4>)) ||
+      (e = smem_attr<decltype(&k_basis32<double, 8>), BasisSmem32<double, 8>>(k_basis32<double, 8>)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_factor_warp<float, 32>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kFW * sizeof(FactorWarpSmem<float, 32>)))) !=
-          cudaSuccess)
+      cudaSuccess)
     return e;
   return cudaFuncSetAttribute(k_factor_warp<double, 32>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -827,11 +872,12 @@ cudaError_t init_local_attributes() {
 }
 
 cudaError_t launch_basis(const DeviceTables &t, const Workspace &w, int prec,
-                         const BasisItem *items, int nitems16, int nitems32, const double *q,
-                         double ir_tol, int ir_max, cudaStream_t st) {
+                         const BasisItem *items, int nitems16, int nitems32, int nc16, int nc32,
+                         const double *q, double ir_tol, int ir_max, cudaStream_t st) {
   if (prec == MRCM_PREC_FP64)
-    return launch_basis_t<double>(t, w, items, nitems16, nitems32, q, ir_tol, 0, st);
-  return launch_basis_t<float>(t, w, items, nitems16, nitems32, q, ir_tol, ir_max, st);
+    return launch_basis_t<double>(t, w, items, nitems16, nitems32, nc16, nc32, q, ir_tol, 0, st);
+  return launch_basis_t<float>(t, w, items, nitems16, nitems32, nc16, nc32, q, ir_tol, ir_max,
+                               st);
 }
 
 }  // namespace mrcm

@@ -33,6 +33,8 @@ struct mrcm_ctx {
   std::vector<RealInfo> real;
   std::vector<BasisItem> items;            // s = 16 subdomains' CTAs first
   int nitems16 = 0;
+  int nc16 = kNC16, nc32 = kNC32;          // basis tile widths (autotuned)
+  int64_t max_items = 0;
   std::vector<int> sub_by_size;
   int nsub16 = 0, smax = 16;
   int64_t coef_elems = 0, w_elems = 0, alpha_elems = 0;
@@ -178,7 +180,6 @@ static mrcm_status build_tables(mrcm_ctx *c) {
   int64_t alpha_off = 0, gam_off = 0, slab_off = 0, xy_off = 0, vec_off = 0;
   int64_t basis_off = 0, g_off = 0, tsc_off = 0, coef_off = 0, w_off = 0;
   int col_off = 0;
-  std::vector<BasisItem> items32;
   std::vector<int> subs32;
   int nslab_all = 1;   // slabs run along the longer side (the same for every s)
   for (int r = 0; r < d.n_real; ++r) {
@@ -288,19 +289,8 @@ static mrcm_status build_tables(mrcm_ctx *c) {
         sb.w_off = w_off;
         w_off += static_cast<int64_t>(S) * S * S;
         const int gid = static_cast<int>(c->sub.size());
-        if (S == 16) {
-          for (int c0 = 0; c0 < ncol; c0 += kNC16)
-            c->items.push_back(BasisItem{gid, c0, (ncol - c0) < kNC16 ? (ncol - c0) : kNC16});
-          c->sub_by_size.push_back(gid);
-        } else {
-          // balanced chunks of at most kNC32 columns
-          const int nch = (ncol + kNC32 - 1) / kNC32;
-          for (int k = 0; k < nch; ++k) {
-            const int c0 = ncol * k / nch, c1 = ncol * (k + 1) / nch;
-            items32.push_back(BasisItem{gid, c0, c1 - c0});
-          }
-          subs32.push_back(gid);
-        }
+        if (S == 16) c->sub_by_size.push_back(gid);
+        else subs32.push_back(gid);
         c->sub.push_back(sb);
       }
     // slabs: block-tridiagonal grouping of the interfaces
@@ -355,8 +345,6 @@ static mrcm_status build_tables(mrcm_ctx *c) {
   }
   c->slab_if_off.push_back(static_cast<int>(c->slab_if.size()));
   c->nunk = unk_tot;
-  c->nitems16 = static_cast<int>(c->items.size());
-  c->items.insert(c->items.end(), items32.begin(), items32.end());
   c->nsub16 = static_cast<int>(c->sub_by_size.size());
   c->sub_by_size.insert(c->sub_by_size.end(), subs32.begin(), subs32.end());
   c->coef_elems = coef_off;
@@ -541,6 +529,32 @@ static void build_plans(mrcm_ctx *c) {
   c->plans_ok = true;
 }
 
+// CTAs of the basis kernels: every subdomain's columns in chunks of at most
+// nc16 (s = 16, fixed chunks) or nc32 (s = 32, balanced chunks); s = 16
+// subdomains first.
+static void rebuild_items(mrcm_ctx *c, int nc16, int nc32) {
+  c->items.clear();
+  std::vector<BasisItem> it32;
+  for (size_t g = 0; g < c->sub.size(); ++g) {
+    const SubInfo &sb = c->sub[g];
+    const int ncol = sb.ncols, gid = static_cast<int>(g);
+    if (sb.s == 16) {
+      for (int c0 = 0; c0 < ncol; c0 += nc16)
+        c->items.push_back(BasisItem{gid, c0, (ncol - c0) < nc16 ? (ncol - c0) : nc16});
+    } else {
+      const int nch = (ncol + nc32 - 1) / nc32;
+      for (int k = 0; k < nch; ++k) {
+        const int c0 = ncol * k / nch, c1 = ncol * (k + 1) / nch;
+        it32.push_back(BasisItem{gid, c0, c1 - c0});
+      }
+    }
+  }
+  c->nitems16 = static_cast<int>(c->items.size());
+  c->items.insert(c->items.end(), it32.begin(), it32.end());
+  c->nc16 = nc16;
+  c->nc32 = nc32;
+}
+
 // GMRES path: one row descriptor per interface unknown, and the CTA plan of
 // the cooperative kernel (each realisation gets CTAs in proportion to its
 // unknowns, about 128 rows each, within the co-resident limit cap).
@@ -674,6 +688,9 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     delete c;
     return st;
   }
+  rebuild_items(c, 4, 4);                 // the largest item count any width gives
+  c->max_items = static_cast<int64_t>(c->items.size());
+  rebuild_items(c, kNC16, kNC32);
   build_plans(c);
   if (c->mmax > kGmMmax) {
     delete c;
@@ -733,7 +750,7 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                o_ui = A.take<int>(nunk ? nunk : 1), o_usp = A.take<int>(nunk ? nunk : 1),
                o_fn = A.take<double>(fnv.size()), o_al = A.take<double>(alpha.size() ? alpha.size() : 1),
                o_bt = A.take<int8_t>(nb), o_bv = A.take<double>(nb),
-               o_items = A.take<BasisItem>(c->items.size()),
+               o_items = A.take<BasisItem>(c->max_items),
                o_p2u = A.take<int>(c->npos ? c->npos : 1),
                o_pro = A.take<int64_t>(c->pos_real_off.size()),
                o_sif = A.take<int>(c->slab_if.size() ? c->slab_if.size() : 1),
@@ -1111,8 +1128,8 @@ mrcm_status mrcm_build_basis(mrcm_ctx *ctx, const double *d_q) {
   if (ctx->state < 1) return fail(ctx, MRCM_EINVAL, "build_basis before factor_local");
   if (!d_q) return fail(ctx, MRCM_EINVAL, "q must be a device pointer");
   cudaError_t e = launch_basis(ctx->t, ctx->w, ctx->prec, ctx->d_items, ctx->nitems16,
-                               static_cast<int>(ctx->items.size()) - ctx->nitems16, d_q,
-                               ctx->d.ir_tol, ctx->d.ir_max, ctx->stream);
+                               static_cast<int>(ctx->items.size()) - ctx->nitems16, ctx->nc16,
+                               ctx->nc32, d_q, ctx->d.ir_tol, ctx->d.ir_max, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "build_basis launch");
   ctx->launches += n_sizes(ctx);
   ctx->state = 2;
@@ -1275,6 +1292,79 @@ mrcm_status mrcm_set_precond_blocks(mrcm_ctx *ctx, const double *d_blocks) {
                                   cudaMemcpyDeviceToDevice, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "copy preconditioner blocks");
   ctx->gm_user_set = true;
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_set_basis_width(mrcm_ctx *ctx, int32_t nc16, int32_t nc32) {
+  if (!ctx) return MRCM_EINVAL;
+  if ((nc16 != 4 && nc16 != 8 && nc16 != 12 && nc16 != 16) || (nc32 != 4 && nc32 != 8))
+    return fail(ctx, MRCM_EINVAL, "basis widths: s = 16 one of 4, 8, 12, 16; s = 32 one of 4, 8");
+  rebuild_items(ctx, nc16, nc32);
+  cudaError_t e = cudaMemcpyAsync(ctx->d_items, ctx->items.data(),
+                                  ctx->items.size() * sizeof(BasisItem), cudaMemcpyHostToDevice,
+                                  ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "basis item upload");
+  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "stream synchronize");
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_autotune(mrcm_ctx *ctx, const double *d_K, const double *d_lambda,
+                          const double *d_q, int32_t reps, int32_t *chosen) {
+  if (!ctx) return MRCM_EINVAL;
+  if (!d_K || !d_lambda || !d_q) return fail(ctx, MRCM_EINVAL, "NULL device pointer");
+  if (reps < 1 || reps > 100) return fail(ctx, MRCM_EINVAL, "reps must be in 1..100");
+  mrcm_status st = mrcm_factor_local(ctx, d_K, d_lambda);
+  if (st != MRCM_OK) return st;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+    return fail(ctx, MRCM_ECUDA, "event create");
+  const bool has16 = ctx->nsub16 > 0, has32 = static_cast<int>(ctx->sub.size()) > ctx->nsub16;
+  auto time_width = [&](int w16, int w32, float *ms) -> mrcm_status {
+    mrcm_status s2 = mrcm_set_basis_width(ctx, w16, w32);
+    if (s2 != MRCM_OK) return s2;
+    std::vector<float> ts;
+    for (int r = 0; r <= reps; ++r) {            // the first run is a warm-up
+      cudaEventRecord(a, ctx->stream);
+      if ((s2 = mrcm_build_basis(ctx, d_q)) != MRCM_OK) return s2;
+      cudaEventRecord(b, ctx->stream);
+      if (cudaEventSynchronize(b) != cudaSuccess) return fail(ctx, MRCM_ECUDA, "event sync");
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, a, b);
+      if (r > 0) ts.push_back(t);
+    }
+    std::sort(ts.begin(), ts.end());
+    *ms = ts[ts.size() / 2];
+    return MRCM_OK;
+  };
+  int best16 = ctx->nc16, best32 = ctx->nc32;
+  float tbest = 0.0f;
+  mrcm_status s2 = MRCM_OK;
+  if (has16) {
+    tbest = 3.4e38f;
+    for (int w16 : {4, 8, 12, 16}) {
+      float t;
+      if ((s2 = time_width(w16, best32, &t)) != MRCM_OK) break;
+      if (t < tbest) { tbest = t; best16 = w16; }
+    }
+  }
+  if (s2 == MRCM_OK && has32) {
+    tbest = 3.4e38f;
+    for (int w32 : {4, 8}) {
+      float t;
+      if ((s2 = time_width(best16, w32, &t)) != MRCM_OK) break;
+      if (t < tbest) { tbest = t; best32 = w32; }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (s2 != MRCM_OK) return s2;
+  if ((s2 = mrcm_set_basis_width(ctx, best16, best32)) != MRCM_OK) return s2;
+  if (chosen) {
+    chosen[0] = best16;
+    chosen[1] = best32;
+  }
+  ctx->state = 1;                                  // factored; the basis is rebuilt by the caller
   return MRCM_OK;
 }
 

@@ -115,8 +115,8 @@ constexpr int kLpMaxNb = 64;      // largest neighbourhood (interfaces) of a tar
 constexpr int kLpMaxLoc = 160;    // largest neighbourhood (unknowns) of a target
 constexpr double kLpClip = 2.0;   // entrywise bound of a target
 
-constexpr int kNC16 = 12;     // basis columns per CTA, s = 16
-constexpr int kNC32 = 8;      // basis columns per CTA, s = 32
+constexpr int kNC16 = 12;     // default basis columns per CTA, s = 16 (4, 8, 12, 16)
+constexpr int kNC32 = 8;      // default basis columns per CTA, s = 32 (4, 8)
 
 // Direct interface path for slabs above 64 unknowns (iface_big.cu)
 constexpr int kBigMaxLev = 20;
@@ -217,8 +217,8 @@ cudaError_t launch_factor(const DeviceTables &t, const Workspace &w, int prec,
                           const double *K, const double *lam, cudaStream_t st);
 // items: the s = 16 subdomains' CTAs first (nitems16), then the s = 32 ones
 cudaError_t launch_basis(const DeviceTables &t, const Workspace &w, int prec,
-                         const BasisItem *items, int nitems16, int nitems32, const double *q,
-                         double ir_tol, int ir_max, cudaStream_t st);
+                         const BasisItem *items, int nitems16, int nitems32, int nc16, int nc32,
+                         const double *q, double ir_tol, int ir_max, cudaStream_t st);
 cudaError_t launch_iface_assemble(const DeviceTables &t, const Workspace &w, int prec,
                                   int64_t slab_elems, const int *pos2unk, int64_t npos,
                                   const int64_t *pos_real_off, cudaStream_t st);

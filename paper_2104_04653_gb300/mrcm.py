@@ -33,7 +33,7 @@ EXPORTED = ["mrcm_setup", "mrcm_factor_local", "mrcm_build_basis", "mrcm_solve_i
             "mrcm_num_interface_unknowns", "mrcm_num_gamma_values",
             "mrcm_copy_interface_solution", "mrcm_destroy", "mrcm_last_error", "mrcm_version",
             "mrcm_local_solve_noalloc", "mrcm_uses_gmres", "mrcm_num_precond_values",
-            "mrcm_set_precond_blocks"]
+            "mrcm_set_precond_blocks", "mrcm_set_basis_width", "mrcm_autotune"]
 
 
 class MrcmDesc(ctypes.Structure):
@@ -116,6 +116,10 @@ def lib(path: Optional[Path] = None):
     L.mrcm_num_precond_values.restype = i64
     L.mrcm_set_precond_blocks.argtypes = [vp, dp]
     L.mrcm_set_precond_blocks.restype = i32
+    L.mrcm_set_basis_width.argtypes = [vp, i32, i32]
+    L.mrcm_set_basis_width.restype = i32
+    L.mrcm_autotune.argtypes = [vp, dp, dp, dp, i32, ctypes.POINTER(ctypes.c_int32)]
+    L.mrcm_autotune.restype = i32
     if path is None:
         _lib = L
     return L
@@ -237,6 +241,16 @@ class Mrcm:
 
     def num_gamma_values(self) -> int:
         return int(self.L.mrcm_num_gamma_values(self.ctx))
+
+    def mrcm_set_basis_width(self, nc16: int, nc32: int):
+        self._check(self.L.mrcm_set_basis_width(self.ctx, nc16, nc32))
+
+    def mrcm_autotune(self, K, lam, q, reps: int = 3):
+        """Time every basis tile width on these inputs and keep the fastest;
+        returns (width for 16x16, width for 32x32 subdomains)."""
+        ch = (ctypes.c_int32 * 2)()
+        self._check(self.L.mrcm_autotune(self.ctx, _ptr(K), _ptr(lam), _ptr(q), reps, ch))
+        return int(ch[0]), int(ch[1])
 
     def uses_gmres(self) -> bool:
         return bool(self.L.mrcm_uses_gmres(self.ctx))

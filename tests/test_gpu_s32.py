@@ -120,3 +120,28 @@ def test_mixed_sizes_direct_paths(path, monkeypatch):
     opts = mrcm.SolverOptions(prec=1, iface_solver=mrcm.IFACE_DIRECT)
     info = _check(prob, opts)
     assert info["gmres_iters"] == 0
+
+
+@pytest.mark.parametrize("case", ["s16", "s32", "mixed"])
+def test_every_basis_width_and_autotune(case):
+    """The basis kernels' tile widths (RHS columns per CTA) change the time,
+    not the result: every width meets the oracle, and the autotuner returns
+    one of them and leaves a context that still does."""
+    O, mrcm, W = _mods()
+    prob = {"s16": lambda: W.config2(), "s32": lambda: W.config4(n=256, s=32, n_ch=8),
+            "mixed": lambda: W.config3(n_real=2, n=64)}[case]()
+    ref = O.mrcm_solve(prob)
+    K, L, Q = mrcm.device_inputs(prob)
+    widths = [(w, 8) for w in (4, 8, 12, 16)] + [(12, 4)]
+    s = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=1))
+    for w16, w32 in widths:
+        s.mrcm_set_basis_width(w16, w32)
+        p, ux, uy = s.solve(K, L, Q)
+        ep, eu = O.errors(dict(p=p.cpu().numpy(), ux=ux.cpu().numpy(), uy=uy.cpu().numpy()), ref)
+        assert ep <= TOL and eu <= TOL, (case, w16, w32, ep, eu)
+    c16, c32 = s.mrcm_autotune(K, L, Q, reps=2)
+    assert c16 in (4, 8, 12, 16) and c32 in (4, 8)
+    p, ux, uy = s.solve(K, L, Q)
+    ep, eu = O.errors(dict(p=p.cpu().numpy(), ux=ux.cpu().numpy(), uy=uy.cpu().numpy()), ref)
+    assert ep <= TOL and eu <= TOL
+    s.close()
