@@ -59,6 +59,69 @@ __device__ void gemm(T *C, const T *A, const T *B, int b, T alpha, bool acc) {
   __syncthreads();
 }
 
+// dst1 = src1 and dst2 = src2 (n values each, sources may be other CTAs'
+// shared memory), both copies in flight together, one barrier
+template <typename T>
+__device__ void copy_in2(T *dst1, const T *src1, T *dst2, const T *src2, int n) {
+  constexpr int U = 4;
+  for (int base = threadIdx.x; base < n; base += blockDim.x * U) {
+    T v[U], w[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * blockDim.x;
+      v[u] = e < n ? src1[e] : T(0);
+      w[u] = e < n ? src2[e] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * blockDim.x;
+      if (e < n) {
+        dst1[e] = v[u];
+        dst2[e] = w[u];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Two products sharing the left operand: C1 = alpha1 A B1 (+ C1 if acc1) and
+// C2 = alpha2 A B2 (+ C2 if acc2), one pass over A (same thread layout as gemm)
+template <typename T>
+__device__ void gemm2(T *C1, T *C2, const T *A, const T *B1, const T *B2, int b, T alpha1,
+                      bool acc1, T alpha2, bool acc2) {
+  const int t = threadIdx.x, j0 = 2 * (t & 31), i0 = 4 * (t >> 5);
+  if (i0 < b && j0 < b) {
+    const bool j1ok = j0 + 1 < b;
+    T c[4][2] = {}, d[4][2] = {};
+    for (int k = 0; k < b; ++k) {
+      const T b0 = B1[k * b + j0], e0 = B2[k * b + j0];
+      const T b1 = j1ok ? B1[k * b + j0 + 1] : T(0);
+      const T e1 = j1ok ? B2[k * b + j0 + 1] : T(0);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const T a = (i0 + p < b) ? A[(i0 + p) * b + k] : T(0);
+        c[p][0] += a * b0;
+        c[p][1] += a * b1;
+        d[p][0] += a * e0;
+        d[p][1] += a * e1;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      if (i0 + p >= b) continue;
+      T *cr = C1 + (i0 + p) * b + j0;
+      T *dr = C2 + (i0 + p) * b + j0;
+      cr[0] = acc1 ? cr[0] + alpha1 * c[p][0] : alpha1 * c[p][0];
+      dr[0] = acc2 ? dr[0] + alpha2 * d[p][0] : alpha2 * d[p][0];
+      if (j1ok) {
+        cr[1] = acc1 ? cr[1] + alpha1 * c[p][1] : alpha1 * c[p][1];
+        dr[1] = acc2 ? dr[1] + alpha2 * d[p][1] : alpha2 * d[p][1];
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // dst[0..n) = src[0..n) (src may be another CTA's shared memory): every
 // thread issues its eight loads before storing, so a copy costs one
 // distributed-shared-memory latency, not eight
@@ -125,14 +188,19 @@ __device__ __forceinline__ T rowdot_t(const T *Mt, const T *x, int b, int i) {
 template <typename T>
 __global__ void __launch_bounds__(kCT, 1)
     k_iface_cluster(DeviceTables t, Workspace w, const int *slab_if, const int *slab_if_off,
-                    double tol, int max_solves) {
+                    double tol, int max_solves, int bS, int nlevS) {
   cg::cluster_group cluster = cg::this_cluster();
   const int K = static_cast<int>(cluster.num_blocks());
   const int k = static_cast<int>(cluster.block_rank());
   const int r = blockIdx.x / K;
   const RealInfo ri = t.real[r];
   const int b = ri.bmax, nlev = ri.nlev;
-  const int bb = (b * b + 3) & ~3;   // tile stride (keeps later FP64 arrays aligned)
+  // tile stride and tile count from the largest slab and level count of
+  // the batch, the same for every realisation: the shared-memory layout
+  // (and the scratch areas that the plan checks against it) does not
+  // shrink with a realisation's own sizes; the stride keeps the FP64 arrays
+  // behind the tiles aligned
+  const int bb = (bS * bS + 3) & ~3;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = kCT / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
   T *tB = reinterpret_cast<T *>(smraw);
@@ -141,8 +209,8 @@ __global__ void __launch_bounds__(kCT, 1)
   T *tW1 = tC + bb;
   T *tW2 = tW1 + bb;
   T *tX = tW2 + bb;             // nlev tiles
-  T *tY = tX + nlev * bb;       // nlev tiles
-  T *v = tY + nlev * bb;        // slab vector (z, then y)
+  T *tY = tX + nlevS * bb;      // nlev tiles (nlevS reserved)
+  T *v = tY + nlevS * bb;       // slab vector (z, then y)
   T *vr1 = v + kCMaxB;
   T *vr2 = vr1 + kCMaxB;
   T *vt = vr2 + kCMaxB;
@@ -153,17 +221,19 @@ __global__ void __launch_bounds__(kCT, 1)
   double *xs = part + 2;                                  // [3 kCMaxB]: x of slabs k-1, k, k+1
   double *fs = xs + 3 * kCMaxB;                           // [kCMaxB] f of the slab rows
   double *Td = fs + kCMaxB;                               // [b][mm] scaling rows (FP64)
-  double *rowc = Td + b * mm;                             // [b][E] row coefficients
-  short *rowi = reinterpret_cast<short *>(rowc + b * E);  // [b][E] term positions
+  double *rowc = Td + b * mm;                             // [E][b] row coefficients
+  short *rowi = reinterpret_cast<short *>(rowc + b * E);  // [E][b] positions in xs
   int *rowcnt = reinterpret_cast<int *>(rowi + ((b * E + 1) & ~1));   // [kCMaxB]
   int *posinf = rowcnt + kCMaxB;   // [kCMaxB] p0 << 16 | m << 8 | i, bit 30 P row, bit 29 pin
   T *Trow = reinterpret_cast<T *>(posinf + kCMaxB);       // [b][mm] scaling rows (working prec.)
   __shared__ int bad;
   __shared__ double red[kCT / 32];
+  __shared__ int diagq[kCMaxB];   // pair index of the diagonal block of the interface at p0
   if (tid == 0) bad = 0;
   const int64_t P0 = ri.vec_off + static_cast<int64_t>(k) * b;   // first slab position
 
   // ---- the slab's interface rows from the precomputed plans: one gather of G
+  for (int p = tid; p < kCMaxB; p += kCT) diagq[p] = -1;
   for (int p = tid; p < b; p += kCT) {
     const int info = t.plan_info[P0 + p];
     posinf[p] = info;
@@ -171,12 +241,28 @@ __global__ void __launch_bounds__(kCT, 1)
     const int f0 = t.plan_fgoff[2 * (P0 + p)], f1 = t.plan_fgoff[2 * (P0 + p) + 1];
     fs[p] = (info >= 0 && f0 >= 0) ? -(w.G[f0] + w.G[f1]) : 0.0;
   }
+  // entry-major (term j of row p at j * b + p: the row-per-thread residual
+  // reads consecutive words); term positions remapped from [0, 3b) to the
+  // three kCMaxB-strided x vectors of xs
   for (int e = tid; e < b * E; e += kCT) {
+    const int p = e / E, j = e - p * E;
     const int go = t.plan_goff[P0 * E + e];
-    rowc[e] = go >= 0 ? w.G[go] : 0.0;
-    rowi[e] = t.plan_xi[P0 * E + e];
+    int xi = t.plan_xi[P0 * E + e];
+    xi += (xi >= b ? (xi >= 2 * b ? 2 : 1) : 0) * (kCMaxB - b);
+    rowc[j * b + p] = go >= 0 ? w.G[go] : 0.0;
+    rowi[j * b + p] = static_cast<short>(xi);
   }
   for (int e = tid; e < 3 * kCMaxB; e += kCT) xs[e] = 0.0;
+  __syncthreads();
+  // the diagonal pairs, found by all threads at once (one pass over the
+  // slab's pair plans instead of a serial scan per warp)
+  {
+    const int pa0 = t.pair_off[r * K + k], pa1 = t.pair_off[r * K + k + 1];
+    for (int q = pa0 + tid; q < pa1; q += kCT) {
+      const PairPlan pp = t.pairs[q];
+      if (pp.ds == 0 && pp.pn0 == pp.p0 && pp.p0 >= 0 && pp.p0 < b) diagq[pp.p0] = q;
+    }
+  }
   __syncthreads();
 
   // ---- scaling of this slab's interfaces from their diagonal blocks, one
@@ -186,20 +272,20 @@ __global__ void __launch_bounds__(kCT, 1)
   {
     const int ld = mm + 1;
     const int per = 2 * mm * ld + mm * mm;                   // floats per warp
-    const int avail = static_cast<int>((static_cast<size_t>(5 + 2 * nlev) * bb * sizeof(T)) /
+    const int avail = static_cast<int>((static_cast<size_t>(5 + 2 * nlevS) * bb * sizeof(T)) /
                                        (sizeof(float) * per));
     const int np = avail < nw ? avail : nw;
     float *scr = reinterpret_cast<float *>(smraw);
-    const int pa0 = t.pair_off[r * K + k], pa1 = t.pair_off[r * K + k + 1];
     if (np < 1) {
       if (tid == 0) atomicOr(&w.status[0], MRCM_FLAG_LAYOUT);
     } else if (wid < np) {
       float *Sd = scr + wid * per, *Xd = Sd + mm * ld, *To = Xd + mm * ld;
       int nth = 0;
-      for (int q = pa0; q < pa1; ++q) {
-        const PairPlan pp = t.pairs[q];
-        if (pp.ds != 0 || pp.pn0 != pp.p0) continue;        // the diagonal block
+      for (int p = 0; p < b; ++p) {
+        const int q = diagq[p];
+        if (q < 0) continue;                                 // not an interface's first row
         if ((nth++ % np) != wid) continue;
+        const PairPlan pp = t.pairs[q];
         const int m = pp.m, nU = pp.nU, p0 = pp.p0;
         // A = -M_UU, C = -M_PP; a pinned unknown gets a unit diagonal
         for (int e = lane; e < m * m; e += 32) {
@@ -236,7 +322,15 @@ __global__ void __launch_bounds__(kCT, 1)
   {
     const int pa0 = t.pair_off[r * K + k], pa1 = t.pair_off[r * K + k + 1];
     double *scr = reinterpret_cast<double *>(tW1) + wid * 2 * mm * mm;
-    for (int q = pa0 + wid; q < pa1; q += nw) {
+    T *scrT = reinterpret_cast<T *>(reinterpret_cast<double *>(tW1) + nw * 2 * mm * mm) +
+              wid * 2 * mm * mm;
+    // the scratch of all warps ends before v (batch-wide sizes only, so the
+    // test has the same outcome in every CTA; the host plan ensures it)
+    const bool fits = reinterpret_cast<const unsigned char *>(
+                          reinterpret_cast<T *>(reinterpret_cast<double *>(tW1) + nw * 2 * mm * mm) +
+                          nw * 2 * mm * mm) <= reinterpret_cast<const unsigned char *>(v);
+    if (!fits && tid == 0) atomicOr(&w.status[0], MRCM_FLAG_LAYOUT);
+    for (int q = pa0 + wid; fits && q < pa1; q += nw) {
       const PairPlan pp = t.pairs[q];
       const int m = pp.m, mn = pp.mn;
       double *Sb = scr, *Xb = scr + mm * mm;
@@ -254,35 +348,44 @@ __global__ void __launch_bounds__(kCT, 1)
       }
       const bool own = pp.ds == 0;
       const bool diag = own && pp.pn0 == pp.p0;
-      const double *Tn = own ? Td + pp.pn0 * mm : w.tsc + pp.tscn;
-      const int ldn = own ? mm : mn;
       // X = T_g S in FP64 (rounding S or X T^T's left factor to the working
       // precision first costs a refinement sweep); the diagonal block, whose
       // T S T^T = [-I *; * I] cancels, also takes Y = X T^T in FP64, the
-      // other blocks in the working precision
+      // other blocks in the working precision.  Off the diagonal X and the
+      // neighbour's T are rounded once per entry (a conversion from FP64
+      // runs on the slow FP64 pipe of this part, so none sits in the inner
+      // product loop).
+      T *XT = scrT, *TnT = scrT + mm * mm;
       {
         const double *Tg = Td + pp.p0 * mm;
         for (int e = lane; e < m * mn; e += 32) {
           const int i = e / mn, j = e % mn;
           double a = 0.0;
           for (int qq = 0; qq <= i; ++qq) a += Tg[i * mm + qq] * Sb[qq * mn + j];
-          Xb[e] = a;
+          if (diag)
+            Xb[e] = a;
+          else
+            XT[e] = static_cast<T>(a);
         }
+        if (!own)
+          for (int e = lane; e < mn * mn; e += 32) TnT[e] = static_cast<T>(w.tsc[pp.tscn + e]);
       }
       __syncwarp();
       if (diag) {
+        const double *Tn = Td + pp.pn0 * mm;
         for (int e = lane; e < m * mn; e += 32) {
           const int i = e / mn, j = e % mn;
           double a = 0.0;
-          for (int qq = 0; qq <= j; ++qq) a += Xb[i * mn + qq] * Tn[j * ldn + qq];
+          for (int qq = 0; qq <= j; ++qq) a += Xb[i * mn + qq] * Tn[j * mm + qq];
           blk[(pp.p0 + i) * b + pp.pn0 + j] = static_cast<T>(a);
         }
       } else {
+        const T *Tn = own ? Trow + pp.pn0 * mm : TnT;
+        const int ldn = own ? mm : mn;
         for (int e = lane; e < m * mn; e += 32) {
           const int i = e / mn, j = e % mn;
           T a = T(0);
-          for (int qq = 0; qq <= j; ++qq)
-            a += static_cast<T>(Xb[i * mn + qq]) * static_cast<T>(Tn[j * ldn + qq]);
+          for (int qq = 0; qq <= j; ++qq) a += XT[i * mn + qq] * Tn[j * ldn + qq];
           blk[(pp.p0 + i) * b + pp.pn0 + j] = a;
         }
       }
@@ -311,22 +414,16 @@ __global__ void __launch_bounds__(kCT, 1)
       if (l >= 0) {
         copy_in(tW1, cluster.map_shared_rank(tB, l), b * b);         // B_l^{-1}
         gemm(X, tA, tW1, b, T(1), false);                          // X = A_k B_l^{-1}
-        copy_in(tW2, cluster.map_shared_rank(tC, l), b * b);
-        gemm(tB, X, tW2, b, T(-1), true);                          // B_k -= X C_l
-        copy_in(tW2, cluster.map_shared_rank(tA, l), b * b);
-        gemm(tW1, X, tW2, b, T(-1), false);                        // -X A_l
-        copy_in(tA, tW1, b * b);
+        copy_in2(tW1, cluster.map_shared_rank(tC, l), tW2, cluster.map_shared_rank(tA, l), b * b);
+        gemm2(tB, tA, X, tW1, tW2, b, T(-1), true, T(-1), false);  // B_k -= X C_l, A_k = -X A_l
       } else {
         for (int e = tid; e < b * b; e += kCT) X[e] = T(0);
       }
       if (rt < K) {
         copy_in(tW1, cluster.map_shared_rank(tB, rt), b * b);        // B_r^{-1}
         gemm(Y, tC, tW1, b, T(1), false);                          // Y = C_k B_r^{-1}
-        copy_in(tW2, cluster.map_shared_rank(tA, rt), b * b);
-        gemm(tB, Y, tW2, b, T(-1), true);                          // B_k -= Y A_r
-        copy_in(tW2, cluster.map_shared_rank(tC, rt), b * b);
-        gemm(tW1, Y, tW2, b, T(-1), false);                        // -Y C_r
-        copy_in(tC, tW1, b * b);
+        copy_in2(tW1, cluster.map_shared_rank(tA, rt), tW2, cluster.map_shared_rank(tC, rt), b * b);
+        gemm2(tB, tC, Y, tW1, tW2, b, T(-1), true, T(-1), false);  // B_k -= Y A_r, C_k = -Y C_r
       } else {
         for (int e = tid; e < b * b; e += kCT) Y[e] = T(0);
       }
@@ -399,25 +496,18 @@ __global__ void __launch_bounds__(kCT, 1)
     if (tid < b) {
       const int pos = tid, cnt = rowcnt[pos];
       double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      const double *rc = rowc + pos * E;
-      const short *ri_ = rowi + pos * E;
+      const double *rc = rowc + pos;
+      const short *ri_ = rowi + pos;
       int e = 0;
       for (; e + 3 < cnt; e += 4) {
-        int x0 = ri_[e], x1 = ri_[e + 1], x2 = ri_[e + 2], x3 = ri_[e + 3];
-        x0 += (x0 >= b ? (x0 >= 2 * b ? 2 : 1) : 0) * (kCMaxB - b);
-        x1 += (x1 >= b ? (x1 >= 2 * b ? 2 : 1) : 0) * (kCMaxB - b);
-        x2 += (x2 >= b ? (x2 >= 2 * b ? 2 : 1) : 0) * (kCMaxB - b);
-        x3 += (x3 >= b ? (x3 >= 2 * b ? 2 : 1) : 0) * (kCMaxB - b);
-        a0 = fma(rc[e], xs[x0], a0);
-        a1 = fma(rc[e + 1], xs[x1], a1);
-        a2 = fma(rc[e + 2], xs[x2], a2);
-        a3 = fma(rc[e + 3], xs[x3], a3);
+        const int x0 = ri_[e * b], x1 = ri_[(e + 1) * b], x2 = ri_[(e + 2) * b],
+                  x3 = ri_[(e + 3) * b];
+        a0 = fma(rc[e * b], xs[x0], a0);
+        a1 = fma(rc[(e + 1) * b], xs[x1], a1);
+        a2 = fma(rc[(e + 2) * b], xs[x2], a2);
+        a3 = fma(rc[(e + 3) * b], xs[x3], a3);
       }
-      for (; e < cnt; ++e) {
-        int x0 = ri_[e];
-        x0 += (x0 >= b ? (x0 >= 2 * b ? 2 : 1) : 0) * (kCMaxB - b);
-        a0 = fma(rc[e], xs[x0], a0);
-      }
+      for (; e < cnt; ++e) a0 = fma(rc[e * b], xs[ri_[e * b]], a0);
       const double rv = cnt > 0 ? fs[pos] - ((a0 + a1) + (a2 + a3)) : 0.0;
       rl[pos] = ((posinf[pos] >> 30) & 1) ? -rv : rv;
       rsq = rv * rv;
@@ -539,7 +629,7 @@ int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int em
   if (nslab < 1 || nslab > 16 || bmax > kCMaxB || 3 * kCMaxB > 32767) return 0;
   const size_t smem = cluster_smem<float>(bmax, nlev, emax, mmax);
   // per-warp assembly scratch must fit behind the first three tiles
-  const size_t scr = static_cast<size_t>(kCT / 32) * 2 * mmax * mmax * sizeof(double);
+  const size_t scr = static_cast<size_t>(kCT / 32) * 2 * mmax * mmax * (sizeof(double) + sizeof(float));
   const size_t behind = (2 + 2 * static_cast<size_t>(nlev)) *
                         ((static_cast<size_t>(bmax) * bmax + 3) & ~static_cast<size_t>(3)) *
                         sizeof(float);
@@ -594,7 +684,7 @@ cudaError_t launch_iface_cluster(const DeviceTables &t, const Workspace &w, cons
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_iface_cluster<float>, t, w, slab_if, slab_if_off, tol,
-                            max_solves);
+                            max_solves, bmax, nlev);
 }
 
 }  // namespace mrcm
