@@ -20,6 +20,7 @@
 #include <cooperative_groups.h>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <type_traits>
 
 namespace cg = cooperative_groups;
 
@@ -30,10 +31,72 @@ constexpr int kCT = 512;        // threads per CTA
 constexpr int kCMaxB = 64;      // largest slab
 constexpr int kGjScr = 64 + 2 * 512;   // blocked Gauss-Jordan scratch (elements)
 
+// FP32 forms of gemm / gemm2 below for b a multiple of 4 (tiles 16-byte
+// aligned): four k per step, a 16-byte load of each of the thread's four A
+// rows and an 8-byte load of each of the four B rows.  The same products are
+// summed in the same order (k ascending) as in the scalar forms.
+__device__ __forceinline__ void fma_k4(float (&c)[4][2], const float4 (&a)[4],
+                                       const float2 (&bv)[4]) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    c[p][0] = fmaf(a[p].x, bv[0].x, c[p][0]);
+    c[p][1] = fmaf(a[p].x, bv[0].y, c[p][1]);
+    c[p][0] = fmaf(a[p].y, bv[1].x, c[p][0]);
+    c[p][1] = fmaf(a[p].y, bv[1].y, c[p][1]);
+    c[p][0] = fmaf(a[p].z, bv[2].x, c[p][0]);
+    c[p][1] = fmaf(a[p].z, bv[2].y, c[p][1]);
+    c[p][0] = fmaf(a[p].w, bv[3].x, c[p][0]);
+    c[p][1] = fmaf(a[p].w, bv[3].y, c[p][1]);
+  }
+}
+
+__device__ void gemm2_v4(float *C1, float *C2, const float *A, const float *B1, const float *B2,
+                         int b, float alpha1, bool acc1, float alpha2, bool acc2, bool two) {
+  const int t = threadIdx.x, j0 = 2 * (t & 31), i0 = 4 * (t >> 5);
+  if (i0 < b && j0 < b) {   // b % 4 == 0: rows i0..i0+3 and columns j0, j0+1 exist
+    float c[4][2] = {}, d[4][2] = {};
+    for (int k = 0; k < b; k += 4) {
+      float4 a[4];
+      float2 bv[4], ev[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) a[p] = *reinterpret_cast<const float4 *>(A + (i0 + p) * b + k);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bv[q] = *reinterpret_cast<const float2 *>(B1 + (k + q) * b + j0);
+      fma_k4(c, a, bv);
+      if (two) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          ev[q] = *reinterpret_cast<const float2 *>(B2 + (k + q) * b + j0);
+        fma_k4(d, a, ev);
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      float2 *cr = reinterpret_cast<float2 *>(C1 + (i0 + p) * b + j0);
+      float2 o = acc1 ? *cr : make_float2(0.f, 0.f);
+      *cr = acc1 ? make_float2(o.x + alpha1 * c[p][0], o.y + alpha1 * c[p][1])
+                 : make_float2(alpha1 * c[p][0], alpha1 * c[p][1]);
+      if (two) {
+        float2 *dr = reinterpret_cast<float2 *>(C2 + (i0 + p) * b + j0);
+        float2 od = acc2 ? *dr : make_float2(0.f, 0.f);
+        *dr = acc2 ? make_float2(od.x + alpha2 * d[p][0], od.y + alpha2 * d[p][1])
+                   : make_float2(alpha2 * d[p][0], alpha2 * d[p][1]);
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // C = alpha A B (+ C), b x b row-major shared matrices; thread owns rows
 // 4*(t/32)..+3, columns 2*(t%32)..+1.  C must not alias A or B.
 template <typename T>
 __device__ void gemm(T *C, const T *A, const T *B, int b, T alpha, bool acc) {
+  if constexpr (std::is_same<T, float>::value) {
+    if ((b & 3) == 0) {
+      gemm2_v4(C, nullptr, A, B, nullptr, b, alpha, acc, 0.f, false, false);
+      return;
+    }
+  }
   const int t = threadIdx.x, j0 = 2 * (t & 31), i0 = 4 * (t >> 5);
   if (i0 < b && j0 < b) {
     const bool j1ok = j0 + 1 < b;
@@ -89,6 +152,12 @@ __device__ void copy_in2(T *dst1, const T *src1, T *dst2, const T *src2, int n) 
 template <typename T>
 __device__ void gemm2(T *C1, T *C2, const T *A, const T *B1, const T *B2, int b, T alpha1,
                       bool acc1, T alpha2, bool acc2) {
+  if constexpr (std::is_same<T, float>::value) {
+    if ((b & 3) == 0) {
+      gemm2_v4(C1, C2, A, B1, B2, b, alpha1, acc1, alpha2, acc2, true);
+      return;
+    }
+  }
   const int t = threadIdx.x, j0 = 2 * (t & 31), i0 = 4 * (t >> 5);
   if (i0 < b && j0 < b) {
     const bool j1ok = j0 + 1 < b;
@@ -156,34 +225,32 @@ __device__ void matvec_acc(T *y, const T *M, const T *x, int b, T alpha) {
   }
 }
 
-// in-place transpose of a b x b shared tile
+// sum_j M[i][j] x[j] for the row i = threadIdx.x / 8 of the b x b row-major
+// shared tile M, by the 8 threads of that row (kCT = 8 kCMaxB threads cover
+// every row): each takes every 8th column, in chunks of 8 columns visited in
+// an order rotated by the row, so the four rows a warp serves read distinct
+// banks; three shuffles add the partial sums.  Every thread of the CTA must
+// call it (rows i >= b return 0); every thread of the row gets the sum.
 template <typename T>
-__device__ void transpose_tile(T *M, int b) {
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int i = e / b, j = e % b;
-    if (i < j) {
-      const T x = M[i * b + j];
-      M[i * b + j] = M[j * b + i];
-      M[j * b + i] = x;
+__device__ __forceinline__ T rowdot8(const T *M, const T *x, int b) {
+  const int i = threadIdx.x >> 3, sub = threadIdx.x & 7;
+  const int nch = (b + 7) >> 3;
+  T a = T(0);
+  if (i < b) {
+    int cc = i & 3;
+    if (cc >= nch) cc = 0;
+    for (int c = 0; c < nch; ++c) {
+      const int j = 8 * cc + sub;
+      if (j < b) a += M[i * b + j] * x[j];
+      if (++cc == nch) cc = 0;
     }
   }
-  __syncthreads();
+  a += __shfl_xor_sync(0xffffffffu, a, 4);
+  a += __shfl_xor_sync(0xffffffffu, a, 2);
+  a += __shfl_xor_sync(0xffffffffu, a, 1);
+  return a;
 }
-
-// sum_j M[i][j] x[j] with M stored transposed (Mt[j*b + i]); four chains
-template <typename T>
-__device__ __forceinline__ T rowdot_t(const T *Mt, const T *x, int b, int i) {
-  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-  int j = 0;
-  for (; j + 3 < b; j += 4) {
-    a0 += Mt[j * b + i] * x[j];
-    a1 += Mt[(j + 1) * b + i] * x[j + 1];
-    a2 += Mt[(j + 2) * b + i] * x[j + 2];
-    a3 += Mt[(j + 3) * b + i] * x[j + 3];
-  }
-  for (; j < b; ++j) a0 += Mt[j * b + i] * x[j];
-  return (a0 + a1) + (a2 + a3);
-}
+static_assert(kCT == 8 * kCMaxB, "rowdot8 maps 8 threads to each of kCMaxB rows");
 
 template <typename T>
 __global__ void __launch_bounds__(kCT, 1)
@@ -229,7 +296,13 @@ __global__ void __launch_bounds__(kCT, 1)
   __shared__ int bad;
   __shared__ double red[kCT / 32];
   __shared__ int diagq[kCMaxB];   // pair index of the diagonal block of the interface at p0
-  if (tid == 0) bad = 0;
+  __shared__ int s_goff0, s_goff1; // the slab's range of pair_goff
+  const int pa0 = t.pair_off[r * K + k], pa1 = t.pair_off[r * K + k + 1];
+  if (tid == 0) {
+    bad = 0;
+    s_goff0 = t.pairs[pa0].goff;
+    s_goff1 = t.pairs[pa1].goff;   // the next slab's first pair, or the sentinel
+  }
   const int64_t P0 = ri.vec_off + static_cast<int64_t>(k) * b;   // first slab position
 
   // ---- the slab's interface rows from the precomputed plans: one gather of G
@@ -244,23 +317,77 @@ __global__ void __launch_bounds__(kCT, 1)
   // entry-major (term j of row p at j * b + p: the row-per-thread residual
   // reads consecutive words); term positions remapped from [0, 3b) to the
   // three kCMaxB-strided x vectors of xs
-  for (int e = tid; e < b * E; e += kCT) {
-    const int p = e / E, j = e - p * E;
-    const int go = t.plan_goff[P0 * E + e];
-    int xi = t.plan_xi[P0 * E + e];
-    xi += (xi >= b ? (xi >= 2 * b ? 2 : 1) : 0) * (kCMaxB - b);
-    rowc[j * b + p] = go >= 0 ? w.G[go] : 0.0;
-    rowi[j * b + p] = static_cast<short>(xi);
+  // (eight terms per thread in flight: the offsets, then the values)
+  {
+    constexpr int U = 8;
+    const int n = b * E;
+    for (int base = tid; base < n; base += kCT * U) {
+      int go[U], xi[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = base + u * kCT;
+        go[u] = e < n ? t.plan_goff[P0 * E + e] : -1;
+        xi[u] = e < n ? t.plan_xi[P0 * E + e] : 0;
+      }
+      double gv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) gv[u] = go[u] >= 0 ? w.G[go[u]] : 0.0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = base + u * kCT;
+        if (e < n) {
+          const int p = e / E, j = e - p * E;
+          const int x = xi[u] + (xi[u] >= b ? (xi[u] >= 2 * b ? 2 : 1) : 0) * (kCMaxB - b);
+          rowc[j * b + p] = gv[u];
+          rowi[j * b + p] = static_cast<short>(x);
+        }
+      }
+    }
   }
   for (int e = tid; e < 3 * kCMaxB; e += kCT) xs[e] = 0.0;
   __syncthreads();
-  // the diagonal pairs, found by all threads at once (one pass over the
-  // slab's pair plans instead of a serial scan per warp)
+  // ---- the slab's pair plans and the G sums of every pair entry, staged
+  // by all threads at once at the end of the tile area (the scaling and the
+  // assembly then read no global memory), if they fit behind both phases'
+  // scratch; otherwise each warp reads its pairs from global memory.  The
+  // diagonal pairs are found in the same pass.
+  const int npair = pa1 - pa0, nst = (s_goff1 - s_goff0) / 2;
+  const size_t ppb = (static_cast<size_t>(npair) * sizeof(PairPlan) + 15) & ~static_cast<size_t>(15);
+  unsigned char *stage = reinterpret_cast<unsigned char *>(v) - ppb - static_cast<size_t>(nst) * 8;
+  PairPlan *pps = reinterpret_cast<PairPlan *>(stage);
+  const double *Sst = reinterpret_cast<const double *>(stage + ppb);
+  const unsigned char *asm_end = reinterpret_cast<const unsigned char *>(tW1) +
+                                 static_cast<size_t>(nw) * 2 * mm * mm * (sizeof(double) + sizeof(T));
+  const bool staged = npair >= 0 && nst >= 0 && stage >= asm_end;
   {
-    const int pa0 = t.pair_off[r * K + k], pa1 = t.pair_off[r * K + k + 1];
     for (int q = pa0 + tid; q < pa1; q += kCT) {
       const PairPlan pp = t.pairs[q];
+      if (staged) pps[q - pa0] = pp;
       if (pp.ds == 0 && pp.pn0 == pp.p0 && pp.p0 >= 0 && pp.p0 < b) diagq[pp.p0] = q;
+    }
+    if (staged) {
+      constexpr int U = 8;
+      double *Sw = reinterpret_cast<double *>(stage + ppb);
+      for (int base = tid; base < nst; base += kCT * U) {
+        int g0[U], g1[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = base + u * kCT;
+          g0[u] = e < nst ? t.pair_goff[s_goff0 + 2 * e] : -1;
+          g1[u] = e < nst ? t.pair_goff[s_goff0 + 2 * e + 1] : -1;
+        }
+        double a0[U], a1[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          a0[u] = g0[u] >= 0 ? w.G[g0[u]] : 0.0;
+          a1[u] = g1[u] >= 0 ? w.G[g1[u]] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = base + u * kCT;
+          if (e < nst) Sw[e] = a0[u] + a1[u];
+        }
+      }
     }
   }
   __syncthreads();
@@ -272,8 +399,9 @@ __global__ void __launch_bounds__(kCT, 1)
   {
     const int ld = mm + 1;
     const int per = 2 * mm * ld + mm * mm;                   // floats per warp
-    const int avail = static_cast<int>((static_cast<size_t>(5 + 2 * nlevS) * bb * sizeof(T)) /
-                                       (sizeof(float) * per));
+    const size_t area = staged ? static_cast<size_t>(stage - smraw)
+                               : static_cast<size_t>(5 + 2 * nlevS) * bb * sizeof(T);
+    const int avail = static_cast<int>(area / (sizeof(float) * per));
     const int np = avail < nw ? avail : nw;
     float *scr = reinterpret_cast<float *>(smraw);
     if (np < 1) {
@@ -285,13 +413,19 @@ __global__ void __launch_bounds__(kCT, 1)
         const int q = diagq[p];
         if (q < 0) continue;                                 // not an interface's first row
         if ((nth++ % np) != wid) continue;
-        const PairPlan pp = t.pairs[q];
+        const PairPlan pp = staged ? pps[q - pa0] : t.pairs[q];
         const int m = pp.m, nU = pp.nU, p0 = pp.p0;
+        const double *Sq = Sst + (pp.goff - s_goff0) / 2;
         // A = -M_UU, C = -M_PP; a pinned unknown gets a unit diagonal
         for (int e = lane; e < m * m; e += 32) {
           const int i = e / m, j = e % m;
-          const int g0 = t.pair_goff[pp.goff + 2 * e], g1 = t.pair_goff[pp.goff + 2 * e + 1];
-          const double val = (g0 >= 0 ? w.G[g0] : 0.0) + (g1 >= 0 ? w.G[g1] : 0.0);
+          double val;
+          if (staged) {
+            val = Sq[e];
+          } else {
+            const int g0 = t.pair_goff[pp.goff + 2 * e], g1 = t.pair_goff[pp.goff + 2 * e + 1];
+            val = (g0 >= 0 ? w.G[g0] : 0.0) + (g1 >= 0 ? w.G[g1] : 0.0);
+          }
           float sv = ((i < nU) == (j < nU)) ? static_cast<float>(-val) : 0.0f;
           if (((posinf[p0 + i] >> 29) & 1) || ((posinf[p0 + j] >> 29) & 1))
             sv = (i == j) ? 1.0f : 0.0f;
@@ -304,7 +438,6 @@ __global__ void __launch_bounds__(kCT, 1)
             if (bd && j < m) tv = (lane == j) ? 1.0f : 0.0f;
             Td[(p0 + lane) * mm + j] = static_cast<double>(tv);
             Trow[(p0 + lane) * mm + j] = static_cast<T>(tv);
-            if (j < m) w.tsc[pp.tsc + lane * m + j] = static_cast<double>(tv);
           }
         }
         if (bd && lane == 0) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
@@ -312,15 +445,13 @@ __global__ void __launch_bounds__(kCT, 1)
       }
     }
   }
-  __threadfence();
-  cluster.sync();
+  cluster.sync();   // every slab's Trow complete (read by its neighbours below)
 
   // ---- assemble the scaled slab blocks: T_g S_{g g'} T_{g'}^T, one warp
   // per (own, neighbour) interface pair, S from the precomputed G offsets
   for (int e = tid; e < 3 * bb; e += kCT) tB[e] = T(0);
   __syncthreads();
   {
-    const int pa0 = t.pair_off[r * K + k], pa1 = t.pair_off[r * K + k + 1];
     double *scr = reinterpret_cast<double *>(tW1) + wid * 2 * mm * mm;
     T *scrT = reinterpret_cast<T *>(reinterpret_cast<double *>(tW1) + nw * 2 * mm * mm) +
               wid * 2 * mm * mm;
@@ -331,13 +462,19 @@ __global__ void __launch_bounds__(kCT, 1)
                           nw * 2 * mm * mm) <= reinterpret_cast<const unsigned char *>(v);
     if (!fits && tid == 0) atomicOr(&w.status[0], MRCM_FLAG_LAYOUT);
     for (int q = pa0 + wid; fits && q < pa1; q += nw) {
-      const PairPlan pp = t.pairs[q];
+      const PairPlan pp = staged ? pps[q - pa0] : t.pairs[q];
       const int m = pp.m, mn = pp.mn;
       double *Sb = scr, *Xb = scr + mm * mm;
+      const double *Sq = Sst + (pp.goff - s_goff0) / 2;
       for (int e = lane; e < m * mn; e += 32) {
         const int i = e / mn;
-        const int g0 = t.pair_goff[pp.goff + 2 * e], g1 = t.pair_goff[pp.goff + 2 * e + 1];
-        double val = (g0 >= 0 ? w.G[g0] : 0.0) + (g1 >= 0 ? w.G[g1] : 0.0);
+        double val;
+        if (staged) {
+          val = Sq[e];
+        } else {
+          const int g0 = t.pair_goff[pp.goff + 2 * e], g1 = t.pair_goff[pp.goff + 2 * e + 1];
+          val = (g0 >= 0 ? w.G[g0] : 0.0) + (g1 >= 0 ? w.G[g1] : 0.0);
+        }
         Sb[e] = (i >= pp.nU) ? -val : val;                 // symmetrising sign
       }
       __syncwarp();
@@ -367,8 +504,10 @@ __global__ void __launch_bounds__(kCT, 1)
           else
             XT[e] = static_cast<T>(a);
         }
-        if (!own)
-          for (int e = lane; e < mn * mn; e += 32) TnT[e] = static_cast<T>(w.tsc[pp.tscn + e]);
+        if (!own) {   // the neighbour slab's scaling rows, from its shared memory
+          const T *rT = cluster.map_shared_rank(Trow, k + pp.ds) + pp.pn0 * mm;
+          for (int e = lane; e < mn * mn; e += 32) TnT[e] = rT[(e / mn) * mm + e % mn];
+        }
       }
       __syncwarp();
       if (diag) {
@@ -433,16 +572,6 @@ __global__ void __launch_bounds__(kCT, 1)
   if (k == 0) gj_inverse_blocked<T, kCT>(tB, b, b, gjs, &bad);
   if (tid == 0 && bad) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
   cluster.sync();
-
-  // ---- transposed copies of the tiles the solve reads (thread-per-row
-  // matrix-vector products with conflict-free shared loads)
-  transpose_tile(tA, b);
-  transpose_tile(tC, b);
-  transpose_tile(tB, b);
-  for (int lev = 0; lev < nlev; ++lev) {
-    transpose_tile(tX + lev * bb, b);
-    transpose_tile(tY + lev * bb, b);
-  }
 
   // ---- refinement: x of this slab and of its two neighbours (xs, FP64),
   // the residual rows (rowc/rowi), f and the scaling rows are all in shared
@@ -544,7 +673,7 @@ __global__ void __launch_bounds__(kCT, 1)
                       (nsolve >= 2 && rn2 > 0.25 * prev2);
     prev2 = rn2;
     if (stop) break;
-    // C: y = Shat^{-1} z, cluster-wide cyclic reduction (transposed tiles)
+    // C: y = Shat^{-1} z, cluster-wide cyclic reduction (8 threads per row)
     for (int lev = 0; lev < nlev; ++lev) {
       const int s = 1 << lev;
       if (k % (2 * s) == 0) {
@@ -554,19 +683,18 @@ __global__ void __launch_bounds__(kCT, 1)
           vr2[p] = rt < K ? cluster.map_shared_rank(v, rt)[p] : T(0);
         }
         __syncthreads();
-        if (tid < b) {
-          T acc = T(0);
-          if (l >= 0) acc += rowdot_t(tX + lev * bb, vr1, b, tid);
-          if (rt < K) acc += rowdot_t(tY + lev * bb, vr2, b, tid);
-          v[tid] -= acc;
-        }
+        T acc = T(0);
+        if (l >= 0) acc += rowdot8(tX + lev * bb, vr1, b);
+        if (rt < K) acc += rowdot8(tY + lev * bb, vr2, b);
+        if ((tid & 7) == 0 && (tid >> 3) < b) v[tid >> 3] -= acc;
       }
       cluster.sync();
     }
     if (k == 0) {
       for (int p = tid; p < b; p += kCT) vr1[p] = v[p];
       __syncthreads();
-      if (tid < b) v[tid] = rowdot_t(tB, vr1, b, tid);
+      const T y = rowdot8(tB, vr1, b);
+      if ((tid & 7) == 0 && (tid >> 3) < b) v[tid >> 3] = y;
     }
     cluster.sync();
     for (int lev = nlev - 1; lev >= 0; --lev) {
@@ -578,13 +706,12 @@ __global__ void __launch_bounds__(kCT, 1)
           vr2[p] = rt < K ? cluster.map_shared_rank(v, rt)[p] : T(0);
         }
         __syncthreads();
-        if (tid < b) {
-          T acc = v[tid] - rowdot_t(tA, vr1, b, tid);
-          if (rt < K) acc -= rowdot_t(tC, vr2, b, tid);
-          vt[tid] = acc;
-        }
+        T acc = rowdot8(tA, vr1, b);
+        if (rt < K) acc += rowdot8(tC, vr2, b);
+        if ((tid & 7) == 0 && (tid >> 3) < b) vt[tid >> 3] = v[tid >> 3] - acc;
         __syncthreads();
-        if (tid < b) v[tid] = rowdot_t(tB, vt, b, tid);
+        const T y = rowdot8(tB, vt, b);
+        if ((tid & 7) == 0 && (tid >> 3) < b) v[tid >> 3] = y;
       }
       cluster.sync();
     }

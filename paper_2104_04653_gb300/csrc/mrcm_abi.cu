@@ -526,6 +526,11 @@ static void build_plans(mrcm_ctx *c) {
     slab_base += ri.nslab;
   }
   c->pair_off.push_back(static_cast<int>(c->pairs.size()));
+  // sentinel (in no slab's range): pairs[pa1].goff ends every slab's range
+  // of pair_goff, the last slab's included
+  PairPlan sentinel = {};
+  sentinel.goff = static_cast<int>(c->pair_goff.size());
+  c->pairs.push_back(sentinel);
   c->plans_ok = true;
 }
 
