@@ -29,7 +29,7 @@ namespace {
 
 constexpr int kCT = 512;        // threads per CTA
 constexpr int kCMaxB = 64;      // largest slab
-constexpr int kGjScr = 64 + 2 * 512;   // blocked Gauss-Jordan scratch (elements)
+constexpr int kGjScr = 2 * 64 + 3 * 512;   // Gauss-Jordan scratch (elements): Pi x2, ColP x2, RowP
 
 // FP32 forms of gemm / gemm2 below for b a multiple of 4 (tiles 16-byte
 // aligned): four k per step, a 16-byte load of each of the thread's four A
@@ -222,6 +222,139 @@ __device__ void matvec_acc(T *y, const T *M, const T *x, int b, T alpha) {
     for (int j = lane; j < b; j += 32) a += M[i * b + j] * x[j];
     a = warp_sum(a);
     if (lane == 0) y[i] += alpha * a;
+  }
+}
+
+// The 8 x 8 pivot block at (k0, k0) of M (kb <= 8 rows used, identity
+// padding) inverted in registers by one warp (lane holds (r, c) and
+// (r + 4, c); shuffles exchange the pivot row and column) into Pi (8 x 8).
+template <typename T>
+__device__ void gj_pivot_block(const T *M, int ld, int k0, int kb, T *Pi, int *bad) {
+  const int lane = threadIdx.x & 31;
+  const int r = lane >> 3, c = lane & 7;
+  T e0 = (r < kb && c < kb) ? M[(k0 + r) * ld + k0 + c] : T(r == c);
+  T e1 = (r + 4 < kb && c < kb) ? M[(k0 + r + 4) * ld + k0 + c] : T(r + 4 == c);
+  for (int p = 0; p < kb; ++p) {
+    const int src = (p & 3) * 8;
+    const T ro = __shfl_sync(0xffffffffu, p < 4 ? e0 : e1, src + c);
+    const T pv = __shfl_sync(0xffffffffu, p < 4 ? e0 : e1, src + p);
+    const T c0 = __shfl_sync(0xffffffffu, e0, r * 8 + p);
+    const T c1 = __shfl_sync(0xffffffffu, e1, r * 8 + p);
+    if (lane == 0 && (!(pv != T(0)) || !isfinite(static_cast<double>(pv)))) *bad = 1;
+    const T ip = fast_recip(pv);
+    const T rv = ro * ip;
+    T n0 = e0 - c0 * rv, n1 = e1 - c1 * rv;
+    n0 = (c == p) ? -c0 * ip : n0;
+    n1 = (c == p) ? -c1 * ip : n1;
+    n0 = (r == p) ? ((c == p) ? ip : rv) : n0;
+    n1 = (r + 4 == p) ? ((c == p) ? ip : rv) : n1;
+    e0 = n0;
+    e1 = n1;
+  }
+  Pi[r * 8 + c] = e0;
+  Pi[(r + 4) * 8 + c] = e1;
+}
+
+// Update of rows 0..b-1 of M for the columns j in [c0, c1) that are not in
+// the pivot block K (k0, kb): pivot rows take RowP, the others the rank-kb
+// update with the column panel CP; columns of block K take -CP Pi.  Threads
+// tf .. tf + nt - 1 take part: thread u owns rows (u / 8) + (nt / 8) * n and
+// the columns (u % 8) + 8 c of the range.  Same products, same order, as in
+// gj_inverse_blocked.
+template <typename T>
+__device__ void gj_update_cols(T *M, int b, int k0, int kb, const T *CP, const T *Pi,
+                               const T *RowP, int c0, int c1, int tf, int nt) {
+  const int u = static_cast<int>(threadIdx.x) - tf;
+  if (u < 0 || u >= nt) return;
+  const int rstep = nt >> 3;
+  for (int i = u >> 3; i < b; i += rstep) {
+    const bool piv = i >= k0 && i < k0 + kb;
+    T cp[8];
+    if (!piv) {
+#pragma unroll
+      for (int p = 0; p < 8; ++p) cp[p] = CP[i * 8 + p];
+    }
+    for (int j = c0 + (u & 7); j < c1; j += 8) {
+      if (j >= b) break;
+      const bool kcol = j >= k0 && j < k0 + kb;
+      T a;
+      if (piv) {
+        a = kcol ? Pi[(i - k0) * 8 + (j - k0)] : RowP[(i - k0) * 64 + j];
+      } else if (kcol) {
+        a = T(0);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) a -= cp[p] * Pi[p * 8 + (j - k0)];
+      } else {
+        a = M[i * b + j];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) a -= cp[p] * RowP[p * 64 + j];
+      }
+      M[i * b + j] = a;
+    }
+  }
+}
+
+// In-place Gauss-Jordan inverse of the b x b shared matrix M (row stride b,
+// b <= 64), no pivoting, in blocks of 8 pivots, by the whole CTA, with one
+// block of lookahead: once the columns of block K+1 are updated, warp 0
+// inverts the next pivot block while the other warps copy the next column
+// panel and update the remaining columns.  Arithmetic per element as in
+// gj_inverse_blocked.  scr: kGjScr elements (Pi and ColP double-buffered,
+// RowP).
+template <typename T>
+__device__ void gj_inverse_la(T *M, int b, T *scr, int *bad) {
+  T *PiB = scr, *CPB = scr + 128, *RowP = scr + 128 + 1024;
+  const int t = threadIdx.x, wid = t >> 5;
+  const int nblk = (b + 7) >> 3;
+  if (nblk < 1) return;
+  // prologue: pivot block 0 (warp 0) and column panel 0 (the other warps)
+  if (wid == 0) {
+    gj_pivot_block(M, b, 0, b < 8 ? b : 8, PiB, bad);
+  } else {
+    const int kb = b < 8 ? b : 8;
+    for (int e = t - 32; e < 64 * 8; e += kCT - 32) {
+      const int i = e >> 3, p = e & 7;
+      CPB[e] = (i < b && p < kb) ? M[i * b + p] : T(0);
+    }
+  }
+  __syncthreads();
+  for (int K = 0; K < nblk; ++K) {
+    const int k0 = 8 * K, kb = (b - k0) < 8 ? (b - k0) : 8;
+    const T *Pi = PiB + (K & 1) * 64;
+    const T *CP = CPB + (K & 1) * 512;
+    // row panel: RowP = Pi M[K rows, :]
+    for (int e = t; e < 8 * 64; e += kCT) {
+      const int q = e >> 6, j = e & 63;
+      T a = T(0);
+      if (q < kb && j < b) {
+#pragma unroll
+        for (int p = 0; p < 8; ++p)
+          if (p < kb) a += Pi[q * 8 + p] * M[(k0 + p) * b + j];
+      }
+      RowP[e] = a;
+    }
+    __syncthreads();
+    if (K + 1 < nblk) {
+      const int k1 = k0 + 8, kb1 = (b - k1) < 8 ? (b - k1) : 8;
+      // the columns of block K+1, by every thread
+      gj_update_cols(M, b, k0, kb, CP, Pi, RowP, k1, k1 + 8, 0, kCT);
+      __syncthreads();
+      if (wid == 0) {
+        gj_pivot_block(M, b, k1, kb1, PiB + ((K + 1) & 1) * 64, bad);
+      } else {
+        T *CPn = CPB + ((K + 1) & 1) * 512;
+        for (int e = t - 32; e < 64 * 8; e += kCT - 32) {
+          const int i = e >> 3, p = e & 7;
+          CPn[e] = (i < b && p < kb1) ? M[i * b + k1 + p] : T(0);
+        }
+        gj_update_cols(M, b, k0, kb, CP, Pi, RowP, 0, k1, 32, kCT - 32);
+        gj_update_cols(M, b, k0, kb, CP, Pi, RowP, k1 + 8, 64, 32, kCT - 32);
+      }
+      __syncthreads();
+    } else {
+      gj_update_cols(M, b, k0, kb, CP, Pi, RowP, 0, 64, 0, kCT);
+      __syncthreads();
+    }
   }
 }
 
@@ -544,7 +677,7 @@ __global__ void __launch_bounds__(kCT, 1)
   // ---- block cyclic reduction
   for (int lev = 0; lev < nlev; ++lev) {
     const int s = 1 << lev;
-    if (k % (2 * s) == s) gj_inverse_blocked<T, kCT>(tB, b, b, gjs, &bad);
+    if (k % (2 * s) == s) gj_inverse_la(tB, b, gjs, &bad);
     cluster.sync();
     if (k % (2 * s) == 0) {
       const int l = k - s, rt = k + s;
@@ -569,7 +702,7 @@ __global__ void __launch_bounds__(kCT, 1)
     }
     cluster.sync();
   }
-  if (k == 0) gj_inverse_blocked<T, kCT>(tB, b, b, gjs, &bad);
+  if (k == 0) gj_inverse_la(tB, b, gjs, &bad);
   if (tid == 0 && bad) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
   cluster.sync();
 
