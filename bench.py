@@ -238,7 +238,12 @@ def run_gpu(args):
     widths = {}
     for name, o in opts.items():
         s = mrcm.Mrcm(prob, o)
-        widths[name] = s.mrcm_autotune(K, L, Q, reps=5)
+        if args.basis_width:
+            w16, w32 = (int(v) for v in args.basis_width.split(","))
+            s.mrcm_set_basis_width(w16, w32)
+            widths[name] = (w16, w32)
+        else:
+            widths[name] = s.mrcm_autotune(K, L, Q, reps=5)
         out = s.alloc_outputs()
         s.solve(K, L, Q, out=out)
         info = s.mrcm_get_info()
@@ -322,7 +327,8 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "precision": "FP32 factors/solves, FP64 refinement",
                    "parallelism": f"replicas x{ws}", "l2": "flushed (256 MB write) before each step",
                    "graph": "CUDA graph replay",
-                   "basis_width_autotuned": {k: {"s16": v[0], "s32": v[1]} for k, v in widths.items()}},
+                   "basis_width": {k: {"s16": v[0], "s32": v[1]} for k, v in widths.items()},
+                   "basis_width_autotuned": not args.basis_width},
         "fp64_path": {"value": cells * ws / (fp64_ms * 1e-3), "ms_per_step": fp64_ms,
                       "calls_ms": {k: v * 1e3 for k, v in calls64.items()}},
         "speedup_vs_fp64": fp64_ms / ms,
@@ -344,10 +350,10 @@ def run_gpu(args):
 # DRAM traffic per launch from the committed ncu capture (profiles/
 # k_iface_cluster_channels-256x64.md), valid only while the kernel sources are
 # the ones that were profiled.
-TRAFFIC = {"k_iface_cluster": {"bytes": 1303296.0, "sha": "d587cc1406d9d325",
+TRAFFIC = {"k_iface_cluster": {"bytes": 1274624.0, "sha": "075ec89513863170",
                                "sources": ["csrc/iface_cluster.cu", "csrc/iface_common.cuh"]},
-           "k_basis": {"bytes": 2124800.0, "sha": "b1411998d5e2eebc", "sources": ["csrc/local.cu"]},
-           "k_factor": {"bytes": 331264.0, "sha": "b1411998d5e2eebc", "sources": ["csrc/local.cu"]}}
+           "k_basis": {"bytes": 2117632.0, "sha": "7d6f1c11b4e50394", "sources": ["csrc/local.cu"]},
+           "k_factor": {"bytes": 336640.0, "sha": "7d6f1c11b4e50394", "sources": ["csrc/local.cu"]}}
 
 
 def _traffic(kernel):
@@ -457,6 +463,9 @@ def main():
     ap.add_argument("--impl", default="mrcm", choices=["mrcm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--basis-width", default="",
+                    help="N16,N32: basis-kernel RHS columns per CTA instead of autotuning "
+                         "(profiling runs that must launch only the timed configuration)")
     ap.add_argument("--suite", default="", help="comma list of resolve,channels,batch: the "
                     "large workloads at full size instead of the headline line")
     ap.add_argument("--suite-steps", type=int, default=3)
