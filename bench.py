@@ -403,6 +403,59 @@ def _global_balance(prob, p, ux, uy):
     return worst
 
 
+def _suite_resolve10(precs, flush, torch, np, mrcm, W):
+    """The re-factor workload as a time-stepping loop: ten solves k = 1..10
+    of the 512x512 Buckley-Leverett front case on ONE context, lambda_k
+    copied into the context's input buffer before each step (outside the
+    timed region), every call inside CUDA events, L2 flushed before each
+    step.  Per step: device time, the solver's FP64 residuals and the
+    global mass balance."""
+    probs = [W.config5(k, n=512) for k in range(1, 11)]
+    st = torch.cuda.current_stream()
+    for prec in precs:
+        opts = mrcm.SolverOptions(prec=prec, iface_tol=1e-11)
+        s = mrcm.Mrcm(probs[0], opts)
+        K, L, Q = mrcm.device_inputs(probs[0])
+        lams = [torch.from_numpy(np.ascontiguousarray(p.lam)).to("cuda") for p in probs]
+        tuned = s.mrcm_autotune(K, L, Q, reps=2)
+        out = s.alloc_outputs()
+        for lam in lams:                       # warm-up pass over the ten steps
+            L.copy_(lam)
+            s.solve(K, L, Q, out=out)
+        torch.cuda.synchronize()
+        steps = []
+        for k, lam in enumerate(lams):
+            L.copy_(lam)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            s.mrcm_factor_local(K, L)
+            s.mrcm_build_basis(Q)
+            inf = s.mrcm_solve_interface(info=True)
+            s.mrcm_reconstruct(*out)
+            e1.record(st)
+            torch.cuda.synchronize()
+            p, ux, uy = (t.cpu().numpy() for t in out)
+            steps.append({"ms": e0.elapsed_time(e1), "iface_resid": inf["iface_resid"],
+                          "local_resid_max": inf["local_resid_max"], "flags": inf["flags"],
+                          "global_balance": _global_balance(probs[k], p, ux, uy)})
+        tot = sum(x["ms"] for x in steps) * 1e-3
+        line = {"suite": "bl-front-512x512-s16-m4, steps 1..10 on one context (re-factor each)",
+                "prec": "fp32_ir" if prec else "fp64", "cells": probs[0].cells(),
+                "interface_solver": "gmres" if s.uses_gmres() else "direct",
+                "ms_total_10_steps": tot * 1e3, "ms_per_step": [round(x["ms"], 4) for x in steps],
+                "cells_per_s": 10 * probs[0].cells() / tot,
+                "iface_resid_max": max(x["iface_resid"] for x in steps),
+                "local_resid_max": max(x["local_resid_max"] for x in steps),
+                "flags": sorted({x["flags"] for x in steps}),
+                "global_balance_max": max(x["global_balance"] for x in steps),
+                "basis_width_autotuned": {"s16": tuned[0], "s32": tuned[1]}}
+        s.close()
+        print(json.dumps(line), flush=True)
+        del K, L, Q, out, lams
+        torch.cuda.empty_cache()
+
+
 def run_suite(args):
     """The large workloads at full size (one line each): per-call device
     times, interface solver, GMRES steps, the solver's own FP64 residuals and
@@ -427,6 +480,8 @@ def run_suite(args):
         cases.append(("channels-1024x1024-s32-m4", W.config4(n=1024, s=32, n_ch=32), {}))
     precs = {"both": (mrcm.PREC_FP32_IR, mrcm.PREC_FP64), "fp32_ir": (mrcm.PREC_FP32_IR,),
              "fp64": (mrcm.PREC_FP64,)}[args.suite_prec]
+    if "resolve10" in args.suite.split(","):
+        _suite_resolve10(precs, flush, torch, np, mrcm, W)
     for name, prob, extra in cases:
         for prec in precs:
             opts = mrcm.SolverOptions(prec=prec, iface_tol=1e-11, gmres_tol=1e-11, gmres_max=6000,
@@ -466,7 +521,7 @@ def main():
     ap.add_argument("--basis-width", default="",
                     help="N16,N32: basis-kernel RHS columns per CTA instead of autotuning "
                          "(profiling runs that must launch only the timed configuration)")
-    ap.add_argument("--suite", default="", help="comma list of resolve,channels,batch: the "
+    ap.add_argument("--suite", default="", help="comma list of resolve,resolve10,channels,batch: the "
                     "large workloads at full size instead of the headline line")
     ap.add_argument("--suite-steps", type=int, default=3)
     ap.add_argument("--suite-prec", default="both", choices=["both", "fp32_ir", "fp64"])

@@ -160,6 +160,27 @@ def test_time_stepping_mobility_downsized():
             _check(prob, prec)
 
 
+def test_ten_refactor_steps_on_one_context():
+    """The re-factor workload as a time-stepping loop: steps 1..10 of the
+    Buckley-Leverett mobility (downsized to 128x128) solved on ONE context,
+    lambda_k copied into the same device buffer before each step; every
+    step meets the oracle of its own lambda."""
+    import torch
+    O, mrcm, W = _mods()
+    probs = [W.config5(k, n=128) for k in range(1, 11)]
+    s = mrcm.Mrcm(probs[0], mrcm.SolverOptions(prec=1))
+    Kd, Ld, Qd = mrcm.device_inputs(probs[0])
+    out = s.alloc_outputs()
+    for prob in probs:
+        assert np.array_equal(prob.K, probs[0].K)         # only the mobility moves
+        Ld.copy_(torch.from_numpy(np.ascontiguousarray(prob.lam)).to("cuda"))
+        s.solve(Kd, Ld, Qd, out=out)
+        got = dict(p=out[0].cpu().numpy(), ux=out[1].cpu().numpy(), uy=out[2].cpu().numpy())
+        ep, eu = O.errors(got, O.mrcm_solve(prob))
+        assert ep <= TOL and eu <= TOL, (prob.name, ep, eu)
+    s.close()
+
+
 def test_deterministic_and_refactor():
     """Two solves give bitwise-identical results; re-factoring with a new
     lambda on the same context gives the new solution."""
