@@ -456,6 +456,85 @@ def _suite_resolve10(precs, flush, torch, np, mrcm, W):
         torch.cuda.empty_cache()
 
 
+def _suite_learned(args, flush, torch, np, mrcm, LP, W):
+    """The learned preconditioner at the channel workload's scale: train on
+    seeded 512x512 channel windows (seeds 5000.., 32x32-cell subdomains,
+    m = 4, channel density of the 2048x2048 case), then solve the
+    2048x2048 system by GMRES to 1e-8 with no preconditioner, block-Jacobi
+    and the network's blocks: steps, interface time (CUDA events, L2
+    flushed), the network's inference time, and the solution's error
+    against the direct path."""
+    ntrain = args.suite_train
+    st = torch.cuda.current_stream()
+    t0 = time.time()
+    train_p = [W.config4(n=512, s=32, n_ch=16, seed=5000 + k) for k in range(ntrain)]
+    x, t = LP.make_dataset(train_p, 4)
+    net = LP.LearnedPrecond(32, 4, max_batch=1024, seed=0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    rep = LP.train(net, x, t, steps=args.suite_train_steps, batch=256, lr=1e-3)
+    e1.record(st)
+    torch.cuda.synchronize()
+    train_s = e0.elapsed_time(e1) * 1e-3
+    prep_s = time.time() - t0 - train_s
+    del x, t
+    prob = W.config4(n=2048, s=32, n_ch=64)
+    K, L, Q = mrcm.device_inputs(prob)
+    # reference interface solution: the direct path
+    sd = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=mrcm.PREC_FP32_IR, iface_tol=1e-12))
+    ref = [t_.clone() for t_ in sd.solve(K, L, Q)]
+    sd.close()
+    xv, tv = LP.make_dataset([prob], 4)
+    w = 1.0 / tv.double().var(dim=0).clamp_min(1e-8)
+    val, _ = net.gradient(xv[:1024].contiguous(), tv[:1024].contiguous())
+    zero = float(((tv[:1024].double() ** 2) * w).mean())
+    del xv, tv
+    res = {}
+    for name, pc in (("none", mrcm.PRECOND_NONE), ("block_jacobi", mrcm.PRECOND_BLOCK_JACOBI),
+                     ("learned", mrcm.PRECOND_USER)):
+        s = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=mrcm.PREC_FP32_IR,
+                                               iface_solver=mrcm.IFACE_GMRES, precond=pc,
+                                               gmres_tol=1e-8, gmres_max=20000))
+        out = s.alloc_outputs()
+        s.mrcm_factor_local(K, L)
+        s.mrcm_build_basis(Q)
+        torch.cuda.synchronize()
+        flush.zero_()
+        a0, a1, a2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a0.record(st)
+        if pc == mrcm.PRECOND_USER:
+            LP.apply(s, net, K, L)
+        a1.record(st)
+        status = "MRCM_OK"
+        try:
+            s.mrcm_solve_interface()
+        except mrcm.MrcmError as ex:          # no convergence within gmres_max: reported
+            status = str(ex).split(":")[0]
+        a2.record(st)
+        inf = s.mrcm_get_info(check=False)
+        s.mrcm_reconstruct(*out)
+        torch.cuda.synchronize()
+        errs = [float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+                for a, b in zip(out, ref)]
+        nunk = s.num_interface_unknowns()
+        res[name] = {"converged": bool(inf["iface_resid"] <= 1e-8),
+                     "fell_back_to_block_jacobi": bool(inf["flags"] & mrcm.FLAG_PRECOND_FALLBACK),
+                     "status": status, "gmres_iters": inf["gmres_iters"],
+                     "iface_ms": a1.elapsed_time(a2),
+                     "apply_ms": a0.elapsed_time(a1), "iface_resid": inf["iface_resid"],
+                     "flags": inf["flags"], "rel_err_vs_direct": {"p": errs[0], "ux": errs[1],
+                                                                  "uy": errs[2]}}
+        s.close()
+    line = {"suite": "learned preconditioner: channels-2048x2048-s32-m4, GMRES to 1e-8",
+            "train": {"systems": ntrain, "grid": "512x512", "samples": rep.samples,
+                      "adam_steps": rep.steps, "train_s": train_s, "dataset_s": prep_s,
+                      "loss_first": rep.loss_first, "loss_last": rep.loss_last},
+            "eval_loss": {"network": val, "zero_block_jacobi": zero, "samples": 1024},
+            "interface_unknowns": nunk, "results": res}
+    net.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_suite(args):
     """The large workloads at full size (one line each): per-call device
     times, interface solver, GMRES steps, the solver's own FP64 residuals and
@@ -482,6 +561,8 @@ def run_suite(args):
              "fp64": (mrcm.PREC_FP64,)}[args.suite_prec]
     if "resolve10" in args.suite.split(","):
         _suite_resolve10(precs, flush, torch, np, mrcm, W)
+    if "learned" in args.suite.split(","):
+        _suite_learned(args, flush, torch, np, mrcm, LP, W)
     for name, prob, extra in cases:
         for prec in precs:
             opts = mrcm.SolverOptions(prec=prec, iface_tol=1e-11, gmres_tol=1e-11, gmres_max=6000,
@@ -521,9 +602,12 @@ def main():
     ap.add_argument("--basis-width", default="",
                     help="N16,N32: basis-kernel RHS columns per CTA instead of autotuning "
                          "(profiling runs that must launch only the timed configuration)")
-    ap.add_argument("--suite", default="", help="comma list of resolve,resolve10,channels,batch: the "
+    ap.add_argument("--suite", default="", help="comma list of resolve,resolve10,channels,batch,learned: the "
                     "large workloads at full size instead of the headline line")
     ap.add_argument("--suite-steps", type=int, default=3)
+    ap.add_argument("--suite-train", type=int, default=64,
+                    help="training systems (512x512 channel windows) for --suite learned")
+    ap.add_argument("--suite-train-steps", type=int, default=2000)
     ap.add_argument("--suite-prec", default="both", choices=["both", "fp32_ir", "fp64"])
     args = ap.parse_args()
     if args.warmup < 3:
