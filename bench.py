@@ -575,10 +575,16 @@ def run_suite(args):
             info = s.mrcm_get_info(check=False)
             calls = _time_calls(s, K, L, Q, out, args.suite_steps, flush, torch)
             tot = sum(calls.values())
+            g = _capture(s, K, L, Q, out, torch)          # the whole solve as one CUDA graph
+            for _ in range(2):
+                g.replay()
+            graph_ms = statistics.median(_time_graph(g, args.suite_steps, flush, torch)) * 1e3
+            del g
             p, ux, uy = (t.cpu().numpy() for t in out)
             line = {"suite": name, "prec": "fp32_ir" if prec else "fp64",
                     "cells": prob.cells(), "interface_solver": "gmres" if s.uses_gmres() else "direct",
                     "ms_per_step": tot * 1e3, "cells_per_s": prob.cells() / tot,
+                    "graph_ms_per_step": graph_ms, "graph_cells_per_s": prob.cells() / (graph_ms * 1e-3),
                     "calls_ms": {k: v * 1e3 for k, v in calls.items()},
                     "gmres_iters": info["gmres_iters"], "iface_resid": info["iface_resid"],
                     "local_resid_max": info["local_resid_max"], "status": info["status"],
@@ -605,7 +611,7 @@ def main():
     ap.add_argument("--suite", default="", help="comma list of resolve,resolve10,channels,batch,learned: the "
                     "large workloads at full size instead of the headline line")
     ap.add_argument("--suite-steps", type=int, default=3)
-    ap.add_argument("--suite-train", type=int, default=64,
+    ap.add_argument("--suite-train", type=int, default=500,
                     help="training systems (512x512 channel windows) for --suite learned")
     ap.add_argument("--suite-train-steps", type=int, default=2000)
     ap.add_argument("--suite-prec", default="both", choices=["both", "fp32_ir", "fp64"])
