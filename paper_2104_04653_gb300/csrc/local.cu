@@ -15,6 +15,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <type_traits>
 
 namespace mrcm {
 namespace {
@@ -88,8 +89,22 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // Stage 2 for one subdomain, executed by one whole warp.  offx[cell]: scaled
 // coupling of (a,b) to (a+1,b); ecp[cell]: to (a,b+1).  Writes W_j to Wg.
+// The S x S working matrix is spread over the warp as a 4 x 8 grid of lanes,
+// lane (rb, cb) = (lane / 8, lane % 8) holding rows LR rb .. LR rb + LR - 1 and
+// columns LC cb .. LC cb + LC - 1 (LR = S / 4, LC = S / 8).  Gauss-Jordan runs
+// two pivots at a time: the 2 x 2 pivot block lies in one lane, is inverted
+// in closed form, and the block update (pivot rows Pi R_K., pivot columns
+// -R_.K Pi, the rest R - R_.K Pi R_K.) is applied in one pass, which halves the
+// dependent chain of shuffles and reciprocals.  A 2 x 2 block of an SPD
+// matrix has a00 > 0 and det > 0 exactly when both sequential pivots are
+// positive, which is the test here.  FP32 only; FP64 takes the single-pivot
+// form above.
+// One pivot at a time, lane = column (S / 32 lanes per column): the form
+// used in FP64, where the pair update's extra products cost more on the
+// slow FP64 pipe than the shorter chain saves.
 template <typename T, int S>
-__device__ __forceinline__ bool schur_inverses(int lane, const T *offx, const T *ecp, T *Wg) {
+__device__ __forceinline__ bool schur_inverses_single(int lane, const T *offx, const T *ecp,
+                                                      T *Wg) {
   constexpr int N = S * S, HL = 32 / S, RPL = S / HL;
   static_assert(HL * S == 32, "S must divide 32 lanes");
   const int c = lane % S, h = lane / S;
@@ -130,6 +145,99 @@ __device__ __forceinline__ bool schur_inverses(int lane, const T *offx, const T 
     }
 #pragma unroll
     for (int q = 0; q < RPL; ++q) Wg[j * N + (RPL * h + q) * S + c] = R[q];
+  }
+  return bad;
+}
+
+template <typename T, int S>
+__device__ __forceinline__ bool schur_inverses(int lane, const T *offx, const T *ecp, T *Wg) {
+  if constexpr (!std::is_same<T, float>::value) {
+    return schur_inverses_single<T, S>(lane, offx, ecp, Wg);
+  }
+  constexpr int N = S * S, LR = S / 4, LC = S / 8;
+  static_assert(LR * 4 == S && LC * 8 == S && LR % 2 == 0 && LC % 2 == 0,
+                "S must be a multiple of 16 so that pivot pairs stay inside a lane block");
+  const int rb = lane >> 3, cb = lane & 7;
+  T R[LR][LC];
+#pragma unroll
+  for (int q = 0; q < LR; ++q)
+#pragma unroll
+    for (int w = 0; w < LC; ++w) R[q][w] = T(0);
+  bool bad = false;
+#pragma unroll 1
+  for (int j = 0; j < S; ++j) {
+    // Schur complement S_j = A_jj - E W_{j-1} E (E diagonal), Jacobi-scaled
+    T ec[LC];
+#pragma unroll
+    for (int w = 0; w < LC; ++w) ec[w] = j > 0 ? ecp[(j - 1) * S + LC * cb + w] : T(0);
+#pragma unroll
+    for (int q = 0; q < LR; ++q) {
+      const int r = LR * rb + q;
+      const T er = j > 0 ? ecp[(j - 1) * S + r] : T(0);
+#pragma unroll
+      for (int w = 0; w < LC; ++w) {
+        const int c = LC * cb + w;
+        T v = T(0);
+        if (r == c) v = T(1);
+        else if (r - c == 1) v = offx[j * S + c];
+        else if (c - r == 1) v = offx[j * S + r];
+        if (j > 0) v -= er * ec[w] * R[q][w];
+        R[q][w] = v;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < S; p += 2) {
+      const int prb = p / LR, pq = p % LR, pcb = p / LC, pw = p % LC;
+      const int lpiv = prb * 8 + pcb;
+      const T a00 = shfl(R[pq][pw], lpiv), a01 = shfl(R[pq][pw + 1], lpiv);
+      const T a10 = shfl(R[pq + 1][pw], lpiv), a11 = shfl(R[pq + 1][pw + 1], lpiv);
+      T rw0[LC], rw1[LC], cl0[LR], cl1[LR];
+#pragma unroll
+      for (int w = 0; w < LC; ++w) {   // the pivot rows at this lane's columns
+        rw0[w] = shfl(R[pq][w], prb * 8 + cb);
+        rw1[w] = shfl(R[pq + 1][w], prb * 8 + cb);
+      }
+#pragma unroll
+      for (int q = 0; q < LR; ++q) {   // this lane's rows at the pivot columns
+        cl0[q] = shfl(R[q][pw], rb * 8 + pcb);
+        cl1[q] = shfl(R[q][pw + 1], rb * 8 + pcb);
+      }
+      const T det = a00 * a11 - a01 * a10;
+      if (!(a00 > T(0)) || !(det > T(0))) bad = true;
+      const T idet = recip(det);
+      const T p00 = a11 * idet, p01 = -a01 * idet, p10 = -a10 * idet, p11 = a00 * idet;
+      T rp0[LC], rp1[LC];
+#pragma unroll
+      for (int w = 0; w < LC; ++w) {   // new pivot rows Pi R_K.
+        rp0[w] = p00 * rw0[w] + p01 * rw1[w];
+        rp1[w] = p10 * rw0[w] + p11 * rw1[w];
+      }
+#pragma unroll
+      for (int q = 0; q < LR; ++q) {
+#pragma unroll
+        for (int w = 0; w < LC; ++w) {
+          T nv = R[q][w] - (cl0[q] * rp0[w] + cl1[q] * rp1[w]);
+          if (w == pw || w == pw + 1) {            // possibly a pivot column
+            const T pc = (w == pw) ? -(cl0[q] * p00 + cl1[q] * p10)
+                                   : -(cl0[q] * p01 + cl1[q] * p11);
+            nv = (cb == pcb) ? pc : nv;
+          }
+          if (q == pq || q == pq + 1) {            // possibly a pivot row
+            T prv = (q == pq) ? rp0[w] : rp1[w];
+            if (w == pw || w == pw + 1) {
+              const T pb = (q == pq) ? ((w == pw) ? p00 : p01) : ((w == pw) ? p10 : p11);
+              prv = (cb == pcb) ? pb : prv;
+            }
+            nv = (rb == prb) ? prv : nv;
+          }
+          R[q][w] = nv;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < LR; ++q)
+#pragma unroll
+      for (int w = 0; w < LC; ++w) Wg[j * N + (LR * rb + q) * S + LC * cb + w] = R[q][w];
   }
   return bad;
 }
