@@ -24,6 +24,7 @@ constexpr int kS = 16;      // subdomain edge of the shared-memory-resident kern
 // per-subdomain coefficient block (at SubInfo::coef_off): tW tE tS tN d
 // kappa [S*S each], then beta on the interface faces [4][S]
 constexpr int kCoefStride = 6 * kS * kS + 4 * kS;
+static_assert(kCoefStride % 2 == 0, "coefficient blocks are staged as 16-byte vectors");
 
 // interface-function table of subdomain size S (RealInfo::fn_off)
 template <int S>
@@ -503,7 +504,10 @@ struct BasisSmem {
 
 template <typename T, int NC>
 __device__ void block_solve(BasisSmem<T, NC> &sm, int nc) {
-  // y = L^{-T} D^{-1} L^{-1} z for the block LDL^T of the scaled operator
+  // y = L^{-T} D^{-1} L^{-1} z for the block LDL^T of the scaled operator.
+  // Column c is carried by the 16 threads (a, c), all in one warp (c = tid /
+  // 16), and its steps touch only its own z and v: a warp barrier orders the
+  // steps; one CTA barrier at the end publishes v to the other warps.
   constexpr int S = kS, N = S * S;
   const int tid = threadIdx.x;
   const int a = tid % S, c = tid / S;
@@ -525,7 +529,7 @@ __device__ void block_solve(BasisSmem<T, NC> &sm, int nc) {
       }
       sm.v[c * N + j * S + a] = acc;
     }
-    __syncthreads();
+    __syncwarp();
   }
   // backward: y_j = v_j - W_j (e_j * y_{j+1})
   for (int j = S - 2; j >= 0; --j) {
@@ -538,8 +542,9 @@ __device__ void block_solve(BasisSmem<T, NC> &sm, int nc) {
       for (int bq = 0; bq < S; ++bq) acc += Wj[bq * S + a] * (ep[bq] * yn[bq]);
       sm.v[c * N + j * S + a] -= acc;
     }
-    __syncthreads();
+    __syncwarp();
   }
+  __syncthreads();
 }
 
 // per-column sum over the CTA of val[c] (c < nc) into out[c]
@@ -580,13 +585,31 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   const int tid = threadIdx.x;
   const int a = tid % S, b = tid / S;
 
-  // stage W_j, the coefficients and the column descriptors
+  // stage W_j, the coefficients and the column descriptors: 16-byte loads,
+  // all of a thread's loads issued before its stores (both arrays start on a
+  // 16-byte boundary: offsets are multiples of S^3 elements and of the even
+  // coefficient stride)
   {
-    const T *Wg = static_cast<const T *>(w.W) + sb.w_off;
-    for (int k = tid; k < S * N; k += N) sm.Ws[k] = Wg[k];
-    const double *coef = w.coef + sb.coef_off;
-    for (int k = tid; k < kCoefStride; k += N) sm.coef[k] = coef[k];
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int NW = S * N * static_cast<int>(sizeof(T)) / 16 / N;   // vectors per thread
+    const V *wsrc = reinterpret_cast<const V *>(static_cast<const T *>(w.W) + sb.w_off);
+    V *wdst = reinterpret_cast<V *>(sm.Ws);
+    constexpr int NCV = kCoefStride / 2, NCT = (NCV + N - 1) / N;
+    const double2 *csrc = reinterpret_cast<const double2 *>(w.coef + sb.coef_off);
+    double2 *cdst = reinterpret_cast<double2 *>(sm.coef);
+    V wv[NW];
+    double2 cv[NCT];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) wv[k] = wsrc[tid + k * N];
+#pragma unroll
+    for (int k = 0; k < NCT; ++k)
+      if (tid + k * N < NCV) cv[k] = csrc[tid + k * N];
     if (tid < nc) sm.col[tid] = t.col[sb.col_off + it.c0 + tid];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) wdst[tid + k * N] = wv[k];
+#pragma unroll
+    for (int k = 0; k < NCT; ++k)
+      if (tid + k * N < NCV) cdst[tid + k * N] = cv[k];
   }
   __syncthreads();
   const double *tWs = sm.coef, *tEs = sm.coef + N, *tSs = sm.coef + 2 * N,
