@@ -39,38 +39,35 @@ __device__ __forceinline__ void atomic_max_pos_double(double *addr, double v) {
             static_cast<unsigned long long>(__double_as_longlong(v)));
 }
 
-// Transmissibilities of the four faces of local cell (a, b) of subdomain sb,
-// in the order W, E, S, N.  Two-point fluxes on square cells: harmonic mean
+
+// Face transmissibilities (two-point fluxes on square cells): harmonic mean
 // between cells, kappa/(alpha H/h + 1/2) on a Robin face, 2 kappa on a
-// Dirichlet face, 0 on a Neumann face.  kn[side]: kappa of the neighbour
-// cell on that side when it lies inside the subdomain.
+// Dirichlet face, 0 on a Neumann face.
+//
+// Harmonic-mean transmissibility of an interior face (square cells).  It is
+// bitwise symmetric in its arguments (2 k1 k2 = 2 (k1 k2) exactly, sum and
+// product commute), so one evaluation serves both cells of the face.
+__device__ __forceinline__ double harmonic_face_T(double k1, double k2) {
+  return 2.0 * k1 * k2 / (k1 + k2);
+}
+
+// A face of cell (a, b) on the subdomain edge ``side``: Robin on an
+// interface edge, Dirichlet / Neumann on the physical boundary.
 template <int S>
-__device__ void face_T(const DeviceTables &t, const SubInfo &sb, double kc, const double kn[4],
-                       int a, int b, double out[4]) {
-  const int nb_a[4] = {a - 1, a + 1, a, a};
-  const int nb_b[4] = {b, b, b - 1, b + 1};
-  const double HoverH = static_cast<double>(S);   // H / h
-#pragma unroll
-  for (int side = 0; side < 4; ++side) {
-    const int na = nb_a[side], nbb = nb_b[side];
-    double T;
-    if (na >= 0 && na < S && nbb >= 0 && nbb < S) {
-      T = 2.0 * kc * kn[side] / (kc + kn[side]);
-    } else if (sb.edge_iface[side] >= 0) {
-      const int e = (side < 2) ? b : a;
-      const double al = t.alpha[t.iface[sb.edge_iface[side]].alpha_off + e];
-      T = kc / (al * HoverH + 0.5);
-    } else {
-      const int gi = sb.x0 + a, gj = sb.y0 + b;
-      int k;
-      if (side == kEdgeW) k = gj;
-      else if (side == kEdgeE) k = t.ny + gj;
-      else if (side == kEdgeS) k = 2 * t.ny + gi;
-      else k = 2 * t.ny + t.nx + gi;
-      T = (t.bc_type[k] == 1) ? 2.0 * kc : 0.0;
-    }
-    out[side] = T;
+__device__ __forceinline__ double edge_face_T(const DeviceTables &t, const SubInfo &sb, double kc,
+                                              int a, int b, int side) {
+  if (sb.edge_iface[side] >= 0) {
+    const int e = (side < 2) ? b : a;
+    const double al = t.alpha[t.iface[sb.edge_iface[side]].alpha_off + e];
+    return kc / (al * static_cast<double>(S) + 0.5);
   }
+  const int gi = sb.x0 + a, gj = sb.y0 + b;
+  int k;
+  if (side == kEdgeW) k = gj;
+  else if (side == kEdgeE) k = t.ny + gj;
+  else if (side == kEdgeS) k = 2 * t.ny + gi;
+  else k = 2 * t.ny + t.nx + gi;
+  return (t.bc_type[k] == 1) ? 2.0 * kc : 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -270,6 +267,7 @@ __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, 
   const int a = tid % S, b = tid / S;
   __shared__ double kap[N];
   __shared__ double dsc[N];
+  __shared__ double tfE[N], tfN[N];   // E and N face transmissibilities
   __shared__ T offx[N];   // scaled coupling of cell (a,b) to (a+1,b)
   __shared__ T ecp[N];    // scaled coupling of cell (a,b) to (a,b+1)
 
@@ -278,13 +276,16 @@ __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, 
   if (!(kc > 0.0) || !isfinite(kc)) atomicOr(&w.status[0], MRCM_FLAG_NAN);
   kap[tid] = kc;
   __syncthreads();
-  double kn[4];
-  kn[0] = a > 0 ? kap[tid - 1] : 0.0;
-  kn[1] = a < S - 1 ? kap[tid + 1] : 0.0;
-  kn[2] = b > 0 ? kap[tid - S] : 0.0;
-  kn[3] = b < S - 1 ? kap[tid + S] : 0.0;
+  // each interior face once: a cell computes its E and N faces, and takes W
+  // and S from the neighbouring cells (the same values, see harmonic_face_T)
   double T4[4];
-  face_T<S>(t, sb, kc, kn, a, b, T4);
+  T4[1] = a < S - 1 ? harmonic_face_T(kc, kap[tid + 1]) : edge_face_T<S>(t, sb, kc, a, b, kEdgeE);
+  T4[3] = b < S - 1 ? harmonic_face_T(kc, kap[tid + S]) : edge_face_T<S>(t, sb, kc, a, b, kEdgeN);
+  tfE[tid] = T4[1];
+  tfN[tid] = T4[3];
+  __syncthreads();
+  T4[0] = a > 0 ? tfE[tid - 1] : edge_face_T<S>(t, sb, kc, a, b, kEdgeW);
+  T4[2] = b > 0 ? tfN[tid - S] : edge_face_T<S>(t, sb, kc, a, b, kEdgeS);
   const double d = 1.0 / sqrt(T4[0] + T4[1] + T4[2] + T4[3]);
   double *coef = w.coef + sb.coef_off;
 #pragma unroll
@@ -333,17 +334,25 @@ __global__ void __launch_bounds__(32 * kFW) k_factor_warp(DeviceTables t, Worksp
     return K[cc] * lam[cc];
   };
   bool nan = false;
+  // lane a walks column a row by row (cell = lane + 32 k, S = 32): kappa is
+  // read once per cell, one row ahead; the E neighbour's kappa and the W
+  // face come from the next / previous lane, the S face from the previous
+  // row (each interior face evaluated once, see harmonic_face_T)
+  static_assert(S == 32, "one lane per column");
+  double kc_next = kappa(lane, 0), tS = 0.0;
   for (int k = 0; k < CPL; ++k) {
-    const int cell = lane + 32 * k, a = cell % S, b = cell / S;
-    const double kc = kappa(a, b);
+    const int cell = lane + 32 * k, a = lane, b = k;
+    const double kc = kc_next;
+    if (k + 1 < CPL) kc_next = kappa(a, b + 1);
     if (!(kc > 0.0) || !isfinite(kc)) nan = true;
-    double kn[4];
-    kn[0] = a > 0 ? kappa(a - 1, b) : 0.0;
-    kn[1] = a < S - 1 ? kappa(a + 1, b) : 0.0;
-    kn[2] = b > 0 ? kappa(a, b - 1) : 0.0;
-    kn[3] = b < S - 1 ? kappa(a, b + 1) : 0.0;
+    const double kE = __shfl_down_sync(0xffffffffu, kc, 1);
     double T4[4];
-    face_T<S>(t, sb, kc, kn, a, b, T4);
+    T4[1] = a < S - 1 ? harmonic_face_T(kc, kE) : edge_face_T<S>(t, sb, kc, a, b, kEdgeE);
+    const double tW = __shfl_up_sync(0xffffffffu, T4[1], 1);
+    T4[0] = a > 0 ? tW : edge_face_T<S>(t, sb, kc, a, b, kEdgeW);
+    T4[3] = b < S - 1 ? harmonic_face_T(kc, kc_next) : edge_face_T<S>(t, sb, kc, a, b, kEdgeN);
+    T4[2] = b > 0 ? tS : edge_face_T<S>(t, sb, kc, a, b, kEdgeS);
+    tS = T4[3];
     const double d = 1.0 / sqrt(T4[0] + T4[1] + T4[2] + T4[3]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) coef[q * N + cell] = T4[q];
