@@ -51,6 +51,26 @@ __device__ __forceinline__ double harmonic_face_T(double k1, double k2) {
   return 2.0 * k1 * k2 / (k1 + k2);
 }
 
+// Jacobi scaling 1/sqrt(A_cc) of a cell.  Any consistent positive scaling is
+// valid (the same d scales the factor, the residuals and the corrections),
+// but the factor takes the scaled diagonal as exactly 1, so d must be close
+// to the exact value: the FP32 factor takes one Newton-Raphson step for
+// x^(-1/2), y (3 - x y^2) / 2, in FP64 from the FP32 estimate (relative error
+// squares, ~1e-14), four FP64 operations instead of a divide and a square
+// root.  The FP64 path, which has no refinement, takes the exact value, and
+// so does any diagonal outside FP32's normal range.
+template <typename T>
+__device__ __forceinline__ double jacobi_scale(double diag) {
+  if constexpr (std::is_same<T, float>::value) {
+    const float f = static_cast<float>(diag);
+    if (f > 1e-30f && f < 1e30f) {
+      const double y = static_cast<double>(rsqrtf(f));
+      return y * fma(-0.5 * diag, y * y, 1.5);
+    }
+  }
+  return 1.0 / sqrt(diag);
+}
+
 // A face of cell (a, b) on the subdomain edge ``side``: Robin on an
 // interface edge, Dirichlet / Neumann on the physical boundary.
 template <int S>
@@ -286,7 +306,7 @@ __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, 
   __syncthreads();
   T4[0] = a > 0 ? tfE[tid - 1] : edge_face_T<S>(t, sb, kc, a, b, kEdgeW);
   T4[2] = b > 0 ? tfN[tid - S] : edge_face_T<S>(t, sb, kc, a, b, kEdgeS);
-  const double d = 1.0 / sqrt(T4[0] + T4[1] + T4[2] + T4[3]);
+  const double d = jacobi_scale<T>(T4[0] + T4[1] + T4[2] + T4[3]);
   double *coef = w.coef + sb.coef_off;
 #pragma unroll
   for (int k = 0; k < 4; ++k) coef[k * N + tid] = T4[k];
@@ -353,7 +373,7 @@ __global__ void __launch_bounds__(32 * kFW) k_factor_warp(DeviceTables t, Worksp
     T4[3] = b < S - 1 ? harmonic_face_T(kc, kc_next) : edge_face_T<S>(t, sb, kc, a, b, kEdgeN);
     T4[2] = b > 0 ? tS : edge_face_T<S>(t, sb, kc, a, b, kEdgeS);
     tS = T4[3];
-    const double d = 1.0 / sqrt(T4[0] + T4[1] + T4[2] + T4[3]);
+    const double d = jacobi_scale<T>(T4[0] + T4[1] + T4[2] + T4[3]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) coef[q * N + cell] = T4[q];
     coef[4 * N + cell] = d;
