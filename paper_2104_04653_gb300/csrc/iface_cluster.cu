@@ -541,11 +541,17 @@ __global__ void __launch_bounds__(kCT, 1)
       if (tid == 0) atomicOr(&w.status[0], MRCM_FLAG_LAYOUT);
     } else if (wid < np) {
       float *Sd = scr + wid * per, *Xd = Sd + mm * ld, *To = Xd + mm * ld;
-      int nth = 0;
-      for (int p = 0; p < b; ++p) {
+      // the slab's interfaces in position order from two ballots over the
+      // diagonal-pair table (kCMaxB = 64 entries, -1 where no interface
+      // starts); warp wid takes interfaces wid, wid + np, ...
+      static_assert(kCMaxB == 64, "two 32-entry ballots cover the table");
+      const unsigned m0 = __ballot_sync(0xffffffffu, diagq[lane] >= 0);
+      const unsigned m1 = __ballot_sync(0xffffffffu, diagq[lane + 32] >= 0);
+      const int n0 = __popc(m0), nif = n0 + __popc(m1);
+      for (int n = wid; n < nif; n += np) {
+        const int p = n < n0 ? static_cast<int>(__fns(m0, 0, n + 1))
+                             : 32 + static_cast<int>(__fns(m1, 0, n - n0 + 1));
         const int q = diagq[p];
-        if (q < 0) continue;                                 // not an interface's first row
-        if ((nth++ % np) != wid) continue;
         const PairPlan pp = staged ? pps[q - pa0] : t.pairs[q];
         const int m = pp.m, nU = pp.nU, p0 = pp.p0;
         const double *Sq = Sst + (pp.goff - s_goff0) / 2;
@@ -627,11 +633,14 @@ __global__ void __launch_bounds__(kCT, 1)
       // product loop).
       T *XT = scrT, *TnT = scrT + mm * mm;
       {
+        // T_g and T_n are block lower triangular, blockdiag(L_A^-1, L_C^-1):
+        // row i of T_g has nonzeros in [lo(i), i], lo = 0 for a flux row and
+        // nU for a pressure row (the skipped terms are exact zeros)
         const double *Tg = Td + pp.p0 * mm;
         for (int e = lane; e < m * mn; e += 32) {
           const int i = e / mn, j = e % mn;
           double a = 0.0;
-          for (int qq = 0; qq <= i; ++qq) a += Tg[i * mm + qq] * Sb[qq * mn + j];
+          for (int qq = i < pp.nU ? 0 : pp.nU; qq <= i; ++qq) a += Tg[i * mm + qq] * Sb[qq * mn + j];
           if (diag)
             Xb[e] = a;
           else
@@ -648,7 +657,7 @@ __global__ void __launch_bounds__(kCT, 1)
         for (int e = lane; e < m * mn; e += 32) {
           const int i = e / mn, j = e % mn;
           double a = 0.0;
-          for (int qq = 0; qq <= j; ++qq) a += Xb[i * mn + qq] * Tn[j * mm + qq];
+          for (int qq = j < pp.nUn ? 0 : pp.nUn; qq <= j; ++qq) a += Xb[i * mn + qq] * Tn[j * mm + qq];
           blk[(pp.p0 + i) * b + pp.pn0 + j] = static_cast<T>(a);
         }
       } else {
@@ -657,7 +666,7 @@ __global__ void __launch_bounds__(kCT, 1)
         for (int e = lane; e < m * mn; e += 32) {
           const int i = e / mn, j = e % mn;
           T a = T(0);
-          for (int qq = 0; qq <= j; ++qq) a += XT[i * mn + qq] * Tn[j * ldn + qq];
+          for (int qq = j < pp.nUn ? 0 : pp.nUn; qq <= j; ++qq) a += XT[i * mn + qq] * Tn[j * ldn + qq];
           blk[(pp.p0 + i) * b + pp.pn0 + j] = a;
         }
       }

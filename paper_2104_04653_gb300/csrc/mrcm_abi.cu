@@ -502,6 +502,7 @@ static void build_plans(mrcm_ctx *c) {
           pp.mn = mn;
           pp.tscn = static_cast<int>(fn.tsc_off);
           pp.ds = fn.slab - fi.slab;
+          pp.nUn = fn.nU;
           pp.goff = static_cast<int>(c->pair_goff.size());
           int eLn = -1, eRn = -1;
           for (int e = 0; e < 4; ++e) {

@@ -71,6 +71,7 @@ struct PairPlan {
   int p0, m, nU, tsc;      // own interface: first slab position, size, flux size, T offset
   int pn0, mn, tscn, ds;   // neighbour: first position in its slab, size, T offset, slab - own
   int goff;
+  int nUn;                 // neighbour's flux size (its T is block lower triangular at nUn)
 };
 
 // GMRES interface path (iface_gmres.cu)
