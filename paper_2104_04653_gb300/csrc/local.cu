@@ -769,16 +769,20 @@ __device__ void block_solve32(BasisSmem32<T, NC> &sm, const T *Wg, int nc) {
   const int ks = tid % kKS, o = tid / kKS, a = o % S, c = o / S;
   const bool act = c < nc;            // uniform over a warp (c = tid / 128)
   const int wrow = (tid / S) * kWst + tid % S;
+  // W_j of step kk (forward j = kk, backward j = 2S - 2 - kk); this thread's
+  // element is loaded two steps ahead (a step is about one L2 round trip)
+  auto wstep = [&](int kk) {
+    const int jj = kk < S ? kk : 2 * S - 2 - kk;
+    return Wg[static_cast<int64_t>(jj) * N + tid];
+  };
   sm.Wb[0][wrow] = Wg[tid];
+  T w1 = NSTEP > 1 ? wstep(1) : T(0);
   __syncthreads();
   int buf = 0;
   for (int k = 0; k < NSTEP; ++k) {
     const int j = k < S ? k : 2 * S - 2 - k;
-    T nextw = T(0);
-    if (k + 1 < NSTEP) {
-      const int jn = k + 1 < S ? k + 1 : 2 * S - 3 - k;
-      nextw = Wg[static_cast<int64_t>(jn) * N + tid];
-    }
+    const T nextw = w1;
+    if (k + 2 < NSTEP) w1 = wstep(k + 2);
     const T *Wj = sm.Wb[buf] + a * kWst;
     T acc = T(0);
     if (act) {
