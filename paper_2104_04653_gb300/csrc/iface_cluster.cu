@@ -481,9 +481,10 @@ __global__ void __launch_bounds__(kCT, 1)
   __syncthreads();
   // ---- the slab's pair plans and the G sums of every pair entry, staged
   // by all threads at once at the end of the tile area (the scaling and the
-  // assembly then read no global memory), if they fit behind both phases'
-  // scratch; otherwise each warp reads its pairs from global memory.  The
-  // diagonal pairs are found in the same pass.
+  // assembly then read no global memory).  The host plan admits the cluster
+  // path only where this fits behind both phases' scratch for every slab;
+  // otherwise the layout flag is raised and the setup skipped.  The diagonal
+  // pairs are found in the same pass.
   const int npair = pa1 - pa0, nst = (s_goff1 - s_goff0) / 2;
   const size_t ppb = (static_cast<size_t>(npair) * sizeof(PairPlan) + 15) & ~static_cast<size_t>(15);
   unsigned char *stage = reinterpret_cast<unsigned char *>(v) - ppb - static_cast<size_t>(nst) * 8;
@@ -492,13 +493,14 @@ __global__ void __launch_bounds__(kCT, 1)
   const unsigned char *asm_end = reinterpret_cast<const unsigned char *>(tW1) +
                                  static_cast<size_t>(nw) * 2 * mm * mm * (sizeof(double) + sizeof(T));
   const bool staged = npair >= 0 && nst >= 0 && stage >= asm_end;
-  {
+  if (!staged && tid == 0) atomicOr(&w.status[0], MRCM_FLAG_LAYOUT);
+  if (staged) {
     for (int q = pa0 + tid; q < pa1; q += kCT) {
       const PairPlan pp = t.pairs[q];
-      if (staged) pps[q - pa0] = pp;
+      pps[q - pa0] = pp;
       if (pp.ds == 0 && pp.pn0 == pp.p0 && pp.p0 >= 0 && pp.p0 < b) diagq[pp.p0] = q;
     }
-    if (staged) {
+    {
       constexpr int U = 8;
       double *Sw = reinterpret_cast<double *>(stage + ppb);
       for (int base = tid; base < nst; base += kCT * U) {
@@ -532,8 +534,7 @@ __global__ void __launch_bounds__(kCT, 1)
   {
     const int ld = mm + 1;
     const int per = 2 * mm * ld + mm * mm;                   // floats per warp
-    const size_t area = staged ? static_cast<size_t>(stage - smraw)
-                               : static_cast<size_t>(5 + 2 * nlevS) * bb * sizeof(T);
+    const size_t area = staged ? static_cast<size_t>(stage - smraw) : 0;
     const int avail = static_cast<int>(area / (sizeof(float) * per));
     const int np = avail < nw ? avail : nw;
     float *scr = reinterpret_cast<float *>(smraw);
@@ -552,19 +553,13 @@ __global__ void __launch_bounds__(kCT, 1)
         const int p = n < n0 ? static_cast<int>(__fns(m0, 0, n + 1))
                              : 32 + static_cast<int>(__fns(m1, 0, n - n0 + 1));
         const int q = diagq[p];
-        const PairPlan pp = staged ? pps[q - pa0] : t.pairs[q];
+        const PairPlan pp = pps[q - pa0];
         const int m = pp.m, nU = pp.nU, p0 = pp.p0;
         const double *Sq = Sst + (pp.goff - s_goff0) / 2;
         // A = -M_UU, C = -M_PP; a pinned unknown gets a unit diagonal
         for (int e = lane; e < m * m; e += 32) {
           const int i = e / m, j = e % m;
-          double val;
-          if (staged) {
-            val = Sq[e];
-          } else {
-            const int g0 = t.pair_goff[pp.goff + 2 * e], g1 = t.pair_goff[pp.goff + 2 * e + 1];
-            val = (g0 >= 0 ? w.G[g0] : 0.0) + (g1 >= 0 ? w.G[g1] : 0.0);
-          }
+          const double val = Sq[e];
           float sv = ((i < nU) == (j < nU)) ? static_cast<float>(-val) : 0.0f;
           if (((posinf[p0 + i] >> 29) & 1) || ((posinf[p0 + j] >> 29) & 1))
             sv = (i == j) ? 1.0f : 0.0f;
@@ -600,21 +595,14 @@ __global__ void __launch_bounds__(kCT, 1)
                           reinterpret_cast<T *>(reinterpret_cast<double *>(tW1) + nw * 2 * mm * mm) +
                           nw * 2 * mm * mm) <= reinterpret_cast<const unsigned char *>(v);
     if (!fits && tid == 0) atomicOr(&w.status[0], MRCM_FLAG_LAYOUT);
-    for (int q = pa0 + wid; fits && q < pa1; q += nw) {
-      const PairPlan pp = staged ? pps[q - pa0] : t.pairs[q];
+    for (int q = pa0 + wid; fits && staged && q < pa1; q += nw) {
+      const PairPlan pp = pps[q - pa0];
       const int m = pp.m, mn = pp.mn;
       double *Sb = scr, *Xb = scr + mm * mm;
       const double *Sq = Sst + (pp.goff - s_goff0) / 2;
       for (int e = lane; e < m * mn; e += 32) {
         const int i = e / mn;
-        double val;
-        if (staged) {
-          val = Sq[e];
-        } else {
-          const int g0 = t.pair_goff[pp.goff + 2 * e], g1 = t.pair_goff[pp.goff + 2 * e + 1];
-          val = (g0 >= 0 ? w.G[g0] : 0.0) + (g1 >= 0 ? w.G[g1] : 0.0);
-        }
-        Sb[e] = (i >= pp.nU) ? -val : val;                 // symmetrising sign
+        Sb[e] = (i >= pp.nU) ? -Sq[e] : Sq[e];             // symmetrising sign
       }
       __syncwarp();
       T *blk = pp.ds == 0 ? tB : (pp.ds == -1 ? tA : tC);
@@ -893,7 +881,8 @@ size_t cluster_smem(int bmax, int nlev, int emax, int mmax) {
 
 // Can the one-launch cluster path run this problem?  Returns the cluster
 // size (0: no).
-int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int emax, int dev) {
+int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int emax,
+                       size_t stage_max, int dev) {
   if (prec != MRCM_PREC_FP32_IR) return 0;
   if (nslab < 1 || nslab > 16 || bmax > kCMaxB || 3 * kCMaxB > 32767) return 0;
   const size_t smem = cluster_smem<float>(bmax, nlev, emax, mmax);
@@ -908,6 +897,12 @@ int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int em
                        sizeof(float);
   if (2 * static_cast<size_t>(mmax) * (mmax + 1) * sizeof(double) > tiles) return 0;
   if (scr > behind) return 0;
+  // every slab's staged pair plans and pair blocks fit behind the assembly
+  // scratch, and one warp's scaling scratch fits in front of them
+  if (scr + stage_max > behind) return 0;
+  const size_t per = (2 * static_cast<size_t>(mmax) * (mmax + 1) + static_cast<size_t>(mmax) * mmax) *
+                     sizeof(float);
+  if (stage_max + per > tiles) return 0;
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem > static_cast<size_t>(optin)) return 0;

@@ -1082,9 +1082,18 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   }
   c->solve_grid = c->use_gmres || BG ? 0 : iface_solve_grid(c->prec, c->dev, c->max_vec);
   if (BG) c->big_grid = big_solve_grid(c->prec, c->dev);
-  if (nunk > 0 && c->plans_ok && !c->use_gmres && !getenv("MRCM_NO_CLUSTER"))
+  if (nunk > 0 && c->plans_ok && !c->use_gmres && !getenv("MRCM_NO_CLUSTER")) {
+    // largest staging footprint of a slab's pair plans and pair blocks
+    size_t stage_max = 0;
+    for (size_t sl = 0; sl + 1 < c->pair_off.size(); ++sl) {
+      const int pa0 = c->pair_off[sl], pa1 = c->pair_off[sl + 1];
+      const size_t ppb = (static_cast<size_t>(pa1 - pa0) * sizeof(PairPlan) + 15) & ~static_cast<size_t>(15);
+      const size_t nst = static_cast<size_t>(c->pairs[pa1].goff - c->pairs[pa0].goff) / 2;
+      stage_max = std::max(stage_max, ppb + nst * sizeof(double));
+    }
     c->cluster_k = iface_cluster_plan(c->prec, c->nslab_max, c->bmax_max, c->nlev_max, c->mmax,
-                                      t.emax, c->dev);
+                                      t.emax, stage_max, c->dev);
+  }
   if (nunk > 0 && BG && c->big_grid < 1) {
     cudaFree(c->arena);
     delete c;

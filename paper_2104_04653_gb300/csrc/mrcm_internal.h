@@ -233,7 +233,10 @@ cudaError_t launch_reconstruct(const DeviceTables &t, const Workspace &w, double
 int iface_solve_grid(int prec, int dev, int max_vec);
 // message returned by mrcm_last_error(NULL) (thread-local)
 void set_global_error(const char *msg);
-int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int emax, int dev);
+// stage_max: the largest per-slab staging footprint (pair plans rounded to
+// 16 bytes + 8 bytes per pair entry) over the batch
+int iface_cluster_plan(int prec, int nslab, int bmax, int nlev, int mmax, int emax,
+                       size_t stage_max, int dev);
 cudaError_t launch_iface_cluster(const DeviceTables &t, const Workspace &w, const int *slab_if,
                                  const int *slab_if_off, int nslab, int bmax, int nlev,
                                  double tol, int max_solves, cudaStream_t st);
