@@ -191,6 +191,54 @@ __device__ void gemm2(T *C1, T *C2, const T *A, const T *B1, const T *B2, int b,
   __syncthreads();
 }
 
+// Two independent products in one pass: C1 = A1 B1 and C2 = A2 B2 (alpha 1,
+// no accumulation), each element summed exactly as in gemm.
+__device__ void gemm_dual_v4(float *C1, const float *A1, const float *B1, float *C2,
+                             const float *A2, const float *B2, int b) {
+  const int t = threadIdx.x, j0 = 2 * (t & 31), i0 = 4 * (t >> 5);
+  if (i0 < b && j0 < b) {
+    float c[4][2] = {}, d[4][2] = {};
+    for (int k = 0; k < b; k += 4) {
+      float4 a[4], e[4];
+      float2 bv[4], ev[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        a[p] = *reinterpret_cast<const float4 *>(A1 + (i0 + p) * b + k);
+        e[p] = *reinterpret_cast<const float4 *>(A2 + (i0 + p) * b + k);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        bv[q] = *reinterpret_cast<const float2 *>(B1 + (k + q) * b + j0);
+        ev[q] = *reinterpret_cast<const float2 *>(B2 + (k + q) * b + j0);
+      }
+      fma_k4(c, a, bv);
+      fma_k4(d, e, ev);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      *reinterpret_cast<float2 *>(C1 + (i0 + p) * b + j0) = make_float2(c[p][0], c[p][1]);
+      *reinterpret_cast<float2 *>(C2 + (i0 + p) * b + j0) = make_float2(d[p][0], d[p][1]);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void gemm(T *C, const T *A, const T *B, int b, T alpha, bool acc);
+
+template <typename T>
+__device__ void gemm_dual(T *C1, const T *A1, const T *B1, T *C2, const T *A2, const T *B2,
+                          int b) {
+  if constexpr (std::is_same<T, float>::value) {
+    if ((b & 3) == 0) {
+      gemm_dual_v4(C1, A1, B1, C2, A2, B2, b);
+      return;
+    }
+  }
+  gemm(C1, A1, B1, b, T(1), false);
+  gemm(C2, A2, B2, b, T(1), false);
+}
+
 // dst[0..n) = src[0..n) (src may be another CTA's shared memory): every
 // thread issues its eight loads before storing, so a copy costs one
 // distributed-shared-memory latency, not eight
@@ -680,20 +728,29 @@ __global__ void __launch_bounds__(kCT, 1)
       const int l = k - s, rt = k + s;
       T *X = tX + lev * bb;
       T *Y = tY + lev * bb;
-      if (l >= 0) {
+      if (l >= 0 && rt < K) {
+        // both neighbours: their inverses in one copy pass, X and Y in one
+        // product pass, then the two fused updates
+        copy_in2(tW1, cluster.map_shared_rank(tB, l), tW2, cluster.map_shared_rank(tB, rt), b * b);
+        gemm_dual(X, tA, tW1, Y, tC, tW2, b);                      // X = A_k B_l^{-1}, Y = C_k B_r^{-1}
+        copy_in2(tW1, cluster.map_shared_rank(tC, l), tW2, cluster.map_shared_rank(tA, l), b * b);
+        gemm2(tB, tA, X, tW1, tW2, b, T(-1), true, T(-1), false);  // B_k -= X C_l, A_k = -X A_l
+        copy_in2(tW1, cluster.map_shared_rank(tA, rt), tW2, cluster.map_shared_rank(tC, rt), b * b);
+        gemm2(tB, tC, Y, tW1, tW2, b, T(-1), true, T(-1), false);  // B_k -= Y A_r, C_k = -Y C_r
+      } else if (l >= 0) {                                         // left neighbour only
         copy_in(tW1, cluster.map_shared_rank(tB, l), b * b);         // B_l^{-1}
         gemm(X, tA, tW1, b, T(1), false);                          // X = A_k B_l^{-1}
         copy_in2(tW1, cluster.map_shared_rank(tC, l), tW2, cluster.map_shared_rank(tA, l), b * b);
         gemm2(tB, tA, X, tW1, tW2, b, T(-1), true, T(-1), false);  // B_k -= X C_l, A_k = -X A_l
-      } else {
+        for (int e = tid; e < b * b; e += kCT) Y[e] = T(0);
+      } else if (rt < K) {                                         // right neighbour only
         for (int e = tid; e < b * b; e += kCT) X[e] = T(0);
-      }
-      if (rt < K) {
         copy_in(tW1, cluster.map_shared_rank(tB, rt), b * b);        // B_r^{-1}
         gemm(Y, tC, tW1, b, T(1), false);                          // Y = C_k B_r^{-1}
         copy_in2(tW1, cluster.map_shared_rank(tA, rt), tW2, cluster.map_shared_rank(tC, rt), b * b);
         gemm2(tB, tC, Y, tW1, tW2, b, T(-1), true, T(-1), false);  // B_k -= Y A_r, C_k = -Y C_r
       } else {
+        for (int e = tid; e < b * b; e += kCT) X[e] = T(0);
         for (int e = tid; e < b * b; e += kCT) Y[e] = T(0);
       }
     }
