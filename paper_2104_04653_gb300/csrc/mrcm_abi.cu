@@ -544,9 +544,14 @@ static void rebuild_items(mrcm_ctx *c, int nc16, int nc32) {
   for (size_t g = 0; g < c->sub.size(); ++g) {
     const SubInfo &sb = c->sub[g];
     const int ncol = sb.ncols, gid = static_cast<int>(g);
+    // as few CTAs as the width allows, with balanced column counts (no
+    // one-column stragglers; each CTA's fixed latency is paid once per item)
     if (sb.s == 16) {
-      for (int c0 = 0; c0 < ncol; c0 += nc16)
-        c->items.push_back(BasisItem{gid, c0, (ncol - c0) < nc16 ? (ncol - c0) : nc16});
+      const int nch = (ncol + nc16 - 1) / nc16;
+      for (int k = 0; k < nch; ++k) {
+        const int c0 = ncol * k / nch, c1 = ncol * (k + 1) / nch;
+        c->items.push_back(BasisItem{gid, c0, c1 - c0});
+      }
     } else {
       const int nch = (ncol + nc32 - 1) / nc32;
       for (int k = 0; k < nch; ++k) {
