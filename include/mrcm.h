@@ -66,7 +66,7 @@ typedef enum {
   MRCM_EIRSTALL = 5,   /* refinement stopped above its tolerance           */
   MRCM_ENOCONV = 6,    /* interface refinement did not converge            */
   MRCM_ENAN = 7,       /* NaN / Inf in inputs or results                   */
-  MRCM_ETIMEOUT = 8    /* reserved: a bounded device wait ran out          */
+  MRCM_ETIMEOUT = 8    /* a bounded device wait ran out (result invalid)   */
 } mrcm_status;
 
 /* Device status flags (bit OR), see mrcm_info.flags. */
@@ -76,6 +76,7 @@ typedef enum {
 #define MRCM_FLAG_NAN         0x8
 #define MRCM_FLAG_IFACE_PIVOT 0x10
 #define MRCM_FLAG_LAYOUT      0x20  /* internal table inconsistency (a bug) */
+#define MRCM_FLAG_TIMEOUT     0x80  /* a bounded device wait ran out         */
 #define MRCM_FLAG_PRECOND_FALLBACK 0x40  /* informational: the caller-supplied   */
                                          /* preconditioner stalled and GMRES was */
                                          /* rerun with block-Jacobi              */

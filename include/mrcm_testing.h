@@ -17,11 +17,19 @@ extern "C" {
  *   C = alpha (A1 B1 + A2 B2) (+ C if acc),  row-major, device pointers,
  * A2/B2 may be NULL.  impl 0: the SIMT kernel; impl 1: the tcgen05 kernel
  * (3 x TF32 split products, FP32 accumulation in tensor memory).  d_status
- * (device int) receives MRCM_FLAG_LAYOUT if a bounded wait of the tensor-core
+ * (device int) receives MRCM_FLAG_TIMEOUT if a bounded wait of the tensor-core
  * kernel ran out.  Synchronises the stream. */
 mrcm_status mrcm_test_gemm(int32_t impl, int32_t n, const float *d_a1, const float *d_b1,
                            const float *d_a2, const float *d_b2, float *d_c, double alpha,
                            int32_t acc, int32_t *d_status, void *cuda_stream);
+
+/* Failure detection without a fault: runs the tensor-core kernels' bounded
+ * mbarrier wait (the one behind MRCM_ETIMEOUT, include/mrcm.h) on a barrier
+ * that nothing completes, giving up after limit tries (1 .. 2^26); the probe
+ * kernel then raises MRCM_FLAG_TIMEOUT in d_status (device int) and returns,
+ * leaving the context usable.  MRCM_EINVAL for a NULL d_status or a limit out
+ * of range.  Synchronises the stream.  (No counterpart in the paper.) */
+mrcm_status mrcm_test_wait_timeout(uint32_t limit, int32_t *d_status, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -1170,6 +1170,7 @@ static mrcm_status read_info(mrcm_ctx *ctx, mrcm_info *info) {
   info->gmres_iters = st[3];
   info->local_resid_max = ds[0];
   info->iface_resid = ds[1];
+  if (st[0] & MRCM_FLAG_TIMEOUT) return fail(ctx, MRCM_ETIMEOUT, "a bounded device wait ran out");
   if (st[0] & MRCM_FLAG_LAYOUT) return fail(ctx, MRCM_EINVAL, "internal slab layout error");
   if (st[0] & MRCM_FLAG_NAN) return fail(ctx, MRCM_ENAN, "NaN/Inf or non-positive kappa");
   if (st[0] & MRCM_FLAG_NOTSPD) return fail(ctx, MRCM_ENOTSPD, "local pivot <= 0");

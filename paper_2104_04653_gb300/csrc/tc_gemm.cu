@@ -83,8 +83,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 }
 
 // wait for the phase with the given parity; false if the limit ran out
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (unsigned it = 0; it < kTcWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          unsigned limit = kTcWaitLimit) {
+  for (unsigned it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -95,6 +96,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (ok) return true;
   }
   return false;
+}
+
+// The tensor-core kernels' bounded wait on an mbarrier that nothing
+// completes (its one expected arrival never comes): the wait gives up after
+// ``limit`` tries and the timeout flag is raised, as in the GEMM kernels.
+__global__ void k_wait_probe(int *status, unsigned limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(smem_u32(&bar), 1);
+  __syncthreads();
+  const bool ok = mbar_wait(smem_u32(&bar), 0, limit);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!ok) atomicOr(status, MRCM_FLAG_TIMEOUT);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)));
+  }
 }
 
 __global__ void __launch_bounds__(256) k_tc_gemm(const GemmJob *jobs, int *status) {
@@ -195,7 +211,7 @@ __global__ void __launch_bounds__(256) k_tc_gemm(const GemmJob *jobs, int *statu
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (fail) {
-    if (t == 0) atomicOr(status, MRCM_FLAG_LAYOUT);
+    if (t == 0) atomicOr(status, MRCM_FLAG_TIMEOUT);
   } else if (total > 0) {
     // epilogue: warp w reads lanes 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63
     const int quarter = warp & 3, half = warp >> 2;
@@ -413,7 +429,7 @@ __global__ void __launch_bounds__(256) k_tc_gemm_tma(const GemmJob *jobs, const 
   ok = ok && !s_fail;
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (!ok) {
-    if (t == 0) atomicOr(status, MRCM_FLAG_LAYOUT);
+    if (t == 0) atomicOr(status, MRCM_FLAG_TIMEOUT);
     mbar_wait(smem_u32(&done), 0);
   } else if (total > 0) {
     const int quarter = warp & 3, half = warp >> 2;
@@ -565,5 +581,15 @@ extern "C" mrcm_status mrcm_test_gemm(int32_t impl, int32_t n, const float *d_a1
     e = launch_simt_gemm(dj, 1, n, st);
   }
   if (e != cudaSuccess) return MRCM_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? MRCM_OK : MRCM_ECUDA;
+}
+
+extern "C" mrcm_status mrcm_test_wait_timeout(uint32_t limit, int32_t *d_status,
+                                              void *cuda_stream) {
+  using namespace mrcm;
+  if (!d_status || limit < 1 || limit > kTcWaitLimit) return MRCM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  k_wait_probe<<<1, 32, 0, st>>>(d_status, limit);
+  if (cudaGetLastError() != cudaSuccess) return MRCM_ECUDA;
   return cudaStreamSynchronize(st) == cudaSuccess ? MRCM_OK : MRCM_ECUDA;
 }

@@ -139,3 +139,26 @@ def test_batched_gemm_kernels(impl, n):
         # product and the TF32 tail truncation grow as sqrt(K) 2^-22
         assert err <= (2e-6 if impl == 0 else 1e-5), (impl, n, two, err)
     assert int(st.item()) == 0
+
+
+def test_bounded_wait_reports_timeout():
+    """Failure detection without a GPU fault: the tensor-core kernels'
+    bounded mbarrier wait, run on a barrier that nothing completes, gives up
+    after its limit; the kernel raises the timeout flag and returns (no
+    hang, no trap), and the context stays usable for a normal solve."""
+    import ctypes
+    import time
+    import torch
+    O, mrcm, W = _mods()
+    L = mrcm.lib()
+    L.mrcm_test_wait_timeout.argtypes = [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]
+    L.mrcm_test_wait_timeout.restype = ctypes.c_int32
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    t0 = time.time()
+    assert L.mrcm_test_wait_timeout(1 << 12, st.data_ptr(), stream) == mrcm.MRCM_OK
+    assert time.time() - t0 < 10.0
+    assert int(st.item()) & mrcm.FLAG_TIMEOUT
+    assert L.mrcm_test_wait_timeout(0, st.data_ptr(), stream) == mrcm.MRCM_EINVAL
+    assert L.mrcm_test_wait_timeout(1 << 12, None, stream) == mrcm.MRCM_EINVAL
+    _check(W.config1(), mrcm.SolverOptions(prec=1))
