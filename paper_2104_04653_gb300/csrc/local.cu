@@ -276,8 +276,10 @@ __device__ __forceinline__ void write_beta(const DeviceTables &t, const SubInfo 
   }
 }
 
-// s = 16: one CTA of 256 threads per subdomain.
-template <typename T>
+// s = 16: one CTA of 256 threads per subdomain.  CHAIN = false: stage 1 only
+// (coefficients and Jacobi scale); the FP32 basis kernel then factors each
+// subdomain itself (k_basis with FUSED).
+template <typename T, bool CHAIN = true>
 __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, const double *K,
                                                    const double *lam) {
   constexpr int S = kS, N = S * S;
@@ -314,6 +316,7 @@ __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, 
   coef[5 * N + tid] = kc;
   write_beta<S>(t, sb, kc, a, b, coef);
   dsc[tid] = d;
+  if constexpr (!CHAIN) return;
   __syncthreads();
   offx[tid] = static_cast<T>(a < S - 1 ? -T4[1] * d * dsc[tid + 1] : 0.0);
   ecp[tid] = static_cast<T>(b < S - 1 ? -T4[3] * d * dsc[tid + S] : 0.0);
@@ -517,6 +520,7 @@ template <typename T, int NC>
 struct BasisSmem {
   T Ws[kS * kS * kS];       // W_j, j = 0..S-1 (symmetric)
   T ec[kS * kS];            // scaled row couplings e_j[a]
+  T offx[kS * kS];          // scaled in-row couplings (fused factor only)
   T z[NC * kS * kS];       // scaled residual (input of the solve)
   T v[NC * kS * kS];       // forward values, then the solution
   double coef[kCoefStride]; // tW tE tS tN d kappa, edge beta
@@ -600,7 +604,11 @@ __device__ void column_sums(BasisSmem<T, NC> &sm, const float *val, int nc, floa
   __syncthreads();
 }
 
-template <typename T, int NC>
+// FUSED: the inverse Schur blocks are computed here (warp 0, into shared
+// memory) from the coefficients instead of read from global memory: the
+// FP32 factor of one subdomain costs one warp's pivot chain per column
+// chunk, and saves a launch and the W round trip.
+template <typename T, int NC, bool FUSED = false>
 __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
                                                   const BasisItem *items, const double *q,
                                                   double tol, int ir_max) {
@@ -628,14 +636,18 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
     double2 *cdst = reinterpret_cast<double2 *>(sm.coef);
     V wv[NW];
     double2 cv[NCT];
+    if constexpr (!FUSED) {
 #pragma unroll
-    for (int k = 0; k < NW; ++k) wv[k] = wsrc[tid + k * N];
+      for (int k = 0; k < NW; ++k) wv[k] = wsrc[tid + k * N];
+    }
 #pragma unroll
     for (int k = 0; k < NCT; ++k)
       if (tid + k * N < NCV) cv[k] = csrc[tid + k * N];
     if (tid < nc) sm.col[tid] = t.col[sb.col_off + it.c0 + tid];
+    if constexpr (!FUSED) {
 #pragma unroll
-    for (int k = 0; k < NW; ++k) wdst[tid + k * N] = wv[k];
+      for (int k = 0; k < NW; ++k) wdst[tid + k * N] = wv[k];
+    }
 #pragma unroll
     for (int k = 0; k < NCT; ++k)
       if (tid + k * N < NCV) cdst[tid + k * N] = cv[k];
@@ -645,6 +657,17 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
                *tNs = sm.coef + 3 * N, *ds = sm.coef + 4 * N, *ks = sm.coef + 5 * N;
   if (b < S - 1) sm.ec[tid] = static_cast<T>(-tNs[tid] * ds[tid] * ds[tid + S]);
   else sm.ec[tid] = T(0);
+  if constexpr (FUSED) {
+    // the scaled couplings exactly as the factor kernel forms them, then
+    // the Schur-block chain of this subdomain in warp 0
+    sm.offx[tid] = a < S - 1 ? static_cast<T>(-tEs[tid] * ds[tid] * ds[tid + 1]) : T(0);
+    __syncthreads();
+    if (tid < 32) {
+      const bool bad = schur_inverses<T, S>(tid, sm.offx, sm.ec, sm.Ws);
+      if (__any_sync(0xffffffffu, bad) && tid == 0) atomicOr(&w.status[0], MRCM_FLAG_NOTSPD);
+    }
+    __syncthreads();
+  }
 
   // right-hand sides (FP64)
   const double myT[4] = {tWs[tid], tEs[tid], tSs[tid], tNs[tid]};
@@ -950,8 +973,8 @@ cudaError_t launch_factor(const DeviceTables &t, const Workspace &w, int prec, c
   if (n16 > 0) {
     if (prec == MRCM_PREC_FP64)
       k_factor<double><<<n16, kS * kS, 0, st>>>(t, w, K, lam);
-    else
-      k_factor<float><<<n16, kS * kS, 0, st>>>(t, w, K, lam);
+    else   // coefficients only: the FP32 basis kernel factors each subdomain
+      k_factor<float, false><<<n16, kS * kS, 0, st>>>(t, w, K, lam);
   }
   if (n32 > 0) {
     const int grid = (n32 + kFW - 1) / kFW;
@@ -968,7 +991,8 @@ cudaError_t launch_factor(const DeviceTables &t, const Workspace &w, int prec, c
 template <typename T, int NC>
 static cudaError_t basis16(const DeviceTables &t, const Workspace &w, const BasisItem *items, int n,
                            const double *q, double tol, int ir_max, cudaStream_t st) {
-  k_basis<T, NC><<<n, kS * kS, sizeof(BasisSmem<T, NC>), st>>>(t, w, items, q, tol, ir_max);
+  constexpr bool F = std::is_same<T, float>::value;   // FP32: the factor is fused in
+  k_basis<T, NC, F><<<n, kS * kS, sizeof(BasisSmem<T, NC>), st>>>(t, w, items, q, tol, ir_max);
   return cudaGetLastError();
 }
 template <typename T, int NC>
@@ -1012,10 +1036,14 @@ static cudaError_t smem_attr(K kern) {
 
 cudaError_t init_local_attributes() {
   cudaError_t e;
-  if ((e = smem_attr<decltype(&k_basis<float, 4>), BasisSmem<float, 4>>(k_basis<float, 4>)) ||
-      (e = smem_attr<decltype(&k_basis<float, 8>), BasisSmem<float, 8>>(k_basis<float, 8>)) ||
-      (e = smem_attr<decltype(&k_basis<float, 12>), BasisSmem<float, 12>>(k_basis<float, 12>)) ||
-      (e = smem_attr<decltype(&k_basis<float, 16>), BasisSmem<float, 16>>(k_basis<float, 16>)) ||
+  if ((e = smem_attr<decltype(&k_basis<float, 4, true>), BasisSmem<float, 4>>(
+               k_basis<float, 4, true>)) ||
+      (e = smem_attr<decltype(&k_basis<float, 8, true>), BasisSmem<float, 8>>(
+               k_basis<float, 8, true>)) ||
+      (e = smem_attr<decltype(&k_basis<float, 12, true>), BasisSmem<float, 12>>(
+               k_basis<float, 12, true>)) ||
+      (e = smem_attr<decltype(&k_basis<float, 16, true>), BasisSmem<float, 16>>(
+               k_basis<float, 16, true>)) ||
       (e = smem_attr<decltype(&k_basis<double, 4>), BasisSmem<double, 4>>(k_basis<double, 4>)) ||
       (e = smem_attr<decltype(&k_basis<double, 8>), BasisSmem<double, 8>>(k_basis<double, 8>)) ||
       (e = smem_attr<decltype(&k_basis<double, 12>), BasisSmem<double, 12>>(k_basis<double, 12>)) ||
