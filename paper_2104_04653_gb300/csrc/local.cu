@@ -657,19 +657,36 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
                *tNs = sm.coef + 3 * N, *ds = sm.coef + 4 * N, *ks = sm.coef + 5 * N;
   if (b < S - 1) sm.ec[tid] = static_cast<T>(-tNs[tid] * ds[tid] * ds[tid + S]);
   else sm.ec[tid] = T(0);
+  // right-hand sides of cell ``cell`` for every column (FP64), the zero
+  // iterate and the scaled residual z = D b
+  auto rhs_cell = [&](int cell) {
+    const double dc = ds[cell];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (c >= nc) continue;
+      const double val = rhs_value<S>(t, sb, sm.coef, q, sm.col[c], cell % S, cell / S);
+      sm.bb[c * N + cell] = val;
+      sm.x[c * N + cell] = 0.0;
+      sm.z[c * N + cell] = static_cast<T>(dc * val);
+    }
+  };
   if constexpr (FUSED) {
-    // the scaled couplings exactly as the factor kernel forms them, then
-    // the Schur-block chain of this subdomain in warp 0
+    // the scaled couplings exactly as the factor kernel forms them; then the
+    // Schur-block chain of this subdomain in warp 0 while the other warps
+    // set up the right-hand sides of all cells
     sm.offx[tid] = a < S - 1 ? static_cast<T>(-tEs[tid] * ds[tid] * ds[tid + 1]) : T(0);
     __syncthreads();
     if (tid < 32) {
       const bool bad = schur_inverses<T, S>(tid, sm.offx, sm.ec, sm.Ws);
       if (__any_sync(0xffffffffu, bad) && tid == 0) atomicOr(&w.status[0], MRCM_FLAG_NOTSPD);
+    } else {
+      for (int cell = tid - 32; cell < N; cell += N - 32) rhs_cell(cell);
     }
     __syncthreads();
+  } else {
+    rhs_cell(tid);
   }
 
-  // right-hand sides (FP64)
   const double myT[4] = {tWs[tid], tEs[tid], tSs[tid], tNs[tid]};
   const double dsl = ds[tid];
   const float dsf = static_cast<float>(dsl);
@@ -677,14 +694,8 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   float bnl[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    bnl[c] = 0.0f;
-    if (c >= nc) continue;
-    const double val = rhs_value<S>(t, sb, sm.coef, q, sm.col[c], a, b);
-    sm.bb[c * N + tid] = val;
-    sm.x[c * N + tid] = 0.0;
-    const T zv = static_cast<T>(dsl * val);
-    sm.z[c * N + tid] = zv;
-    bnl[c] = static_cast<float>(zv) * static_cast<float>(zv);
+    const float zv = c < nc ? static_cast<float>(sm.z[c * N + tid]) : 0.0f;
+    bnl[c] = zv * zv;
   }
   column_sums(sm, bnl, nc, sm.bnf);
 
