@@ -163,9 +163,10 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
  * (two-point fluxes: harmonic mean inside, T_R = kappa/(alpha H/h + 1/2) on
  * interface faces, 2 kappa on Dirichlet faces) and factors all of them in
  * one batched launch.  Re-callable with new lambda (re-factors).  With
- * MRCM_PREC_FP32_IR the FP32 factor of 16 x 16-cell subdomains is formed
- * inside mrcm_build_basis (each basis CTA factors its subdomain in shared
- * memory); this call then assembles the operators and their Jacobi scaling,
+ * MRCM_PREC_FP32_IR and at most two 16 x 16-cell subdomains per SM, their
+ * FP32 factor is formed inside mrcm_build_basis (each basis CTA factors its
+ * subdomain in shared memory); this call then assembles the operators and
+ * their Jacobi scaling,
  * which is all that is read from d_K and d_lambda, so the inputs may change
  * once it returns (stream-ordered) as before.  Eq. "mrc1", Eq. "beta". */
 mrcm_status mrcm_factor_local(mrcm_ctx *ctx, const double *d_K, const double *d_lambda);

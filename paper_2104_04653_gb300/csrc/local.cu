@@ -984,8 +984,10 @@ cudaError_t launch_factor(const DeviceTables &t, const Workspace &w, int prec, c
   if (n16 > 0) {
     if (prec == MRCM_PREC_FP64)
       k_factor<double><<<n16, kS * kS, 0, st>>>(t, w, K, lam);
-    else   // coefficients only: the FP32 basis kernel factors each subdomain
+    else if (t.fuse16)   // coefficients only: the basis kernel factors each subdomain
       k_factor<float, false><<<n16, kS * kS, 0, st>>>(t, w, K, lam);
+    else
+      k_factor<float, true><<<n16, kS * kS, 0, st>>>(t, w, K, lam);
   }
   if (n32 > 0) {
     const int grid = (n32 + kFW - 1) / kFW;
@@ -1002,8 +1004,10 @@ cudaError_t launch_factor(const DeviceTables &t, const Workspace &w, int prec, c
 template <typename T, int NC>
 static cudaError_t basis16(const DeviceTables &t, const Workspace &w, const BasisItem *items, int n,
                            const double *q, double tol, int ir_max, cudaStream_t st) {
-  constexpr bool F = std::is_same<T, float>::value;   // FP32: the factor is fused in
-  k_basis<T, NC, F><<<n, kS * kS, sizeof(BasisSmem<T, NC>), st>>>(t, w, items, q, tol, ir_max);
+  if (std::is_same<T, float>::value && t.fuse16)   // the factor is fused in
+    k_basis<T, NC, true><<<n, kS * kS, sizeof(BasisSmem<T, NC>), st>>>(t, w, items, q, tol, ir_max);
+  else
+    k_basis<T, NC, false><<<n, kS * kS, sizeof(BasisSmem<T, NC>), st>>>(t, w, items, q, tol, ir_max);
   return cudaGetLastError();
 }
 template <typename T, int NC>
@@ -1049,12 +1053,20 @@ cudaError_t init_local_attributes() {
   cudaError_t e;
   if ((e = smem_attr<decltype(&k_basis<float, 4, true>), BasisSmem<float, 4>>(
                k_basis<float, 4, true>)) ||
+      (e = smem_attr<decltype(&k_basis<float, 4, false>), BasisSmem<float, 4>>(
+               k_basis<float, 4, false>)) ||
       (e = smem_attr<decltype(&k_basis<float, 8, true>), BasisSmem<float, 8>>(
                k_basis<float, 8, true>)) ||
+      (e = smem_attr<decltype(&k_basis<float, 8, false>), BasisSmem<float, 8>>(
+               k_basis<float, 8, false>)) ||
       (e = smem_attr<decltype(&k_basis<float, 12, true>), BasisSmem<float, 12>>(
                k_basis<float, 12, true>)) ||
+      (e = smem_attr<decltype(&k_basis<float, 12, false>), BasisSmem<float, 12>>(
+               k_basis<float, 12, false>)) ||
       (e = smem_attr<decltype(&k_basis<float, 16, true>), BasisSmem<float, 16>>(
                k_basis<float, 16, true>)) ||
+      (e = smem_attr<decltype(&k_basis<float, 16, false>), BasisSmem<float, 16>>(
+               k_basis<float, 16, false>)) ||
       (e = smem_attr<decltype(&k_basis<double, 4>), BasisSmem<double, 4>>(k_basis<double, 4>)) ||
       (e = smem_attr<decltype(&k_basis<double, 8>), BasisSmem<double, 8>>(k_basis<double, 8>)) ||
       (e = smem_attr<decltype(&k_basis<double, 12>), BasisSmem<double, 12>>(k_basis<double, 12>)) ||

@@ -898,6 +898,16 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   t.inv_h = d.ny / d.ly;
   t.sub_by_size = reinterpret_cast<const int *>(base + o_sbs);
   t.nsub16 = c->nsub16;
+  {
+    // FP32, few 16 x 16 subdomains (at most two per SM): a separate factor
+    // launch would leave most SMs idle behind one pivot chain per subdomain,
+    // so each basis CTA factors its subdomain itself; with more subdomains
+    // the separate, throughput-bound factor is cheaper than the repeated
+    // chains (one per column chunk)
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->dev);
+    t.fuse16 = (c->prec == MRCM_PREC_FP32_IR && c->nsub16 > 0 && c->nsub16 <= 2 * nsm) ? 1 : 0;
+  }
   t.sub = reinterpret_cast<const SubInfo *>(base + o_sub);
   t.iface = reinterpret_cast<const IfaceInfo *>(base + o_if);
   t.col = reinterpret_cast<const ColInfo *>(base + o_col);

@@ -165,6 +165,7 @@ struct DeviceTables {
   const SubInfo *sub;
   const int *sub_by_size;   // subdomain ids: the s = 16 ones first, then s = 32
   int nsub16;               // how many of them have s = 16
+  int fuse16;               // FP32: factor the s = 16 subdomains inside the basis kernel
   const IfaceInfo *iface;
   const ColInfo *col;
   const RealInfo *real;
