@@ -374,10 +374,10 @@ def run_gpu(args):
 # DRAM traffic per launch from the committed ncu capture (profiles/
 # k_iface_cluster_channels-256x64.md), valid only while the kernel sources are
 # the ones that were profiled.
-TRAFFIC = {"k_iface_cluster": {"bytes": 1274112.0, "sha": "9f9e86a7b2ce2f92",
+TRAFFIC = {"k_iface_cluster": {"bytes": 1280512.0, "sha": "fc2fabef3c08027c",
                                "sources": ["csrc/iface_cluster.cu", "csrc/iface_common.cuh"]},
-           "k_basis": {"bytes": 2117376.0, "sha": "cfa4a40ee288e88e", "sources": ["csrc/local.cu"]},
-           "k_factor": {"bytes": 331008.0, "sha": "cfa4a40ee288e88e", "sources": ["csrc/local.cu"]}}
+           "k_basis": {"bytes": 1081856.0, "sha": "a5ce841f6842de58", "sources": ["csrc/local.cu"]},
+           "k_factor": {"bytes": 315648.0, "sha": "a5ce841f6842de58", "sources": ["csrc/local.cu"]}}
 
 
 def _traffic(kernel):
