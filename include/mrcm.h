@@ -155,7 +155,10 @@ typedef struct {
  * the launch shapes and allocate all workspace on the current device.  The
  * stream (a cudaStream_t, NULL = legacy default stream) is used by every
  * later call.  On success *out owns the context; on failure *out is NULL
- * and the return value says why.  Section 3 ("mrc1", "mrc2"). */
+ * and the return value says why.  Section 3 ("mrc1", "mrc2").
+ * With the environment variable MRCM_DEBUG_POISON=1 the floating-point part
+ * of the workspace is filled with NaN bytes at allocation (a check that no
+ * step reads a value that no earlier step wrote: results must not change). */
 mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out);
 
 /* Steps (a)+(b).  d_K, d_lambda: device [n_real][ny][nx] FP64, kappa =

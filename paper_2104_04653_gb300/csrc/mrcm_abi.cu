@@ -840,6 +840,37 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     return fail(nullptr, MRCM_ENOMEM, "cudaMalloc(%zu bytes): %s", A.off, cudaGetErrorString(e));
   }
   char *base = static_cast<char *>(c->arena);
+  // MRCM_DEBUG_POISON: fill the floating-point workspace with 0xFF bytes (NaN
+  // in FP32 and FP64) before anything is written.  Every value a step reads
+  // must come from an earlier step or from the setup, so results stay the same
+  // bit for bit; a read of an unwritten value turns up as a NaN.  "1" fills
+  // every buffer below; "0x<mask>" fills buffer i when bit i is set (to find
+  // the one at fault).  Integer tables are left alone.
+  if (const char *pv = getenv("MRCM_DEBUG_POISON"); pv && pv[0]) {
+    const uint64_t mask = (pv[0] == '0' && pv[1] == 'x') ? strtoull(pv, nullptr, 16)
+                          : pv[0] == '1'                 ? ~uint64_t(0)
+                                                         : 0;
+    const size_t cut[] = {o_coef, o_W,      o_basis,  o_G,      o_sB,   o_sA,    o_sC,
+                          o_sI,   o_X,      o_Y,      o_ds,     o_f,    o_x,     o_r,
+                          o_vec,  o_ps,     o_gt,     o_st,     o_gmGp, o_gmPbj, o_gmPid,
+                          o_gmPus, o_gmV,   o_gmW,    o_gmY,    o_gmpart, o_gmres, o_gmint,
+                          o_tcp,  o_tcm,    o_vec2,   o_iscr,   o_ijob};
+    // spans [cut[k], cut[k+1]) hold floating-point data except those that
+    // start at o_st, o_gmint and o_tcm (entries 17, 27 and 29); bit i names
+    // the i-th floating-point span: 0 coef .. 16 gt, 17 gmGp .. 25 gmres,
+    // 26 tcp, 27 vec2, 28 iscr
+    int bit = 0;
+    for (size_t k = 0; k + 1 < sizeof(cut) / sizeof(cut[0]); ++k) {
+      if (k == 17 || k == 27 || k == 29) continue;
+      const size_t a = cut[k], b = cut[k + 1];
+      if (((mask >> bit++) & 1) && b > a &&
+          (e = cudaMemset(base + a, 0xFF, b - a)) != cudaSuccess) {
+        cudaFree(c->arena);
+        delete c;
+        return cuda_fail(nullptr, e, "mrcm_setup poison fill");
+      }
+    }
+  }
   auto up = [&](size_t off, const void *src, size_t bytes) {
     if (!bytes) return cudaSuccess;
     return cudaMemcpy(base + off, src, bytes, cudaMemcpyHostToDevice);
@@ -880,7 +911,12 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
       (G && (e = up(o_nblist, c->nb_list.data(), c->nb_list.size() * sizeof(int))) !=
                 cudaSuccess) ||
       (e = cudaMemset(base + o_st, 0, 4 * sizeof(int))) != cudaSuccess ||
-      (e = cudaMemset(base + o_dst, 0, (2 + 2 * d.n_real) * sizeof(double))) != cudaSuccess) {
+      (e = cudaMemset(base + o_dst, 0, (2 + 2 * d.n_real) * sizeof(double))) != cudaSuccess ||
+      // slab vectors: positions past a slab's own width pad it to the widest
+      // slab of its realisation; no kernel writes them and the block solves
+      // multiply them by the zero padding of the slab blocks, so they start
+      // (and stay) zero
+      (e = cudaMemset(base + o_vec, 0, (c->npos ? c->npos : 1) * esz)) != cudaSuccess) {
     cudaFree(c->arena);
     delete c;
     return cuda_fail(nullptr, e, "mrcm_setup upload");

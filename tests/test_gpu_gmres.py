@@ -162,6 +162,12 @@ def test_stalled_user_blocks_fall_back_to_block_jacobi():
     flat = _blocks_flat(M, blocks, lambda b: np.eye(b.shape[0]))
     got = _check(prob, _opts(1, precond=mrcm.PRECOND_USER), ref=ref, blocks=flat)
     assert got["info"]["flags"] & mrcm.FLAG_PRECOND_FALLBACK
+    # the rerun is a fresh block-Jacobi solve: same fields, bit for bit, and
+    # the reported count adds the stalled steps to block-Jacobi's
+    bj = _run(prob, _opts(1))
+    for k in ("p", "ux", "uy"):
+        assert np.array_equal(got[k], bj[k]), k
+    assert bj["info"]["gmres_iters"] + 10 < got["info"]["gmres_iters"]
 
 
 def test_user_precond_requires_blocks():
@@ -207,3 +213,18 @@ def test_gmres_graph_replay_matches_eager():
     for x, y in zip(eager, out):
         assert torch.equal(x, y)
     s.close()
+
+
+def test_gmres_is_deterministic_on_a_long_solve():
+    """Block-Jacobi GMRES on a 512 x 512 channel system (contrast 1e6,
+    32 x 32-cell subdomains, several hundred steps to 1e-8) run in two
+    contexts: the same step count and bit-identical fields (every sum is
+    taken in a fixed order; no floating-point atomics)."""
+    _, _, mrcm, W = _mods()
+    prob = W.config4(n=512, s=32, n_ch=16, seed=4001)
+    opts = _opts(1, gmres_tol=1e-8, gmres_max=8000)
+    a, b = _run(prob, opts), _run(prob, opts)
+    assert a["info"]["gmres_iters"] > 100
+    assert a["info"]["gmres_iters"] == b["info"]["gmres_iters"]
+    for k in ("p", "ux", "uy"):
+        assert np.array_equal(a[k], b[k]), k

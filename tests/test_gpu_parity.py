@@ -279,3 +279,33 @@ def test_interface_paths_agree(path, monkeypatch):
     else:
         monkeypatch.delenv("MRCM_NO_CLUSTER", raising=False)
     _check(W.config2(), 1)
+
+
+@pytest.mark.parametrize("case", ["direct-fp64", "direct-mixed", "mixed-sizes", "wide-slabs",
+                                  "gmres"])
+def test_workspace_poisoned_with_nan_gives_identical_results(case, monkeypatch):
+    """With the floating-point workspace filled with NaN bytes at setup
+    (MRCM_DEBUG_POISON=1) every path returns the same fields, bit for bit,
+    as with an untouched workspace: no step reads a value that no earlier
+    step wrote."""
+    import torch
+    O, mrcm, W = _mods()
+    prob, opts = {
+        "direct-fp64": (W.config2(), mrcm.SolverOptions(prec=0)),
+        "direct-mixed": (W.config2(), mrcm.SolverOptions(prec=1)),
+        "mixed-sizes": (W.config3(n_real=2, n=128), mrcm.SolverOptions(prec=1)),
+        "wide-slabs": (W.config5(2, n=256), mrcm.SolverOptions(prec=1)),
+        "gmres": (W.config4(n=256, s=32, n_ch=8),
+                  mrcm.SolverOptions(prec=1, iface_solver=mrcm.IFACE_GMRES, gmres_tol=1e-8)),
+    }[case]
+    Kd, Ld, Qd = mrcm.device_inputs(prob)
+    out = []
+    for poison in ("0", "1"):
+        monkeypatch.setenv("MRCM_DEBUG_POISON", poison)
+        s = mrcm.Mrcm(prob, opts)
+        out.append(([t.clone() for t in s.solve(Kd, Ld, Qd)], s.mrcm_get_info()))
+        s.close()
+    (a, ia), (b, ib) = out
+    assert ia == ib
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
