@@ -31,10 +31,17 @@ one subdomain of g's two subdomains (Chebyshev distance), and theta = 1/2.
 The clip keeps the rare near-singular blocks of high-contrast media (2% of
 the targets above 5 in size, some above 100) from dominating the loss.
 
+``neighbourhood_rows`` gives the whole row block of that restricted inverse
+instead of its diagonal block: P[g, N(g)] = ((M_N(g))^{-1})[g, :], the rows of
+a restricted additive Schwarz preconditioner (Cai and Sarkis, SIAM J. Sci.
+Comput. 21, 1999) with one subdomain of overlap.  It is the candidate target
+of a network that also proposes the couplings to neighbouring interfaces.
+
 Pinned by ``tests/test_oracle_cnn.py``: central finite differences of the
 loss against the analytic gradient, the convolution against a direct
-sum, zero head = block-Jacobi, and the target against a brute-force
-restriction of the dense interface matrix.
+sum, zero head = block-Jacobi, the target against a brute-force
+restriction of the dense interface matrix, and the neighbourhood rows
+against the full inverse and against the target.
 """
 from __future__ import annotations
 
@@ -190,3 +197,18 @@ def targets(M, lay, theta=THETA, clip=CLIP):
         Bg = np.linalg.inv(M[np.ix_(idx, idx)])[pos:pos + m, pos:pos + m]
         out.append(np.clip(theta * (M[off:off + m, off:off + m] @ Bg - np.eye(m)), -clip, clip))
     return np.array(out)
+
+
+def neighbourhood_rows(M, lay):
+    """Dense P with P[g, N(g)] = ((M_N(g))^{-1})[g, :] for every interface g,
+    N(g) the unknowns of g's neighbourhood (``neighbourhood``), zero
+    elsewhere (see the module text)."""
+    P = np.zeros_like(M)
+    for g, f in enumerate(lay.ifaces):
+        idx = np.concatenate([np.arange(lay.ifaces[h]["off"],
+                                        lay.ifaces[h]["off"] + lay.ifaces[h]["nU"] +
+                                        lay.ifaces[h]["nP"]) for h in neighbourhood(lay, g)])
+        off, m = f["off"], f["nU"] + f["nP"]
+        pos = int(np.searchsorted(idx, off))
+        P[off:off + m, idx] = np.linalg.inv(M[np.ix_(idx, idx)])[pos:pos + m, :]
+    return P

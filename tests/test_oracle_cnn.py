@@ -166,3 +166,54 @@ def test_targets_reduce_gmres_steps_and_their_negation_does_not(seed):
     assert bj is not None and learned_exact is not None
     assert learned_exact < 0.92 * bj, (learned_exact, bj)
     assert negated is None
+
+
+def test_neighbourhood_rows_are_the_inverse_on_a_whole_domain_neighbourhood():
+    # 2 x 2 subdomains: every neighbourhood is the whole interface set, so
+    # the rows are those of M^{-1} (M is not symmetric: a transposed block
+    # would fail) and GMRES converges in one step
+    from oracle import gmres as G
+    prob, M, lay = _system(n=32, s=16)
+    assert not np.allclose(M, M.T)
+    P = C.neighbourhood_rows(M, lay)
+    np.testing.assert_allclose(P, np.linalg.inv(M), atol=1e-9 * np.abs(np.linalg.inv(M)).max())
+    b = np.random.default_rng(0).standard_normal(M.shape[0])
+    _, info = G.gmres(M, b, P=P, tol=1e-10, maxiter=50)
+    assert info["converged"] and info["iters"] == 1
+
+
+def test_neighbourhood_rows_diagonal_block_is_the_target():
+    # the (g, g) block of the rows is the B_g of the training target:
+    # M_gg B_g - I = target with theta = 1 and no clip
+    prob, M, lay = _system(n=64, s=16)
+    P = C.neighbourhood_rows(M, lay)
+    T = C.targets(M, lay, theta=1.0, clip=np.inf)
+    for g, f in enumerate(lay.ifaces):
+        off, m = f["off"], f["nU"] + f["nP"]
+        sl = slice(off, off + m)
+        np.testing.assert_allclose(M[sl, sl] @ P[sl, sl] - np.eye(m), T[g], atol=1e-9)
+    # and every row block reaches no further than the neighbourhood
+    for g, f in enumerate(lay.ifaces):
+        off, m = f["off"], f["nU"] + f["nP"]
+        cols = np.flatnonzero(np.abs(P[off:off + m]).sum(axis=0))
+        allowed = np.concatenate([np.arange(lay.ifaces[h]["off"], lay.ifaces[h]["off"] +
+                                            lay.ifaces[h]["nU"] + lay.ifaces[h]["nP"])
+                                  for h in C.neighbourhood(lay, g)])
+        assert set(cols) <= set(allowed)
+
+
+def test_neighbourhood_rows_cut_gmres_steps_on_channels():
+    """On the 128 x 128 channel system (contrast 1e6, seed 4000) the
+    neighbourhood rows need under a third of block-Jacobi's GMRES steps to
+    1e-8 (measured: 25 against 163); the diagonal block alone saves little
+    (136)."""
+    from oracle import gmres as G, mrcm_oracle as O
+    from paper_2104_04653_gb300 import workloads as W
+    prob = W.config4(n=128, s=16, n_ch=4, seed=4000)
+    S = O.mrcm_solve(prob, return_system=True)["systems"][0]
+    M, rhs, lay = S["M"], S["rhs"], S["layout"]
+    _, bj = G.gmres(M, rhs, P=G.block_jacobi(M, G.diagonal_blocks(lay.ifaces)), tol=1e-8,
+                    maxiter=3000)
+    _, ras = G.gmres(M, rhs, P=C.neighbourhood_rows(M, lay), tol=1e-8, maxiter=3000)
+    assert bj["converged"] and ras["converged"]
+    assert ras["iters"] < bj["iters"] / 3, (ras["iters"], bj["iters"])
