@@ -36,6 +36,24 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest x over the ranks of the default process group (x itself
+    on one rank).  Every rank must call it at the same point."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_value(units_per_rank_step: float, steps: int, ws: int, t_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed (each rank owns
+    its own problems, weak scaling) over the slowest rank's time."""
+    return units_per_rank_step * steps * ws / t_max
+
+
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -293,14 +311,10 @@ def run_gpu(args):
     t_fp64 = _time_graph(results["fp64"]["graph"], max(args.steps // 4, 3), flush, torch)
     if ws > 1:
         torch.distributed.barrier()
-    tot = sum(t_mixed)
-    if ws > 1:
-        tt = torch.tensor([tot], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        tot = float(tt.item())
-    value = cells * args.steps * ws / tot
+    tot = _max_over_ranks(sum(t_mixed), ws, "cuda")
+    value = _job_value(cells, args.steps, ws, tot)
     ms = 1e3 * tot / args.steps
-    fp64_ms = 1e3 * statistics.mean(t_fp64)
+    fp64_ms = 1e3 * _max_over_ranks(statistics.mean(t_fp64), ws, "cuda")
     # per-call breakdown (eager) and the dominant kernel's roofline
     s = results["fp32_ir"]["solver"]
     calls = _time_calls(s, K, L, Q, results["fp32_ir"]["out"], 30, flush, torch)
@@ -333,7 +347,7 @@ def run_gpu(args):
         b.record(st)
         evs.append((a, b))
     torch.cuda.synchronize()
-    e2e_t = statistics.mean(a.elapsed_time(b) * 1e-3 for a, b in evs)
+    e2e_t = _max_over_ranks(statistics.mean(a.elapsed_time(b) * 1e-3 for a, b in evs), ws, "cuda")
     h2d = hin.numel() * hin.element_size()
     d2h = hout.numel() * hout.element_size()
     if rank != 0:
