@@ -150,6 +150,49 @@ def cpu_baseline(seconds: float = 12.0, max_solves: int = 50):
                       f"numpy/scipy FP64, 1 thread"}
 
 
+def _host_cores() -> int:
+    """Cores this process may run on: the CPU affinity set, capped by a
+    cgroup (v2) CPU quota when one is set."""
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    try:
+        quota, period = open("/sys/fs/cgroup/cpu.max").read().split()[:2]
+        if quota != "max":
+            n = min(n, max(1, int(int(quota) // int(period))))
+    except (OSError, ValueError):
+        pass
+    return max(1, n)
+
+
+def cpu_baseline_all_cores(seconds: float = 12.0, max_solves: int = 50):
+    """The same single-threaded oracle run as one process per host core,
+    all at once (each solves the whole workload; the realisations of a job
+    are independent, so this is the host's job throughput)."""
+    n = _host_cores()
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench._oracle_worker(%f, %d)))" % (str(ROOT), seconds, max_solves))
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=env, cwd=str(ROOT))
+             for _ in range(n)]
+    total, solves = 0.0, 0
+    for p in procs:
+        try:
+            out, err = p.communicate(timeout=600)
+        except subprocess.TimeoutExpired:
+            p.kill()
+            out, err = p.communicate()
+        if p.returncode != 0:
+            return {"value": None, "unit": "cells/s", "cores": n, "kind": "oracle",
+                    "sample": "failed: " + (err.strip().splitlines() or [""])[-1][:200]}
+        d = json.loads(out.strip().splitlines()[-1])
+        total += d["cells"] / statistics.median(d["times"])     # as cpu_baseline
+        solves += len(d["times"])
+    return {"value": total, "unit": "cells/s", "cores": n, "kind": "oracle",
+            "sample": f"{n} concurrent single-threaded processes, {solves} full solves of the "
+                      f"workload in all"}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -382,6 +425,7 @@ def run_gpu(args):
     }
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores()
     print(json.dumps(line), flush=True)
 
 
