@@ -101,8 +101,13 @@ class Layout:
             f["nU"], f["nP"] = int(nU[g]), int(nP[g])
             f["off"] = off
             off += f["nU"] + f["nP"]
-            f["phi"] = interface_functions(f["nU"], s, prob.basis)
-            f["psi"] = interface_functions(f["nP"], s, prob.basis)
+            if getattr(prob, "iface_fn", None) is None:
+                f["phi"] = interface_functions(f["nU"], s, prob.basis)
+                f["psi"] = interface_functions(f["nP"], s, prob.basis)
+            else:                                     # per-interface tables
+                phi, psi = prob.iface_fn[r][g]
+                f["phi"] = np.asarray(phi, np.float64).reshape(f["nU"], s)
+                f["psi"] = np.asarray(psi, np.float64).reshape(f["nP"], s)
             if prob.alpha is None:
                 f["alpha"] = np.ones(s)
             else:

@@ -184,6 +184,9 @@ class Mrcm:
         d.bc_type = bct.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
         d.bc_val = bcv.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         d.pure_neumann = 1 if prob.pure_neumann else 0
+        if getattr(prob, "iface_fn", None) is not None:
+            raise NotImplementedError("per-interface function tables (physics-based interface "
+                                      "spaces) are not supported by the library")
         d.basis_family = BASIS_LEGENDRE if prob.basis == "legendre" else BASIS_MONOMIAL
         d.prec = opts.prec
         d.ir_tol, d.ir_max = opts.ir_tol, opts.ir_max

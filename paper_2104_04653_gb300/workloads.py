@@ -63,6 +63,9 @@ class Problem:
     iface_nU: List[np.ndarray]        # per realisation, canonical order
     iface_nP: List[np.ndarray]
     alpha: Optional[List[np.ndarray]] = None   # per realisation, [n_iface, s]
+    # per realisation, per interface: (flux functions [nU, s], pressure
+    # functions [nP, s]) at face midpoints; None: the family given by ``basis``
+    iface_fn: Optional[list] = None
     pure_neumann: bool = False
     basis: str = "legendre"           # interface function family
     name: str = ""
