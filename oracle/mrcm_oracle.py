@@ -61,6 +61,20 @@ def robin_T(kc, alpha, H, h):
     return kc / (alpha * H / h + 0.5)
 
 
+def gravity_face(kl, kr, wl, wr):
+    """Gravity part of the two-point flux across a face normal to +y (Eq.
+    "Darcy_wg" with the height along +y), from the two half-cell fluxes
+    2 kappa (p_c - p_f)/h + w_c and continuity of the flux at the face:
+    (kappa_l w_r + kappa_r w_l) / (kappa_l + kappa_r); w = K lambda_g g."""
+    return (kl * wr + kr * wl) / (kl + kr)
+
+
+def grav_field(prob, r):
+    """The gravity velocity K lambda_g g of realisation r, or None."""
+    gv = getattr(prob, "grav", None)
+    return None if gv is None else np.asarray(gv[r], np.float64)
+
+
 def interface_functions(n_fn, s, family="legendre"):
     """[n_fn, s] values of the interface functions at face midpoints."""
     t = -1.0 + (2.0 * np.arange(s) + 1.0) / s
@@ -147,12 +161,23 @@ class Local:
         A = np.zeros((n, n))
         b0 = np.zeros(n)
         # Robin transmissibility and beta on each interface edge face
-        self.TR, self.beta = {}, {}
+        self.TR, self.beta, self.wR = {}, {}, {}
+        wfull = grav_field(prob, r)
+        wl = None if wfull is None else wfull[J * s:(J + 1) * s, I * s:(I + 1) * s]
+        ny_of = {"W": 0.0, "E": 0.0, "S": -1.0, "N": 1.0}     # outward normal, y part
         for side, (g, sigma) in self.edges.items():
             f = lay.ifaces[g]
             kc = np.array([self.kap[edge_face_cell(side, e, s)[::-1]] for e in range(s)])
             self.TR[side] = robin_T(kc, f["alpha"], lay.H, h)
             self.beta[side] = f["alpha"] * lay.H / kc
+            # gravity part of the outward Robin-face velocity: eliminating p_f
+            # between u = 2 kappa (p_c - p_f)/h + n_y w_c and -beta u + p_f = g
+            # leaves n_y w_c T_R / (2 kappa_c)
+            if wl is None or ny_of[side] == 0.0:
+                self.wR[side] = np.zeros(s)
+            else:
+                wc = np.array([wl[edge_face_cell(side, e, s)[::-1]] for e in range(s)])
+                self.wR[side] = ny_of[side] * wc * self.TR[side] / (2.0 * kc)
         for b in range(s):
             for a in range(s):
                 c = b * s + a
@@ -165,15 +190,21 @@ class Local:
                         T = harmonic_T(kc, self.kap[bb, aa])
                         A[c, c] += T
                         A[c, bb * s + aa] -= T
+                        if wl is not None and db != 0:        # known gravity outflow
+                            b0[c] -= h * db * gravity_face(kc, self.kap[bb, aa], wl[b, a],
+                                                           wl[bb, aa])
                     elif side in self.edges:                  # Robin face on Gamma
                         e = b if side in ("W", "E") else a
                         A[c, c] += self.TR[side][e]
+                        b0[c] -= h * self.wR[side][e]
                     else:                                     # physical boundary
                         k = boundary_face(prob, side, gi, gj)
                         if prob.bc_type[k] == DIRICHLET:
                             T = 2.0 * kc
                             A[c, c] += T
                             b0[c] += T * prob.bc_val[k]
+                            if wl is not None:
+                                b0[c] -= h * ny_of[side] * wl[b, a]
                         else:
                             b0[c] -= prob.bc_val[k] * h
         self.A, self.b0 = A, b0
@@ -273,6 +304,8 @@ def mrcm_solve(prob, refine=False, return_system=False):
             pc = np.array([X[edge_face_cell(side, e, s)[1] * s + edge_face_cell(side, e, s)[0],
                              col_index] for e in range(s)])
             u = lo.TR[side] * (pc - gdata) / h           # outward normal velocity
+            if col_index == 0:                           # the known gravity part
+                u = u + lo.wR[side]
             pf = gdata + lo.beta[side] * u               # face pressure
             return u, pf
 
@@ -325,7 +358,7 @@ def mrcm_solve(prob, refine=False, return_system=False):
                 g = robin_data(f, sigma, lo.beta[side], x)
                 pc = np.array([pl[edge_face_cell(side, e, s)[1] * s + edge_face_cell(side, e, s)[0]]
                                for e in range(s)])
-                gamma_u[g_if, 0 if sigma > 0 else 1] = lo.TR[side] * (pc - g) / h
+                gamma_u[g_if, 0 if sigma > 0 else 1] = lo.TR[side] * (pc - g) / h + lo.wR[side]
         ux, uy = fluxes_from_pressure(prob, r, p, lay, gamma_u)
         if prob.pure_neumann:
             p = p - p.mean()
@@ -354,6 +387,7 @@ def fluxes_from_pressure(prob, r, p, lay, gamma_u):
     faces, and boundary data / Dirichlet fluxes on physical faces."""
     ny, nx, h, s = prob.ny, prob.nx, prob.h, lay.s
     kap = prob.lam[r] * prob.K[r]
+    w = grav_field(prob, r)
     ux = np.zeros((ny, nx + 1))
     uy = np.zeros((ny + 1, nx))
     for j in range(ny):
@@ -377,6 +411,8 @@ def fluxes_from_pressure(prob, r, p, lay, gamma_u):
             else:
                 T = harmonic_T(kap[j - 1, i], kap[j, i])
                 uy[j, i] = T * (p[j - 1, i] - p[j, i]) / h
+                if w is not None:
+                    uy[j, i] += gravity_face(kap[j - 1, i], kap[j, i], w[j - 1, i], w[j, i])
     for j in range(ny):
         for side, i, sign in (("W", 0, -1.0), ("E", nx - 1, 1.0)):
             k = boundary_face(prob, side, i, j)
@@ -388,6 +424,8 @@ def fluxes_from_pressure(prob, r, p, lay, gamma_u):
             k = boundary_face(prob, side, i, j)
             un = (2.0 * kap[j, i] * (p[j, i] - prob.bc_val[k]) / h
                   if prob.bc_type[k] == DIRICHLET else prob.bc_val[k])
+            if w is not None and prob.bc_type[k] == DIRICHLET:
+                un += sign * w[j, i]                  # outward part of the gravity velocity
             uy[0 if side == "S" else ny, i] = sign * un
     return ux, uy
 
@@ -403,6 +441,7 @@ def fine_solve(prob):
     N = nx * ny
     for r in range(R):
         kap = prob.lam[r] * prob.K[r]
+        w = grav_field(prob, r)
         rows, cols, vals = [], [], []
         b = (prob.q[r] * h * h).reshape(-1).copy()
         for j in range(ny):
@@ -415,6 +454,9 @@ def fine_solve(prob):
                         rows += [c, c]
                         cols += [c, jj * nx + ii]
                         vals += [T, -T]
+                        if w is not None and dj != 0:     # known gravity outflow
+                            b[c] -= h * dj * gravity_face(kap[j, i], kap[jj, ii], w[j, i],
+                                                          w[jj, ii])
                     else:
                         k = boundary_face(prob, side, i, j)
                         if prob.bc_type[k] == DIRICHLET:
@@ -422,6 +464,8 @@ def fine_solve(prob):
                             cols.append(c)
                             vals.append(2.0 * kap[j, i])
                             b[c] += 2.0 * kap[j, i] * prob.bc_val[k]
+                            if w is not None:
+                                b[c] -= h * dj * w[j, i]
                         else:
                             b[c] -= prob.bc_val[k] * h
         A = sp.csr_matrix((vals, (rows, cols)), shape=(N, N))
@@ -436,6 +480,8 @@ def fine_solve(prob):
         uy = np.zeros((ny + 1, nx))
         ux[:, 1:nx] = harmonic_T(kap[:, :-1], kap[:, 1:]) * (p[:, :-1] - p[:, 1:]) / h
         uy[1:ny, :] = harmonic_T(kap[:-1, :], kap[1:, :]) * (p[:-1, :] - p[1:, :]) / h
+        if w is not None:
+            uy[1:ny, :] += gravity_face(kap[:-1, :], kap[1:, :], w[:-1, :], w[1:, :])
         for j in range(ny):
             for side, i, sign in (("W", 0, -1.0), ("E", nx - 1, 1.0)):
                 k = boundary_face(prob, side, i, j)
@@ -447,6 +493,8 @@ def fine_solve(prob):
                 k = boundary_face(prob, side, i, j)
                 un = (2.0 * kap[j, i] * (p[j, i] - prob.bc_val[k]) / h
                       if prob.bc_type[k] == DIRICHLET else prob.bc_val[k])
+                if w is not None and prob.bc_type[k] == DIRICHLET:
+                    un += sign * w[j, i]
                 uy[0 if side == "S" else ny, i] = sign * un
         if prob.pure_neumann:
             p = p - p.mean()
@@ -470,6 +518,7 @@ def monolithic_solve(prob, r=0):
     lay = Layout(prob, r)
     s, h = lay.s, prob.h
     kap = prob.lam[r] * prob.K[r]
+    w = grav_field(prob, r)
     ny, nx = prob.ny, prob.nx
     nc = nx * ny
     faces = []                                # (iface, side index, e, cell (i, j))
@@ -504,6 +553,11 @@ def monolithic_solve(prob, r=0):
                         T = 2.0 * kap[j, i] * kap[jj, ii] / (kap[j, i] + kap[jj, ii])
                         A[row, c] += T
                         A[row, jj * nx + ii] -= T
+                        if w is not None and dj != 0:
+                            # the face pressure eliminated between the two
+                            # half-cell fluxes, gravity included
+                            b[row] -= h * dj * (kap[j, i] * w[jj, ii] + kap[jj, ii] * w[j, i]) / (
+                                kap[j, i] + kap[jj, ii])
                     else:                    # interface face: flux h*u of this side
                         if side in ("E", "W"):
                             g = (j // s) * (lay.Sx - 1) + min(i, ii) // s
@@ -518,6 +572,8 @@ def monolithic_solve(prob, r=0):
                     if prob.bc_type[k] == DIRICHLET:
                         A[row, c] += 2.0 * kap[j, i]
                         b[row] += 2.0 * kap[j, i] * prob.bc_val[k]
+                        if w is not None:
+                            b[row] -= h * dj * w[j, i]
                     else:
                         b[row] -= prob.bc_val[k] * h
             row += 1
@@ -528,6 +584,8 @@ def monolithic_solve(prob, r=0):
         A[row, o_u + k] = 1.0
         A[row, j * nx + i] -= 2.0 * kc / h
         A[row, o_pf + k] += 2.0 * kc / h
+        if w is not None and f["kind"] == "H":       # u = 2 kappa (p_c - p_f)/h + n_y w_c
+            b[row] = (1.0 if sd == 0 else -1.0) * w[j, i]
         row += 1
         beta = f["alpha"][e] * lay.H / kc
         sigma = 1.0 if sd == 0 else -1.0

@@ -187,6 +187,8 @@ class Mrcm:
         if getattr(prob, "iface_fn", None) is not None:
             raise NotImplementedError("per-interface function tables (physics-based interface "
                                       "spaces) are not supported by the library")
+        if getattr(prob, "grav", None) is not None:
+            raise NotImplementedError("the gravity term is not supported by the library")
         d.basis_family = BASIS_LEGENDRE if prob.basis == "legendre" else BASIS_MONOMIAL
         d.prec = opts.prec
         d.ir_tol, d.ir_max = opts.ir_tol, opts.ir_max

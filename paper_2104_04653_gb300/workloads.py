@@ -66,6 +66,9 @@ class Problem:
     # per realisation, per interface: (flux functions [nU, s], pressure
     # functions [nP, s]) at face midpoints; None: the family given by ``basis``
     iface_fn: Optional[list] = None
+    # per realisation [ny, nx]: the gravity velocity K lambda_g g of Eq.
+    # "Darcy_wg" (along +y, the direction of the height h); None: no gravity
+    grav: Optional[list] = None
     pure_neumann: bool = False
     basis: str = "legendre"           # interface function family
     name: str = ""
