@@ -139,6 +139,12 @@ typedef struct {
   int32_t gmres_max;         /* max GMRES steps in total (0: 5000)            */
   double  gmres_tol;         /* stop at ||f - M x|| <= tol ||f||, the TRUE    */
                              /* residual (0: iface_tol)                       */
+  const double *iface_fn;    /* NULL: the functions of basis_family.  Else    */
+                             /* per interface (realisations concatenated,     */
+                             /* canonical order): nU flux then nP pressure    */
+                             /* functions, s face-midpoint values each, along */
+                             /* +y (vertical) or +x (horizontal interfaces);  */
+                             /* e.g. the physics-based spaces of Section 3    */
 } mrcm_desc;
 
 typedef struct {

@@ -33,10 +33,10 @@ constexpr int kS = 16;      // subdomain edge of the shared-memory-resident kern
 constexpr int kCoefStride = 6 * kS * kS + 4 * kS;
 static_assert(kCoefStride % 2 == 0, "coefficient blocks are staged as 16-byte vectors");
 
-// interface-function table of subdomain size S (RealInfo::fn_off)
+// interface-function rows of subdomain size S (IfaceInfo::fnU / fnP index them)
 template <int S>
 __device__ __forceinline__ const double *fn_table(const DeviceTables &t) {
-  return t.fnval + (S == 16 ? 0 : 16 * 16);
+  return t.fnval + (S == 16 ? 0 : t.fn_off32);
 }
 
 __device__ __forceinline__ void atomic_max_pos_double(double *addr, double v) {
@@ -504,10 +504,11 @@ __device__ __forceinline__ void traces_and_rows(const DeviceTables &t, const Wor
                          row < sb.edge_row[side] + t.iface[sb.edge_iface[side]].nU +
                                    t.iface[sb.edge_iface[side]].nP))
       ++side;
-    const int nU = t.iface[sb.edge_iface[side]].nU;
+    const IfaceInfo &fr = t.iface[sb.edge_iface[side]];
+    const int nU = fr.nU;
     const int k = row - sb.edge_row[side];
     const bool urow = k < nU;
-    const double *fn = fnt + (urow ? k : k - nU) * S;
+    const double *fn = fnt + (urow ? fr.fnU + k : fr.fnP + k - nU) * S;
     double acc = 0.0;
     if (urow) {
       for (int e = 0; e < S; ++e) acc += fn[e] * sp[side][e][c];

@@ -81,6 +81,8 @@ struct mrcm_ctx {
   // learned preconditioner: interface neighbourhoods of the training target
   std::vector<int> nb_off, nb_list;
   int nb_max = 0, nloc_max = 0, m_uniform = 0, s_uniform = 0;
+  // caller's interface functions (mrcm_desc::iface_fn): rows per size
+  int fn_rows16 = 0, fn_rows32 = 0;
   int *d_nb_off = nullptr, *d_nb_list = nullptr;
 };
 
@@ -162,6 +164,21 @@ static mrcm_status validate(const mrcm_desc *d) {
       return fail(nullptr, MRCM_EINVAL, "grid %dx%d not divisible by subdomain size %d", d->nx,
                   d->ny, s);
   }
+  if (d->iface_fn) {             // every value of the caller's interface functions
+    int64_t src = 0, ifc = 0;
+    for (int r = 0; r < d->n_real; ++r) {
+      const int s = d->sub_size[r], sx = d->nx / s, sy = d->ny / s;
+      const int64_t nif = static_cast<int64_t>(sx - 1) * sy + static_cast<int64_t>(sx) * (sy - 1);
+      for (int64_t g = 0; g < nif; ++g, ++ifc) {
+        const int n = std::max(0, d->iface_nU[ifc]) + std::max(0, d->iface_nP[ifc]);
+        for (int64_t k = 0; k < static_cast<int64_t>(n) * s; ++k)
+          if (!std::isfinite(d->iface_fn[src + k]))
+            return fail(nullptr, MRCM_EINVAL, "iface_fn: non-finite value at %lld",
+                        static_cast<long long>(src + k));
+        src += static_cast<int64_t>(n) * s;
+      }
+    }
+  }
   const int nb = 2 * d->nx + 2 * d->ny;
   for (int k = 0; k < nb; ++k) {
     if (d->bc_type[k] != 0 && d->bc_type[k] != 1)
@@ -191,7 +208,6 @@ static mrcm_status build_tables(mrcm_ctx *c) {
     c->smax = std::max(c->smax, S);
     RealInfo ri{};
     ri.s = S;
-    ri.fn_off = S == 16 ? 0 : 16 * 16;
     ri.Sx = d.nx / S;
     ri.Sy = d.ny / S;
     ri.sub0 = nsub_tot;
@@ -238,6 +254,14 @@ static mrcm_status build_tables(mrcm_ctx *c) {
       gam_off += 2 * S;
       fi.tsc_off = tsc_off;
       tsc_off += static_cast<int64_t>(fi.nU + fi.nP) * (fi.nU + fi.nP);
+      if (d.iface_fn) {          // own rows: phi_0 .. then psi_0 .. in the size-S section
+        int &rows = S == 16 ? c->fn_rows16 : c->fn_rows32;
+        fi.fnU = rows;
+        fi.fnP = rows + fi.nU;
+        rows += fi.nU + fi.nP;
+      } else {                   // the family's rows: phi_k = psi_k = row k
+        fi.fnU = fi.fnP = 0;
+      }
       c->iface.push_back(fi);
     }
     ri.nunk = unk_tot - ri.unk0;
@@ -272,8 +296,10 @@ static mrcm_status build_tables(mrcm_ctx *c) {
           sb.edge_row[e] = nrow;
           if (sb.edge_iface[e] < 0) continue;
           const IfaceInfo &fi = c->iface[sb.edge_iface[e]];
-          for (int k = 0; k < fi.nU; ++k) c->col.push_back(ColInfo{fi.unk + k, e, k, 1});
-          for (int k = 0; k < fi.nP; ++k) c->col.push_back(ColInfo{fi.unk + fi.nU + k, e, k, 0});
+          for (int k = 0; k < fi.nU; ++k)
+            c->col.push_back(ColInfo{fi.unk + k, e, fi.fnU + k, 1});
+          for (int k = 0; k < fi.nP; ++k)
+            c->col.push_back(ColInfo{fi.unk + fi.nU + k, e, fi.fnP + k, 0});
           ncol += fi.nU + fi.nP;
           nrow += fi.nU + fi.nP;
         }
@@ -741,9 +767,25 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   const int nb = 2 * d.nx + 2 * d.ny;
   // interface-function tables for s = 16 (offset 0) and s = 32 (offset 256)
   std::vector<double> fnv, fn32;
-  fn_table(d.basis_family, 16, fnv);
-  fn_table(d.basis_family, 32, fn32);
+  int64_t fn_off32 = 16 * 16;
+  if (d.iface_fn) {
+    // caller's rows, copied in the order the interfaces took them
+    fnv.assign(static_cast<size_t>(c->fn_rows16) * 16, 0.0);
+    fn32.assign(static_cast<size_t>(c->fn_rows32) * 32, 0.0);
+    int64_t src = 0;
+    for (const IfaceInfo &fi : c->iface) {
+      const int n = (fi.nU + fi.nP) * fi.s;
+      double *dst = (fi.s == 16 ? fnv.data() : fn32.data()) + static_cast<int64_t>(fi.fnU) * fi.s;
+      for (int k = 0; k < n; ++k) dst[k] = d.iface_fn[src + k];   // finite (validate)
+      src += n;
+    }
+    fn_off32 = static_cast<int64_t>(c->fn_rows16) * 16;
+  } else {
+    fn_table(d.basis_family, 16, fnv);
+    fn_table(d.basis_family, 32, fn32);
+  }
   fnv.insert(fnv.end(), fn32.begin(), fn32.end());
+  if (fnv.empty()) fnv.push_back(0.0);
   std::vector<double> alpha(static_cast<size_t>(c->alpha_elems), 1.0);
   if (d.alpha) {
     for (size_t k = 0; k < alpha.size(); ++k) {
@@ -951,6 +993,7 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   t.unk_iface = reinterpret_cast<const int *>(base + o_ui);
   t.unk_slabpos = reinterpret_cast<const int *>(base + o_usp);
   t.fnval = reinterpret_cast<const double *>(base + o_fn);
+  t.fn_off32 = fn_off32;
   t.alpha = reinterpret_cast<const double *>(base + o_al);
   t.bc_type = reinterpret_cast<const int8_t *>(base + o_bt);
   t.bc_val = reinterpret_cast<const double *>(base + o_bv);

@@ -39,6 +39,7 @@ struct IfaceInfo {
   int64_t alpha_off; // offset into the per-face alpha array (s values)
   int64_t gam_off;   // offset into the one-sided velocity output (2*s values)
   int64_t tsc_off;   // offset into the congruence scaling blocks (m*m values)
+  int fnU, fnP;      // rows of phi_0 and psi_0 in the function table of size s
 };
 
 // Column c of a subdomain: global unknown it multiplies (-1: particular),
@@ -56,7 +57,6 @@ struct RealInfo {
   int iface0, niface;
   int unk0, nunk;
   int pin;           // pinned global unknown (pure Neumann) or -1
-  int fn_off;        // offset of the interface-function table for s (stride s)
   int nslab, bmax;   // BCR slabs and padded slab size
   int nlev;          // BCR reduction levels
   int64_t slab_off;  // offset (elements) of this realisation's slab blocks
@@ -184,7 +184,8 @@ struct DeviceTables {
   const int *pair_off;      // [n_real * nslab + 1]
   const int *pair_goff;     // G offsets of every pair entry (2 per entry, -1: none)
   int emax;                 // largest number of terms of one interface row
-  const double *fnval;      // per subdomain size s (RealInfo::fn_off): [s][s]
+  const double *fnval;      // function rows of s values: size 16 first, size 32 at fn_off32
+  int64_t fn_off32;
                             // interface function k at face midpoint e
   const double *alpha;      // per face
   const int8_t *bc_type;

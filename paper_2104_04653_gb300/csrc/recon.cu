@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace 
   const int g = t.sub_by_size[first + blockIdx.x];
   const SubInfo sb = t.sub[g];
   const int tid = threadIdx.x, a = tid % S, b = tid / S;
-  const double *fnt = t.fnval + (S == 16 ? 0 : 16 * 16);
+  const double *fnt = t.fnval + (S == 16 ? 0 : t.fn_off32);
   __shared__ double p[N];
   __shared__ double coefc[1 + 8 * S];
   __shared__ double red[N / 32];
@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace 
       const IfaceInfo fi = t.iface[sb.edge_iface[side]];
       const double beta = coef[6 * N + side * S + e];
       double UH = 0.0, PH = 0.0;
-      for (int k = 0; k < fi.nU; ++k) UH += w.x[fi.unk + k] * fnt[k * S + e];
-      for (int k = 0; k < fi.nP; ++k) PH += w.x[fi.unk + fi.nU + k] * fnt[k * S + e];
+      for (int k = 0; k < fi.nU; ++k) UH += w.x[fi.unk + k] * fnt[(fi.fnU + k) * S + e];
+      for (int k = 0; k < fi.nP; ++k) PH += w.x[fi.unk + fi.nU + k] * fnt[(fi.fnP + k) * S + e];
       const double gval = -beta * sgn * UH + PH;
       un = Tf[side] * (pc - gval) / h;
       GAM[fi.gam_off + (sgn > 0 ? 0 : S) + e] = un;

@@ -55,6 +55,7 @@ class MrcmDesc(ctypes.Structure):
         ("iface_solver", ctypes.c_int32), ("precond", ctypes.c_int32),
         ("gmres_restart", ctypes.c_int32), ("gmres_max", ctypes.c_int32),
         ("gmres_tol", ctypes.c_double),
+        ("iface_fn", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -184,12 +185,19 @@ class Mrcm:
         d.bc_type = bct.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
         d.bc_val = bcv.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         d.pure_neumann = 1 if prob.pure_neumann else 0
-        if getattr(prob, "iface_fn", None) is not None:
-            raise NotImplementedError("per-interface function tables (physics-based interface "
-                                      "spaces) are not supported by the library")
         if getattr(prob, "grav", None) is not None:
             raise NotImplementedError("the gravity term is not supported by the library")
         d.basis_family = BASIS_LEGENDRE if prob.basis == "legendre" else BASIS_MONOMIAL
+        fn = None
+        if getattr(prob, "iface_fn", None) is not None:
+            # per interface: nU flux rows then nP pressure rows of s values
+            fn = np.ascontiguousarray(np.concatenate(
+                [np.concatenate([np.asarray(phi, np.float64).reshape(-1),
+                                 np.asarray(psi, np.float64).reshape(-1)])
+                 for tabs in prob.iface_fn for phi, psi in tabs]))
+            self._keep.append(fn)
+        d.iface_fn = (fn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if fn is not None
+                      else ctypes.POINTER(ctypes.c_double)())
         d.prec = opts.prec
         d.ir_tol, d.ir_max = opts.ir_tol, opts.ir_max
         d.iface_tol, d.iface_ir_max = opts.iface_tol, opts.iface_ir_max

@@ -1,0 +1,65 @@
+"""GPU parity of the MRCM solve with caller-supplied interface functions
+(mrcm_desc.iface_fn): the physics-based interface spaces and adaptive
+Robin parameter of Section 3 ("Interface spaces") built by the oracle
+(oracle/physics_spaces.py), solved by the library and by the oracle.
+
+Tolerance: relative L2 <= 1e-8 in p and u, as for the polynomial spaces."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_04653_gb300 import build
+    build.build()
+
+
+def _check(prob, prec, **kw):
+    from oracle import mrcm_oracle as O
+    from paper_2104_04653_gb300 import mrcm
+    ref = O.mrcm_solve(prob)
+    s = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=prec, **kw))
+    Kd, Ld, Qd = mrcm.device_inputs(prob)
+    p, ux, uy = s.solve(Kd, Ld, Qd)
+    got = dict(p=p.cpu().numpy(), ux=ux.cpu().numpy(), uy=uy.cpu().numpy())
+    info = s.mrcm_get_info()
+    s.close()
+    ep, eu = O.errors(got, ref)
+    assert ep <= TOL and eu <= TOL, (prob.name, prec, ep, eu, info)
+
+
+def _planted():
+    from paper_2104_04653_gb300 import workloads as W
+    n = 64
+    K = np.ones((n, n))
+    K[20:24, :] = 1e3
+    K[:, 40:42] = 1e-3
+    return W.make_problem(n, n, 16, K, bc=W.bc_left_right(n, n), n_u=2, n_p=2)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", ["channels-256x64", "planted", "channels-256-s32", "mixed-sizes"])
+def test_physics_spaces_match_oracle(case, prec):
+    from oracle import physics_spaces as PS
+    from paper_2104_04653_gb300 import workloads as W
+    base = {"channels-256x64": lambda: W.config2(n_fn=1),
+            "planted": _planted,
+            "channels-256-s32": lambda: W.config4(n=256, s=32, n_ch=8),
+            "mixed-sizes": lambda: W.config3(n_real=2, n=128)}[case]()
+    prob = PS.physics_problem(base)
+    assert any(np.any(v != 2) for v in prob.iface_nP)       # some physics-based spaces
+    _check(prob, prec)
+
+
+def test_physics_spaces_gmres_path():
+    from oracle import physics_spaces as PS
+    from paper_2104_04653_gb300 import mrcm, workloads as W
+    prob = PS.physics_problem(W.config4(n=256, s=32, n_ch=8), adaptive_alpha=False)
+    _check(prob, 1, iface_solver=mrcm.IFACE_GMRES)

@@ -135,11 +135,35 @@ def test_physics_spaces_cut_the_flux_error_on_channels():
     assert eu1 < 0.6 * eu0 and ep1 < ep0, (ep0, eu0, ep1, eu1)
 
 
-def test_library_binding_refuses_per_interface_tables():
-    """The CUDA library takes a function family, not per-interface tables:
-    its binding refuses such a problem instead of solving another one."""
+def test_setup_rejects_non_finite_function_tables():
+    """Per-interface tables reach the library through the descriptor
+    (mrcm_desc.iface_fn); a non-finite value is refused before any device
+    work."""
+    import ctypes
     from paper_2104_04653_gb300 import build, mrcm
     build.build()
+    L = mrcm.lib()
     ph = PS.physics_problem(_planted())
-    with pytest.raises(NotImplementedError):
-        mrcm.Mrcm(ph)
+    fn = np.concatenate([np.concatenate([phi.ravel(), psi.ravel()])
+                         for tabs in ph.iface_fn for phi, psi in tabs])
+    nu = np.concatenate(ph.iface_nU).astype(np.int32)
+    npp = np.concatenate(ph.iface_nP).astype(np.int32)
+    sub = np.asarray(ph.sub_size, np.int32)
+    bct = ph.bc_type.astype(np.int8)
+    bcv = ph.bc_val.astype(np.float64)
+    d = mrcm.MrcmDesc()
+    d.nx, d.ny, d.n_real, d.ly = ph.nx, ph.ny, ph.n_real, ph.ly
+    P = ctypes.POINTER
+    d.sub_size = sub.ctypes.data_as(P(ctypes.c_int32))
+    d.iface_nU = nu.ctypes.data_as(P(ctypes.c_int32))
+    d.iface_nP = npp.ctypes.data_as(P(ctypes.c_int32))
+    d.bc_type = bct.ctypes.data_as(P(ctypes.c_int8))
+    d.bc_val = bcv.ctypes.data_as(P(ctypes.c_double))
+    d.prec = 1
+    d.ir_tol, d.ir_max, d.iface_tol, d.iface_ir_max = 1e-13, 30, 1e-13, 40
+    fn[5] = np.nan
+    d.iface_fn = fn.ctypes.data_as(P(ctypes.c_double))
+    ctx = ctypes.c_void_p()
+    assert L.mrcm_setup(ctypes.byref(d), None, ctypes.byref(ctx)) == mrcm.MRCM_EINVAL
+    assert not ctx.value
+    assert b"iface_fn" in L.mrcm_last_error(None)
