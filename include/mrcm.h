@@ -187,6 +187,18 @@ mrcm_status mrcm_factor_local(mrcm_ctx *ctx, const double *d_K, const double *d_
  * its interface traces to workspace.  Text after Eq. "beta". */
 mrcm_status mrcm_build_basis(mrcm_ctx *ctx, const double *d_q);
 
+/* Gravity (Section 5.4, Eq. "Darcy_wg", the height along +y).  d_w: device
+ * [n_real][ny][nx] FP64, the gravity velocity K lambda_g g of every cell, or
+ * NULL for none (the default).  The pointer is kept, not copied: the buffer
+ * must stay valid, and hold the values, through the mrcm_build_basis and
+ * mrcm_reconstruct calls that use it; set it before capturing those calls
+ * in a graph.  Its known fluxes enter the particular right-hand side and
+ * traces (step c) and the face velocities (step e): on a face normal to y
+ * (kappa_l w_r + kappa_r w_l)/(kappa_l + kappa_r), on a Dirichlet face
+ * n_y w_c, on a Robin face n_y w_c T_R / (2 kappa_c).  EINVAL for a NULL
+ * context. */
+mrcm_status mrcm_set_gravity(mrcm_ctx *ctx, const double *d_w);
+
 /* Step (d).  Solves the interface system (Eq. "mrc2"), whose rows are the
  * traces of the basis, for (U_H, P_H).  Direct path: assembles the slab
  * blocks, factors them by block cyclic reduction (FP64, or FP32 with FP64

@@ -409,8 +409,41 @@ __global__ void __launch_bounds__(32 * kFW) k_factor_warp(DeviceTables t, Worksp
 // Right-hand side of one basis column at cell (a, b), FP64: the particular
 // column carries the sources q h^2 and the physical boundary data (2 kappa
 // p_b on a Dirichlet face, -u_b h on a Neumann face); a basis column carries
+// Gravity (Eq. "Darcy_wg", height along +y, w = K lambda_g g per cell): the
+// known part of a cell's outward flux through its S (n_y = -1) and N
+// (n_y = +1) faces.  Inside the subdomain the face pressure is eliminated
+// between the two half-cell fluxes 2 kappa (p_c - p_f)/h + n_y w_c, which
+// leaves (kappa_c w_n + kappa_n w_c)/(kappa_c + kappa_n); a Robin face keeps
+// n_y w_c T_R / (2 kappa_c) (p_f eliminated with -beta u + p_f = g); a
+// Dirichlet face n_y w_c; a Neumann face nothing (its flux is given).
+template <int S>
+__device__ __forceinline__ double gravity_outflow(const DeviceTables &t, const SubInfo &sb,
+                                                  const double *coef, int a, int b) {
+  constexpr int N = S * S;
+  const int tid = b * S + a, gi = sb.x0 + a, gj = sb.y0 + b;
+  const double *wr = t.grav + static_cast<int64_t>(sb.r) * t.ny * t.nx;
+  const double wc = wr[static_cast<int64_t>(gj) * t.nx + gi], kc = coef[5 * N + tid];
+  double out = 0.0;
+  for (int side = kEdgeS; side <= kEdgeN; ++side) {
+    const double ny = side == kEdgeN ? 1.0 : -1.0;
+    const bool edge = side == kEdgeN ? b == S - 1 : b == 0;
+    if (!edge) {
+      const int dn = side == kEdgeN ? S : -S, gjn = side == kEdgeN ? gj + 1 : gj - 1;
+      const double kn = coef[5 * N + tid + dn], wn = wr[static_cast<int64_t>(gjn) * t.nx + gi];
+      out += ny * (kc * wn + kn * wc) / (kc + kn);
+    } else if (sb.edge_iface[side] >= 0) {
+      out += ny * wc * coef[side * N + tid] / (2.0 * kc);
+    } else {
+      const int k = side == kEdgeS ? 2 * t.ny + gi : 2 * t.ny + t.nx + gi;
+      if (t.bc_type[k] == 1) out += ny * wc;
+    }
+  }
+  return out;
+}
+
 // T_R g on its own edge, g = -beta sigma phi_k(e) for a flux function and
-// psi_k(e) for a pressure function (Eq. "mrc1").
+// psi_k(e) for a pressure function (Eq. "mrc1").  With gravity the
+// particular column also carries minus the known gravity outflow.
 template <int S>
 __device__ __forceinline__ double rhs_value(const DeviceTables &t, const SubInfo &sb,
                                             const double *coef, const double *q,
@@ -435,6 +468,7 @@ __device__ __forceinline__ double rhs_value(const DeviceTables &t, const SubInfo
       if (t.bc_type[k] == 1) val += coef[side * N + tid] * t.bc_val[k];
       else val -= t.bc_val[k] * h;
     }
+    if (t.grav) val -= h * gravity_outflow<S>(t, sb, coef, a, b);
   } else {
     const int side = ci.edge;
     const bool adj = (side == kEdgeW && a == 0) || (side == kEdgeE && a == S - 1) ||
@@ -490,7 +524,11 @@ __device__ __forceinline__ void traces_and_rows(const DeviceTables &t, const Wor
       const double sigma = (side == kEdgeE || side == kEdgeN) ? 1.0 : -1.0;
       ge = ci.is_u ? -beta * sigma * fv : fv;
     }
-    const double u = TR * inv_h * (x[c * N + cl] - ge);
+    double u = TR * inv_h * (x[c * N + cl] - ge);
+    if (t.grav && ci.unk < 0 && side >= kEdgeS) {   // the particular column's gravity part
+      const double wc = t.grav[(static_cast<int64_t>(sb.r) * t.ny + sb.y0 + lb) * t.nx + sb.x0 + la];
+      u += (side == kEdgeN ? 1.0 : -1.0) * wc * TR / (2.0 * coef[5 * N + cl]);
+    }
     su[side][e][c] = u;
     sp[side][e][c] = ge + beta * u;
   }

@@ -1363,6 +1363,12 @@ mrcm_status mrcm_solve_interface(mrcm_ctx *ctx, mrcm_info *info) {
   return MRCM_OK;
 }
 
+mrcm_status mrcm_set_gravity(mrcm_ctx *ctx, const double *d_w) {
+  if (!ctx) return MRCM_EINVAL;
+  ctx->t.grav = d_w;
+  return MRCM_OK;
+}
+
 mrcm_status mrcm_reconstruct(mrcm_ctx *ctx, double *d_p, double *d_ux, double *d_uy,
                              double *d_gamma_u) {
   if (!ctx) return MRCM_EINVAL;

@@ -184,6 +184,7 @@ struct DeviceTables {
   const int *pair_off;      // [n_real * nslab + 1]
   const int *pair_goff;     // G offsets of every pair entry (2 per entry, -1: none)
   int emax;                 // largest number of terms of one interface row
+  const double *grav;       // caller's gravity velocity K lambda_g g [R][ny][nx], or null
   const double *fnval;      // function rows of s values: size 16 first, size 32 at fn_off32
   int64_t fn_off32;
                             // interface function k at face midpoint e

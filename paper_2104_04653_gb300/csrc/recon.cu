@@ -47,7 +47,16 @@ __global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace 
   double *ux = UX + static_cast<int64_t>(sb.r) * ny * (nx + 1);
   double *uy = UY + static_cast<int64_t>(sb.r) * (ny + 1) * nx;
   if (a < S - 1) ux[static_cast<int64_t>(gj) * (nx + 1) + gi + 1] = tE * (pc - p[tid + 1]) / h;
-  if (b < S - 1) uy[static_cast<int64_t>(gj + 1) * nx + gi] = tN * (pc - p[tid + S]) / h;
+  if (b < S - 1) {
+    double v = tN * (pc - p[tid + S]) / h;
+    if (t.grav) {     // gravity flux of the face (the half-cell elimination)
+      const double *wr = t.grav + static_cast<int64_t>(sb.r) * ny * nx;
+      const double k0 = coef[5 * N + tid], k1 = coef[5 * N + tid + S];
+      const double w0 = wr[static_cast<int64_t>(gj) * nx + gi], w1 = wr[static_cast<int64_t>(gj + 1) * nx + gi];
+      v += (k0 * w1 + k1 * w0) / (k0 + k1);
+    }
+    uy[static_cast<int64_t>(gj + 1) * nx + gi] = v;
+  }
   const bool onface[4] = {a == 0, a == S - 1, b == 0, b == S - 1};
   const double Tf[4] = {tW, tE, tS, tN};
 #pragma unroll
@@ -64,6 +73,9 @@ __global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace 
       for (int k = 0; k < fi.nP; ++k) PH += w.x[fi.unk + fi.nU + k] * fnt[(fi.fnP + k) * S + e];
       const double gval = -beta * sgn * UH + PH;
       un = Tf[side] * (pc - gval) / h;
+      if (t.grav && side >= kEdgeS)
+        un += sgn * t.grav[(static_cast<int64_t>(sb.r) * ny + gj) * nx + gi] * Tf[side] /
+              (2.0 * coef[5 * N + tid]);
       GAM[fi.gam_off + (sgn > 0 ? 0 : S) + e] = un;
       continue;
     }
@@ -73,6 +85,8 @@ __global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace 
     else if (side == kEdgeS) k = 2 * ny + gi;
     else k = 2 * ny + nx + gi;
     un = t.bc_type[k] == 1 ? Tf[side] * (pc - t.bc_val[k]) / h : t.bc_val[k];
+    if (t.grav && t.bc_type[k] == 1 && side >= kEdgeS)
+      un += sgn * t.grav[(static_cast<int64_t>(sb.r) * ny + gj) * nx + gi];
     if (side == kEdgeW) ux[static_cast<int64_t>(gj) * (nx + 1)] = -un;
     else if (side == kEdgeE) ux[static_cast<int64_t>(gj) * (nx + 1) + nx] = un;
     else if (side == kEdgeS) uy[gi] = -un;

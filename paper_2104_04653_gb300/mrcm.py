@@ -34,7 +34,8 @@ EXPORTED = ["mrcm_setup", "mrcm_factor_local", "mrcm_build_basis", "mrcm_solve_i
             "mrcm_num_interface_unknowns", "mrcm_num_gamma_values",
             "mrcm_copy_interface_solution", "mrcm_destroy", "mrcm_last_error", "mrcm_version",
             "mrcm_local_solve_noalloc", "mrcm_uses_gmres", "mrcm_num_precond_values",
-            "mrcm_set_precond_blocks", "mrcm_set_basis_width", "mrcm_autotune"]
+            "mrcm_set_precond_blocks", "mrcm_set_basis_width", "mrcm_autotune",
+            "mrcm_set_gravity"]
 
 
 class MrcmDesc(ctypes.Structure):
@@ -122,6 +123,8 @@ def lib(path: Optional[Path] = None):
     L.mrcm_set_basis_width.restype = i32
     L.mrcm_autotune.argtypes = [vp, dp, dp, dp, i32, ctypes.POINTER(ctypes.c_int32)]
     L.mrcm_autotune.restype = i32
+    L.mrcm_set_gravity.argtypes = [vp, vp]
+    L.mrcm_set_gravity.restype = i32
     if path is None:
         _lib = L
     return L
@@ -185,8 +188,6 @@ class Mrcm:
         d.bc_type = bct.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
         d.bc_val = bcv.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         d.pure_neumann = 1 if prob.pure_neumann else 0
-        if getattr(prob, "grav", None) is not None:
-            raise NotImplementedError("the gravity term is not supported by the library")
         d.basis_family = BASIS_LEGENDRE if prob.basis == "legendre" else BASIS_MONOMIAL
         fn = None
         if getattr(prob, "iface_fn", None) is not None:
@@ -214,6 +215,12 @@ class Mrcm:
         if st != MRCM_OK:
             raise MrcmError(st, self.L.mrcm_last_error(None).decode())
         self.ctx = ctx
+        self._grav = None
+        if getattr(prob, "grav", None) is not None:
+            # the gravity velocity K lambda_g g per cell, kept alive with the context
+            self._grav = torch.as_tensor(np.stack([np.asarray(w, np.float64) for w in prob.grav]),
+                                         device="cuda").contiguous()
+            self._check(self.L.mrcm_set_gravity(self.ctx, _ptr(self._grav)))
 
     # -- the five calls (same names as the C ABI) --------------------------
     def _check(self, st):

@@ -114,9 +114,7 @@ def test_gravity_changes_the_solution_and_keeps_the_mass_balance():
             assert abs(out * h - prob.q[0, j, i] * h * h) < 1e-11 * max(1.0, np.abs(gam).max())
 
 
-def test_library_binding_refuses_gravity():
+def test_set_gravity_needs_a_context():
     from paper_2104_04653_gb300 import build, mrcm
     build.build()
-    prob = _heterogeneous(32, 32, 16, 2, 2, seed=1)
-    with pytest.raises(NotImplementedError):
-        mrcm.Mrcm(prob)
+    assert mrcm.lib().mrcm_set_gravity(None, None) == mrcm.MRCM_EINVAL
