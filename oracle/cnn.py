@@ -212,3 +212,20 @@ def neighbourhood_rows(M, lay):
         pos = int(np.searchsorted(idx, off))
         P[off:off + m, idx] = np.linalg.inv(M[np.ix_(idx, idx)])[pos:pos + m, :]
     return P
+
+
+def neighbourhood_columns(M, lay):
+    """Dense P with P[N(g), g] = ((M_N(g))^{-1})[:, g] for every interface g
+    (the columns of the restricted inverse that belong to g, placed on the
+    rows of g's neighbourhood): the right-preconditioning counterpart of
+    ``neighbourhood_rows``, and what the library's neighbourhood
+    preconditioner builds."""
+    P = np.zeros_like(M)
+    for g, f in enumerate(lay.ifaces):
+        idx = np.concatenate([np.arange(lay.ifaces[h]["off"],
+                                        lay.ifaces[h]["off"] + lay.ifaces[h]["nU"] +
+                                        lay.ifaces[h]["nP"]) for h in neighbourhood(lay, g)])
+        off, m = f["off"], f["nU"] + f["nP"]
+        pos = int(np.searchsorted(idx, off))
+        P[idx, off:off + m] = np.linalg.inv(M[np.ix_(idx, idx)])[:, pos:pos + m]
+    return P

@@ -217,3 +217,24 @@ def test_neighbourhood_rows_cut_gmres_steps_on_channels():
     _, ras = G.gmres(M, rhs, P=C.neighbourhood_rows(M, lay), tol=1e-8, maxiter=3000)
     assert bj["converged"] and ras["converged"]
     assert ras["iters"] < bj["iters"] / 3, (ras["iters"], bj["iters"])
+
+
+def test_neighbourhood_columns_are_the_inverse_on_a_whole_domain_neighbourhood():
+    from oracle import gmres as G
+    prob, M, lay = _system(n=32, s=16)
+    P = C.neighbourhood_columns(M, lay)
+    Mi = np.linalg.inv(M)
+    np.testing.assert_allclose(P, Mi, atol=1e-9 * np.abs(Mi).max())
+    b = np.random.default_rng(1).standard_normal(M.shape[0])
+    _, info = G.gmres(M, b, P=P, tol=1e-10, maxiter=50)
+    assert info["converged"] and info["iters"] == 1
+
+
+def test_neighbourhood_columns_diagonal_block_is_the_target():
+    prob, M, lay = _system(n=64, s=16)
+    P = C.neighbourhood_columns(M, lay)
+    T = C.targets(M, lay, theta=1.0, clip=np.inf)
+    for g, f in enumerate(lay.ifaces):
+        off, m = f["off"], f["nU"] + f["nP"]
+        sl = slice(off, off + m)
+        np.testing.assert_allclose(M[sl, sl] @ P[sl, sl] - np.eye(m), T[g], atol=1e-9)
