@@ -16,6 +16,12 @@
 // an Arnoldi step needs three grid-wide barriers.  The small Hessenberg
 // least-squares problem is solved redundantly, bit-identically, by every
 // block of a realisation, so no block ever waits for a broadcast.
+//
+// The neighbourhood preconditioner (MRCM_PRECOND_NEIGHBOURHOOD) is not
+// block-diagonal: column block g of P is the part of the inverse of the
+// interface matrix restricted to g's neighbourhood that belongs to g.  G P
+// is then folded into wider rows (the column blocks that reach each row),
+// and x = P y gathers over the blocks whose neighbourhood holds the row.
 #include "mrcm_internal.h"
 #include "iface_common.cuh"
 #include "nbsolve.cuh"
