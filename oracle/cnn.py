@@ -214,17 +214,26 @@ def neighbourhood_rows(M, lay):
     return P
 
 
-def neighbourhood_columns(M, lay):
+def shared_neighbourhood(lay, g):
+    """Interfaces that share a subdomain with g (g included), ascending."""
+    f = lay.ifaces[g]
+    subs = {tuple(f["L"]), tuple(f["R"])}
+    return [h for h, fh in enumerate(lay.ifaces) if tuple(fh["L"]) in subs or tuple(fh["R"]) in subs]
+
+
+def neighbourhood_columns(M, lay, shared=False):
     """Dense P with P[N(g), g] = ((M_N(g))^{-1})[:, g] for every interface g
     (the columns of the restricted inverse that belong to g, placed on the
     rows of g's neighbourhood): the right-preconditioning counterpart of
     ``neighbourhood_rows``, and what the library's neighbourhood
-    preconditioner builds."""
+    preconditioner builds.  shared: N(g) = the interfaces that share a
+    subdomain with g instead."""
     P = np.zeros_like(M)
     for g, f in enumerate(lay.ifaces):
+        nb = shared_neighbourhood(lay, g) if shared else neighbourhood(lay, g)
         idx = np.concatenate([np.arange(lay.ifaces[h]["off"],
                                         lay.ifaces[h]["off"] + lay.ifaces[h]["nU"] +
-                                        lay.ifaces[h]["nP"]) for h in neighbourhood(lay, g)])
+                                        lay.ifaces[h]["nP"]) for h in nb])
         off, m = f["off"], f["nU"] + f["nP"]
         pos = int(np.searchsorted(idx, off))
         P[idx, off:off + m] = np.linalg.inv(M[np.ix_(idx, idx)])[:, pos:pos + m]

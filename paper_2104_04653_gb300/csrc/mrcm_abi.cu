@@ -82,8 +82,11 @@ struct mrcm_ctx {
   std::vector<int> nb_off, nb_list;
   int nb_max = 0, nloc_max = 0, m_uniform = 0, s_uniform = 0;
   int *d_nb_off = nullptr, *d_nb_list = nullptr;
-  // neighbourhood preconditioner (GmArgs): host tables
+  // neighbourhood preconditioner (GmArgs): its neighbourhood lists and host tables
   bool use_nb = false;
+  std::vector<int> pnb_off, pnb_list;
+  int pnb_max = 0, pnloc_max = 0;
+  int *d_pnb_off = nullptr, *d_pnb_list = nullptr;
   std::vector<int64_t> p_off, gw_off, gat_o;
   std::vector<int> gw_w, pb_off, pb_list, pb_pos, gat_off, gat_g;
 };
@@ -152,7 +155,7 @@ static mrcm_status validate(const mrcm_desc *d) {
     return fail(nullptr, MRCM_EINVAL, "sweep limits above 1000");
   if (d->iface_solver < MRCM_IFACE_AUTO || d->iface_solver > MRCM_IFACE_GMRES)
     return fail(nullptr, MRCM_EINVAL, "unknown interface solver %d", d->iface_solver);
-  if (d->precond < MRCM_PRECOND_BLOCK_JACOBI || d->precond > MRCM_PRECOND_NEIGHBOURHOOD)
+  if (d->precond < MRCM_PRECOND_BLOCK_JACOBI || d->precond > MRCM_PRECOND_NEIGHBOURHOOD_SHARED)
     return fail(nullptr, MRCM_EINVAL, "unknown preconditioner %d", d->precond);
   if (d->gmres_restart < 0 || d->gmres_restart > kGmKmax)
     return fail(nullptr, MRCM_EINVAL, "gmres_restart must be in 0..%d", kGmKmax);
@@ -626,27 +629,60 @@ static void build_neighbourhoods(mrcm_ctx *c) {
     if (ri.s != c->s_uniform) c->s_uniform = 0;
 }
 
-// Tables of the neighbourhood preconditioner (see GmArgs).  The relation
-// "h in N(g)" is symmetric (a subdomain of h within one subdomain of a
-// subdomain of g), so the blocks g' with h in N(g') are N(h) itself.
+// Neighbourhood lists of the preconditioner: the training-target
+// neighbourhoods, or only the interfaces sharing a subdomain with g.
+static void build_precond_neighbourhoods(mrcm_ctx *c, bool shared) {
+  if (!shared) {
+    c->pnb_off = c->nb_off;
+    c->pnb_list = c->nb_list;
+    c->pnb_max = c->nb_max;
+    c->pnloc_max = c->nloc_max;
+    return;
+  }
+  c->pnb_off.assign(1, 0);
+  c->pnb_list.clear();
+  c->pnb_max = c->pnloc_max = 0;
+  std::vector<int> nb;
+  for (const IfaceInfo &fi : c->iface) {
+    nb.clear();
+    for (int side = 0; side < 2; ++side) {
+      const SubInfo &sb = c->sub[side ? fi.R : fi.L];
+      for (int e = 0; e < 4; ++e)
+        if (sb.edge_iface[e] >= 0) nb.push_back(sb.edge_iface[e]);
+    }
+    std::sort(nb.begin(), nb.end());
+    nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+    int nloc = 0;
+    for (int h : nb) nloc += c->iface[h].nU + c->iface[h].nP;
+    c->pnb_max = std::max(c->pnb_max, static_cast<int>(nb.size()));
+    c->pnloc_max = std::max(c->pnloc_max, nloc);
+    c->pnb_list.insert(c->pnb_list.end(), nb.begin(), nb.end());
+    c->pnb_off.push_back(static_cast<int>(c->pnb_list.size()));
+  }
+}
+
+// Tables of the neighbourhood preconditioner (see GmArgs).  Both relations
+// ("a subdomain of h within one subdomain of a subdomain of g", "h and g
+// share a subdomain") are symmetric, so the blocks g' with h in N(g') are
+// N(h) itself.
 static void build_nb_tables(mrcm_ctx *c) {
   const int nif = static_cast<int>(c->iface.size());
   auto msz = [&](int g) { return c->iface[g].nU + c->iface[g].nP; };
-  std::vector<int> nb_loc(c->nb_list.size(), 0);
+  std::vector<int> nb_loc(c->pnb_list.size(), 0);
   c->p_off.assign(nif + 1, 0);
   for (int g = 0; g < nif; ++g) {
     int o = 0;
-    for (int j = c->nb_off[g]; j < c->nb_off[g + 1]; ++j) {
+    for (int j = c->pnb_off[g]; j < c->pnb_off[g + 1]; ++j) {
       nb_loc[j] = o;
-      o += msz(c->nb_list[j]);
+      o += msz(c->pnb_list[j]);
     }
     c->p_off[g + 1] = c->p_off[g] + static_cast<int64_t>(o) * msz(g);
   }
   // for every h: the blocks g' holding h, with the P offset of h's first row
   std::vector<std::vector<std::pair<int, int64_t>>> gl(nif);
   for (int g = 0; g < nif; ++g)
-    for (int j = c->nb_off[g]; j < c->nb_off[g + 1]; ++j)
-      gl[c->nb_list[j]].push_back({g, c->p_off[g] + static_cast<int64_t>(nb_loc[j]) * msz(g)});
+    for (int j = c->pnb_off[g]; j < c->pnb_off[g + 1]; ++j)
+      gl[c->pnb_list[j]].push_back({g, c->p_off[g] + static_cast<int64_t>(nb_loc[j]) * msz(g)});
   c->gat_off.assign(1, 0);
   c->gat_g.clear();
   c->gat_o.clear();
@@ -673,7 +709,7 @@ static void build_nb_tables(mrcm_ctx *c) {
       for (int e = 0; e < 4; ++e) {
         const int h = sb.edge_iface[e];
         if (h < 0) continue;
-        for (int j = c->nb_off[h]; j < c->nb_off[h + 1]; ++j) blk.push_back(c->nb_list[j]);
+        for (int j = c->pnb_off[h]; j < c->pnb_off[h + 1]; ++j) blk.push_back(c->pnb_list[j]);
       }
     }
     std::sort(blk.begin(), blk.end());
@@ -787,9 +823,11 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     c->gm_precond = desc->precond;
     build_gmres_rows(c);
     build_neighbourhoods(c);
-    if (c->gm_precond == MRCM_PRECOND_NEIGHBOURHOOD) {
-      if (c->nb_max > kLpMaxNb || c->nloc_max > kLpMaxLoc) {
-        const int nl = c->nloc_max;
+    if (c->gm_precond == MRCM_PRECOND_NEIGHBOURHOOD ||
+        c->gm_precond == MRCM_PRECOND_NEIGHBOURHOOD_SHARED) {
+      build_precond_neighbourhoods(c, c->gm_precond == MRCM_PRECOND_NEIGHBOURHOOD_SHARED);
+      if (c->pnb_max > kLpMaxNb || c->pnloc_max > kLpMaxLoc) {
+        const int nl = c->pnloc_max;
         delete c;
         return fail(nullptr, MRCM_EINVAL,
                     "neighbourhood preconditioner: neighbourhood of %d unknowns above %d", nl,
@@ -887,6 +925,8 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                o_nboff = A.take<int>(G ? c->nb_off.size() : 0),
                o_nblist = A.take<int>(G ? c->nb_list.size() + 1 : 0);
   const bool NB = G && c->use_nb;
+  const size_t o_pnboff = A.take<int>(NB ? c->pnb_off.size() : 0),
+               o_pnblist = A.take<int>(NB ? c->pnb_list.size() + 1 : 0);
   const size_t o_nbP = A.take<double>(NB ? c->p_off.back() + 1 : 0),
                o_nbGw = A.take<double>(NB ? c->gw_off.back() + 1 : 0),
                o_poff = A.take<int64_t>(NB ? c->p_off.size() : 0),
@@ -999,6 +1039,10 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
       (G && (e = up(o_gmblk, c->gm_blocks.data(), c->gm_blocks.size() * sizeof(GmBlock))) !=
                 cudaSuccess) ||
       (G && (e = up(o_nboff, c->nb_off.data(), c->nb_off.size() * sizeof(int))) != cudaSuccess) ||
+      (NB && (e = up(o_pnboff, c->pnb_off.data(), c->pnb_off.size() * sizeof(int))) !=
+                 cudaSuccess) ||
+      (NB && (e = up(o_pnblist, c->pnb_list.data(), c->pnb_list.size() * sizeof(int))) !=
+                 cudaSuccess) ||
       (NB && (e = up(o_poff, c->p_off.data(), c->p_off.size() * sizeof(int64_t))) !=
                  cudaSuccess) ||
       (NB && (e = up(o_gwoff, c->gw_off.data(), c->gw_off.size() * sizeof(int64_t))) !=
@@ -1118,6 +1162,8 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     c->d_nb_list = reinterpret_cast<int *>(base + o_nblist);
     a.nb = 0;
     if (NB) {
+      c->d_pnb_off = reinterpret_cast<int *>(base + o_pnboff);
+      c->d_pnb_list = reinterpret_cast<int *>(base + o_pnblist);
       a.Pnb = reinterpret_cast<double *>(base + o_nbP);
       a.Gw = reinterpret_cast<double *>(base + o_nbGw);
       a.p_off = reinterpret_cast<const int64_t *>(base + o_poff);
@@ -1361,11 +1407,11 @@ static mrcm_status solve_gmres(mrcm_ctx *ctx) {
   const int pc = ctx->gm_precond;
   if (pc == MRCM_PRECOND_USER && !ctx->gm_user_set)
     return fail(ctx, MRCM_EINVAL, "precond = MRCM_PRECOND_USER but no blocks were set");
-  if (pc == MRCM_PRECOND_NEIGHBOURHOOD) {
+  if (pc == MRCM_PRECOND_NEIGHBOURHOOD || pc == MRCM_PRECOND_NEIGHBOURHOOD_SHARED) {
     a.nb = 1;
     a.stall = 0;
     a.gate = 0;
-    if ((e = launch_gmres_nb(ctx->t, ctx->w, a, ctx->d_nb_off, ctx->d_nb_list, ctx->nloc_max,
+    if ((e = launch_gmres_nb(ctx->t, ctx->w, a, ctx->d_pnb_off, ctx->d_pnb_list, ctx->pnloc_max,
                              ctx->mmax, st)) != cudaSuccess)
       return cuda_fail(ctx, e, "neighbourhood preconditioner launch");
     ctx->launches += 2;

@@ -67,7 +67,7 @@ def test_setup_rejects_bad_descriptors(L, bad):
         kw = dict(pure=1, bct=bt)
     ctx = ctypes.c_void_p()
     field = {"solver": ("iface_solver", 3), "precond": ("precond", -1),
-             "precond_high": ("precond", 4), "restart": ("gmres_restart", 65)}.get(bad)
+             "precond_high": ("precond", 5), "restart": ("gmres_restart", 65)}.get(bad)
     if bad == "null":
         st = L.mrcm_setup(None, None, ctypes.byref(ctx))
     else:

@@ -44,28 +44,31 @@ def _run(prob, precond, **kw):
     return out
 
 
+@pytest.mark.parametrize("shared", [False, True])
 @pytest.mark.parametrize("case", ["channels-256-s32", "fronts-128", "fivespot-pure-neumann"])
-def test_solution_matches_oracle(case):
+def test_solution_matches_oracle(case, shared):
     O, OG, C, mrcm, W = _mods()
     prob = {"channels-256-s32": lambda: W.config4(n=256, s=32, n_ch=8),
             "fronts-128": lambda: W.config5(3, n=128),
             "fivespot-pure-neumann": W.config1}[case]()
     ref = O.mrcm_solve(prob)
-    got = _run(prob, mrcm.PRECOND_NEIGHBOURHOOD)
+    got = _run(prob, mrcm.PRECOND_NEIGHBOURHOOD_SHARED if shared else mrcm.PRECOND_NEIGHBOURHOOD)
     ep, eu = O.errors(got, ref)
     assert ep <= TOL and eu <= TOL, (ep, eu, got["info"])
     assert got["info"]["gmres_iters"] > 0
 
 
-def test_step_count_matches_oracle_gmres():
+@pytest.mark.parametrize("shared", [False, True])
+def test_step_count_matches_oracle_gmres(shared):
     O, OG, C, mrcm, W = _mods()
     prob = W.config4(n=256, s=32, n_ch=8)
     ref = O.mrcm_solve(prob, return_system=True)
     S = ref["systems"][0]
     tol = 1e-10
-    _, oi = OG.gmres(S["M"], S["rhs"], P=C.neighbourhood_columns(S["M"], S["layout"]), restart=40,
-                     tol=tol)
-    got = _run(prob, mrcm.PRECOND_NEIGHBOURHOOD, gmres_restart=40, gmres_tol=tol)
+    _, oi = OG.gmres(S["M"], S["rhs"], P=C.neighbourhood_columns(S["M"], S["layout"], shared),
+                     restart=40, tol=tol)
+    got = _run(prob, mrcm.PRECOND_NEIGHBOURHOOD_SHARED if shared else mrcm.PRECOND_NEIGHBOURHOOD,
+               gmres_restart=40, gmres_tol=tol)
     n_gpu, n_cpu = got["info"]["gmres_iters"], oi["iters"]
     assert abs(n_gpu - n_cpu) <= max(3, 0.05 * n_cpu), (n_gpu, n_cpu)
 
@@ -89,3 +92,17 @@ def test_setup_refuses_neighbourhoods_above_160_unknowns():
         mrcm.Mrcm(W.config2(), mrcm.SolverOptions(prec=1, iface_solver=mrcm.IFACE_GMRES,
                                                   precond=mrcm.PRECOND_NEIGHBOURHOOD))
     assert e.value.status == mrcm.MRCM_EINVAL
+
+
+def test_shared_form_serves_eight_unknowns_per_interface():
+    """The 256 x 64 channels with m = 8 (neighbourhoods of 216 unknowns,
+    refused by the full form): the shared form (at most 56 unknowns) solves
+    them, and in fewer steps than block-Jacobi."""
+    O, _, _, mrcm, W = _mods()
+    prob = W.config2()
+    ref = O.mrcm_solve(prob)
+    got = _run(prob, mrcm.PRECOND_NEIGHBOURHOOD_SHARED)
+    bj = _run(prob, mrcm.PRECOND_BLOCK_JACOBI)
+    ep, eu = O.errors(got, ref)
+    assert ep <= TOL and eu <= TOL, (ep, eu, got["info"])
+    assert 2 * got["info"]["gmres_iters"] < bj["info"]["gmres_iters"], (got["info"], bj["info"])
