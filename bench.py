@@ -451,7 +451,7 @@ def _traffic(kernel):
 
 def roofline_entry(call, seconds, prob, solver, peaks, src, clocks):
     """Algorithmic work of the dominant call per launch, over its device
-    time; the bound and per-unit figures are stated in the design doc."""
+    time; the bound and the per-unit figures come from perfmodel.call_work."""
     from paper_2104_04653_gb300 import perfmodel
     w = perfmodel.call_work(call, prob, solver)
     sm_mhz = (clocks or {}).get("sm_mhz") or 1900.0

@@ -24,7 +24,8 @@ solution of the Darcy problem (Section 2, Eq. "Darcy"):
 4. the solution is the linear combination of the basis with the interface
    coefficients.
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open (the same readings hold for the
+CUDA path):
 interface functions are Legendre polynomials sampled at face midpoints of
 t in [-1, 1]; unknowns per interface are ordered [U_0..U_{nU-1},
 P_0..P_{nP-1}]; on an interface face the reported velocity is the mean of

@@ -87,3 +87,56 @@ def test_calls_on_null_context_fail_cleanly(L):
     assert L.mrcm_solve_interface(None, None) == mrcm.MRCM_EINVAL
     assert L.mrcm_reconstruct(None, None, None, None, None) == mrcm.MRCM_EINVAL
     L.mrcm_destroy(None)
+
+
+def test_seeded_random_descriptors_fail_cleanly(L):
+    """500 seeded descriptors, mostly valid, some with one corrupted field:
+    setup either refuses them (EINVAL, no context) or gets as far as the
+    device (ECUDA here, where there is none); the host code never crashes."""
+    from paper_2104_04653_gb300 import mrcm
+    rng = np.random.default_rng(2024)
+    P = ctypes.POINTER
+    seen = set()
+    for _ in range(500):
+        R = int(rng.integers(1, 4))
+        subs = rng.choice([16, 32], size=R).astype(np.int32)
+        nx, ny = int(rng.choice([32, 64, 96, 128])), int(rng.choice([32, 64, 128]))
+        tot = sum(max(0, (nx // s - 1) * (ny // s) + (nx // s) * (ny // s - 1)) for s in subs)
+        nu = rng.integers(1, 5, size=tot + 1).astype(np.int32)
+        npp = rng.integers(1, 5, size=tot + 1).astype(np.int32)
+        nb = 2 * nx + 2 * ny
+        bt = rng.integers(0, 2, size=nb).astype(np.int8)
+        bv = rng.standard_normal(nb)
+        alpha = rng.uniform(0.1, 2.0, size=max(tot * 32, 1))
+        corrupt = int(rng.integers(0, 8))
+        if corrupt == 0:
+            nu[rng.integers(0, tot + 1)] = int(rng.choice([-1, 40]))
+        elif corrupt == 1:
+            bt[rng.integers(0, nb)] = 3
+        elif corrupt == 2:
+            bv[rng.integers(0, nb)] = np.nan
+        elif corrupt == 3:
+            alpha[rng.integers(0, max(tot * 32, 1))] = -1.0
+        d = mrcm.MrcmDesc()
+        d.nx, d.ny, d.n_real, d.ly = nx, ny, R, 1.0
+        d.sub_size = subs.ctypes.data_as(P(ctypes.c_int32))
+        d.iface_nU = nu.ctypes.data_as(P(ctypes.c_int32))
+        d.iface_nP = npp.ctypes.data_as(P(ctypes.c_int32))
+        d.bc_type = bt.ctypes.data_as(P(ctypes.c_int8))
+        d.bc_val = bv.ctypes.data_as(P(ctypes.c_double))
+        d.alpha = alpha.ctypes.data_as(P(ctypes.c_double)) if rng.random() < 0.5 \
+            else P(ctypes.c_double)()
+        d.pure_neumann = int(rng.random() < 0.2)
+        d.basis_family, d.prec = int(rng.integers(0, 2)), int(rng.integers(0, 2))
+        d.ir_tol, d.ir_max, d.iface_tol, d.iface_ir_max = 1e-13, 30, 1e-13, 40
+        d.iface_solver, d.precond = int(rng.integers(0, 3)), int(rng.integers(0, 3))
+        d.gmres_restart, d.gmres_max = int(rng.integers(0, 65)), int(rng.integers(0, 100))
+        ctx = ctypes.c_void_p()
+        st = L.mrcm_setup(ctypes.byref(d), None, ctypes.byref(ctx))
+        seen.add(st)
+        if st != mrcm.MRCM_OK:
+            assert not ctx.value
+            assert len(L.mrcm_last_error(None)) > 0
+        else:
+            L.mrcm_destroy(ctx)
+    assert mrcm.MRCM_EINVAL in seen
