@@ -573,7 +573,8 @@ def _suite_learned(args, flush, torch, np, mrcm, LP, W):
     del xv, tv
     res = {}
     for name, pc in (("none", mrcm.PRECOND_NONE), ("block_jacobi", mrcm.PRECOND_BLOCK_JACOBI),
-                     ("learned", mrcm.PRECOND_USER)):
+                     ("learned", mrcm.PRECOND_USER),
+                     ("neighbourhood", mrcm.PRECOND_NEIGHBOURHOOD)):
         s = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=mrcm.PREC_FP32_IR,
                                                iface_solver=mrcm.IFACE_GMRES, precond=pc,
                                                gmres_tol=1e-8, gmres_max=20000))

@@ -102,7 +102,15 @@ typedef enum {
   MRCM_PRECOND_USER = 1,          /* blocks from mrcm_set_precond_blocks (the  */
                                   /* learned preconditioner); block-Jacobi    */
                                   /* takes over if the residual stalls        */
-  MRCM_PRECOND_NONE = 2
+  MRCM_PRECOND_NONE = 2,
+  MRCM_PRECOND_NEIGHBOURHOOD = 3, /* restricted inverse of each interface's    */
+                                  /* neighbourhood: P[N(g), g] = columns g of  */
+                                  /* (M_N(g))^-1, FP64, built every solve; N(g) */
+                                  /* = interfaces with a subdomain within one  */
+                                  /* subdomain of g's two (up to 31; at most   */
+                                  /* 160 unknowns)                             */
+  MRCM_PRECOND_NEIGHBOURHOOD_SHARED = 4  /* the same with N(g) = interfaces    */
+                                         /* sharing a subdomain with g (<= 7)  */
 } mrcm_precond;
 
 typedef struct mrcm_ctx mrcm_ctx;   /* opaque, owned by the library */

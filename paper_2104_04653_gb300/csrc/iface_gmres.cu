@@ -16,10 +16,18 @@
 // an Arnoldi step needs three grid-wide barriers.  The small Hessenberg
 // least-squares problem is solved redundantly, bit-identically, by every
 // block of a realisation, so no block ever waits for a broadcast.
+//
+// The neighbourhood preconditioner (MRCM_PRECOND_NEIGHBOURHOOD) is not
+// block-diagonal: column block g of P is the part of the inverse of the
+// interface matrix restricted to g's neighbourhood that belongs to g.  G P
+// is then folded into wider rows (the column blocks that reach each row),
+// and x = P y gathers over the blocks whose neighbourhood holds the row.
 #include "mrcm_internal.h"
 #include "iface_common.cuh"
+#include "nbsolve.cuh"
 #include "../../include/mrcm.h"
 
+#include <algorithm>
 #include <cooperative_groups.h>
 #include <cstdint>
 
@@ -144,7 +152,120 @@ __global__ void __launch_bounds__(128) k_gm_gprime(DeviceTables t, Workspace w, 
 }
 
 // ---------------------------------------------------------------------------
+// Neighbourhood preconditioner (restricted additive Schwarz with one
+// subdomain of overlap, Cai and Sarkis 1999, applied on the right): column
+// block g of P is the m_g columns of (M_N(g))^{-1} that belong to g, placed
+// on the rows of N(g).  One CTA per interface builds its block (FP64
+// Gaussian elimination in shared memory, nbsolve.cuh).
+__global__ void __launch_bounds__(256) k_gm_nbcols(DeviceTables t, Workspace w, GmArgs a,
+                                                   const int *nb_off, const int *nb_list) {
+  extern __shared__ __align__(16) double nsm[];
+  const int g = blockIdx.x;
+  const IfaceInfo fg = t.iface[g];
+  const int m = fg.nU + fg.nP;
+  const int h0 = nb_off[g], nh = nb_off[g + 1] - h0;
+  __shared__ int loc[kLpMaxNb + 1];
+  __shared__ int s_n, s_pos, s_piv, s_bad;
+  const bool bad = nb_inverse_columns(t, w, a.row, nb_list, h0, nh, g, nsm, nullptr, loc, &s_n,
+                                      &s_pos, &s_piv, &s_bad);
+  const int n = s_n, ld = n + m;
+  double *Pg = a.Pnb + a.p_off[g];
+  for (int e = threadIdx.x; e < n * m; e += blockDim.x)
+    Pg[e] = bad ? 0.0 : nsm[static_cast<size_t>(e / m) * ld + n + e % m];
+  if (bad && threadIdx.x == 0) atomicOr(&w.status[0], MRCM_FLAG_IFACE_PIVOT);
+}
+
+// The P entries of interface h's rows in column block g' (null if h is not
+// in N(g')): gat lists the blocks holding h, in increasing g'.
+__device__ __forceinline__ const double *nb_rows(const GmArgs &a, int h, int gp) {
+  for (int j = a.gat_off[h]; j < a.gat_off[h + 1]; ++j)
+    if (a.gat_g[j] == gp) return a.Pnb + a.gat_o[j];
+  return nullptr;
+}
+
+// Wide G P: entry (row i of interface g, column k of block g' in pb(g)) =
+// sum over the columns q of the row (both sides, the pinned unknown left
+// out) of G[u, q] P[q, (g', k)].  One CTA per interface.
+__global__ void __launch_bounds__(128) k_gm_gwide(DeviceTables t, Workspace w, GmArgs a) {
+  const int g = blockIdx.x;
+  const IfaceInfo fg = t.iface[g];
+  const int m = fg.nU + fg.nP, wg = a.gw_w[g];
+  const int pin = t.real[fg.r].pin;
+  const int b0 = a.pb_off[g], nbk = a.pb_off[g + 1] - b0;
+  double *Gw = a.Gw + a.gw_off[g];
+  for (int e = threadIdx.x; e < m * wg; e += blockDim.x) {
+    const int i = e / wg, col = e % wg;
+    int j = nbk - 1;
+    while (a.pb_pos[b0 + j] > col) --j;              // block holding this column
+    const int gp = a.pb_list[b0 + j], k = col - a.pb_pos[b0 + j];
+    const int mp = t.iface[gp].nU + t.iface[gp].nP;
+    const int u = fg.unk + i;
+    double acc = 0.0;
+    if (u != pin) {
+      const GmRow R = a.row[u];
+      int hlast = -1;
+      const double *Ph = nullptr;
+      for (int side = 0; side < 2; ++side) {
+        const double *gr = w.G + (side ? R.gR : R.gL);
+        const ColInfo *cl = t.col + (side ? R.cR : R.cL);
+        const int nc = side ? R.nR : R.nL;
+        for (int c = 0; c < nc; ++c) {
+          const int q = cl[c].unk;
+          if (q == pin) continue;
+          const int h = t.unk_iface[q];
+          if (h != hlast) {
+            Ph = nb_rows(a, h, gp);
+            hlast = h;
+          }
+          if (Ph) acc = fma(gr[c], Ph[(q - t.iface[h].unk) * mp + k], acc);
+        }
+      }
+    }
+    Gw[static_cast<int64_t>(i) * wg + col] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // GMRES kernel helpers.
+
+// (M P v)[u] with the neighbourhood preconditioner (wide rows).
+__device__ __forceinline__ double gm_apply_nb(const DeviceTables &t, const GmArgs &a, int u,
+                                              const double *v, int u0, int pin) {
+  if (u == pin) return __ldcg(v + (u - u0));
+  const int g = t.unk_iface[u];
+  const IfaceInfo fg = t.iface[g];
+  const int wg = a.gw_w[g];
+  const double *row = a.Gw + a.gw_off[g] + static_cast<int64_t>(u - fg.unk) * wg;
+  double s0 = 0.0, s1 = 0.0;
+  for (int j = a.pb_off[g]; j < a.pb_off[g + 1]; ++j) {
+    const IfaceInfo fp = t.iface[a.pb_list[j]];
+    const int mp = fp.nU + fp.nP;
+    const double *rj = row + a.pb_pos[j];
+    for (int k = 0; k < mp; ++k) {
+      const int q = fp.unk + k;
+      if (q == pin) continue;
+      if (k & 1) s1 = fma(rj[k], __ldcg(v + (q - u0)), s1);
+      else s0 = fma(rj[k], __ldcg(v + (q - u0)), s0);
+    }
+  }
+  return s0 + s1;
+}
+
+// (P y)[u] with the neighbourhood preconditioner: the blocks g' whose
+// neighbourhood holds u's interface h.
+__device__ __forceinline__ double gm_prec_nb(const DeviceTables &t, const GmArgs &a, int u,
+                                             const double *y, int u0) {
+  const int h = t.unk_iface[u];
+  const int i = u - t.iface[h].unk;
+  double acc = 0.0;
+  for (int j = a.gat_off[h]; j < a.gat_off[h + 1]; ++j) {
+    const IfaceInfo fp = t.iface[a.gat_g[j]];
+    const int mp = fp.nU + fp.nP;
+    const double *Pr = a.Pnb + a.gat_o[j] + static_cast<int64_t>(i) * mp;
+    for (int k = 0; k < mp; ++k) acc = fma(Pr[k], __ldcg(y + (fp.unk - u0 + k)), acc);
+  }
+  return acc;
+}
 
 // (M P v)[u] for a realisation-local vector v (index = unknown - u0).
 __device__ __forceinline__ double gm_apply(const DeviceTables &t, const GmArgs &a, int u,
@@ -247,6 +368,8 @@ __device__ __forceinline__ double gm_comb(const double *h, const double *V, int6
 
 enum { kIter = 0, kUpdate = 1, kDone = 2 };
 
+// NB: the neighbourhood preconditioner (wide rows of G P, x = P y by gather)
+template <bool NB>
 __global__ void __launch_bounds__(kGmThreads) k_gmres(DeviceTables t, Workspace w, GmArgs a) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) double gsm[];
@@ -382,7 +505,8 @@ __global__ void __launch_bounds__(kGmThreads) k_gmres(DeviceTables t, Workspace 
         const double inv = 1.0 / beta;
         const double *vj = V + j * n;
         for (int ul = rl0 + tid; ul < rl1; ul += kGmThreads)
-          Wv[ul] = inv * gm_apply(t, a, u0 + ul, vj, u0, pin);
+          Wv[ul] = inv * (NB ? gm_apply_nb(t, a, u0 + ul, vj, u0, pin)
+                             : gm_apply(t, a, u0 + ul, vj, u0, pin));
         __syncthreads();
         gm_dots(V, n, rl0, rl1, Wv, j + 1, inv, mypart);
       }
@@ -409,7 +533,8 @@ __global__ void __launch_bounds__(kGmThreads) k_gmres(DeviceTables t, Workspace 
       double s = 0.0;
       for (int ul = rl0 + tid; ul < rl1; ul += kGmThreads) {
         const int u = u0 + ul;
-        const double r = gm_rhs(w, a, u, pin) - gm_apply(t, a, u, Y, u0, pin);
+        const double r = gm_rhs(w, a, u, pin) -
+                         (NB ? gm_apply_nb(t, a, u, Y, u0, pin) : gm_apply(t, a, u, Y, u0, pin));
         V[ul] = r;
         s = fma(r, r, s);
       }
@@ -445,7 +570,9 @@ __global__ void __launch_bounds__(kGmThreads) k_gmres(DeviceTables t, Workspace 
     grid.sync();
   }
   // x = P y on this CTA's rows
-  if (ran)
+  if (ran && NB)
+    for (int ul = rl0 + tid; ul < rl1; ul += kGmThreads) w.x[u0 + ul] = gm_prec_nb(t, a, u0 + ul, Y, u0);
+  else if (ran)
     for (int ul = rl0 + tid; ul < rl1; ul += kGmThreads) {
       const int u = u0 + ul;
       const IfaceInfo fi = t.iface[t.unk_iface[u]];
@@ -467,12 +594,18 @@ int gmres_max_blocks(int K, int dev) {
   int nsm = 0, per = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = gmres_smem_bytes(K);
-  if (cudaFuncSetAttribute(k_gmres, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  int per_nb = 0;
+  if (cudaFuncSetAttribute(k_gmres<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_gmres<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gmres, kGmThreads, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gmres<false>, kGmThreads, smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_nb, k_gmres<true>, kGmThreads, smem) !=
+          cudaSuccess)
     return 0;
-  return nsm * per;
+  return nsm * std::min(per, per_nb);
 }
 
 cudaError_t launch_gmres_bj(const DeviceTables &t, const Workspace &w, const GmArgs &a, double *Pbj,
@@ -493,6 +626,20 @@ cudaError_t launch_gmres_precond(const DeviceTables &t, const Workspace &w, cons
   return cudaGetLastError();
 }
 
+cudaError_t launch_gmres_nb(const DeviceTables &t, const Workspace &w, const GmArgs &a,
+                            const int *nb_off, const int *nb_list, int nloc_max, int mmax,
+                            cudaStream_t st) {
+  if (t.niface == 0) return cudaSuccess;
+  const size_t smem = lp_targets_smem(nloc_max, mmax);
+  cudaError_t e = cudaFuncSetAttribute(k_gm_nbcols, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  k_gm_nbcols<<<t.niface, 256, smem, st>>>(t, w, a, nb_off, nb_list);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_gm_gwide<<<t.niface, 128, 0, st>>>(t, w, a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gmres(const DeviceTables &t, const Workspace &w, const GmArgs &a, int nblk,
                          cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
@@ -505,7 +652,8 @@ cudaError_t launch_gmres(const DeviceTables &t, const Workspace &w, const GmArgs
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_gmres, t, w, a);
+  return a.nb ? cudaLaunchKernelEx(&cfg, k_gmres<true>, t, w, a)
+              : cudaLaunchKernelEx(&cfg, k_gmres<false>, t, w, a);
 }
 
 }  // namespace mrcm

@@ -16,6 +16,7 @@
 // here in FP64.
 #include "mrcm_internal.h"
 #include "iface_common.cuh"
+#include "nbsolve.cuh"
 #include "../../include/mrcm.h"
 #include "../../include/mrcm_learned.h"
 
@@ -317,127 +318,21 @@ __global__ void k_lp_blocks(DeviceTables t, const double *Pbj, const float *delt
 // of the (g, g) block of A^{-1}, then theta (M_gg B_g - I).
 __global__ void __launch_bounds__(256) k_lp_targets(DeviceTables t, Workspace w, GmArgs a,
                                                     const int *nb_off, const int *nb_list,
-                                                    double theta, float *target, int *bad_out) {
+                                                    int nloc_max, double theta, float *target,
+                                                    int *bad_out) {
   extern __shared__ __align__(16) double lsm[];
   const int g = blockIdx.x;
   const IfaceInfo fg = t.iface[g];
   const int m = fg.nU + fg.nP;
   const int h0 = nb_off[g], nh = nb_off[g + 1] - h0;
   __shared__ int loc[kLpMaxNb + 1];     // local offset of each neighbourhood interface
-  __shared__ int pos_g, s_piv, s_bad;
-  if (threadIdx.x == 0) {
-    int o = 0;
-    for (int q = 0; q < nh; ++q) {
-      loc[q] = o;
-      const IfaceInfo fh = t.iface[nb_list[h0 + q]];
-      if (nb_list[h0 + q] == g) pos_g = o;
-      o += fh.nU + fh.nP;
-    }
-    loc[nh] = o;
-    s_bad = 0;
-  }
-  __syncthreads();
-  const int n = loc[nh], ld = n + m;
-  double *A = lsm;                       // [n][n + m]
-  double *Mgg = A + static_cast<size_t>(n) * ld;   // [m][m] copy of the diagonal block
-  const int pin = t.real[fg.r].pin;
-  for (int e = threadIdx.x; e < n * ld; e += blockDim.x) A[e] = 0.0;
-  __syncthreads();
-  for (int row = threadIdx.x; row < n; row += blockDim.x) {
-    int q = 0;
-    while (loc[q + 1] <= row) ++q;
-    const IfaceInfo fh = t.iface[nb_list[h0 + q]];
-    const int u = fh.unk + (row - loc[q]);
-    double *Ar = A + static_cast<size_t>(row) * ld;
-    if (u == pin) {
-      Ar[row] = 1.0;
-    } else {
-      const GmRow R = a.row[u];
-      for (int side = 0; side < 2; ++side) {
-        const double *gr = w.G + (side ? R.gR : R.gL);
-        const ColInfo *cl = t.col + (side ? R.cR : R.cL);
-        const int nc = side ? R.nR : R.nL;
-        for (int c = 0; c < nc; ++c) {
-          const int v = cl[c].unk;
-          if (v == pin) continue;
-          const int hv = t.unk_iface[v];
-          int qq = -1;
-          for (int z = 0; z < nh; ++z)
-            if (nb_list[h0 + z] == hv) {
-              qq = z;
-              break;
-            }
-          if (qq < 0) continue;
-          Ar[loc[qq] + (v - t.iface[hv].unk)] += gr[c];
-        }
-      }
-    }
-    if (row >= pos_g && row < pos_g + m) Ar[n + row - pos_g] = 1.0;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x)
-    Mgg[e] = A[static_cast<size_t>(pos_g + e / m) * ld + pos_g + e % m];
-  // forward elimination with partial pivoting
-  for (int p = 0; p < n; ++p) {
-    if (threadIdx.x < 32) {
-      double best = -1.0;
-      int bi = p;
-      for (int r = p + threadIdx.x; r < n; r += 32) {
-        const double v = fabs(A[static_cast<size_t>(r) * ld + p]);
-        if (v > best) {
-          best = v;
-          bi = r;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
-        }
-      }
-      if (threadIdx.x == 0) {
-        s_piv = bi;
-        if (!(best > 0.0) || !isfinite(best)) s_bad = 1;
-      }
-    }
-    __syncthreads();
-    if (s_bad) break;
-    const int pr = s_piv;
-    if (pr != p)
-      for (int c = threadIdx.x; c < ld; c += blockDim.x) {
-        const double tmp = A[static_cast<size_t>(p) * ld + c];
-        A[static_cast<size_t>(p) * ld + c] = A[static_cast<size_t>(pr) * ld + c];
-        A[static_cast<size_t>(pr) * ld + c] = tmp;
-      }
-    __syncthreads();
-    const double ip = 1.0 / A[static_cast<size_t>(p) * ld + p];
-    const int rows = n - p - 1, cols = ld - p - 1;
-    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-      const int r = p + 1 + e / cols, c = p + 1 + e % cols;
-      const double f = A[static_cast<size_t>(r) * ld + p] * ip;
-      A[static_cast<size_t>(r) * ld + c] -= f * A[static_cast<size_t>(p) * ld + c];
-    }
-    __syncthreads();
-  }
-  // back substitution for the m right-hand sides, column-oriented: solve
-  // row r, then remove its contribution from every row above in parallel
-  if (!s_bad)
-    for (int r = n - 1; r >= 0; --r) {
-      if (threadIdx.x < m) {
-        double *ar = A + static_cast<size_t>(r) * ld;
-        ar[n + threadIdx.x] /= ar[r];
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < r * m; e += blockDim.x) {
-        const int k = e / m, c = n + e % m;
-        A[static_cast<size_t>(k) * ld + c] -=
-            A[static_cast<size_t>(k) * ld + r] * A[static_cast<size_t>(r) * ld + c];
-      }
-      __syncthreads();
-    }
+  __shared__ int s_n, s_pos, s_piv, s_bad;
+  // A: [n][n + m], then the [m][m] copy of the diagonal block; n is known
+  // only inside the helper, so the copy goes to the end of the largest A
+  double *A = lsm;
+  double *Mgg = lsm + static_cast<size_t>(nloc_max) * (nloc_max + m);
+  nb_inverse_columns(t, w, a.row, nb_list, h0, nh, g, A, Mgg, loc, &s_n, &s_pos, &s_piv, &s_bad);
+  const int n = s_n, ld = n + m, pos_g = s_pos;
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int i = e / m, k = e % m;
     double v = 0.0;
@@ -553,7 +448,8 @@ cudaError_t lp_targets(const DeviceTables &t, const Workspace &w, const GmArgs &
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   if (t.niface == 0) return cudaSuccess;
-  k_lp_targets<<<t.niface, 256, smem, st>>>(t, w, a, nb_off, nb_list, theta, target, bad);
+  k_lp_targets<<<t.niface, 256, smem, st>>>(t, w, a, nb_off, nb_list, nloc_max, theta, target,
+                                            bad);
   return cudaGetLastError();
 }
 

@@ -84,6 +84,13 @@ struct mrcm_ctx {
   // caller's interface functions (mrcm_desc::iface_fn): rows per size
   int fn_rows16 = 0, fn_rows32 = 0;
   int *d_nb_off = nullptr, *d_nb_list = nullptr;
+  // neighbourhood preconditioner (GmArgs): its neighbourhood lists and host tables
+  bool use_nb = false;
+  std::vector<int> pnb_off, pnb_list;
+  int pnb_max = 0, pnloc_max = 0;
+  int *d_pnb_off = nullptr, *d_pnb_list = nullptr;
+  std::vector<int64_t> p_off, gw_off, gat_o;
+  std::vector<int> gw_w, pb_off, pb_list, pb_pos, gat_off, gat_g;
 };
 
 static thread_local std::string g_setup_err;
@@ -150,7 +157,7 @@ static mrcm_status validate(const mrcm_desc *d) {
     return fail(nullptr, MRCM_EINVAL, "sweep limits above 1000");
   if (d->iface_solver < MRCM_IFACE_AUTO || d->iface_solver > MRCM_IFACE_GMRES)
     return fail(nullptr, MRCM_EINVAL, "unknown interface solver %d", d->iface_solver);
-  if (d->precond < MRCM_PRECOND_BLOCK_JACOBI || d->precond > MRCM_PRECOND_NONE)
+  if (d->precond < MRCM_PRECOND_BLOCK_JACOBI || d->precond > MRCM_PRECOND_NEIGHBOURHOOD_SHARED)
     return fail(nullptr, MRCM_EINVAL, "unknown preconditioner %d", d->precond);
   if (d->gmres_restart < 0 || d->gmres_restart > kGmKmax)
     return fail(nullptr, MRCM_EINVAL, "gmres_restart must be in 0..%d", kGmKmax);
@@ -648,6 +655,103 @@ static void build_neighbourhoods(mrcm_ctx *c) {
     if (ri.s != c->s_uniform) c->s_uniform = 0;
 }
 
+// Neighbourhood lists of the preconditioner: the training-target
+// neighbourhoods, or only the interfaces sharing a subdomain with g.
+static void build_precond_neighbourhoods(mrcm_ctx *c, bool shared) {
+  if (!shared) {
+    c->pnb_off = c->nb_off;
+    c->pnb_list = c->nb_list;
+    c->pnb_max = c->nb_max;
+    c->pnloc_max = c->nloc_max;
+    return;
+  }
+  c->pnb_off.assign(1, 0);
+  c->pnb_list.clear();
+  c->pnb_max = c->pnloc_max = 0;
+  std::vector<int> nb;
+  for (const IfaceInfo &fi : c->iface) {
+    nb.clear();
+    for (int side = 0; side < 2; ++side) {
+      const SubInfo &sb = c->sub[side ? fi.R : fi.L];
+      for (int e = 0; e < 4; ++e)
+        if (sb.edge_iface[e] >= 0) nb.push_back(sb.edge_iface[e]);
+    }
+    std::sort(nb.begin(), nb.end());
+    nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+    int nloc = 0;
+    for (int h : nb) nloc += c->iface[h].nU + c->iface[h].nP;
+    c->pnb_max = std::max(c->pnb_max, static_cast<int>(nb.size()));
+    c->pnloc_max = std::max(c->pnloc_max, nloc);
+    c->pnb_list.insert(c->pnb_list.end(), nb.begin(), nb.end());
+    c->pnb_off.push_back(static_cast<int>(c->pnb_list.size()));
+  }
+}
+
+// Tables of the neighbourhood preconditioner (see GmArgs).  Both relations
+// ("a subdomain of h within one subdomain of a subdomain of g", "h and g
+// share a subdomain") are symmetric, so the blocks g' with h in N(g') are
+// N(h) itself.
+static void build_nb_tables(mrcm_ctx *c) {
+  const int nif = static_cast<int>(c->iface.size());
+  auto msz = [&](int g) { return c->iface[g].nU + c->iface[g].nP; };
+  std::vector<int> nb_loc(c->pnb_list.size(), 0);
+  c->p_off.assign(nif + 1, 0);
+  for (int g = 0; g < nif; ++g) {
+    int o = 0;
+    for (int j = c->pnb_off[g]; j < c->pnb_off[g + 1]; ++j) {
+      nb_loc[j] = o;
+      o += msz(c->pnb_list[j]);
+    }
+    c->p_off[g + 1] = c->p_off[g] + static_cast<int64_t>(o) * msz(g);
+  }
+  // for every h: the blocks g' holding h, with the P offset of h's first row
+  std::vector<std::vector<std::pair<int, int64_t>>> gl(nif);
+  for (int g = 0; g < nif; ++g)
+    for (int j = c->pnb_off[g]; j < c->pnb_off[g + 1]; ++j)
+      gl[c->pnb_list[j]].push_back({g, c->p_off[g] + static_cast<int64_t>(nb_loc[j]) * msz(g)});
+  c->gat_off.assign(1, 0);
+  c->gat_g.clear();
+  c->gat_o.clear();
+  for (int h = 0; h < nif; ++h) {
+    for (const auto &pr : gl[h]) {
+      c->gat_g.push_back(pr.first);
+      c->gat_o.push_back(pr.second);
+    }
+    c->gat_off.push_back(static_cast<int>(c->gat_g.size()));
+  }
+  // column blocks of the rows of G P: N(h) for every interface h whose
+  // unknowns are columns of g's rows (the edge interfaces of g's subdomains)
+  c->pb_off.assign(1, 0);
+  c->pb_list.clear();
+  c->pb_pos.clear();
+  c->gw_w.assign(nif, 0);
+  c->gw_off.assign(nif + 1, 0);
+  std::vector<int> blk;
+  for (int g = 0; g < nif; ++g) {
+    const IfaceInfo &fi = c->iface[g];
+    blk.clear();
+    for (int side = 0; side < 2; ++side) {
+      const SubInfo &sb = c->sub[side ? fi.R : fi.L];
+      for (int e = 0; e < 4; ++e) {
+        const int h = sb.edge_iface[e];
+        if (h < 0) continue;
+        for (int j = c->pnb_off[h]; j < c->pnb_off[h + 1]; ++j) blk.push_back(c->pnb_list[j]);
+      }
+    }
+    std::sort(blk.begin(), blk.end());
+    blk.erase(std::unique(blk.begin(), blk.end()), blk.end());
+    int w = 0;
+    for (int gp : blk) {
+      c->pb_list.push_back(gp);
+      c->pb_pos.push_back(w);
+      w += msz(gp);
+    }
+    c->pb_off.push_back(static_cast<int>(c->pb_list.size()));
+    c->gw_w[g] = w;
+    c->gw_off[g + 1] = c->gw_off[g] + static_cast<int64_t>(msz(g)) * w;
+  }
+}
+
 static bool plan_gmres_blocks(mrcm_ctx *c, int cap) {
   const int R = static_cast<int>(c->real.size());
   if (cap < R) return false;
@@ -745,6 +849,19 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     c->gm_precond = desc->precond;
     build_gmres_rows(c);
     build_neighbourhoods(c);
+    if (c->gm_precond == MRCM_PRECOND_NEIGHBOURHOOD ||
+        c->gm_precond == MRCM_PRECOND_NEIGHBOURHOOD_SHARED) {
+      build_precond_neighbourhoods(c, c->gm_precond == MRCM_PRECOND_NEIGHBOURHOOD_SHARED);
+      if (c->pnb_max > kLpMaxNb || c->pnloc_max > kLpMaxLoc) {
+        const int nl = c->pnloc_max;
+        delete c;
+        return fail(nullptr, MRCM_EINVAL,
+                    "neighbourhood preconditioner: neighbourhood of %d unknowns above %d", nl,
+                    kLpMaxLoc);
+      }
+      c->use_nb = true;
+      build_nb_tables(c);
+    }
   }
   cudaError_t e = cudaGetDevice(&c->dev);
   if (e != cudaSuccess) {
@@ -849,6 +966,20 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                o_gmint = A.take<int>(G ? 3 * d.n_real : 0),
                o_nboff = A.take<int>(G ? c->nb_off.size() : 0),
                o_nblist = A.take<int>(G ? c->nb_list.size() + 1 : 0);
+  const bool NB = G && c->use_nb;
+  const size_t o_pnboff = A.take<int>(NB ? c->pnb_off.size() : 0),
+               o_pnblist = A.take<int>(NB ? c->pnb_list.size() + 1 : 0);
+  const size_t o_nbP = A.take<double>(NB ? c->p_off.back() + 1 : 0),
+               o_nbGw = A.take<double>(NB ? c->gw_off.back() + 1 : 0),
+               o_poff = A.take<int64_t>(NB ? c->p_off.size() : 0),
+               o_gwoff = A.take<int64_t>(NB ? c->gw_off.size() : 0),
+               o_gww = A.take<int>(NB ? c->gw_w.size() : 0),
+               o_pboff = A.take<int>(NB ? c->pb_off.size() : 0),
+               o_pblist = A.take<int>(NB ? c->pb_list.size() + 1 : 0),
+               o_pbpos = A.take<int>(NB ? c->pb_pos.size() + 1 : 0),
+               o_gatoff = A.take<int>(NB ? c->gat_off.size() : 0),
+               o_gatg = A.take<int>(NB ? c->gat_g.size() + 1 : 0),
+               o_gato = A.take<int64_t>(NB ? c->gat_o.size() + 1 : 0);
   // big-slab direct path: second slab vector, inverse scratch, job lists
   const bool BG = c->use_big;
   const int bigK = c->real.empty() ? 1 : c->real[0].nslab;
@@ -950,6 +1081,24 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
       (G && (e = up(o_gmblk, c->gm_blocks.data(), c->gm_blocks.size() * sizeof(GmBlock))) !=
                 cudaSuccess) ||
       (G && (e = up(o_nboff, c->nb_off.data(), c->nb_off.size() * sizeof(int))) != cudaSuccess) ||
+      (NB && (e = up(o_pnboff, c->pnb_off.data(), c->pnb_off.size() * sizeof(int))) !=
+                 cudaSuccess) ||
+      (NB && (e = up(o_pnblist, c->pnb_list.data(), c->pnb_list.size() * sizeof(int))) !=
+                 cudaSuccess) ||
+      (NB && (e = up(o_poff, c->p_off.data(), c->p_off.size() * sizeof(int64_t))) !=
+                 cudaSuccess) ||
+      (NB && (e = up(o_gwoff, c->gw_off.data(), c->gw_off.size() * sizeof(int64_t))) !=
+                 cudaSuccess) ||
+      (NB && (e = up(o_gww, c->gw_w.data(), c->gw_w.size() * sizeof(int))) != cudaSuccess) ||
+      (NB && (e = up(o_pboff, c->pb_off.data(), c->pb_off.size() * sizeof(int))) != cudaSuccess) ||
+      (NB && (e = up(o_pblist, c->pb_list.data(), c->pb_list.size() * sizeof(int))) !=
+                 cudaSuccess) ||
+      (NB && (e = up(o_pbpos, c->pb_pos.data(), c->pb_pos.size() * sizeof(int))) != cudaSuccess) ||
+      (NB && (e = up(o_gatoff, c->gat_off.data(), c->gat_off.size() * sizeof(int))) !=
+                 cudaSuccess) ||
+      (NB && (e = up(o_gatg, c->gat_g.data(), c->gat_g.size() * sizeof(int))) != cudaSuccess) ||
+      (NB && (e = up(o_gato, c->gat_o.data(), c->gat_o.size() * sizeof(int64_t))) !=
+                 cudaSuccess) ||
       (G && (e = up(o_nblist, c->nb_list.data(), c->nb_list.size() * sizeof(int))) !=
                 cudaSuccess) ||
       (e = cudaMemset(base + o_st, 0, 4 * sizeof(int))) != cudaSuccess ||
@@ -1054,6 +1203,22 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     a.iters = a.fallback + d.n_real;
     c->d_nb_off = reinterpret_cast<int *>(base + o_nboff);
     c->d_nb_list = reinterpret_cast<int *>(base + o_nblist);
+    a.nb = 0;
+    if (NB) {
+      c->d_pnb_off = reinterpret_cast<int *>(base + o_pnboff);
+      c->d_pnb_list = reinterpret_cast<int *>(base + o_pnblist);
+      a.Pnb = reinterpret_cast<double *>(base + o_nbP);
+      a.Gw = reinterpret_cast<double *>(base + o_nbGw);
+      a.p_off = reinterpret_cast<const int64_t *>(base + o_poff);
+      a.gw_off = reinterpret_cast<const int64_t *>(base + o_gwoff);
+      a.gw_w = reinterpret_cast<const int *>(base + o_gww);
+      a.pb_off = reinterpret_cast<const int *>(base + o_pboff);
+      a.pb_list = reinterpret_cast<const int *>(base + o_pblist);
+      a.pb_pos = reinterpret_cast<const int *>(base + o_pbpos);
+      a.gat_off = reinterpret_cast<const int *>(base + o_gatoff);
+      a.gat_g = reinterpret_cast<const int *>(base + o_gatg);
+      a.gat_o = reinterpret_cast<const int64_t *>(base + o_gato);
+    }
     a.K = c->gm_K;
     a.maxit = c->gm_maxit;
     a.tol = c->gm_tol;
@@ -1285,6 +1450,19 @@ static mrcm_status solve_gmres(mrcm_ctx *ctx) {
   const int pc = ctx->gm_precond;
   if (pc == MRCM_PRECOND_USER && !ctx->gm_user_set)
     return fail(ctx, MRCM_EINVAL, "precond = MRCM_PRECOND_USER but no blocks were set");
+  if (pc == MRCM_PRECOND_NEIGHBOURHOOD || pc == MRCM_PRECOND_NEIGHBOURHOOD_SHARED) {
+    a.nb = 1;
+    a.stall = 0;
+    a.gate = 0;
+    if ((e = launch_gmres_nb(ctx->t, ctx->w, a, ctx->d_pnb_off, ctx->d_pnb_list, ctx->pnloc_max,
+                             ctx->mmax, st)) != cudaSuccess)
+      return cuda_fail(ctx, e, "neighbourhood preconditioner launch");
+    ctx->launches += 2;
+    if ((e = launch_gmres(ctx->t, ctx->w, a, ctx->gm_nblk, st)) != cudaSuccess)
+      return cuda_fail(ctx, e, "GMRES launch");
+    ctx->launches += 1;
+    return MRCM_OK;
+  }
   a.P = pc == MRCM_PRECOND_BLOCK_JACOBI ? ctx->gm_Pbj
         : pc == MRCM_PRECOND_USER       ? ctx->gm_Puser
                                         : ctx->gm_Pid;

@@ -107,6 +107,21 @@ struct GmArgs {
   int stall;         // 1: stop on a stalled residual and request the rerun
   int gate;          // 1: run only the realisations whose fallback flag is set
   double tol;
+  // neighbourhood preconditioner (nb = 1): P has, for every interface g, the
+  // column block P[N(g), g] ([n_g][m_g], rows in neighbourhood order) at
+  // p_off[g]; G P is stored wide: row i of interface g holds m_g' values for
+  // each column block g' of pb(g) (pb_list[pb_off[g] ..], pb_pos = position
+  // of the block in the row, gw_w[g] = row length), at gw_off[g] + i gw_w[g];
+  // gat lists, for every interface h, the blocks g' with h in N(g') and the
+  // P offset of h's first row in them
+  int nb;
+  double *Pnb;
+  const int64_t *p_off;
+  double *Gw;
+  const int64_t *gw_off;
+  const int *gw_w, *pb_off, *pb_list, *pb_pos;
+  const int *gat_off, *gat_g;
+  const int64_t *gat_o;
 };
 
 // learned interface preconditioner (learned.cu)
@@ -271,6 +286,9 @@ cudaError_t lp_windows(const DeviceTables &t, const double *K, const double *lam
 cudaError_t lp_blocks(const DeviceTables &t, const double *Pbj, const float *delta, double *Puser,
                       int g0, int count, int m, cudaStream_t st);
 size_t lp_targets_smem(int nloc, int m);
+cudaError_t launch_gmres_nb(const DeviceTables &t, const Workspace &w, const GmArgs &a,
+                            const int *nb_off, const int *nb_list, int nloc_max, int mmax,
+                            cudaStream_t st);
 cudaError_t launch_gmres_bj(const DeviceTables &t, const Workspace &w, const GmArgs &a, double *Pbj,
                             cudaStream_t st);
 cudaError_t lp_targets(const DeviceTables &t, const Workspace &w, const GmArgs &a,

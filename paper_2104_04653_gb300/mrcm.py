@@ -23,6 +23,7 @@ PREC_FP64, PREC_FP32_IR = 0, 1
 BASIS_LEGENDRE, BASIS_MONOMIAL = 0, 1
 IFACE_AUTO, IFACE_DIRECT, IFACE_GMRES = 0, 1, 2
 PRECOND_BLOCK_JACOBI, PRECOND_USER, PRECOND_NONE = 0, 1, 2
+PRECOND_NEIGHBOURHOOD, PRECOND_NEIGHBOURHOOD_SHARED = 3, 4
 FLAG_PRECOND_FALLBACK = 0x40
 FLAG_TIMEOUT = 0x80          # a bounded device wait ran out (MRCM_ETIMEOUT)
 STATUS_NAMES = {0: "MRCM_OK", 1: "MRCM_EINVAL", 2: "MRCM_ENOMEM", 3: "MRCM_ECUDA",

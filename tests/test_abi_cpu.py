@@ -49,7 +49,7 @@ def _desc(mrcm, nx=64, ny=32, sub=16, prec=1, nU=2, nP=2, pure=0, bct=None):
 
 
 @pytest.mark.parametrize("bad", ["nx", "sub", "prec", "nU", "pure_dirichlet", "null", "solver",
-                                 "precond", "restart"])
+                                 "precond", "precond_high", "restart"])
 def test_setup_rejects_bad_descriptors(L, bad):
     from paper_2104_04653_gb300 import mrcm
     kw = {}
@@ -67,7 +67,7 @@ def test_setup_rejects_bad_descriptors(L, bad):
         kw = dict(pure=1, bct=bt)
     ctx = ctypes.c_void_p()
     field = {"solver": ("iface_solver", 3), "precond": ("precond", -1),
-             "restart": ("gmres_restart", 65)}.get(bad)
+             "precond_high": ("precond", 5), "restart": ("gmres_restart", 65)}.get(bad)
     if bad == "null":
         st = L.mrcm_setup(None, None, ctypes.byref(ctx))
     else:
