@@ -264,6 +264,24 @@ mrcm_status mrcm_autotune(mrcm_ctx *ctx, const double *d_K, const double *d_lamb
 /* 1 if step (d) runs the GMRES path, 0 for the direct path. */
 int32_t mrcm_uses_gmres(const mrcm_ctx *ctx);
 
+/* The kernels that run step (d) in this context, fixed at mrcm_setup (the
+ * direct paths are chosen by slab size, the cluster path also by whether its
+ * shared-memory plan fits; MRCM_NO_CLUSTER=1 in the environment at setup
+ * turns the cluster path off).  -1 for a NULL context. */
+typedef enum {
+  MRCM_PATH_NONE = 0,        /* no interface unknowns (one subdomain)         */
+  MRCM_PATH_CLUSTER = 1,     /* one cluster launch per batch: slab block      */
+                             /* cyclic reduction and refinement in shared     */
+                             /* memory (FP32 factor, slabs <= 64 unknowns)    */
+  MRCM_PATH_SLAB = 2,        /* the same reduction over several launches in  */
+                             /* global memory (FP64, or FP32 if the cluster   */
+                             /* plan does not fit)                            */
+  MRCM_PATH_WIDE_SLAB = 3,   /* slabs above 64 unknowns: batched Gauss-Jordan */
+                             /* and tensor-core products                      */
+  MRCM_PATH_GMRES = 4        /* restarted FP64 GMRES                          */
+} mrcm_iface_path;
+int32_t mrcm_interface_path(const mrcm_ctx *ctx);
+
 /* Length of the preconditioner-block array: for every interface in
  * canonical order (realisations concatenated) an m x m row-major block,
  * m = nU + nP. */
@@ -301,10 +319,11 @@ int32_t mrcm_version(void);
  * Its only scratch is a fixed 1 MiB __device__ array in the library, held by
  * every GPU that loads the library until the process exits.  The first call
  * on a device looks up that array's device address, so make it before any
- * stream capture.  Every call reuses the same array and overwrites what it
+ * stream capture; a call in a new context (after cudaDeviceReset) looks it
+ * up again.  Every call reuses the same array and overwrites what it
  * reads, so calls whose kernels overlap on the GPU (e.g. on two streams)
- * race: serialise them.  nsub outside 1..64 returns MRCM_EINVAL (message from
- * mrcm_last_error(NULL)). */
+ * race: serialise them.  nsub outside 1..64, or a current device index
+ * above 63, returns MRCM_EINVAL (message from mrcm_last_error(NULL)). */
 mrcm_status mrcm_local_solve_noalloc(int32_t nsub, const double *d_kappa, const double *d_tface,
                                      const double *d_rhs, double *d_x, void *cuda_stream);
 

@@ -20,6 +20,8 @@
 #include <cstdio>
 #include <mutex>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 namespace {
@@ -34,8 +36,30 @@ constexpr int kMaxDevices = 64;
 // cudaGetSymbolAddress once per device.
 static __device__ __align__(256) float g_noalloc_W[kNoAllocMaxSub * kS * kN];
 
+// Per device: the array's device address and the context it was looked up
+// in.  A device reset (cudaDeviceReset) destroys the primary context and the
+// module with it; the next context may place the array elsewhere, so the
+// address is looked up again whenever the current context differs.
 float *g_sym[kMaxDevices] = {};
+CUcontext g_sym_ctx[kMaxDevices] = {};
 std::mutex g_sym_mu;
+
+// The current driver context, through the runtime's driver entry point (the
+// library does not link the driver library); null if unavailable.
+CUcontext current_context() {
+  static PFN_cuCtxGetCurrent_v4000 get = nullptr;
+  if (!get) {
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return nullptr;
+    get = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+  }
+  CUcontext ctx = nullptr;
+  return get(&ctx) == CUDA_SUCCESS ? ctx : nullptr;
+}
 
 __device__ __forceinline__ float shflf(float v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
@@ -202,18 +226,27 @@ extern "C" mrcm_status mrcm_local_solve_noalloc(int32_t nsub, const double *d_ka
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (e != cudaSuccess) {
     snprintf(msg, sizeof msg, "mrcm_local_solve_noalloc: cudaGetDevice: %s",
              cudaGetErrorString(e));
     mrcm::set_global_error(msg);
     return MRCM_ECUDA;
   }
+  if (dev < 0 || dev >= kMaxDevices) {
+    snprintf(msg, sizeof msg,
+             "mrcm_local_solve_noalloc: device index %d outside 0..%d (per-device table size)",
+             dev, kMaxDevices - 1);
+    mrcm::set_global_error(msg);
+    return MRCM_EINVAL;
+  }
   float *W = nullptr;
   {
-    // first call on this device: look up the device address of the scratch
-    // array (must happen before any stream capture of this entry point)
+    // first call on this device (or in a new context after a device reset):
+    // look up the device address of the scratch array; this must happen
+    // before any stream capture of this entry point
     std::lock_guard<std::mutex> lk(g_sym_mu);
-    if (!g_sym[dev]) {
+    const CUcontext ctx = current_context();
+    if (!g_sym[dev] || !ctx || ctx != g_sym_ctx[dev]) {
       void *ptr = nullptr;
       e = cudaGetSymbolAddress(&ptr, g_noalloc_W);
       if (e != cudaSuccess || !ptr) {
@@ -223,6 +256,7 @@ extern "C" mrcm_status mrcm_local_solve_noalloc(int32_t nsub, const double *d_ka
         return MRCM_ECUDA;
       }
       g_sym[dev] = static_cast<float *>(ptr);
+      g_sym_ctx[dev] = current_context();
     }
     W = g_sym[dev];
   }
