@@ -1571,6 +1571,15 @@ int64_t mrcm_num_gamma_values(const mrcm_ctx *ctx) { return ctx ? ctx->gam_elems
 
 int32_t mrcm_uses_gmres(const mrcm_ctx *ctx) { return ctx && ctx->use_gmres ? 1 : 0; }
 
+int32_t mrcm_interface_path(const mrcm_ctx *ctx) {
+  if (!ctx) return -1;
+  if (ctx->nunk == 0) return MRCM_PATH_NONE;
+  if (ctx->use_gmres) return MRCM_PATH_GMRES;
+  if (ctx->use_big) return MRCM_PATH_WIDE_SLAB;
+  if (ctx->cluster_k > 0) return MRCM_PATH_CLUSTER;
+  return MRCM_PATH_SLAB;
+}
+
 int64_t mrcm_num_precond_values(const mrcm_ctx *ctx) { return ctx ? ctx->tsc_elems : 0; }
 
 mrcm_status mrcm_set_precond_blocks(mrcm_ctx *ctx, const double *d_blocks) {

@@ -24,6 +24,8 @@ BASIS_LEGENDRE, BASIS_MONOMIAL = 0, 1
 IFACE_AUTO, IFACE_DIRECT, IFACE_GMRES = 0, 1, 2
 PRECOND_BLOCK_JACOBI, PRECOND_USER, PRECOND_NONE = 0, 1, 2
 PRECOND_NEIGHBOURHOOD, PRECOND_NEIGHBOURHOOD_SHARED = 3, 4
+PATH_NONE, PATH_CLUSTER, PATH_SLAB, PATH_WIDE_SLAB, PATH_GMRES = 0, 1, 2, 3, 4
+PATH_NAMES = {0: "none", 1: "cluster", 2: "slab", 3: "wide-slab", 4: "gmres"}
 FLAG_PRECOND_FALLBACK = 0x40
 FLAG_TIMEOUT = 0x80          # a bounded device wait ran out (MRCM_ETIMEOUT)
 STATUS_NAMES = {0: "MRCM_OK", 1: "MRCM_EINVAL", 2: "MRCM_ENOMEM", 3: "MRCM_ECUDA",
@@ -36,7 +38,7 @@ EXPORTED = ["mrcm_setup", "mrcm_factor_local", "mrcm_build_basis", "mrcm_solve_i
             "mrcm_copy_interface_solution", "mrcm_destroy", "mrcm_last_error", "mrcm_version",
             "mrcm_local_solve_noalloc", "mrcm_uses_gmres", "mrcm_num_precond_values",
             "mrcm_set_precond_blocks", "mrcm_set_basis_width", "mrcm_autotune",
-            "mrcm_set_gravity"]
+            "mrcm_set_gravity", "mrcm_interface_path"]
 
 
 class MrcmDesc(ctypes.Structure):
@@ -116,6 +118,8 @@ def lib(path: Optional[Path] = None):
     L.mrcm_local_solve_noalloc.restype = i32
     L.mrcm_uses_gmres.argtypes = [vp]
     L.mrcm_uses_gmres.restype = i32
+    L.mrcm_interface_path.argtypes = [vp]
+    L.mrcm_interface_path.restype = i32
     L.mrcm_num_precond_values.argtypes = [vp]
     L.mrcm_num_precond_values.restype = i64
     L.mrcm_set_precond_blocks.argtypes = [vp, dp]
@@ -276,6 +280,11 @@ class Mrcm:
 
     def uses_gmres(self) -> bool:
         return bool(self.L.mrcm_uses_gmres(self.ctx))
+
+    def interface_path(self) -> str:
+        """The step-(d) kernels of this context: "none", "cluster", "slab",
+        "wide-slab" or "gmres" (mrcm_interface_path)."""
+        return PATH_NAMES[int(self.L.mrcm_interface_path(self.ctx))]
 
     def num_precond_values(self) -> int:
         return int(self.L.mrcm_num_precond_values(self.ctx))

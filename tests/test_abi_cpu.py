@@ -86,6 +86,7 @@ def test_calls_on_null_context_fail_cleanly(L):
     assert L.mrcm_build_basis(None, None) == mrcm.MRCM_EINVAL
     assert L.mrcm_solve_interface(None, None) == mrcm.MRCM_EINVAL
     assert L.mrcm_reconstruct(None, None, None, None, None) == mrcm.MRCM_EINVAL
+    assert L.mrcm_interface_path(None) == -1
     L.mrcm_destroy(None)
 
 

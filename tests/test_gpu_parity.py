@@ -37,17 +37,19 @@ def _run(prob, prec, gamma=False, opts=None):
     p, ux, uy = s.solve(Kd, Ld, Qd, gamma_u=g)
     info = s.mrcm_get_info()
     out = dict(p=p.cpu().numpy(), ux=ux.cpu().numpy(), uy=uy.cpu().numpy(), info=info,
-               x=s.interface_solution().cpu().numpy())
+               x=s.interface_solution().cpu().numpy(), path=s.interface_path())
     if gamma:
         out["gamma"] = g.cpu().numpy()
     s.close()
     return out
 
 
-def _check(prob, prec, tol=TOL, gamma=True):
+def _check(prob, prec, tol=TOL, gamma=True, path=None):
     O, mrcm, W = _mods()
     ref = O.mrcm_solve(prob)
     got = _run(prob, prec, gamma=gamma)
+    if path is not None:
+        assert got["path"] == path, (got["path"], path)
     ep, eu = O.errors(got, ref)
     assert ep <= tol and eu <= tol, (prob.name, prec, ep, eu, got["info"])
     if gamma:
@@ -272,13 +274,33 @@ def test_refinement_limit_reports_stall():
 @pytest.mark.parametrize("path", ["cluster", "multi-kernel"])
 def test_interface_paths_agree(path, monkeypatch):
     """The one-launch cluster interface solve and the multi-kernel global
-    memory one both meet the tolerance on the bench workload."""
+    memory one both meet the tolerance on the bench workload, and the
+    context reports the one that ran."""
     O, mrcm, W = _mods()
     if path == "multi-kernel":
         monkeypatch.setenv("MRCM_NO_CLUSTER", "1")
     else:
         monkeypatch.delenv("MRCM_NO_CLUSTER", raising=False)
-    _check(W.config2(), 1)
+    _check(W.config2(), 1, path="slab" if path == "multi-kernel" else "cluster")
+
+
+@pytest.mark.parametrize("case,prec,path", [("channels", 0, "slab"), ("channels", 1, "cluster"),
+                                             ("resolve-256", 1, "wide-slab"),
+                                             ("single", 1, "none")])
+def test_interface_path_query(case, prec, path, monkeypatch):
+    """mrcm_interface_path names the step-(d) kernels chosen at setup: FP64
+    runs the multi-kernel slab reduction (its tiles do not fit one cluster),
+    FP32 the cluster kernel, slabs above 64 unknowns the wide-slab path, and
+    a single subdomain has no interface system."""
+    import torch
+    O, mrcm, W = _mods()
+    monkeypatch.delenv("MRCM_NO_CLUSTER", raising=False)
+    prob = {"channels": W.config2, "resolve-256": lambda: W.config5(2, n=256),
+            "single": lambda: W.make_problem(16, 16, 16, np.ones((16, 16)),
+                                             bc=W.bc_left_right(16, 16), n_u=2, n_p=2)}[case]()
+    s = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=prec))
+    assert s.interface_path() == path
+    s.close()
 
 
 @pytest.mark.parametrize("case", ["direct-fp64", "direct-mixed", "mixed-sizes", "wide-slabs",
