@@ -56,74 +56,14 @@ def _solve(prob, prec):
     return p.cpu().numpy(), ux.cpu().numpy(), uy.cpu().numpy(), x, info
 
 
-def _local_solution(O, prob, r, lay, kappa, x, I, J):
-    """Pressures of subdomain (I, J) from the Robin data of x, and, per
-    interface edge, the outward velocity and face pressure traces."""
-    lo = O.Local(prob, r, lay, I, J, kappa)
-    rhs = lo.b0.copy()
-    data = {}
-    for side, (g, sigma) in lo.edges.items():
-        f = lay.ifaces[g]
-        gd = O.robin_data(f, sigma, lo.beta[side], x)
-        data[side] = gd
-        rhs += lo.robin_rhs(side, gd)
-    p = O.solve_local(lo.A, rhs[:, None], refine=True)[:, 0]
-    s, h = lay.s, lay.h
-    tr = {}
-    for side, gd in data.items():
-        pc = np.array([p[O.edge_face_cell(side, e, s)[1] * s + O.edge_face_cell(side, e, s)[0]]
-                       for e in range(s)])
-        u = lo.TR[side] * (pc - gd) / h
-        tr[side] = (u, gd + lo.beta[side] * u)
-    return p.reshape(s, s), tr
-
-
 def _sampled_checks(prob, p, x, rng, n_sub=6, n_if=6):
-    O, mrcm, W = _mods()
-    off = 0
-    worst_p = worst_d = 0.0
-    for r in range(prob.n_real):
-        lay = O.Layout(prob, r)
-        s = lay.s
-        kappa = prob.lam[r] * prob.K[r]
-        xr = x[off:off + lay.n_unknowns]
-        off += lay.n_unknowns
-        corners = [(0, 0), (lay.Sx - 1, 0), (0, lay.Sy - 1), (lay.Sx - 1, lay.Sy - 1),
-                   (lay.Sx // 2, lay.Sy // 2)]
-        subs = corners + [(int(rng.integers(lay.Sx)), int(rng.integers(lay.Sy)))
-                          for _ in range(max(0, n_sub - len(corners)))]
-        for I, J in subs:
-            pl, _ = _local_solution(O, prob, r, lay, kappa, xr, I, J)
-            pg = p[r, J * s:(J + 1) * s, I * s:(I + 1) * s]
-            e = np.linalg.norm(pg - pl) / max(np.linalg.norm(pl), 1e-300)
-            worst_p = max(worst_p, e)
-        for g in rng.choice(len(lay.ifaces), size=min(n_if, len(lay.ifaces)), replace=False):
-            f = lay.ifaces[int(g)]
-            Ls, Rs = ("E", "W") if f["kind"] == "V" else ("N", "S")
-            _, trL = _local_solution(O, prob, r, lay, kappa, xr, *f["L"])
-            _, trR = _local_solution(O, prob, r, lay, kappa, xr, *f["R"])
-            (uL, pfL), (uR, pfR) = trL[Ls], trR[Rs]
-            h = lay.h
-            for k in range(f["nU"]):          # pressure continuity, tested by phi_k
-                d = h * np.dot(f["phi"][k], pfL - pfR)
-                sc = h * np.dot(np.abs(f["phi"][k]), np.abs(pfL) + np.abs(pfR))
-                worst_d = max(worst_d, abs(d) / max(sc, 1e-300))
-            for k in range(f["nP"]):          # flux continuity, tested by psi_k
-                d = h * np.dot(f["psi"][k], uL + uR)
-                sc = h * np.dot(np.abs(f["psi"][k]), np.abs(uL) + np.abs(uR))
-                worst_d = max(worst_d, abs(d) / max(sc, 1e-300))
-    return worst_p, worst_d
+    from oracle import sampled as S
+    return S.sampled_checks(prob, p, x, rng, n_sub=n_sub, n_if=n_if)
 
 
 def _global_balance(prob, ux, uy):
-    h = prob.h
-    worst = 0.0
-    for r in range(prob.n_real):
-        src = float(prob.q[r].sum()) * h * h
-        out = (ux[r][:, -1].sum() - ux[r][:, 0].sum() + uy[r][-1, :].sum() - uy[r][0, :].sum()) * h
-        scale = max(abs(src), float(np.abs(ux[r][:, 0]).sum() * h), 1e-300)
-        worst = max(worst, abs(src - out) / scale)
-    return worst
+    from oracle import sampled as S
+    return S.global_balance(prob, ux, uy)
 
 
 def test_interface_solution_order_matches_oracle():
