@@ -8,6 +8,17 @@ from a CUDA graph with inputs resident in HBM.  The workload (0.4 MB) fits in
 L2, so L2 is flushed (a 256 MB write) before every timed step; only the step
 itself is inside the CUDA events.  Prints one JSON line.
 
+The same line carries, under "batched", the batched workload: 32 lognormal
+realisations of 1024 x 1024 cells (16 x 16-cell subdomains in the first 16,
+32 x 32 in the rest, 2 to 8 unknowns per interface), timed the same way
+(whole solve as one CUDA graph, inputs in HBM; its 2.4 GB of inputs and
+outputs exceed L2), with its own FP64 path, roofline, e2e and CPU baseline,
+checked against the oracle on sampled outputs.
+
+A value is reported only when the accuracy check passed: relative L2 error
+<= 1e-8 in p and u against the oracle (headline), sampled pressures and
+continuity defects <= 1e-10 and global balance <= 1e-8 (batched).
+
 --impl reference times the FP64 CPU oracle on the same workload instead.
 """
 from __future__ import annotations
@@ -27,6 +38,12 @@ if str(ROOT) not in sys.path:
 
 METRIC = "fine cells/s of MRCM Darcy solve, mixed vs FP64 GPU, at rel L2 err ≤1e-8"
 WORKLOAD = "channels-256x64 binary K 1e3/1e-3, 16x16 subdomains (64), m=8 per interface (864 unknowns)"
+BATCH_WORKLOAD = ("lognormal-32x1024x1024 sigma^2=3, 16x16 subdomains (r<16) and 32x32 (r>=16), "
+                  "m in {2,4,6,8} per interface")
+ACC_TOL = 1e-8            # relative L2 in p and u against the oracle (the metric's bound)
+SAMPLE_P_TOL = 1e-10      # batched: sampled subdomain pressures (relative)
+SAMPLE_DEFECT_TOL = 1e-10 # batched: sampled interface continuity defects (relative)
+BALANCE_TOL = 1e-8        # batched: global mass balance
 
 
 def _dist():
@@ -290,6 +307,225 @@ def _time_calls(solver, K, L, Q, out, steps, flush, torch):
     res = {}
     for i, n in enumerate(names):
         res[n] = statistics.median(r[i].elapsed_time(r[i + 1]) * 1e-3 for r in recs)
+    res["_steps"] = [r[0].elapsed_time(r[4]) * 1e-3 for r in recs]
+    return res
+
+
+def _e2e(inbuf, outbuf, graph, steps, warmup, flush, torch):
+    """Mean time of a step that copies the inputs in from pinned host memory,
+    replays the solve and copies p, ux, uy back (one copy each way: the
+    buffers are contiguous), all inside CUDA events; warm-up steps first."""
+    hin = inbuf.cpu().pin_memory()
+    hout = torch.empty(outbuf.shape, dtype=outbuf.dtype).pin_memory()
+    st = torch.cuda.current_stream()
+
+    def step():
+        inbuf.copy_(hin, non_blocking=True)
+        graph.replay()
+        hout.copy_(outbuf, non_blocking=True)
+
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        step()
+        b.record(st)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    t = statistics.mean(a.elapsed_time(b) * 1e-3 for a, b in evs)
+    return t, hin.numel() * hin.element_size(), hout.numel() * hout.element_size()
+
+
+def _survey_roofline(prob, solver, step_s, peaks, src, clocks):
+    """The whole step against the scope table's own counts (perfmodel.
+    survey_work): 40 B per cell of HBM traffic over the step time against the
+    HBM peak, and the banded factor + solve flops over the step time against
+    the FP32 SIMT peak."""
+    from paper_2104_04653_gb300 import perfmodel
+    w = perfmodel.survey_work(prob, solver)
+    sm_mhz = (clocks or {}).get("sm_mhz") or 1900.0
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    simt = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    gbs = w["path_bytes"] / step_s / 1e9
+    tfl = w["flops"] / step_s / 1e12
+    return {"path_hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "bytes_per_step": w["path_bytes"], "peak_source": f"{src} HBM copy"},
+            "path_flops": {"achieved": tfl, "peak": simt, "unit": "TFLOP/s", "frac": tfl / simt,
+                           "flops_per_step": w["flops"], "local_sweeps": w["sweeps"],
+                           "peak_source": f"FP32 SIMT at the sampled {sm_mhz:.0f} MHz"},
+            "per_unit": w["per_unit"]}
+
+
+def _batch_sample_problems():
+    """The batched workload's CPU sample: the lower-left 384 x 384 window of
+    realisation 0 (16 x 16-cell subdomains) and of realisation 16 (32 x 32)."""
+    import numpy as np
+    from paper_2104_04653_gb300 import workloads as W
+    out = []
+    for r in (0, 16):
+        K, s, m = W.config3_realisation(r, 32, 1024, 3.0)
+        t, v = W.bc_left_right(1024, 1024)
+        one = W.Problem(nx=1024, ny=1024, ly=1.0, sub_size=[s], K=K[None], lam=np.ones((1,) + K.shape),
+                        q=np.zeros((1,) + K.shape), bc_type=t, bc_val=v,
+                        iface_nU=[(m // 2).astype(np.int32)], iface_nP=[(m // 2).astype(np.int32)],
+                        name=f"lognormal-1024x1024 r={r}")
+        out.append(W.window(one, 0, 384))
+    return out
+
+
+def _oracle_batch_worker(reps: int):
+    """Times the oracle as it stands on the batched workload's sample."""
+    from oracle import mrcm_oracle as O
+    probs = _batch_sample_problems()
+    cells, secs = 0, 0.0
+    for _ in range(reps):
+        for p in probs:
+            t0 = time.perf_counter()
+            O.mrcm_solve(p)
+            secs += time.perf_counter() - t0
+            cells += p.cells()
+    return {"cells": cells, "secs": secs}
+
+
+def cpu_baseline_batch(all_cores: bool):
+    n = _host_cores() if all_cores else 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench._oracle_batch_worker(1)))" % str(ROOT))
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=env, cwd=str(ROOT))
+             for _ in range(n)]
+    total = 0.0
+    for p in procs:
+        try:
+            out, err = p.communicate(timeout=900)
+        except subprocess.TimeoutExpired:
+            p.kill()
+            out, err = p.communicate()
+        if p.returncode != 0:
+            return {"value": None, "unit": "cells/s", "cores": n, "kind": "oracle",
+                    "sample": "failed: " + (err.strip().splitlines() or [""])[-1][:200]}
+        d = json.loads(out.strip().splitlines()[-1])
+        total += d["cells"] / d["secs"]
+    what = ("one process" if n == 1 else f"{n} concurrent single-threaded processes, each")
+    return {"value": total, "unit": "cells/s", "cores": n, "kind": "oracle",
+            "sample": f"{what} solving the 384x384 lower-left windows of realisations 0 "
+                      f"(16x16 subdomains) and 16 (32x32) of the batch, numpy/scipy FP64, "
+                      f"1 thread each"}
+
+
+def run_batched(args, flush, torch, ws, rank, local):
+    """The batched workload: mixed path timed as CUDA-graph replays, FP64
+    path by per-call events (its graph replay matches the eager sum within
+    0.1%), e2e through pinned host buffers, accuracy on sampled outputs."""
+    import numpy as np
+    from paper_2104_04653_gb300 import mrcm, workloads as W
+    from oracle import sampled as S
+    t_gen = time.time()
+    prob = W.config3(workers=min(16, _host_cores()))
+    gen_s = time.time() - t_gen
+    cells = prob.cells()
+    inbuf, (K, L, Q) = _packed(mrcm.device_inputs(prob), torch)
+    opts = mrcm.SolverOptions(prec=mrcm.PREC_FP32_IR, iface_tol=1e-11)
+    s = mrcm.Mrcm(prob, opts)
+    widths = s.mrcm_autotune(K, L, Q, reps=2)
+    outbuf, out = _packed(s.alloc_outputs(), torch)
+    s.solve(K, L, Q, out=out)
+    info = s.mrcm_get_info(check=False)
+    g = _capture(s, K, L, Q, out, torch)
+    for _ in range(3):
+        flush.zero_()
+        g.replay()
+    torch.cuda.synchronize()
+    nb = max(3, args.steps // 40)
+    clock = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clock.start()
+    time.sleep(0.3)
+    t_mixed = _time_graph(g, nb, flush, torch)
+    torch.cuda.synchronize()
+    clocks = clock.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    tot = _max_over_ranks(sum(t_mixed), ws, "cuda")
+    value = _job_value(cells, nb, ws, tot)
+    ms = 1e3 * tot / nb
+    calls = _time_calls(s, K, L, Q, out, 3, flush, torch)
+    calls.pop("_steps")
+    launches = s.launch_count()
+    e2e_t, h2d, d2h = _e2e(inbuf, outbuf, g, 2, 1, flush, torch)
+    e2e_t = _max_over_ranks(e2e_t, ws, "cuda")
+    # accuracy on sampled outputs (oracle building blocks, FP64)
+    p, ux, uy = (t_.cpu().numpy() for t_ in out)
+    x = s.interface_solution().cpu().numpy()
+    rng = np.random.default_rng(2024)
+    wp, wd = S.sampled_checks(prob, p, x, rng, n_sub=6, n_if=6, reals=[0, 16])
+    bal = S.global_balance(prob, ux, uy)
+    ok = (wp <= SAMPLE_P_TOL and wd <= SAMPLE_DEFECT_TOL and bal <= BALANCE_TOL
+          and info["flags"] == 0 and info["iface_resid"] <= 1e-10)
+    peaks, src = measured_peaks()
+    dom = max(calls, key=calls.get)
+    roof = roofline_entry(dom, calls[dom], prob, s, peaks, src, clocks)
+    roof.pop("algorithmic", None)
+    survey = _survey_roofline(prob, s, ms * 1e-3, peaks, src, clocks)
+    path = s.interface_path()
+    del g
+    s.close()
+    del out, outbuf
+    torch.cuda.empty_cache()
+    # FP64 path on the same inputs: one warm-up solve, then two timed steps
+    s64 = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=mrcm.PREC_FP64, iface_tol=1e-11))
+    s64.mrcm_set_basis_width(*widths)
+    out64 = s64.alloc_outputs()
+    s64.solve(K, L, Q, out=out64)
+    info64 = s64.mrcm_get_info(check=False)
+    c64 = _time_calls(s64, K, L, Q, out64, 2, flush, torch)
+    fp64_ms = 1e3 * _max_over_ranks(statistics.mean(c64.pop("_steps")), ws, "cuda")
+    p64 = out64[0].cpu().numpy()
+    x64 = s64.interface_solution().cpu().numpy()
+    wp64, wd64 = S.sampled_checks(prob, p64, x64, np.random.default_rng(2024), n_sub=6, n_if=6,
+                                  reals=[0, 16])
+    s64.close()
+    del out64, K, L, Q, inbuf
+    torch.cuda.empty_cache()
+    res = {
+        "workload": BATCH_WORKLOAD, "cells_per_step": cells, "value": value if ok else None,
+        "unit": "cells/s", "steps": nb, "warmup": 3, "ms_per_step": ms,
+        "interface_path": path, "interface_unknowns": int(sum(
+            int(np.sum(prob.iface_nU[r] + prob.iface_nP[r])) for r in range(prob.n_real))),
+        "basis_width_autotuned": {"s16": widths[0], "s32": widths[1]},
+        "l2": "inputs and outputs (2.4 GB) larger than L2; flushed (256 MB write) as well",
+        "fp64_path": {"value": cells * ws / (fp64_ms * 1e-3), "ms_per_step": fp64_ms,
+                      "calls_ms": {k: v * 1e3 for k, v in c64.items()},
+                      "timing": "per-call CUDA events, eager launches, 2 steps after 1 warm-up",
+                      "accuracy": {"sampled_p": wp64, "sampled_defect": wd64}},
+        "speedup_vs_fp64": fp64_ms / ms,
+        "speedup_per_call": {k: c64[k] / calls[k] for k in calls},
+        "calls_ms": {k: v * 1e3 for k, v in calls.items()},
+        "accuracy": {"valid": bool(ok), "sampled_p": wp, "sampled_defect": wd,
+                     "global_balance": bal, "iface_resid": info["iface_resid"],
+                     "local_resid_max": info["local_resid_max"], "flags": info["flags"],
+                     "fp64_iface_resid": info64["iface_resid"],
+                     "how": "realisations 0 and 16: 6 subdomains re-solved by the oracle from the "
+                            "GPU's interface solution, 6 interfaces' continuity defects; global "
+                            "balance over all 32"},
+        "roofline": roof, "survey_roofline": survey,
+        "e2e": {"value": cells * ws / e2e_t, "unit": "cells/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * nb,
+        "clocks": clocks, "generation_s": gen_s,
+    }
+    if ws == 1 and rank == 0 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline_batch(False)
+        res["cpu_baseline"]["all_cores"] = cpu_baseline_batch(True)
     return res
 
 
@@ -309,13 +545,25 @@ def run_gpu(args):
     # K, lambda, q (and below each solver's p, ux, uy) as views of one
     # contiguous buffer, so the end-to-end run moves each direction in one copy
     inbuf, (K, L, Q) = _packed(mrcm.device_inputs(prob), torch)
-    opts = {"fp32_ir": mrcm.SolverOptions(prec=mrcm.PREC_FP32_IR),
-            "fp64": mrcm.SolverOptions(prec=mrcm.PREC_FP64)}
+    # fp32_ir: the headline (one-launch cluster interface kernel); fp64: the
+    # plain FP64 path (its slab tiles do not fit one cluster, so it runs the
+    # multi-kernel reduction); fp32_ir_slab: the mixed path forced onto that
+    # same multi-kernel reduction, so that fp64 / fp32_ir_slab compares
+    # precision alone
+    opts = {"fp32_ir": (mrcm.SolverOptions(prec=mrcm.PREC_FP32_IR), False),
+            "fp64": (mrcm.SolverOptions(prec=mrcm.PREC_FP64), False),
+            "fp32_ir_slab": (mrcm.SolverOptions(prec=mrcm.PREC_FP32_IR), True)}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     results = {}
     widths = {}
-    for name, o in opts.items():
+    for name, (o, no_cluster) in opts.items():
+        prev = os.environ.pop("MRCM_NO_CLUSTER", None)
+        if no_cluster:
+            os.environ["MRCM_NO_CLUSTER"] = "1"
         s = mrcm.Mrcm(prob, o)
+        os.environ.pop("MRCM_NO_CLUSTER", None)
+        if prev is not None:
+            os.environ["MRCM_NO_CLUSTER"] = prev
         if args.basis_width:
             w16, w32 = (int(v) for v in args.basis_width.split(","))
             s.mrcm_set_basis_width(w16, w32)
@@ -331,9 +579,10 @@ def run_gpu(args):
             g.replay()
         torch.cuda.synchronize()
         results[name] = dict(solver=s, graph=g, out=out, outbuf=outbuf, info=info,
-                             launches=s.launch_count())
+                             launches=s.launch_count(), path=s.interface_path())
     # accuracy against the oracle (computed once on the host)
     acc = {}
+    acc_ok = True
     if rank == 0 and not args.no_accuracy:
         from oracle import mrcm_oracle as O
         ref = O.mrcm_solve(prob)
@@ -341,6 +590,7 @@ def run_gpu(args):
             p, ux, uy = (t.cpu().numpy() for t in r["out"])
             ep, eu = O.errors(dict(p=p, ux=ux, uy=uy), ref)
             acc[name] = {"p": ep, "u": eu}
+            acc_ok = acc_ok and ep <= ACC_TOL and eu <= ACC_TOL
     # timed region: mixed path (the headline), clocks sampled meanwhile
     clock = ClockSampler(local)
     if ws > 1:
@@ -352,81 +602,89 @@ def run_gpu(args):
     torch.cuda.synchronize()
     clocks = clock.stop()
     t_fp64 = _time_graph(results["fp64"]["graph"], max(args.steps // 4, 3), flush, torch)
+    t_slab = _time_graph(results["fp32_ir_slab"]["graph"], max(args.steps // 4, 3), flush, torch)
     if ws > 1:
         torch.distributed.barrier()
     tot = _max_over_ranks(sum(t_mixed), ws, "cuda")
     value = _job_value(cells, args.steps, ws, tot)
     ms = 1e3 * tot / args.steps
     fp64_ms = 1e3 * _max_over_ranks(statistics.mean(t_fp64), ws, "cuda")
+    slab_ms = 1e3 * _max_over_ranks(statistics.mean(t_slab), ws, "cuda")
     # per-call breakdown (eager) and the dominant kernel's roofline
     s = results["fp32_ir"]["solver"]
     calls = _time_calls(s, K, L, Q, results["fp32_ir"]["out"], 30, flush, torch)
     calls64 = _time_calls(results["fp64"]["solver"], K, L, Q, results["fp64"]["out"], 10, flush,
                           torch)
-    # e2e: K, lambda, q from pinned host memory and p, ux, uy back to it (one
-    # copy each way: the buffers are contiguous), the graph between them, all
-    # inside the timed region; warm-up steps first, as for the device loop
-    hin = inbuf.cpu().pin_memory()
-    outbuf = results["fp32_ir"]["outbuf"]
-    hout = torch.empty(outbuf.shape, dtype=outbuf.dtype).pin_memory()
-    st = torch.cuda.current_stream()
-    e2e_steps = max(args.steps // 4, 3)
-
-    def e2e_step():
-        inbuf.copy_(hin, non_blocking=True)
-        results["fp32_ir"]["graph"].replay()
-        hout.copy_(outbuf, non_blocking=True)
-
-    for _ in range(args.warmup):
-        flush.zero_()
-        e2e_step()
-    torch.cuda.synchronize()
-    evs = []
-    for _ in range(e2e_steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        e2e_step()
-        b.record(st)
-        evs.append((a, b))
-    torch.cuda.synchronize()
-    e2e_t = _max_over_ranks(statistics.mean(a.elapsed_time(b) * 1e-3 for a, b in evs), ws, "cuda")
-    h2d = hin.numel() * hin.element_size()
-    d2h = hout.numel() * hout.element_size()
-    if rank != 0:
-        return
+    calls_slab = _time_calls(results["fp32_ir_slab"]["solver"], K, L, Q,
+                             results["fp32_ir_slab"]["out"], 10, flush, torch)
+    for c in (calls, calls64, calls_slab):
+        c.pop("_steps")
+    e2e_t, h2d, d2h = _e2e(inbuf, results["fp32_ir"]["outbuf"], results["fp32_ir"]["graph"],
+                           max(args.steps // 4, 3), args.warmup, flush, torch)
+    e2e_t = _max_over_ranks(e2e_t, ws, "cuda")
     peaks, src = measured_peaks()
     dom = max(calls, key=calls.get)
     roof = roofline_entry(dom, calls[dom], prob, s, peaks, src, clocks)
     all_roofs = {c: roofline_entry(c, calls[c], prob, s, peaks, src, clocks) for c in calls}
     for v in all_roofs.values():
         v.pop("algorithmic", None)
+    survey = _survey_roofline(prob, s, ms * 1e-3, peaks, src, clocks)
+    launches = results["fp32_ir"]["launches"]
+    infos = {k: r["info"] for k, r in results.items()}
+    paths = {k: r["path"] for k, r in results.items()}
+    for r in results.values():
+        del r["graph"]
+        r["solver"].close()
+    del results, inbuf, K, L, Q
+    torch.cuda.empty_cache()
+    batched = None
+    if not args.no_batch:
+        batched = run_batched(args, flush, torch, ws, rank, local)
+    if rank != 0:
+        return
+    valid = acc_ok and not args.no_accuracy
     line = {
-        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64-refine", "data": "synthetic",
+        "metric": METRIC, "value": value if valid else None, "unit": "cells/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64-refine", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": "FP32 factors/solves, FP64 refinement",
                    "parallelism": f"replicas x{ws}", "l2": "flushed (256 MB write) before each step",
                    "graph": "CUDA graph replay",
                    "basis_width": {k: {"s16": v[0], "s32": v[1]} for k, v in widths.items()},
                    "basis_width_autotuned": not args.basis_width},
         "fp64_path": {"value": cells * ws / (fp64_ms * 1e-3), "ms_per_step": fp64_ms,
+                      "interface_path": paths["fp64"],
                       "calls_ms": {k: v * 1e3 for k, v in calls64.items()}},
         "speedup_vs_fp64": fp64_ms / ms,
+        "speedup_per_call": {k: calls64[k] / calls[k] for k in calls},
+        "mixed_same_kernels_as_fp64": {
+            "ms_per_step": slab_ms, "interface_path": paths["fp32_ir_slab"],
+            "calls_ms": {k: v * 1e3 for k, v in calls_slab.items()},
+            "speedup_vs_fp64": fp64_ms / slab_ms,
+            "note": "the mixed path on the FP64 path's multi-kernel interface reduction: "
+                    "the speedup from precision alone"},
+        "interface_path": paths["fp32_ir"],
         "rel_err_vs_oracle": acc,
+        "accuracy": {"valid": bool(valid), "tol": ACC_TOL,
+                     "checked": not args.no_accuracy},
         "calls_ms": {k: v * 1e3 for k, v in calls.items()},
-        "solver_info": {k: {kk: vv for kk, vv in r["info"].items()} for k, r in results.items()},
+        "solver_info": infos,
         "roofline": roof,
         "calls_roofline": all_roofs,
+        "survey_roofline": survey,
         "e2e": {"value": cells * ws / e2e_t, "unit": "cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": results["fp32_ir"]["launches"] * args.steps,
+        "gpu_launches": launches * args.steps,
         "clocks": clocks,
     }
+    if batched is not None:
+        line["batched"] = batched
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
         line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores()
     print(json.dumps(line), flush=True)
+    if not valid:
+        sys.exit(1 if not args.no_accuracy else 0)
 
 
 # DRAM traffic per launch from the committed ncu capture (profiles/
@@ -657,6 +915,7 @@ def run_suite(args):
             s.solve(K, L, Q, out=out)
             info = s.mrcm_get_info(check=False)
             calls = _time_calls(s, K, L, Q, out, args.suite_steps, flush, torch)
+            calls.pop("_steps")
             tot = sum(calls.values())
             g = _capture(s, K, L, Q, out, torch)          # the whole solve as one CUDA graph
             for _ in range(2):
@@ -687,7 +946,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="mrcm", choices=["mrcm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the accuracy check (the line then carries no value)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="leave out the batched 32 x 1024^2 workload")
     ap.add_argument("--basis-width", default="",
                     help="N16,N32: basis-kernel RHS columns per CTA instead of autotuning "
                          "(profiling runs that must launch only the timed configuration)")
@@ -701,6 +963,21 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    ws_env = os.environ.get("WORLD_SIZE")
+    if ws_env is None and args.gpus > 1:
+        # one process per GPU: run this same command under torch.distributed.run
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+               f"--nproc-per-node={args.gpus}", "--master-addr", "127.0.0.1",
+               "--master-port", str(port), str(Path(__file__).resolve()), *sys.argv[1:]]
+        sys.exit(subprocess.call(cmd))
+    if ws_env is not None and int(ws_env) != args.gpus:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={ws_env}; launch one process per GPU "
+              f"with --nproc-per-node equal to --gpus", file=sys.stderr)
+        sys.exit(2)
     if args.suite:
         run_suite(args)
     elif args.impl == "reference":

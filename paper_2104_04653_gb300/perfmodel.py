@@ -30,24 +30,34 @@ def _ncols(prob, r=0):
     return cols
 
 
+def _sizes_and_cols(prob):
+    """(subdomain edge s, basis columns) of every subdomain of the batch."""
+    out = []
+    for r in range(prob.n_real):
+        s = prob.sub_size[r]
+        out += [(s, c) for c in _ncols(prob, r)]
+    return out
+
+
 def call_work(call: str, prob, solver=None) -> dict:
-    s = prob.sub_size[0]
-    n = s * s
+    subs = _sizes_and_cols(prob)
     R = prob.n_real
-    cols = [c for r in range(R) for c in _ncols(prob, r)]
-    nsub = len(cols)
     info = solver.mrcm_get_info(check=False) if solver is not None else {}
     sweeps = 1 + int(info.get("local_sweeps_max", 0) or 0)
     if call == "factor_local":
-        flops = 2.0 * nsub * s ** 4            # s Gauss-Jordan inverses of s x s blocks
-        byts = nsub * n * (16 + 48) + nsub * s ** 3 * 4
-        return {"kernel": "k_factor", "bound": "alu", "flops": flops, "bytes": byts,
+        flops = sum(2.0 * s ** 4 for s, _ in subs)    # s Gauss-Jordan inverses of s x s blocks
+        byts = sum(s * s * (16 + 48) + s ** 3 * 4 for s, _ in subs)
+        sizes = sorted({sz for sz, _ in subs})
+        kern = " + ".join({16: "k_factor", 32: "k_factor_warp"}[sz] for sz in sizes)
+        return {"kernel": kern, "bound": "alu", "flops": flops, "bytes": float(byts),
                 "per_unit": "2 s^4 flop per subdomain (s block inverses of s^3 FMA)"}
     if call == "build_basis":
-        solve = 2.0 * (2 * s - 1) * s * s      # 2s-1 block steps of an s x s matvec
-        flops = sweeps * solve * sum(cols)
-        byts = sum(c * n * 8 for c in cols) + nsub * (s ** 3 * 4 + 6 * n * 8)
-        return {"kernel": "k_basis", "bound": "alu", "flops": flops, "bytes": byts,
+        # 2s-1 block steps of an s x s matvec per column and sweep
+        flops = sum(sweeps * 2.0 * (2 * s - 1) * s * s * c for s, c in subs)
+        byts = sum(c * s * s * 8 + s ** 3 * 4 + 6 * s * s * 8 for s, c in subs)
+        sizes = sorted({sz for sz, _ in subs})
+        kern = " + ".join({16: "k_basis", 32: "k_basis32"}[sz] for sz in sizes)
+        return {"kernel": kern, "bound": "alu", "flops": flops, "bytes": float(byts),
                 "sweeps": sweeps,
                 "per_unit": "(1 + refinement sweeps) x 2 (2s-1) s^2 flop per basis column"}
     if call == "solve_interface":
@@ -99,7 +109,11 @@ def call_work(call: str, prob, solver=None) -> dict:
             solve = 2.0 * b * b * (4 * (K - 1) + 1)
             tot_f64 += sweeps * 2.0 * terms
             tot_f32 += max(sweeps - 1, 0) * solve
-        return {"kernel": "k_iface_cluster", "bound": "alu", "flops": tot_f32 + tot_f64,
+        path = solver.interface_path() if solver is not None else "cluster"
+        kern = {"cluster": "k_iface_cluster", "slab": "k_bcr_level + k_iface_solve",
+                "wide-slab": "k_gj_* + k_tc_gemm_tma + k_big_solve", "gmres": "k_gmres",
+                "none": "-"}[path]
+        return {"kernel": kern, "bound": "alu", "flops": tot_f32 + tot_f64,
                 "flops_fp32": tot_f32, "flops_fp64": tot_f64,
                 "bytes": float(sum(int(np.sum(np.asarray(prob.iface_nU[r]) +
                                               np.asarray(prob.iface_nP[r]))) for r in range(R)) * 8),
@@ -107,7 +121,30 @@ def call_work(call: str, prob, solver=None) -> dict:
                             "surviving slab (three GEMMs per side); per sweep 2 flop per FP64 "
                             "residual term and 2 b^2 per slab matvec"}
     if call == "reconstruct":
-        byts = sum(c * n * 8 for c in cols) + prob.cells() * 8 * 3
+        byts = sum(c * s * s * 8 for s, c in subs) + prob.cells() * 8 * 3
         return {"kernel": "k_recon_cells", "bound": "hbm", "flops": 0.0, "bytes": float(byts),
                 "per_unit": "basis columns read once (8 B per column per cell) + p, ux, uy"}
     raise ValueError(call)
+
+
+def survey_work(prob, solver=None) -> dict:
+    """The method's work per solve counted as the scope table of the build
+    counts it (banded work, not the dense blocks the kernels use): factor
+    n s^2 = s^4 flop per subdomain; solve 4 n s flop per right-hand side and
+    sweep (a forward and a backward banded substitution); 40 B per cell of
+    HBM traffic for the whole path (K and lambda in, p, ux and uy out);
+    7 m^2 x 12 B per interface for one interface SpMV (block-sparse, at most
+    seven m x m blocks per block row: 8 B value + 4 B index)."""
+    info = solver.mrcm_get_info(check=False) if solver is not None else {}
+    sweeps = 1 + int(info.get("local_sweeps_max", 0) or 0)
+    subs = _sizes_and_cols(prob)
+    factor = sum(float(s) ** 4 for s, _ in subs)
+    solve = sum(sweeps * 4.0 * s * s * s * c for s, c in subs)
+    spmv = 0.0
+    for r in range(prob.n_real):
+        m = np.asarray(prob.iface_nU[r]) + np.asarray(prob.iface_nP[r])
+        spmv += float(np.sum(7.0 * m.astype(np.float64) ** 2 * 12.0))
+    return {"factor_flops": factor, "solve_flops": solve, "flops": factor + solve,
+            "path_bytes": 40.0 * prob.cells(), "iface_spmv_bytes": spmv, "sweeps": sweeps,
+            "per_unit": "factor s^4 per subdomain; solve 4 n s per RHS per sweep; 40 B per cell; "
+                        "7 m^2 x 12 B per interface per SpMV"}

@@ -279,24 +279,63 @@ def config2(nx: int = 256, ny: int = 64, s: int = 16, n_fn: int = 4,
                         name=f"channels-{nx}x{ny}-s{s}-m{2 * n_fn}")
 
 
-def config3(n_real: int = 32, n: int = 1024, variance: float = 3.0) -> Problem:
-    """Lognormal realisations; r < n_real/2 use 16x16 subdomains, the rest
-    32x32; each interface draws its total size m from {2,4,6,8}."""
+def config3_realisation(r: int, n_real: int, n: int, variance: float):
+    """Field, subdomain size and interface sizes of realisation r of
+    config3 (its own seed, so realisations can be drawn in any order)."""
     h = 1.0 / n
-    Ks, subs, nus, nps = [], [], [], []
-    for r in range(n_real):
-        rng = np.random.default_rng(1000 * 3 + r)
-        Ks.append(np.exp(grf_exponential(n, n, h, variance, 0.1, rng)))
-        s = 16 if r < n_real // 2 else 32
-        subs.append(s)
-        m = rng.choice(np.array([2, 4, 6, 8], np.int32), size=n_interfaces(n, n, s))
-        nus.append((m // 2).astype(np.int32))
-        nps.append((m // 2).astype(np.int32))
-    K = np.stack(Ks)
+    rng = np.random.default_rng(1000 * 3 + r)
+    K = np.exp(grf_exponential(n, n, h, variance, 0.1, rng))
+    s = 16 if r < n_real // 2 else 32
+    m = rng.choice(np.array([2, 4, 6, 8], np.int32), size=n_interfaces(n, n, s))
+    return K, s, m
+
+
+def config3(n_real: int = 32, n: int = 1024, variance: float = 3.0,
+            workers: int = 1) -> Problem:
+    """Lognormal realisations; r < n_real/2 use 16x16 subdomains, the rest
+    32x32; each interface draws its total size m from {2,4,6,8}.  With
+    workers > 1 the realisations are drawn by that many spawned processes
+    (same values: every realisation has its own seed)."""
+    if workers > 1 and n_real > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=min(workers, n_real),
+                                 mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(config3_realisation, range(n_real), [n_real] * n_real,
+                                [n] * n_real, [variance] * n_real))
+    else:
+        parts = [config3_realisation(r, n_real, n, variance) for r in range(n_real)]
+    K = np.stack([p[0] for p in parts])
+    subs = [p[1] for p in parts]
+    nus = [(p[2] // 2).astype(np.int32) for p in parts]
+    nps = [(p[2] // 2).astype(np.int32) for p in parts]
     t, v = bc_left_right(n, n)
     return Problem(nx=n, ny=n, ly=1.0, sub_size=subs, K=K, lam=np.ones_like(K),
                    q=np.zeros_like(K), bc_type=t, bc_val=v, iface_nU=nus, iface_nP=nps,
                    name=f"lognormal-{n_real}x{n}x{n}-s16/32-m2..8")
+
+
+def window(prob: Problem, r: int, n: int) -> Problem:
+    """Realisation r of prob cut to its lower-left n x n cells (n a multiple
+    of its subdomain size), with the same subdomain size, the interface
+    sizes of the interfaces it keeps, and left-to-right boundary data: a
+    sample of the workload at a size the CPU oracle solves in seconds."""
+    s = prob.sub_size[r]
+    if n % s or n > prob.nx or n > prob.ny:
+        raise ValueError("window must be a multiple of the subdomain size")
+    sx, sy = prob.nx // s, prob.ny // s
+    wx = wy = n // s
+    nV = (sx - 1) * sy
+    ids = [J * (sx - 1) + I for J in range(wy) for I in range(wx - 1)]
+    ids += [nV + J * sx + I for J in range(wy - 1) for I in range(wx)]
+    ids = np.asarray(ids, np.int64)
+    t, v = bc_left_right(n, n)
+    ly = n * prob.h
+    return Problem(nx=n, ny=n, ly=ly, sub_size=[s], K=prob.K[r:r + 1, :n, :n].copy(),
+                   lam=prob.lam[r:r + 1, :n, :n].copy(), q=prob.q[r:r + 1, :n, :n].copy(),
+                   bc_type=t, bc_val=v, iface_nU=[prob.iface_nU[r][ids]],
+                   iface_nP=[prob.iface_nP[r][ids]], basis=prob.basis,
+                   name=f"{prob.name}[r={r}, {n}x{n} window]")
 
 
 def config4(n: int = 2048, s: int = 32, n_ch: int = 64, seed: int = 4000) -> Problem:

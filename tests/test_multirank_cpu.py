@@ -73,3 +73,14 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     assert bench.run_reference(A()) is None
     assert capsys.readouterr().out == ""
+
+
+def test_gpus_flag_must_match_the_world_size():
+    """bench.py --gpus N under a launcher with another WORLD_SIZE refuses to
+    run instead of reporting the wrong n_gpus."""
+    import subprocess
+    env = dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0")
+    res = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--gpus", "2", "--steps", "1"],
+                         capture_output=True, text=True, env=env, cwd=str(ROOT), timeout=120)
+    assert res.returncode == 2, (res.returncode, res.stderr[-500:])
+    assert "WORLD_SIZE=1" in res.stderr
