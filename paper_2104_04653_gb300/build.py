@@ -19,7 +19,7 @@ INCLUDE = HERE.parent / "include"
 LIBDIR = HERE / "_lib"
 LIB = LIBDIR / "libmrcm.so"
 SOURCES = ["mrcm_abi.cu", "local.cu", "iface.cu", "iface_cluster.cu", "iface_gmres.cu", "recon.cu",
-           "noalloc.cu", "learned.cu", "iface_big.cu", "tc_gemm.cu"]
+           "noalloc.cu", "learned.cu", "iface_big.cu", "tc_gemm.cu", "transport.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -141,3 +141,29 @@ def test_seeded_random_descriptors_fail_cleanly(L):
         else:
             L.mrcm_destroy(ctx)
     assert mrcm.MRCM_EINVAL in seen
+
+
+@pytest.mark.parametrize("bad", ["grid", "M", "mu_w", "s_in", "eta", "newton", "real"])
+def test_transport_rejects_bad_descriptors(L, bad):
+    """mrcm_transport_create validates its descriptor on the host."""
+    from paper_2104_04653_gb300 import mrcm, transport as TP
+    TP.lib()
+    d = TP.TransportDesc()
+    d.nx, d.ny, d.n_real, d.ly, d.M, d.mu_w, d.s_in = 16, 16, 1, 1.0, 10.0, 1.0, 1.0
+    setattr(d, *{"grid": ("nx", 0), "M": ("M", -1.0), "mu_w": ("mu_w", 0.0),
+                 "s_in": ("s_in", 1.5), "eta": ("eta", -1.0), "newton": ("max_newton", -2),
+                 "real": ("n_real", 0)}[bad])
+    h = ctypes.c_void_p()
+    assert L.mrcm_transport_create(ctypes.byref(d), None, ctypes.byref(h)) == mrcm.MRCM_EINVAL
+    assert not h.value
+    assert L.mrcm_transport_last_error()
+
+
+def test_transport_calls_on_null_context_fail_cleanly(L):
+    from paper_2104_04653_gb300 import mrcm, transport as TP
+    TP.lib()
+    assert L.mrcm_transport_step(None, 0.1, None, None, None, None, None, None) == mrcm.MRCM_EINVAL
+    assert L.mrcm_transport_get_info(None, None, None) == mrcm.MRCM_EINVAL
+    assert L.mrcm_si_step(None, None, 0.1, *([None] * 8)) == mrcm.MRCM_EINVAL
+    assert L.mrcm_sfi_step(None, None, 0.1, 1e-4, 5, *([None] * 9), None) == mrcm.MRCM_EINVAL
+    L.mrcm_transport_destroy(None)
