@@ -207,8 +207,9 @@ def test_trained_network_gain(capsys):
     """Train on 32 seeded 256^2 channel systems (contrast 1e6, 32 x 32-cell
     subdomains, m = 4), then on a held-out system: the network predicts the
     held-out targets far better than zero (block-Jacobi), the solve with its
-    blocks meets the oracle, and GMRES needs a small fraction of the steps
-    it takes without a preconditioner.  Block-Jacobi's steps are reported."""
+    blocks meets the oracle, GMRES needs a small fraction of the steps it
+    takes without a preconditioner, and -- the measured relation, which the
+    network does not improve on -- no more than 1.3 times block-Jacobi's."""
     import torch
     C, O, LP, mrcm, W = _mods()
     train_p = [W.config4(n=256, s=32, n_ch=8, seed=5000 + k) for k in range(32)]
@@ -245,5 +246,13 @@ def test_trained_network_gain(capsys):
     with capsys.disabled():
         print(f"\n[learned preconditioner] held-out loss {val:.3f} (zero {zero:.3f}); "
               f"GMRES steps to 1e-12: {iters}")
+    # What the trained network does today, asserted as measured: it does
+    # NOT beat block-Jacobi (256 against 210 steps on this held-out system;
+    # a block-diagonal correction has little to gain here and the network's
+    # error spoils it), but its blocks keep GMRES within 1.3 times
+    # block-Jacobi's steps and an order of magnitude under no preconditioner.
+    # The neighbourhood preconditioner (tests/test_gpu_nbprecond.py) is the
+    # form that beats block-Jacobi.
     assert iters["learned"] * 10 <= iters["none"], iters
+    assert iters["learned"] <= 1.3 * iters["block_jacobi"], iters
     net.close()
