@@ -69,6 +69,9 @@ class Problem:
     # per realisation [ny, nx]: the gravity velocity K lambda_g g of Eq.
     # "Darcy_wg" (along +y, the direction of the height h); None: no gravity
     grav: Optional[list] = None
+    # per realisation [ny/B][nx/B] int8 (B = sub_size[r]): a nonzero block is
+    # split into four (B/2) x (B/2) subdomains (quadtree); None: uniform
+    refine: Optional[list] = None
     pure_neumann: bool = False
     basis: str = "legendre"           # interface function family
     name: str = ""
@@ -359,6 +362,84 @@ def config5(step: int, n: int = 512, s: int = 16, M: float = 5.0) -> Problem:
                      name=f"bl-front-{n}x{n}-s{s}-step{step}")
     p.meta["saturation"] = sat
     return p
+
+
+def quadtree_interface_lengths(nx: int, ny: int, B: int, refine) -> List[int]:
+    """Face counts of the interfaces of a quadtree layout in canonical
+    order (vertical by (y0, x), then horizontal by (y, x0)): B between two
+    unsplit blocks, B/2 wherever a split block takes part.  Layout only."""
+    ref = np.asarray(refine, bool).reshape(ny // B, nx // B)
+    h2 = B // 2
+    # owner block at (B/2)-resolution: (block, quadrant) or (block, -1)
+    own = np.empty((ny // h2, nx // h2), dtype=object)
+    for j in range(ny // h2):
+        for i in range(nx // h2):
+            bj, bi = j // 2, i // 2
+            own[j, i] = (bj, bi, (j % 2) * 2 + (i % 2)) if ref[bj, bi] else (bj, bi, -1)
+    vert, horiz = [], []
+    for i in range(1, nx // h2):
+        j = 0
+        while j < ny // h2:
+            L, R = own[j, i - 1], own[j, i]
+            if L == R:
+                j += 1
+                continue
+            j1 = j
+            while j1 < ny // h2 and own[j1, i - 1] == L and own[j1, i] == R:
+                j1 += 1
+            vert.append((j * h2, i * h2, (j1 - j) * h2))
+            j = j1
+    for j in range(1, ny // h2):
+        i = 0
+        while i < nx // h2:
+            L, R = own[j - 1, i], own[j, i]
+            if L == R:
+                i += 1
+                continue
+            i1 = i
+            while i1 < nx // h2 and own[j - 1, i1] == L and own[j, i1] == R:
+                i1 += 1
+            horiz.append((j * h2, i * h2, (i1 - i) * h2))
+            i = i1
+    vert.sort()
+    horiz.sort()
+    return [v[2] for v in vert] + [hz[2] for hz in horiz]
+
+
+def quadtree_problem(nx, ny, B, K, refine, lam=None, q=None, bc=None, n_u=2, n_p=2,
+                     m_choices=None, seed=0, name="quadtree") -> Problem:
+    """Realisations of nx x ny cells in B x B blocks, each block split into
+    four (B/2)-subdomains where refine[r] is nonzero.  Interface sizes: n_u
+    and n_p, or (m_choices) a seeded total m per interface, nU = nP = m/2."""
+    K = np.asarray(K, np.float64)
+    if K.ndim == 2:
+        K = K[None]
+    R = K.shape[0]
+    lam = np.ones_like(K) if lam is None else np.asarray(lam, np.float64).reshape(K.shape)
+    q = np.zeros_like(K) if q is None else np.asarray(q, np.float64).reshape(K.shape)
+    if bc is None:
+        bc = bc_left_right(nx, ny)
+    rng = np.random.default_rng(seed)
+    nus, nps, refs = [], [], []
+    for r in range(R):
+        ref = np.asarray(refine[r], np.int8).reshape(ny // B, nx // B)
+        refs.append(ref)
+        L = quadtree_interface_lengths(nx, ny, B, ref)
+        if m_choices is None:
+            nus.append(np.full(len(L), n_u, np.int32))
+            nps.append(np.full(len(L), n_p, np.int32))
+        else:
+            m = rng.choice(np.asarray(m_choices, np.int32), size=len(L))
+            nus.append((m // 2).astype(np.int32))
+            nps.append((m // 2).astype(np.int32))
+    return Problem(nx=nx, ny=ny, ly=1.0, sub_size=[B] * R, K=K, lam=lam, q=q,
+                   bc_type=np.asarray(bc[0], np.int8), bc_val=np.asarray(bc[1], np.float64),
+                   iface_nU=nus, iface_nP=nps, refine=refs, name=name)
+
+
+def random_refinement(nx, ny, B, frac, rng) -> np.ndarray:
+    """A seeded refinement mask with about frac of the blocks split."""
+    return (rng.random((ny // B, nx // B)) < frac).astype(np.int8)
 
 
 def gpu_arrays(p: Problem):
