@@ -153,6 +153,21 @@ typedef struct {
                              /* functions, s face-midpoint values each, along */
                              /* +y (vertical) or +x (horizontal interfaces);  */
                              /* e.g. the physics-based spaces of Section 3    */
+  const int8_t *refine;      /* NULL: uniform subdomains.  Else, for every    */
+                             /* realisation, (ny/s) x (nx/s) entries (s =     */
+                             /* sub_size[r], row-major): a nonzero 32 x 32    */
+                             /* block is split into four 16 x 16 subdomains   */
+                             /* (a one-level quadtree, Section 3's            */
+                             /* decomposition with two sizes).  Interfaces    */
+                             /* are then the maximal runs of faces shared by  */
+                             /* the same two subdomains (32 or 16 faces: half */
+                             /* an edge next to a split block), vertical ones */
+                             /* by (first row, x) then horizontal ones by     */
+                             /* (y, first column), normal +x / +y, and        */
+                             /* beta = alpha H / kappa takes H = the          */
+                             /* interface's length.  Such a context solves    */
+                             /* step (d) by GMRES (block-Jacobi or none);     */
+                             /* pure-Neumann problems and gravity are refused */
 } mrcm_desc;
 
 typedef struct {

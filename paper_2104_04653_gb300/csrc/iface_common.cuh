@@ -28,15 +28,13 @@ __device__ __forceinline__ RowRef row_ref(const DeviceTables &t, const Workspace
                                           const IfaceInfo &fi, int i) {
   const SubInfo &L = t.sub[fi.L];
   const SubInfo &R = t.sub[fi.R];
-  const int eL = fi.kind == 0 ? kEdgeE : kEdgeN;
-  const int eR = fi.kind == 0 ? kEdgeW : kEdgeS;
   RowRef rr;
   rr.ncL = L.ncols;
   rr.ncR = R.ncols;
-  rr.gL = w.G + L.g_off + static_cast<int64_t>(L.edge_row[eL] + i) * L.ncols;
-  rr.gR = w.G + R.g_off + static_cast<int64_t>(R.edge_row[eR] + i) * R.ncols;
-  rr.colL = L.edge_col[eL] + i;
-  rr.colR = R.edge_col[eR] + i;
+  rr.gL = w.G + L.g_off + static_cast<int64_t>(fi.rowL + i) * L.ncols;
+  rr.gR = w.G + R.g_off + static_cast<int64_t>(fi.rowR + i) * R.ncols;
+  rr.colL = fi.colL + i;
+  rr.colR = fi.colR + i;
   rr.offL = L.col_off;
   rr.offR = R.col_off;
   return rr;

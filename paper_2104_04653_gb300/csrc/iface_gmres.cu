@@ -69,13 +69,10 @@ __global__ void __launch_bounds__(32 * kBjWarps) k_gm_bj(DeviceTables t, Workspa
   const int ipin = pin_in(fi, t.real[fi.r].pin);
   double(*Ab)[2 * kGmMmax + 1] = aug[wid];
   const SubInfo L = t.sub[fi.L], R = t.sub[fi.R];
-  const int eL = fi.kind == 0 ? kEdgeE : kEdgeN, eR = fi.kind == 0 ? kEdgeW : kEdgeS;
   if (lane < m) {
     const int i = lane;
-    const double *gl = w.G + L.g_off + static_cast<int64_t>(L.edge_row[eL] + i) * L.ncols +
-                       L.edge_col[eL];
-    const double *gr = w.G + R.g_off + static_cast<int64_t>(R.edge_row[eR] + i) * R.ncols +
-                       R.edge_col[eR];
+    const double *gl = w.G + L.g_off + static_cast<int64_t>(fi.rowL + i) * L.ncols + fi.colL;
+    const double *gr = w.G + R.g_off + static_cast<int64_t>(fi.rowR + i) * R.ncols + fi.colR;
     for (int k = 0; k < m; ++k) {
       double v = gl[k] + gr[k];
       if (i == ipin || k == ipin) v = (i == k) ? 1.0 : 0.0;
@@ -140,8 +137,9 @@ __global__ void __launch_bounds__(128) k_gm_gprime(DeviceTables t, Workspace w, 
   for (int e = threadIdx.x; e < sb.nrows * nc; e += blockDim.x) {
     const int row = e / nc, c = 1 + e % nc;
     const ColInfo ci = t.col[sb.col_off + c];
-    const IfaceInfo fi = t.iface[sb.edge_iface[ci.edge]];
-    const int m = fi.nU + fi.nP, c0 = sb.edge_col[ci.edge], k = c - c0;
+    const IfaceInfo fi = t.iface[t.unk_iface[ci.unk]];
+    const int m = fi.nU + fi.nP, c0 = fi.L == static_cast<int>(blockIdx.x) ? fi.colL : fi.colR,
+              k = c - c0;
     const int ipin = pin_in(fi, pin);
     const double *Pg = P + fi.tsc_off;
     const double *gr = G + static_cast<int64_t>(row) * sb.ncols + c0;

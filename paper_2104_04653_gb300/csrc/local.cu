@@ -33,12 +33,6 @@ constexpr int kS = 16;      // subdomain edge of the shared-memory-resident kern
 constexpr int kCoefStride = 6 * kS * kS + 4 * kS;
 static_assert(kCoefStride % 2 == 0, "coefficient blocks are staged as 16-byte vectors");
 
-// interface-function rows of subdomain size S (IfaceInfo::fnU / fnP index them)
-template <int S>
-__device__ __forceinline__ const double *fn_table(const DeviceTables &t) {
-  return t.fnval + (S == 16 ? 0 : t.fn_off32);
-}
-
 __device__ __forceinline__ void atomic_max_pos_double(double *addr, double v) {
   // valid for v >= 0: IEEE order of non-negative doubles matches their bits
   if (!(v >= 0.0)) v = 1e300;
@@ -84,9 +78,10 @@ template <int S>
 __device__ __forceinline__ double edge_face_T(const DeviceTables &t, const SubInfo &sb, double kc,
                                               int a, int b, int side) {
   if (sb.edge_iface[side] >= 0) {
-    const int e = (side < 2) ? b : a;
-    const double al = t.alpha[t.iface[sb.edge_iface[side]].alpha_off + e];
-    return kc / (al * static_cast<double>(S) + 0.5);
+    // H / h is the length of the face's interface (S without refinement)
+    const FaceIface fi = face_iface(sb, side, (side < 2) ? b : a);
+    const double al = t.alpha[t.iface[fi.g].alpha_off + fi.e];
+    return kc / (al * static_cast<double>(fi.len) + 0.5);
   }
   const int gi = sb.x0 + a, gj = sb.y0 + b;
   int k;
@@ -273,12 +268,13 @@ __device__ __forceinline__ void write_beta(const DeviceTables &t, const SubInfo 
                                            int a, int b, double *coef) {
   constexpr int N = S * S;
   const bool onface[4] = {a == 0, a == S - 1, b == 0, b == S - 1};
-  const double H = S * t.h;
 #pragma unroll
   for (int side = 0; side < 4; ++side) {
     if (!onface[side] || sb.edge_iface[side] < 0) continue;
     const int e = (side < 2) ? b : a;
-    const double al = t.alpha[t.iface[sb.edge_iface[side]].alpha_off + e];
+    const FaceIface fi = face_iface(sb, side, e);   // H = the interface's length
+    const double H = fi.len * t.h;
+    const double al = t.alpha[t.iface[fi.g].alpha_off + fi.e];
     coef[6 * N + side * S + e] = al * H / kc;
   }
 }
@@ -473,9 +469,11 @@ __device__ __forceinline__ double rhs_value(const DeviceTables &t, const SubInfo
     const int side = ci.edge;
     const bool adj = (side == kEdgeW && a == 0) || (side == kEdgeE && a == S - 1) ||
                      (side == kEdgeS && b == 0) || (side == kEdgeN && b == S - 1);
-    if (adj) {
-      const int e = (side < 2) ? b : a;
-      const double fv = fn_table<S>(t)[ci.fn * S + e];
+    const int e = (side < 2) ? b : a;
+    const FaceIface fi = face_iface(sb, side, e);
+    // the column's data lives on the faces of its own interface only
+    if (adj && fi.g == t.unk_iface[ci.unk]) {
+      const double fv = iface_fn_at(t, fi.len, ci.fn, fi.e);
       double gval;
       if (ci.is_u) {
         const double beta = coef[6 * N + side * S + e];
@@ -505,10 +503,10 @@ __device__ __forceinline__ void traces_and_rows(const DeviceTables &t, const Wor
   constexpr int N = S * S;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const double h = t.h, inv_h = t.inv_h;
-  const double *fnt = fn_table<S>(t);
   for (int q = tid; q < 4 * S * nc; q += nthr) {
     const int side = q / (S * nc), e = (q / nc) % S, c = q % nc;
     if (sb.edge_iface[side] < 0) continue;
+    const FaceIface fe = face_iface(sb, side, e);
     int la, lb;
     if (side == kEdgeW) { la = 0; lb = e; }
     else if (side == kEdgeE) { la = S - 1; lb = e; }
@@ -519,8 +517,8 @@ __device__ __forceinline__ void traces_and_rows(const DeviceTables &t, const Wor
     const double beta = coef[6 * N + side * S + e];
     const ColInfo ci = col[c];
     double ge = 0.0;
-    if (ci.edge == side) {
-      const double fv = fnt[ci.fn * S + e];
+    if (ci.edge == side && fe.g == t.unk_iface[ci.unk]) {
+      const double fv = iface_fn_at(t, fe.len, ci.fn, fe.e);
       const double sigma = (side == kEdgeE || side == kEdgeN) ? 1.0 : -1.0;
       ge = ci.is_u ? -beta * sigma * fv : fv;
     }
@@ -537,22 +535,31 @@ __device__ __forceinline__ void traces_and_rows(const DeviceTables &t, const Wor
   const int nrow = sb.nrows;
   for (int pr = tid; pr < nrow * nc; pr += nthr) {
     const int row = pr / nc, c = pr % nc;
-    int side = 0;
-    while (side < 3 && !(sb.edge_iface[side] >= 0 && row >= sb.edge_row[side] &&
-                         row < sb.edge_row[side] + t.iface[sb.edge_iface[side]].nU +
-                                   t.iface[sb.edge_iface[side]].nP))
-      ++side;
-    const IfaceInfo &fr = t.iface[sb.edge_iface[side]];
-    const int nU = fr.nU;
-    const int k = row - sb.edge_row[side];
+    // the interface (segment) whose rows hold this row: edge side, half hf
+    int side = 0, hf = 0;
+    for (int q = 0; q < 8; ++q) {
+      const int sd = q >> 1, hh = q & 1;
+      const int g = hh ? sb.edge_iface2[sd] : sb.edge_iface[sd];
+      if (g < 0) continue;
+      const int r0 = hh ? sb.edge_row2[sd] : sb.edge_row[sd];
+      if (row >= r0 && row < r0 + t.iface[g].nU + t.iface[g].nP) {
+        side = sd;
+        hf = hh;
+        break;
+      }
+    }
+    const IfaceInfo &fr = t.iface[hf ? sb.edge_iface2[side] : sb.edge_iface[side]];
+    const int nU = fr.nU, len = fr.s, e0 = hf ? len : 0;
+    const int k = row - (hf ? sb.edge_row2[side] : sb.edge_row[side]);
     const bool urow = k < nU;
-    const double *fn = fnt + (urow ? fr.fnU + k : fr.fnP + k - nU) * S;
+    const double *fn = t.fnval + (len == 16 ? 0 : t.fn_off32) +
+                       static_cast<int64_t>(urow ? fr.fnU + k : fr.fnP + k - nU) * len;
     double acc = 0.0;
     if (urow) {
-      for (int e = 0; e < S; ++e) acc += fn[e] * sp[side][e][c];
+      for (int e = 0; e < len; ++e) acc += fn[e] * sp[side][e0 + e][c];
       acc *= (side == kEdgeE || side == kEdgeN) ? h : -h;
     } else {
-      for (int e = 0; e < S; ++e) acc += fn[e] * su[side][e][c];
+      for (int e = 0; e < len; ++e) acc += fn[e] * su[side][e0 + e][c];
       acc *= h;
     }
     G[static_cast<int64_t>(row) * sb.ncols + c0 + c] = acc;

@@ -5,6 +5,7 @@
 #include "../../include/mrcm.h"
 #include "../../include/mrcm_learned.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -66,6 +67,7 @@ struct mrcm_ctx {
   bool use_gmres = false;
   // direct path with slabs above 64 unknowns
   bool use_big = false;
+  bool quad = false;                       // some realisation has a quadtree layout
   std::vector<int> big_lev_off;
   std::vector<InvJob> big_inv;
   std::vector<GemmJob> big_gemm;
@@ -139,6 +141,102 @@ static void fn_table(int family, int s, std::vector<double> &out) {
   }
 }
 
+// Quadtree realisation (mrcm_desc.refine): the subdomains (sorted by
+// (y0, x0)) and the interface segments in canonical order -- vertical ones
+// by (first row, x line), then horizontal ones by (y line, first column);
+// L is the subdomain on the -x / -y side.  A segment is a maximal run of
+// faces shared by the same two subdomains.
+struct QSub {
+  int x0, y0, s;
+};
+struct QSeg {
+  int kind, fx, fy, len, L, R;   // L, R: indices into the realisation's subdomains
+};
+
+static int64_t refine_entries(const mrcm_desc &d, int r) {
+  const int B = d.sub_size[r];
+  return static_cast<int64_t>(d.nx / B) * (d.ny / B);
+}
+
+static bool is_quad(const mrcm_desc &d, int r, int64_t ref_off) {
+  if (!d.refine) return false;
+  for (int64_t k = 0; k < refine_entries(d, r); ++k)
+    if (d.refine[ref_off + k]) return true;
+  return false;
+}
+
+static void quad_layout(const mrcm_desc &d, int r, int64_t ref_off, std::vector<QSub> &subs,
+                        std::vector<QSeg> &segs) {
+  const int B = d.sub_size[r], bx = d.nx / B, by = d.ny / B, q = B / 2;
+  subs.clear();
+  segs.clear();
+  for (int BJ = 0; BJ < by; ++BJ)
+    for (int BI = 0; BI < bx; ++BI) {
+      if (d.refine[ref_off + static_cast<int64_t>(BJ) * bx + BI]) {
+        for (int j = 0; j < 2; ++j)
+          for (int i = 0; i < 2; ++i) subs.push_back(QSub{BI * B + i * q, BJ * B + j * q, q});
+      } else {
+        subs.push_back(QSub{BI * B, BJ * B, B});
+      }
+    }
+  std::sort(subs.begin(), subs.end(), [](const QSub &a, const QSub &b) {
+    return a.y0 != b.y0 ? a.y0 < b.y0 : a.x0 < b.x0;
+  });
+  const int mx = d.nx / q, my = d.ny / q;
+  std::vector<int> own(static_cast<size_t>(mx) * my, -1);
+  for (size_t k = 0; k < subs.size(); ++k)
+    for (int j = subs[k].y0 / q; j < (subs[k].y0 + subs[k].s) / q; ++j)
+      for (int i = subs[k].x0 / q; i < (subs[k].x0 + subs[k].s) / q; ++i)
+        own[static_cast<size_t>(j) * mx + i] = static_cast<int>(k);
+  auto at = [&](int j, int i) { return own[static_cast<size_t>(j) * mx + i]; };
+  std::vector<QSeg> vert, horiz;
+  for (int i = 1; i < mx; ++i)
+    for (int j = 0; j < my;) {
+      const int L = at(j, i - 1), R = at(j, i);
+      if (L == R) {
+        ++j;
+        continue;
+      }
+      int j1 = j;
+      while (j1 < my && at(j1, i - 1) == L && at(j1, i) == R) ++j1;
+      vert.push_back(QSeg{0, i * q, j * q, (j1 - j) * q, L, R});
+      j = j1;
+    }
+  for (int j = 1; j < my; ++j)
+    for (int i = 0; i < mx;) {
+      const int L = at(j - 1, i), R = at(j, i);
+      if (L == R) {
+        ++i;
+        continue;
+      }
+      int i1 = i;
+      while (i1 < mx && at(j - 1, i1) == L && at(j, i1) == R) ++i1;
+      horiz.push_back(QSeg{1, i * q, j * q, (i1 - i) * q, L, R});
+      i = i1;
+    }
+  auto by_fy_fx = [](const QSeg &a, const QSeg &b) {
+    return a.fy != b.fy ? a.fy < b.fy : a.fx < b.fx;
+  };
+  std::sort(vert.begin(), vert.end(), by_fy_fx);
+  std::sort(horiz.begin(), horiz.end(), by_fy_fx);
+  segs = vert;
+  segs.insert(segs.end(), horiz.begin(), horiz.end());
+}
+
+// Interfaces of realisation r and their lengths in faces (canonical order).
+static void iface_lengths(const mrcm_desc &d, int r, int64_t ref_off, std::vector<int> &len) {
+  len.clear();
+  if (is_quad(d, r, ref_off)) {
+    std::vector<QSub> subs;
+    std::vector<QSeg> segs;
+    quad_layout(d, r, ref_off, subs, segs);
+    for (const QSeg &sg : segs) len.push_back(sg.len);
+    return;
+  }
+  const int s = d.sub_size[r], sx = d.nx / s, sy = d.ny / s;
+  len.assign(static_cast<size_t>(sx - 1) * sy + static_cast<size_t>(sx) * (sy - 1), s);
+}
+
 static mrcm_status validate(const mrcm_desc *d) {
   if (!d) return fail(nullptr, MRCM_EINVAL, "descriptor is NULL");
   if (d->nx <= 0 || d->ny <= 0) return fail(nullptr, MRCM_EINVAL, "nx, ny must be positive");
@@ -171,18 +269,42 @@ static mrcm_status validate(const mrcm_desc *d) {
       return fail(nullptr, MRCM_EINVAL, "grid %dx%d not divisible by subdomain size %d", d->nx,
                   d->ny, s);
   }
-  if (d->iface_fn) {             // every value of the caller's interface functions
-    int64_t src = 0, ifc = 0;
+  bool any_quad = false;
+  if (d->refine) {               // quadtree: only 32 x 32 blocks split, into 16 x 16
+    int64_t ro = 0;
     for (int r = 0; r < d->n_real; ++r) {
-      const int s = d->sub_size[r], sx = d->nx / s, sy = d->ny / s;
-      const int64_t nif = static_cast<int64_t>(sx - 1) * sy + static_cast<int64_t>(sx) * (sy - 1);
-      for (int64_t g = 0; g < nif; ++g, ++ifc) {
+      if (is_quad(*d, r, ro)) {
+        any_quad = true;
+        if (d->sub_size[r] != 32)
+          return fail(nullptr, MRCM_EINVAL,
+                      "refine: realisation %d splits %dx%d subdomains (only 32x32 split)", r,
+                      d->sub_size[r], d->sub_size[r]);
+      }
+      ro += refine_entries(*d, r);
+    }
+  }
+  if (any_quad) {
+    if (d->iface_solver == MRCM_IFACE_DIRECT)
+      return fail(nullptr, MRCM_EINVAL, "refine: the direct interface solvers need uniform "
+                                        "subdomains (use GMRES)");
+    if (d->precond != MRCM_PRECOND_BLOCK_JACOBI && d->precond != MRCM_PRECOND_NONE)
+      return fail(nullptr, MRCM_EINVAL, "refine: only block-Jacobi or no preconditioner");
+    if (d->pure_neumann)
+      return fail(nullptr, MRCM_EINVAL, "refine: pure-Neumann problems need uniform subdomains");
+  }
+  if (d->iface_fn) {             // every value of the caller's interface functions
+    int64_t src = 0, ifc = 0, ro = 0;
+    std::vector<int> len;
+    for (int r = 0; r < d->n_real; ++r) {
+      iface_lengths(*d, r, ro, len);
+      if (d->refine) ro += refine_entries(*d, r);
+      for (size_t g = 0; g < len.size(); ++g, ++ifc) {
         const int n = std::max(0, d->iface_nU[ifc]) + std::max(0, d->iface_nP[ifc]);
-        for (int64_t k = 0; k < static_cast<int64_t>(n) * s; ++k)
+        for (int64_t k = 0; k < static_cast<int64_t>(n) * len[g]; ++k)
           if (!std::isfinite(d->iface_fn[src + k]))
             return fail(nullptr, MRCM_EINVAL, "iface_fn: non-finite value at %lld",
                         static_cast<long long>(src + k));
-        src += static_cast<int64_t>(n) * s;
+        src += static_cast<int64_t>(n) * len[g];
       }
     }
   }
@@ -204,6 +326,8 @@ static mrcm_status build_tables(mrcm_ctx *c) {
   int64_t alpha_off = 0, gam_off = 0, slab_off = 0, xy_off = 0, vec_off = 0;
   int64_t basis_off = 0, g_off = 0, tsc_off = 0, coef_off = 0, w_off = 0;
   int col_off = 0;
+  int64_t ref_off = 0;  // this realisation's entries of d.refine
+  bool any_quad = false;
   std::vector<int> subs32;
   int nslab_all = 1;   // slabs run along the longer side (the same for every s)
   for (int r = 0; r < d.n_real; ++r) {
@@ -226,6 +350,155 @@ static mrcm_status build_tables(mrcm_ctx *c) {
     ri.H = S * h;
     if (d.pure_neumann && ri.nsub < 2)
       return fail(nullptr, MRCM_EINVAL, "pure_neumann needs at least two subdomains");
+    if (is_quad(d, r, ref_off)) {
+      // quadtree realisation: 32 x 32 blocks, the refined ones as four 16 x 16
+      // subdomains; interfaces are the segments of quad_layout
+      any_quad = true;
+      std::vector<QSub> qs;
+      std::vector<QSeg> qg;
+      quad_layout(d, r, ref_off, qs, qg);
+      ri.quad = 1;
+      ri.nsub = static_cast<int>(qs.size());
+      ri.niface = static_cast<int>(qg.size());
+      for (int g = 0; g < ri.niface; ++g) {
+        const QSeg &sg = qg[g];
+        IfaceInfo fi{};
+        fi.r = r;
+        fi.kind = sg.kind;
+        fi.L = ri.sub0 + sg.L;
+        fi.R = ri.sub0 + sg.R;
+        fi.fx = sg.fx;
+        fi.fy = sg.fy;
+        fi.nU = d.iface_nU[nif_tot + g];
+        fi.nP = d.iface_nP[nif_tot + g];
+        if (fi.nU < 0 || fi.nP < 0 || fi.nU > sg.len || fi.nP > sg.len || fi.nU + fi.nP < 1)
+          return fail(nullptr, MRCM_EINVAL, "interface %d: need 0 <= nU,nP <= %d, nU+nP >= 1",
+                      nif_tot + g, sg.len);
+        fi.s = sg.len;
+        fi.unk = unk_tot;
+        unk_tot += fi.nU + fi.nP;
+        fi.alpha_off = alpha_off;
+        alpha_off += sg.len;
+        fi.gam_off = gam_off;
+        gam_off += 2 * sg.len;
+        fi.tsc_off = tsc_off;
+        tsc_off += static_cast<int64_t>(fi.nU + fi.nP) * (fi.nU + fi.nP);
+        fi.rowL = fi.rowR = fi.colL = fi.colR = -1;
+        if (d.iface_fn) {
+          int &rows = sg.len == 16 ? c->fn_rows16 : c->fn_rows32;
+          fi.fnU = rows;
+          fi.fnP = rows + fi.nU;
+          rows += fi.nU + fi.nP;
+        } else {
+          fi.fnU = fi.fnP = 0;
+        }
+        c->iface.push_back(fi);
+      }
+      ri.nunk = unk_tot - ri.unk0;
+      ri.pin = -1;
+      // the segments on every side of every subdomain, in order along the edge
+      std::vector<int> side_seg(qs.size() * 8, -1);
+      for (int g = 0; g < ri.niface; ++g) {
+        const QSeg &sg = qg[g];
+        const int sL = sg.kind == 0 ? kEdgeE : kEdgeN, sR = sg.kind == 0 ? kEdgeW : kEdgeS;
+        for (const int k : {sg.L * 8 + sL * 2, sg.R * 8 + sR * 2}) {
+          if (side_seg[k] < 0) side_seg[k] = g;
+          else if (side_seg[k + 1] < 0) side_seg[k + 1] = g;
+          else return fail(nullptr, MRCM_EINVAL, "refine: more than two interfaces on an edge");
+        }
+      }
+      for (size_t k = 0; k < qs.size(); ++k) {
+        const int Sk = qs[k].s;
+        SubInfo sb{};
+        sb.r = r;
+        sb.I = qs[k].x0 / 16;
+        sb.J = qs[k].y0 / 16;
+        sb.x0 = qs[k].x0;
+        sb.y0 = qs[k].y0;
+        sb.s = Sk;
+        const int gid = static_cast<int>(c->sub.size());
+        sb.col_off = col_off;
+        c->col.push_back(ColInfo{-1, -1, 0, 0});
+        int ncol = 1, nrow = 0;
+        for (int e = 0; e < 4; ++e) {
+          const int a0 = side_seg[k * 8 + e * 2], a1 = side_seg[k * 8 + e * 2 + 1];
+          // one interface over the whole edge, or two over its halves
+          const bool ok = a0 < 0 ? a1 < 0
+                                 : (a1 < 0 ? qg[a0].len == Sk
+                                           : qg[a0].len == Sk / 2 && qg[a1].len == Sk / 2);
+          if (!ok) return fail(nullptr, MRCM_EINVAL, "refine: unsupported edge layout");
+          sb.edge_iface[e] = a0 < 0 ? -1 : ri.iface0 + a0;
+          sb.edge_iface2[e] = a1 < 0 ? -1 : ri.iface0 + a1;
+          sb.edge_col2[e] = sb.edge_row2[e] = -1;
+          for (int half = 0; half < 2; ++half) {
+            const int a = half ? a1 : a0;
+            if (half) {
+              sb.edge_col2[e] = a < 0 ? -1 : ncol;
+              sb.edge_row2[e] = a < 0 ? -1 : nrow;
+            } else {
+              sb.edge_col[e] = ncol;
+              sb.edge_row[e] = nrow;
+            }
+            if (a < 0) continue;
+            IfaceInfo &fi = c->iface[ri.iface0 + a];
+            if (fi.L == gid) {
+              fi.rowL = nrow;
+              fi.colL = ncol;
+            } else {
+              fi.rowR = nrow;
+              fi.colR = ncol;
+            }
+            for (int kk = 0; kk < fi.nU; ++kk)
+              c->col.push_back(ColInfo{fi.unk + kk, e, fi.fnU + kk, 1});
+            for (int kk = 0; kk < fi.nP; ++kk)
+              c->col.push_back(ColInfo{fi.unk + fi.nU + kk, e, fi.fnP + kk, 0});
+            ncol += fi.nU + fi.nP;
+            nrow += fi.nU + fi.nP;
+          }
+        }
+        sb.ncols = ncol;
+        sb.nrows = nrow;
+        col_off += ncol;
+        sb.basis_off = basis_off;
+        basis_off += static_cast<int64_t>(ncol) * Sk * Sk;
+        sb.g_off = g_off;
+        g_off += static_cast<int64_t>(nrow) * ncol;
+        sb.coef_off = coef_off;
+        coef_off += 6 * Sk * Sk + 4 * Sk;
+        sb.w_off = w_off;
+        w_off += static_cast<int64_t>(Sk) * Sk * Sk;
+        if (Sk == 16) c->sub_by_size.push_back(gid);
+        else subs32.push_back(gid);
+        c->sub.push_back(sb);
+      }
+      // no slab structure: every interface in slab 0 (the direct solvers refuse
+      // quadtree layouts; the GMRES path uses no slabs)
+      ri.nslab = nslab_all;
+      int pos = 0;
+      for (int k = 0; k < ri.nslab; ++k) {
+        c->slab_if_off.push_back(static_cast<int>(c->slab_if.size()));
+        if (k == 0)
+          for (int g = 0; g < ri.niface; ++g) {
+            c->slab_if.push_back(ri.iface0 + g);
+            IfaceInfo &fi = c->iface[ri.iface0 + g];
+            fi.slab = 0;
+            fi.pos = pos;
+            pos += fi.nU + fi.nP;
+          }
+      }
+      ri.bmax = std::max(1, pos);
+      ri.nlev = 0;
+      ri.slab_off = slab_off;
+      ri.xy_off = xy_off;
+      ri.vec_off = vec_off;
+      c->pos_real_off.push_back(vec_off);
+      vec_off += static_cast<int64_t>(ri.nslab) * ri.bmax;
+      c->real.push_back(ri);
+      nsub_tot += ri.nsub;
+      nif_tot += ri.niface;
+      ref_off += refine_entries(d, r);
+      continue;
+    }
     // interfaces in canonical order
     const int nV = (ri.Sx - 1) * ri.Sy;
     for (int g = 0; g < ri.niface; ++g) {
@@ -245,6 +518,8 @@ static mrcm_status build_tables(mrcm_ctx *c) {
         fi.L = ri.sub0 + J * ri.Sx + I;
         fi.R = fi.L + ri.Sx;
       }
+      fi.fx = fi.kind == 0 ? (I + 1) * S : I * S;
+      fi.fy = fi.kind == 0 ? J * S : (J + 1) * S;
       fi.nU = d.iface_nU[nif_tot + g];
       fi.nP = d.iface_nP[nif_tot + g];
       if (fi.nU < 0 || fi.nP < 0 || fi.nU > S || fi.nP > S || fi.nU + fi.nP < 1)
@@ -295,14 +570,23 @@ static mrcm_status build_tables(mrcm_ctx *c) {
         sb.edge_iface[1] = ifE;
         sb.edge_iface[2] = ifS;
         sb.edge_iface[3] = ifN;
+        for (int e = 0; e < 4; ++e) sb.edge_iface2[e] = sb.edge_col2[e] = sb.edge_row2[e] = -1;
         sb.col_off = col_off;
         c->col.push_back(ColInfo{-1, -1, 0, 0});
         int ncol = 1, nrow = 0;
+        const int gid_here = static_cast<int>(c->sub.size());
         for (int e = 0; e < 4; ++e) {
           sb.edge_col[e] = ncol;
           sb.edge_row[e] = nrow;
           if (sb.edge_iface[e] < 0) continue;
-          const IfaceInfo &fi = c->iface[sb.edge_iface[e]];
+          IfaceInfo &fi = c->iface[sb.edge_iface[e]];
+          if (fi.L == gid_here) {
+            fi.rowL = nrow;
+            fi.colL = ncol;
+          } else {
+            fi.rowR = nrow;
+            fi.colR = ncol;
+          }
           for (int k = 0; k < fi.nU; ++k)
             c->col.push_back(ColInfo{fi.unk + k, e, fi.fnU + k, 1});
           for (int k = 0; k < fi.nP; ++k)
@@ -375,6 +659,7 @@ static mrcm_status build_tables(mrcm_ctx *c) {
     c->real.push_back(ri);
     nsub_tot += ri.nsub;
     nif_tot += ri.niface;
+    if (d.refine) ref_off += refine_entries(d, r);
   }
   c->slab_if_off.push_back(static_cast<int>(c->slab_if.size()));
   c->nunk = unk_tot;
@@ -383,7 +668,8 @@ static mrcm_status build_tables(mrcm_ctx *c) {
   c->coef_elems = coef_off;
   c->w_elems = w_off;
   c->alpha_elems = alpha_off;
-  if (d.iface_solver == MRCM_IFACE_GMRES) c->use_gmres = true;
+  c->quad = any_quad;
+  if (d.iface_solver == MRCM_IFACE_GMRES || any_quad) c->use_gmres = true;
   if (c->use_gmres) {
     // no slab blocks on the GMRES path
     c->use_big = false;
@@ -606,11 +892,10 @@ static void build_gmres_rows(mrcm_ctx *c) {
   c->gm_rows.assign(c->nunk, GmRow{});
   for (const IfaceInfo &fi : c->iface) {
     const SubInfo &L = c->sub[fi.L], &R = c->sub[fi.R];
-    const int eL = fi.kind == 0 ? kEdgeE : kEdgeN, eR = fi.kind == 0 ? kEdgeW : kEdgeS;
     for (int i = 0; i < fi.nU + fi.nP; ++i) {
       GmRow gr;
-      gr.gL = L.g_off + static_cast<int64_t>(L.edge_row[eL] + i) * L.ncols + 1;
-      gr.gR = R.g_off + static_cast<int64_t>(R.edge_row[eR] + i) * R.ncols + 1;
+      gr.gL = L.g_off + static_cast<int64_t>(fi.rowL + i) * L.ncols + 1;
+      gr.gR = R.g_off + static_cast<int64_t>(fi.rowR + i) * R.ncols + 1;
       gr.cL = L.col_off + 1;
       gr.cR = R.col_off + 1;
       gr.nL = L.ncols - 1;
@@ -631,6 +916,10 @@ static void build_neighbourhoods(mrcm_ctx *c) {
     const RealInfo &ri = c->real[fi.r];
     const SubInfo &L = c->sub[fi.L], &R = c->sub[fi.R];
     nb.clear();
+    if (ri.quad) {              // no subdomain grid: the interface alone
+      const int g = static_cast<int>(&fi - c->iface.data());
+      nb.push_back(g);
+    } else
     for (int J = std::min(L.J, R.J) - 1; J <= std::max(L.J, R.J) + 1; ++J)
       for (int I = std::min(L.I, R.I) - 1; I <= std::max(L.I, R.I) + 1; ++I) {
         if (I < 0 || J < 0 || I >= ri.Sx || J >= ri.Sy) continue;
@@ -1543,6 +1832,7 @@ mrcm_status mrcm_solve_interface(mrcm_ctx *ctx, mrcm_info *info) {
 
 mrcm_status mrcm_set_gravity(mrcm_ctx *ctx, const double *d_w) {
   if (!ctx) return MRCM_EINVAL;
+  if (ctx->quad && d_w) return fail(ctx, MRCM_EINVAL, "gravity with a quadtree layout");
   ctx->t.grav = d_w;
   return MRCM_OK;
 }

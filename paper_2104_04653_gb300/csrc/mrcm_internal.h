@@ -19,6 +19,12 @@ struct SubInfo {
   int edge_iface[4]; // W,E,S,N: global interface id, -1 on the physical boundary
   int edge_col[4];   // first basis column of the edge's functions
   int edge_row[4];   // first row of the edge in G
+  // quadtree layouts: an edge next to two half-size subdomains carries two
+  // interfaces, the first on faces [0, s/2) (edge_iface, edge_col, edge_row)
+  // and this second one on [s/2, s); -1 when the edge has one interface
+  int edge_iface2[4];
+  int edge_col2[4];
+  int edge_row2[4];
   int col_off;       // offset into the column table (ncols entries)
   int s;             // subdomain edge in cells (16 or 32)
   int64_t basis_off; // offset (doubles) of basis [ncols][S*S]
@@ -40,6 +46,17 @@ struct IfaceInfo {
   int64_t gam_off;   // offset into the one-sided velocity output (2*s values)
   int64_t tsc_off;   // offset into the congruence scaling blocks (m*m values)
   int fnU, fnP;      // rows of phi_0 and psi_0 in the function table of size s
+  int fx, fy;        // its first face: vertical (x line, first row), horizontal
+                     // (first column, y line)
+  int rowL, rowR;    // first row of its unknowns in the G rows of L and R
+  int colL, colR;    // first basis column of its functions in L and R
+};
+
+// The interface of face e (0 .. s-1, along +y on W/E, +x on S/N) of edge
+// `side` of a subdomain: its id (-1 on the physical boundary), the face's
+// index along the interface and the interface's length in faces.
+struct FaceIface {
+  int g, e, len;
 };
 
 // Column c of a subdomain: global unknown it multiplies (-1: particular),
@@ -57,6 +74,7 @@ struct RealInfo {
   int iface0, niface;
   int unk0, nunk;
   int pin;           // pinned global unknown (pure Neumann) or -1
+  int quad;          // 1: quadtree layout (mrcm_desc.refine), GMRES path only
   int nslab, bmax;   // BCR slabs and padded slab size
   int nlev;          // BCR reduction levels
   int64_t slab_off;  // offset (elements) of this realisation's slab blocks
@@ -207,6 +225,21 @@ struct DeviceTables {
   const int8_t *bc_type;
   const double *bc_val;
 };
+
+#ifdef __CUDACC__
+// Face e of edge `side` of subdomain sb -> its interface (see FaceIface).
+__device__ __forceinline__ FaceIface face_iface(const SubInfo &sb, int side, int e) {
+  const int g2 = sb.edge_iface2[side];
+  if (g2 < 0) return FaceIface{sb.edge_iface[side], e, sb.s};
+  const int hf = sb.s >> 1;
+  return e < hf ? FaceIface{sb.edge_iface[side], e, hf} : FaceIface{g2, e - hf, hf};
+}
+
+// Value of function row `row` of an interface of `len` faces at face e.
+__device__ __forceinline__ double iface_fn_at(const DeviceTables &t, int len, int row, int e) {
+  return t.fnval[(len == 16 ? 0 : t.fn_off32) + static_cast<int64_t>(row) * len + e];
+}
+#endif
 
 // Workspace (device pointers), owned by the context.
 struct Workspace {

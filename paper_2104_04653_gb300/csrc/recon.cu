@@ -23,7 +23,6 @@ __global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace 
   const int g = t.sub_by_size[first + blockIdx.x];
   const SubInfo sb = t.sub[g];
   const int tid = threadIdx.x, a = tid % S, b = tid / S;
-  const double *fnt = t.fnval + (S == 16 ? 0 : t.fn_off32);
   __shared__ double p[N];
   __shared__ double coefc[1 + 8 * S];
   __shared__ double red[N / 32];
@@ -66,17 +65,19 @@ __global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace 
     const double sgn = (side == kEdgeE || side == kEdgeN) ? 1.0 : -1.0;  // outward along +x/+y
     double un;  // outward normal velocity
     if (sb.edge_iface[side] >= 0) {
-      const IfaceInfo fi = t.iface[sb.edge_iface[side]];
+      const FaceIface fe = face_iface(sb, side, e);
+      const IfaceInfo fi = t.iface[fe.g];
       const double beta = coef[6 * N + side * S + e];
       double UH = 0.0, PH = 0.0;
-      for (int k = 0; k < fi.nU; ++k) UH += w.x[fi.unk + k] * fnt[(fi.fnU + k) * S + e];
-      for (int k = 0; k < fi.nP; ++k) PH += w.x[fi.unk + fi.nU + k] * fnt[(fi.fnP + k) * S + e];
+      for (int k = 0; k < fi.nU; ++k) UH += w.x[fi.unk + k] * iface_fn_at(t, fe.len, fi.fnU + k, fe.e);
+      for (int k = 0; k < fi.nP; ++k)
+        PH += w.x[fi.unk + fi.nU + k] * iface_fn_at(t, fe.len, fi.fnP + k, fe.e);
       const double gval = -beta * sgn * UH + PH;
       un = Tf[side] * (pc - gval) / h;
       if (t.grav && side >= kEdgeS)
         un += sgn * t.grav[(static_cast<int64_t>(sb.r) * ny + gj) * nx + gi] * Tf[side] /
               (2.0 * coef[5 * N + tid]);
-      GAM[fi.gam_off + (sgn > 0 ? 0 : S) + e] = un;
+      GAM[fi.gam_off + (sgn > 0 ? 0 : fe.len) + fe.e] = un;
       continue;
     }
     int k;
@@ -132,13 +133,12 @@ __global__ void k_recon_final(DeviceTables t, Workspace w, double *P, double *UX
     const IfaceInfo fi = t.iface[gi];
     const int S = fi.s;
     if (e >= S) continue;
-    const SubInfo L = t.sub[fi.L];
     const double v = 0.5 * (GAM[fi.gam_off + e] - GAM[fi.gam_off + S + e]);
     if (fi.kind == 0) {
-      const int i = L.x0 + S, j = L.y0 + e;
+      const int i = fi.fx, j = fi.fy + e;
       UX[(static_cast<int64_t>(fi.r) * t.ny + j) * (t.nx + 1) + i] = v;
     } else {
-      const int i = L.x0 + e, j = L.y0 + S;
+      const int i = fi.fx + e, j = fi.fy;
       UY[(static_cast<int64_t>(fi.r) * (t.ny + 1) + j) * t.nx + i] = v;
     }
   }

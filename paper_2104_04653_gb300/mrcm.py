@@ -60,6 +60,7 @@ class MrcmDesc(ctypes.Structure):
         ("gmres_restart", ctypes.c_int32), ("gmres_max", ctypes.c_int32),
         ("gmres_tol", ctypes.c_double),
         ("iface_fn", ctypes.POINTER(ctypes.c_double)),
+        ("refine", ctypes.POINTER(ctypes.c_int8)),
     ]
 
 
@@ -180,8 +181,11 @@ class Mrcm:
         bcv = np.ascontiguousarray(prob.bc_val.astype(np.float64))
         alpha = None
         if prob.alpha is not None:
-            alpha = np.ascontiguousarray(np.concatenate([np.asarray(a, np.float64).reshape(-1)
-                                                         for a in prob.alpha]))
+            # per realisation: an [n_iface, s] array, or a list of per-interface
+            # arrays (interfaces of different lengths)
+            alpha = np.ascontiguousarray(np.concatenate(
+                [np.asarray(x, np.float64).reshape(-1) for a in prob.alpha
+                 for x in (a if isinstance(a, (list, tuple)) else [a])]))
         self._keep += [nu, npp, sub, bct, bcv, alpha]
         d = MrcmDesc()
         d.nx, d.ny, d.n_real, d.ly = prob.nx, prob.ny, prob.n_real, prob.ly
@@ -204,6 +208,14 @@ class Mrcm:
             self._keep.append(fn)
         d.iface_fn = (fn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if fn is not None
                       else ctypes.POINTER(ctypes.c_double)())
+        ref = None
+        if getattr(prob, "refine", None) is not None:
+            # per realisation (ny/s) x (nx/s) int8, concatenated
+            ref = np.ascontiguousarray(np.concatenate(
+                [np.asarray(m, np.int8).reshape(-1) for m in prob.refine]))
+            self._keep.append(ref)
+        d.refine = (ref.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)) if ref is not None
+                    else ctypes.POINTER(ctypes.c_int8)())
         d.prec = opts.prec
         d.ir_tol, d.ir_max = opts.ir_tol, opts.ir_max
         d.iface_tol, d.iface_ir_max = opts.iface_tol, opts.iface_ir_max

@@ -167,3 +167,37 @@ def test_transport_calls_on_null_context_fail_cleanly(L):
     assert L.mrcm_si_step(None, None, 0.1, *([None] * 8)) == mrcm.MRCM_EINVAL
     assert L.mrcm_sfi_step(None, None, 0.1, 1e-4, 5, *([None] * 9), None) == mrcm.MRCM_EINVAL
     L.mrcm_transport_destroy(None)
+
+
+def test_quadtree_refusals(L):
+    """A refine mask is checked on the host: only 32 x 32 blocks split, no
+    direct interface solver, no neighbourhood or learned preconditioner."""
+    from paper_2104_04653_gb300 import mrcm
+    nx = ny = 64
+    for case in ("split16", "direct", "nb"):
+        sub = 16 if case == "split16" else 32
+        nb = nx // sub
+        nif = 2 * nb * (nb - 1) + 8          # room for the quadtree's extra interfaces
+        keep = dict(sub=np.array([sub], np.int32), nu=np.full(nif, 2, np.int32),
+                    np_=np.full(nif, 2, np.int32), bt=np.zeros(2 * nx + 2 * ny, np.int8),
+                    bv=np.zeros(2 * nx + 2 * ny), ref=np.zeros(nb * nb, np.int8))
+        keep["bt"][:ny] = 1
+        keep["ref"][0] = 1
+        d = mrcm.MrcmDesc()
+        d.nx, d.ny, d.n_real, d.ly = nx, ny, 1, 1.0
+        P = ctypes.POINTER
+        d.sub_size = keep["sub"].ctypes.data_as(P(ctypes.c_int32))
+        d.iface_nU = keep["nu"].ctypes.data_as(P(ctypes.c_int32))
+        d.iface_nP = keep["np_"].ctypes.data_as(P(ctypes.c_int32))
+        d.bc_type = keep["bt"].ctypes.data_as(P(ctypes.c_int8))
+        d.bc_val = keep["bv"].ctypes.data_as(P(ctypes.c_double))
+        d.refine = keep["ref"].ctypes.data_as(P(ctypes.c_int8))
+        d.prec = 1
+        d.ir_tol, d.ir_max, d.iface_tol, d.iface_ir_max = 1e-13, 30, 1e-13, 40
+        if case == "direct":
+            d.iface_solver = mrcm.IFACE_DIRECT
+        if case == "nb":
+            d.precond = mrcm.PRECOND_NEIGHBOURHOOD
+        ctx = ctypes.c_void_p()
+        assert L.mrcm_setup(ctypes.byref(d), None, ctypes.byref(ctx)) == mrcm.MRCM_EINVAL, case
+        assert b"refine" in L.mrcm_last_error(None), case
