@@ -876,6 +876,120 @@ def _suite_learned(args, flush, torch, np, mrcm, LP, W):
     print(json.dumps(line), flush=True)
 
 
+def _suite_transport(flush, torch, np, mrcm, W):
+    """Sequential implicit and sequential fully implicit time stepping on the
+    512 x 512 lognormal field (variance 2, 16 x 16 subdomains, m = 4, M = 5):
+    from the Buckley-Leverett front of step 1, ten SI steps (mrcm_si_step:
+    the five Darcy calls then the transport step) and two SFI steps
+    (mrcm_sfi_step, outer tolerance 1e-4), each inside CUDA events; per step
+    the Darcy and transport device times, Newton iterations and the water
+    balance of the transport step."""
+    from paper_2104_04653_gb300 import transport as TP
+    from oracle import transport as T
+    prob = W.config5(1, n=512)
+    M = 5.0
+    n = prob.nx
+    h = prob.h
+    st = torch.cuda.current_stream()
+    ctx = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=mrcm.PREC_FP32_IR, iface_tol=1e-11))
+    tp = TP.Transport(n, n, 1, prob.ly, TP.TransportOptions(M=M))
+    K, L, Q = mrcm.device_inputs(prob)
+    s0 = torch.as_tensor(np.asarray(prob.meta["saturation"])[None], device="cuda").contiguous()
+    lam = (s0 * s0 + (1 - s0) ** 2 / M).contiguous()
+    p, ux, uy = ctx.alloc_outputs()
+    sa, sb = s0.clone(), torch.empty_like(s0)
+    dt = 0.01
+    # warm-up: one SI step from s0 (not counted)
+    TP.mrcm_si_step(ctx, tp, dt, K, lam.clone(), Q, s0, sb, p, ux, uy)
+    tp.mrcm_transport_get_info()
+    lam = (s0 * s0 + (1 - s0) ** 2 / M).contiguous()
+    steps = []
+    for k in range(10):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        ctx.solve(K, lam, Q, out=(p, ux, uy))
+        e1.record(st)
+        tp.mrcm_transport_step(dt, ux, uy, sa, sb, lam)
+        e2.record(st)
+        inf = tp.mrcm_transport_get_info()
+        s_old, s_new = sa.cpu().numpy()[0], sb.cpu().numpy()[0]
+        uxn, uyn = ux.cpu().numpy()[0], uy.cpu().numpy()[0]
+        dv = float(np.sum(s_new - s_old)) * h * h
+        out = T.boundary_outflow(s_new, uxn, uyn, h, M)
+        steps.append({"darcy_ms": e0.elapsed_time(e1), "transport_ms": e1.elapsed_time(e2),
+                      "newton": inf["newton_iters"][0], "linear_max": inf["linear_iters_max"],
+                      "water_balance_rel": abs(dv + dt * out) / max(dt * abs(out), 1e-300)})
+        sa, sb = sb, sa
+    tot = sum(x["darcy_ms"] + x["transport_ms"] for x in steps) * 1e-3
+    # SFI steps from the state reached, at this dt and at a quarter of it;
+    # an outer loop that does not reach the tolerance is reported as such
+    sfi = []
+    sw = torch.empty_like(sa)
+    for dts in (dt, 0.25 * dt):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            outer = TP.mrcm_sfi_step(ctx, tp, dts, 1e-4, 20, K, lam, Q, sa, sb, sw, p, ux, uy)
+            ok = True
+        except mrcm.MrcmError as ex:
+            outer, ok = 20, False
+        torch.cuda.synchronize()
+        inf = tp.mrcm_transport_get_info(check=False)
+        sfi.append({"dt": dts, "outer": outer, "converged": ok,
+                    "last_change": inf["change_max"], "wall_ms": 1e3 * (time.perf_counter() - t0)})
+    line = {"suite": "si/sfi: bl-front-512x512-s16-m4, M=5, dt=0.01 (10 SI steps; SFI at dt and dt/4)",
+            "cells": prob.cells(), "si_ms_per_step": 1e3 * tot / len(steps),
+            "si_cells_per_s": len(steps) * prob.cells() / tot, "si_steps": steps,
+            "sfi_steps": sfi}
+    tp.close()
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
+def _suite_quadtree(flush, torch, np, mrcm, W):
+    """Lognormal fields (variance 2) on 32 x 32 blocks with 30% of them split
+    into 16 x 16 subdomains, m = 4, mixed precision, GMRES(64) to 1e-10:
+    512 x 512 with block-Jacobi and with the shared neighbourhood
+    preconditioner, 1024 x 1024 with block-Jacobi, each next to the same
+    field on uniform 32 x 32 subdomains: per-call device times, GMRES steps,
+    cells/s.  (The shared form wins on channel fields and loses on these
+    lognormal ones: the oracle's own GMRES on the uniform 512^2 system takes
+    2,359 steps with it against 357 with block-Jacobi.)"""
+    cases = []
+    for n in (512, 1024):
+        K = np.exp(W.grf_exponential(n, n, 1.0 / n, 2.0, 0.1, np.random.default_rng(3000)))
+        ref = W.random_refinement(n, n, 32, 0.3, np.random.default_rng(3001))
+        qt = W.quadtree_problem(n, n, 32, K, [ref])
+        uni = W.make_problem(n, n, 32, K, bc=W.bc_left_right(n, n), n_u=2, n_p=2)
+        nsub = int(np.sum(1 + 3 * ref.astype(np.int64)))
+        pcs = [mrcm.PRECOND_BLOCK_JACOBI] + ([mrcm.PRECOND_NEIGHBOURHOOD_SHARED] if n == 512 else [])
+        for pc in pcs:
+            pname = "block-Jacobi" if pc == mrcm.PRECOND_BLOCK_JACOBI else "shared neighbourhood"
+            cases.append((f"{n}x{n}, quadtree 30% split, {pname}", qt, pc, nsub))
+            cases.append((f"{n}x{n}, uniform 32x32, {pname}", uni, pc, (n // 32) ** 2))
+    for name, prob, pc, nsub in cases:
+        s = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=mrcm.PREC_FP32_IR, iface_solver=mrcm.IFACE_GMRES,
+                                               precond=pc, gmres_tol=1e-10, gmres_max=20000,
+                                               gmres_restart=64))
+        Kd, Ld, Qd = mrcm.device_inputs(prob)
+        out = s.alloc_outputs()
+        s.solve(Kd, Ld, Qd, out=out)
+        info = s.mrcm_get_info(check=False)
+        calls = _time_calls(s, Kd, Ld, Qd, out, 2, flush, torch)
+        calls.pop("_steps")
+        tot = sum(calls.values())
+        line = {"suite": f"quadtree: lognormal {name}, m=4, GMRES(64) to 1e-10",
+                "cells": prob.cells(), "subdomains": nsub,
+                "interface_unknowns": s.num_interface_unknowns(), "ms_per_step": tot * 1e3,
+                "cells_per_s": prob.cells() / tot,
+                "calls_ms": {k: v * 1e3 for k, v in calls.items()},
+                "gmres_iters": info["gmres_iters"], "iface_resid": info["iface_resid"],
+                "status": info["status"]}
+        s.close()
+        print(json.dumps(line), flush=True)
+
+
 def run_suite(args):
     """The large workloads at full size (one line each): per-call device
     times, interface solver, GMRES steps, the solver's own FP64 residuals and
@@ -904,13 +1018,23 @@ def run_suite(args):
         _suite_resolve10(precs, flush, torch, np, mrcm, W)
     if "learned" in args.suite.split(","):
         _suite_learned(args, flush, torch, np, mrcm, LP, W)
+    if "transport" in args.suite.split(","):
+        _suite_transport(flush, torch, np, mrcm, W)
+    if "quadtree" in args.suite.split(","):
+        _suite_quadtree(flush, torch, np, mrcm, W)
+    if "batch2" in args.suite.split(","):
+        cases.append(("lognormal-2x1024x1024-s16/32-m2..8", W.config3(n_real=2), {}))
     for name, prob, extra in cases:
         for prec in precs:
             opts = mrcm.SolverOptions(prec=prec, iface_tol=1e-11, gmres_tol=1e-11, gmres_max=6000,
                                       **extra)
             s = mrcm.Mrcm(prob, opts)
             K, L, Q = mrcm.device_inputs(prob)
-            tuned = s.mrcm_autotune(K, L, Q, reps=2)
+            if args.basis_width:
+                tuned = tuple(int(v) for v in args.basis_width.split(","))
+                s.mrcm_set_basis_width(*tuned)
+            else:
+                tuned = s.mrcm_autotune(K, L, Q, reps=2)
             out = s.alloc_outputs()
             s.solve(K, L, Q, out=out)
             info = s.mrcm_get_info(check=False)
@@ -953,8 +1077,9 @@ def main():
     ap.add_argument("--basis-width", default="",
                     help="N16,N32: basis-kernel RHS columns per CTA instead of autotuning "
                          "(profiling runs that must launch only the timed configuration)")
-    ap.add_argument("--suite", default="", help="comma list of resolve,resolve10,channels,batch,learned: the "
-                    "large workloads at full size instead of the headline line")
+    ap.add_argument("--suite", default="", help="comma list of resolve,resolve10,channels,batch,"
+                    "batch2,learned,transport,quadtree: the large workloads at full size instead "
+                    "of the headline line")
     ap.add_argument("--suite-steps", type=int, default=3)
     ap.add_argument("--suite-train", type=int, default=500,
                     help="training systems (512x512 channel windows) for --suite learned")

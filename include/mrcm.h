@@ -166,7 +166,8 @@ typedef struct {
                              /* (y, first column), normal +x / +y, and        */
                              /* beta = alpha H / kappa takes H = the          */
                              /* interface's length.  Such a context solves    */
-                             /* step (d) by GMRES (block-Jacobi or none);     */
+                             /* step (d) by GMRES (block-Jacobi, the shared   */
+                             /* neighbourhood form, or none);                 */
                              /* pure-Neumann problems and gravity are refused */
 } mrcm_desc;
 

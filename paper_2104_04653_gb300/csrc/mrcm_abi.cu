@@ -287,8 +287,10 @@ static mrcm_status validate(const mrcm_desc *d) {
     if (d->iface_solver == MRCM_IFACE_DIRECT)
       return fail(nullptr, MRCM_EINVAL, "refine: the direct interface solvers need uniform "
                                         "subdomains (use GMRES)");
-    if (d->precond != MRCM_PRECOND_BLOCK_JACOBI && d->precond != MRCM_PRECOND_NONE)
-      return fail(nullptr, MRCM_EINVAL, "refine: only block-Jacobi or no preconditioner");
+    if (d->precond != MRCM_PRECOND_BLOCK_JACOBI && d->precond != MRCM_PRECOND_NONE &&
+        d->precond != MRCM_PRECOND_NEIGHBOURHOOD_SHARED)
+      return fail(nullptr, MRCM_EINVAL, "refine: block-Jacobi, the shared neighbourhood or no "
+                                        "preconditioner");
     if (d->pure_neumann)
       return fail(nullptr, MRCM_EINVAL, "refine: pure-Neumann problems need uniform subdomains");
   }
@@ -962,8 +964,10 @@ static void build_precond_neighbourhoods(mrcm_ctx *c, bool shared) {
     nb.clear();
     for (int side = 0; side < 2; ++side) {
       const SubInfo &sb = c->sub[side ? fi.R : fi.L];
-      for (int e = 0; e < 4; ++e)
+      for (int e = 0; e < 4; ++e) {
         if (sb.edge_iface[e] >= 0) nb.push_back(sb.edge_iface[e]);
+        if (sb.edge_iface2[e] >= 0) nb.push_back(sb.edge_iface2[e]);   // quadtree half edges
+      }
     }
     std::sort(nb.begin(), nb.end());
     nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
@@ -1021,8 +1025,8 @@ static void build_nb_tables(mrcm_ctx *c) {
     blk.clear();
     for (int side = 0; side < 2; ++side) {
       const SubInfo &sb = c->sub[side ? fi.R : fi.L];
-      for (int e = 0; e < 4; ++e) {
-        const int h = sb.edge_iface[e];
+      for (int e = 0; e < 8; ++e) {
+        const int h = e < 4 ? sb.edge_iface[e] : sb.edge_iface2[e - 4];   // quadtree: 2nd halves
         if (h < 0) continue;
         for (int j = c->pnb_off[h]; j < c->pnb_off[h + 1]; ++j) blk.push_back(c->pnb_list[j]);
       }

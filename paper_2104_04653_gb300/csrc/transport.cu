@@ -63,7 +63,8 @@ struct TArgs {
   int max_newton, max_linear, trust_region;
   const double *ux, *uy, *s_old, *s_ref;
   double *s, *lambda;
-  double *diag, *cw, *ce, *cs, *cn, *rhs, *dA, *dB;
+  double *idiag, *cw, *ce, *cs, *cn, *rhs, *dA, *dB;
+  double *fv, *fd;                       // f and f' of every cell (phase A0)
   double *tile_nrm2;                     // [R * tiles per realisation]
   // reductions as bit patterns of non-negative doubles: [0..2] max change
   // and [3..5] max |d| of the linear iterations (three rotating slots: a
@@ -74,22 +75,23 @@ struct TArgs {
   int *status;                           // [0] flags, [1] largest linear count
 };
 
-// f(s) = M s^2 / (M s^2 + (1 - s)^2) and its derivatives by the quotient
-// rule (Section 5).
-__device__ __forceinline__ double tf(double s, double M) {
-  const double a = M * s * s, b = (1.0 - s) * (1.0 - s);
-  return a / (a + b);
-}
-__device__ __forceinline__ double tf1(double s, double M) {
+// f(s) = M s^2 / (M s^2 + (1 - s)^2) and f'(s) = 2 M s (1 - s) / den^2 by
+// the quotient rule (Section 5), sharing one division (FP64 division is
+// slow on this part: 442 clocks measured).
+__device__ __forceinline__ void tf01(double s, double M, double &f, double &d) {
   const double den = M * s * s + (1.0 - s) * (1.0 - s);
-  return 2.0 * M * s * (1.0 - s) / (den * den);
+  const double inv = 1.0 / den;
+  f = M * s * s * inv;
+  d = 2.0 * M * s * (1.0 - s) * inv * inv;
 }
-__device__ __forceinline__ double tf2(double s, double M) {
+// f''(s) = (g' den - 2 g den') / den^3 with g = 2 M s (1 - s): den > 0, so
+// the numerator carries its sign, which is all the trust region needs.
+__device__ __forceinline__ double tf2_num(double s, double M) {
   const double den = M * s * s + (1.0 - s) * (1.0 - s);
   const double g = 2.0 * M * s * (1.0 - s);
   const double gp = 2.0 * M * (1.0 - 2.0 * s);
   const double denp = 2.0 * M * s - 2.0 * (1.0 - s);
-  return (gp * den - 2.0 * g * denp) / (den * den * den);
+  return gp * den - 2.0 * g * denp;
 }
 
 __device__ __forceinline__ unsigned long long dbits(double v) {
@@ -156,22 +158,22 @@ __device__ void assemble_cell(const TArgs &a, const Cell &q) {
   double u[4];
   outward(a, q, u);
   const double sI = a.s[q.c];
-  const double fI = tf(sI, a.M), dI = tf1(sI, a.M);
+  const double fI = a.fv[q.c], dI = a.fd[q.c];
   const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
   const double c = a.dt / a.h;
   double out = 0.0, diag = 1.0, cpl[4];
   for (int k = 0; k < 4; ++k) {
     const int ni = q.i + di[k], nj = q.j + dj[k];
     const bool inside = ni >= 0 && ni < a.nx && nj >= 0 && nj < a.ny;
-    const double sJ = inside ? a.s[q.c + dj[k] * static_cast<int64_t>(a.nx) + di[k]] : 0.0;
-    const double fJ = inside ? tf(sJ, a.M) : a.f_in;
+    const int64_t nc = q.c + dj[k] * static_cast<int64_t>(a.nx) + di[k];
+    const double fJ = inside ? a.fv[nc] : a.f_in;
     out += (u[k] > 0.0 ? u[k] * fI : u[k] * fJ) * a.h;
     if (u[k] > 0.0) diag += c * u[k] * dI;
-    cpl[k] = (u[k] <= 0.0 && inside) ? c * u[k] * tf1(sJ, a.M) : 0.0;
+    cpl[k] = (u[k] <= 0.0 && inside) ? c * u[k] * a.fd[nc] : 0.0;
   }
   const double H = sI - a.s_old[q.c] + a.dt / (a.h * a.h) * out;
   a.rhs[q.c] = -H;
-  a.diag[q.c] = diag;
+  a.idiag[q.c] = 1.0 / diag;     // the sweeps multiply (diag >= 1)
   a.cw[q.c] = cpl[0];
   a.ce[q.c] = cpl[1];
   a.cs[q.c] = cpl[2];
@@ -198,9 +200,9 @@ __device__ void solve_tile(const TArgs &a, int t, const double *src, double *dst
       v = src[(static_cast<int64_t>(q.r) * a.ny + gj) * a.nx + gi];
     sd[e] = v;
   }
-  double dg = 1.0, cw = 0.0, ce = 0.0, cs = 0.0, cn = 0.0, b = 0.0, old = 0.0;
+  double idg = 1.0, cw = 0.0, ce = 0.0, cs = 0.0, cn = 0.0, b = 0.0, old = 0.0;
   if (q.in) {
-    dg = a.diag[q.c];
+    idg = a.idiag[q.c];
     cw = a.cw[q.c];
     ce = a.ce[q.c];
     cs = a.cs[q.c];
@@ -213,7 +215,7 @@ __device__ void solve_tile(const TArgs &a, int t, const double *src, double *dst
     double v = old;
     if (q.in)
       v = (b - cw * sd[ly * W + lx - 1] - ce * sd[ly * W + lx + 1] - cs * sd[(ly - 1) * W + lx] -
-           cn * sd[(ly + 1) * W + lx]) / dg;
+           cn * sd[(ly + 1) * W + lx]) * idg;
     const int changed = q.in && v != sd[ly * W + lx];
     __syncthreads();
     if (q.in) sd[ly * W + lx] = v;
@@ -237,6 +239,12 @@ __global__ void __launch_bounds__(kThreads) k_transport(TArgs a) {
   const int T = a.ntiles, per = a.tx * a.ty;
   int all_done = 0;
   for (int it = 1; it <= a.max_newton && !all_done; ++it) {
+    // A0: f and f' of every cell (one division each)
+    for (int t = blockIdx.x; t < T; t += gridDim.x) {
+      const Cell q = tile_cell(a, t);
+      if (q.in && !a.done[q.r]) tf01(a.s[q.c], a.M, a.fv[q.c], a.fd[q.c]);
+    }
+    grid.sync();
     // A: residual and Jacobian
     for (int t = blockIdx.x; t < T; t += gridDim.x) {
       const Cell q = tile_cell(a, t);
@@ -277,7 +285,7 @@ __global__ void __launch_bounds__(kThreads) k_transport(TArgs a) {
       if (q.in) {
         const double so = a.s[q.c];
         double nv = fmin(fmax(so + src[q.c], 0.0), 1.0);
-        if (a.trust_region && tf2(nv, a.M) * tf2(so, a.M) < 0.0) nv = 0.5 * (nv + so);
+        if (a.trust_region && tf2_num(nv, a.M) * tf2_num(so, a.M) < 0.0) nv = 0.5 * (nv + so);
         if (!isfinite(nv)) atomicOr(&a.status[0], kFlagNan);
         a.s[q.c] = nv;
         d2 = (nv - so) * (nv - so) * a.h * a.h;
@@ -389,11 +397,12 @@ mrcm_status mrcm_transport_create(const mrcm_transport_desc *desc, void *cuda_st
     return terr(MRCM_ECUDA, "occupancy of the transport kernel: %s", cudaGetErrorString(e));
   }
   t->grid = std::min(t->ntiles, nsm * per);
-  // workspace: 8 cell arrays, tile norms, reductions and per-realisation
+  // workspace: 10 cell arrays, tile norms, reductions and per-realisation
   // state, each rounded up to 256 bytes
   const int64_t nc = t->ncell, R = d.n_real;
   auto rnd = [](size_t n) { return (n + 255) & ~static_cast<size_t>(255); };
-  const size_t sizes[14] = {8 * static_cast<size_t>(nc), 8 * static_cast<size_t>(nc),
+  const size_t sizes[16] = {8 * static_cast<size_t>(nc), 8 * static_cast<size_t>(nc),
+                            8 * static_cast<size_t>(nc), 8 * static_cast<size_t>(nc),
                             8 * static_cast<size_t>(nc), 8 * static_cast<size_t>(nc),
                             8 * static_cast<size_t>(nc), 8 * static_cast<size_t>(nc),
                             8 * static_cast<size_t>(nc), 8 * static_cast<size_t>(nc),
@@ -429,7 +438,7 @@ mrcm_status mrcm_transport_create(const mrcm_transport_desc *desc, void *cuda_st
   a.max_newton = t->d.max_newton;
   a.max_linear = t->d.max_linear;
   a.trust_region = d.plain_newton ? 0 : 1;
-  a.diag = reinterpret_cast<double *>(take(nc * 8));
+  a.idiag = reinterpret_cast<double *>(take(nc * 8));
   a.cw = reinterpret_cast<double *>(take(nc * 8));
   a.ce = reinterpret_cast<double *>(take(nc * 8));
   a.cs = reinterpret_cast<double *>(take(nc * 8));
@@ -437,13 +446,15 @@ mrcm_status mrcm_transport_create(const mrcm_transport_desc *desc, void *cuda_st
   a.rhs = reinterpret_cast<double *>(take(nc * 8));
   a.dA = reinterpret_cast<double *>(take(nc * 8));
   a.dB = reinterpret_cast<double *>(take(nc * 8));
+  a.fv = reinterpret_cast<double *>(take(nc * 8));
+  a.fd = reinterpret_cast<double *>(take(nc * 8));
   a.tile_nrm2 = reinterpret_cast<double *>(take(t->ntiles * 8));
   a.last_norm = reinterpret_cast<double *>(take(R * 8));
   a.red = reinterpret_cast<unsigned long long *>(take(8 * 8));
   a.done = reinterpret_cast<int *>(take(R * 4));
   a.iters = reinterpret_cast<int *>(take(R * 4));
   a.status = reinterpret_cast<int *>(take(16));
-  if (taken != 14 || p != t->arena + bytes) {       // the takes above match sizes[]
+  if (taken != 16 || p != t->arena + bytes) {       // the takes above match sizes[]
     cudaFree(t->arena);
     delete t;
     return terr(MRCM_ECUDA, "transport workspace layout mismatch");
