@@ -800,18 +800,27 @@ __global__ void __launch_bounds__(kCT, 1)
       }
       cluster.sync();
     }
-    // neighbours' x
-    if (k > 0)
-      for (int p = tid; p < b; p += kCT) xs[p] = cluster.map_shared_rank(xs, k - 1)[kCMaxB + p];
-    if (k + 1 < K)
-      for (int p = tid; p < b; p += kCT)
-        xs[2 * kCMaxB + p] = cluster.map_shared_rank(xs, k + 1)[kCMaxB + p];
+    // neighbours' x (all zero before the first solve)
+    if (nsolve > 0) {
+      if (k > 0)
+        for (int p = tid; p < b; p += kCT) xs[p] = cluster.map_shared_rank(xs, k - 1)[kCMaxB + p];
+      if (k + 1 < K)
+        for (int p = tid; p < b; p += kCT)
+          xs[2 * kCMaxB + p] = cluster.map_shared_rank(xs, k + 1)[kCMaxB + p];
+    }
     __syncthreads();
     // B: FP64 residual, one thread per row with four independent chains (no
     // FP64 warp reductions: every FP64 warp instruction costs the FP64 pipe
-    // ~19 clocks on this part)
+    // ~19 clocks on this part).  Before the first solve x = 0, so r = f: no
+    // products.
     double rsq = 0.0;
-    if (tid < b) {
+    if (nsolve == 0) {
+      if (tid < b) {
+        const double rv = rowcnt[tid] > 0 ? fs[tid] : 0.0;
+        rl[tid] = ((posinf[tid] >> 30) & 1) ? -rv : rv;
+        rsq = rv * rv;
+      }
+    } else if (tid < b) {
       const int pos = tid, cnt = rowcnt[pos];
       double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
       const double *rc = rowc + pos;
