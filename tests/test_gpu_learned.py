@@ -256,3 +256,44 @@ def test_trained_network_gain(capsys):
     assert iters["learned"] * 10 <= iters["none"], iters
     assert iters["learned"] <= 1.3 * iters["block_jacobi"], iters
     net.close()
+
+
+def test_gmres_after_a_training_run_reads_no_stale_memory(monkeypatch):
+    """Block-Jacobi GMRES on a 512^2 channel system (32 x 32 subdomains,
+    several hundred steps) in a context created before, and in contexts
+    created after, a training run that built and destroyed many contexts
+    and network buffers: the same step count and the same fields, bit for
+    bit, also with the new context's floating-point workspace filled with
+    NaN at setup (MRCM_DEBUG_POISON=1).  A read of memory that no step of
+    the solve wrote would show up as a different count, a difference in the
+    fields, or NaN."""
+    import torch
+    C, O, LP, mrcm, W = _mods()
+    prob = W.config4(n=512, s=32, n_ch=16, seed=4001)
+    Kd, Ld, Qd = mrcm.device_inputs(prob)
+    opts = mrcm.SolverOptions(prec=1, iface_solver=mrcm.IFACE_GMRES, gmres_tol=1e-8,
+                              gmres_max=8000)
+
+    def solve():
+        s = mrcm.Mrcm(prob, opts)
+        f = [t.clone() for t in s.solve(Kd, Ld, Qd)]
+        info = s.mrcm_get_info()
+        s.close()
+        return f, info
+
+    monkeypatch.setenv("MRCM_DEBUG_POISON", "0")
+    before, ib = solve()
+    train_p = [W.config4(n=256, s=32, n_ch=8, seed=5100 + k) for k in range(16)]
+    x, t = LP.make_dataset(train_p, 4)
+    net = LP.LearnedPrecond(32, 4, max_batch=256, seed=1)
+    LP.train(net, x, t, steps=50, batch=128, lr=1e-3)
+    net.close()
+    del x, t
+    torch.cuda.synchronize()
+    for poison in ("0", "1"):
+        monkeypatch.setenv("MRCM_DEBUG_POISON", poison)
+        after, ia = solve()
+        assert ia == ib, (poison, ib, ia)
+        for a, b in zip(before, after):
+            assert torch.equal(a, b), poison
+    assert ib["gmres_iters"] > 100
