@@ -483,7 +483,7 @@ def run_batched(args, flush, torch, ws, rank, local):
     torch.cuda.empty_cache()
     # FP64 path on the same inputs: one warm-up solve, then two timed steps
     s64 = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=mrcm.PREC_FP64, iface_tol=1e-11))
-    s64.mrcm_set_basis_width(*widths)
+    s64.mrcm_set_basis_width(widths[0], min(widths[1], 8))   # FP64: s = 32 width 4 or 8
     out64 = s64.alloc_outputs()
     s64.solve(K, L, Q, out=out64)
     info64 = s64.mrcm_get_info(check=False)

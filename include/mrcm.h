@@ -262,7 +262,8 @@ int64_t mrcm_num_gamma_values(const mrcm_ctx *ctx);
 mrcm_status mrcm_copy_interface_solution(mrcm_ctx *ctx, double *d_x);
 
 /* Tile width of the basis kernels (step c): right-hand-side columns per CTA,
- * one of 4, 8, 12, 16 for 16 x 16-cell subdomains and 4, 8 for 32 x 32.
+ * one of 4, 8, 12, 16 for 16 x 16-cell subdomains and 4, 8 for 32 x 32
+ * (also 16 for 32 x 32 with MRCM_PREC_FP32_IR; MRCM_EINVAL otherwise).
  * Results do not depend on it; the time does.  Synchronises the stream; call
  * it before capturing the calls in a CUDA graph. */
 mrcm_status mrcm_set_basis_width(mrcm_ctx *ctx, int32_t nc16, int32_t nc32);

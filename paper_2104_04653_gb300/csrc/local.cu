@@ -1029,6 +1029,164 @@ __global__ void __launch_bounds__(kS32 *kS32, 1) k_basis32(DeviceTables t, Works
   traces_and_rows<S, NC>(t, w, sb, coef, sm.col, X, it.c0, nc, sm.su, sm.sp);
 }
 
+// ---------------------------------------------------------------------------
+// (c) for s = 32 on the mixed path: one warp per basis column.
+//
+// The columns of a subdomain are independent right-hand sides, and the block
+// solve's 63 dependent steps (forward j = 0..31, backward j = 30..0) only
+// couple the 32 cells of one grid row of one column.  So each warp carries
+// one column: lane a holds z and v of cell (a, j) for every block row j in
+// registers, a step is the 32 x 32 product W_j in, with `in` broadcast by
+// shuffles, and no step waits for another warp.  All 32 inverse Schur blocks
+// (128 KB, FP32) stay resident in shared memory, copied asynchronously while
+// the right-hand sides are formed.  Lane a reads row a of W_j with a
+// diagonal skew (column (k + a) mod 32 at inner step k), which keeps the 32
+// lanes on 32 banks.  The FP64 residual takes the lane's own iterate values
+// of rows j-1, j, j+1 and its neighbours' by shuffles.  Each column stops on
+// its own test, so the result does not depend on how columns are grouped
+// into CTAs.
+template <int NW>
+struct Basis32W {
+  float W[kS32 * kS32 * kS32];   // W_j, j = 0..31, row-major [j][a][q]
+  float ec[kS32 * kS32];         // scaled row couplings e_j[a]
+  float z[NW][kS32 * kS32];      // each warp's scaled residual, [j][a]
+  ColInfo col[NW];
+};
+
+template <int NW>
+__global__ void __launch_bounds__(32 * NW, 1) k_basis32w(DeviceTables t, Workspace w,
+                                                         const BasisItem *items, const double *q,
+                                                         double tol, int ir_max) {
+  constexpr int S = kS32, N = S * S;
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Basis32W<NW> &sm = *reinterpret_cast<Basis32W<NW> *>(smraw);
+  const BasisItem it = items[blockIdx.x];
+  const SubInfo sb = t.sub[it.sub];
+  const int nc = it.nc;
+  const int tid = threadIdx.x, lane = tid & 31, c = tid >> 5;
+  const float *Wg = static_cast<const float *>(w.W) + sb.w_off;
+  const double *coef = w.coef + sb.coef_off;   // tW tE tS tN d: read through L1
+  double *X = w.basis + sb.basis_off + static_cast<int64_t>(it.c0) * N;
+  // W (16-byte chunks; w_off is a multiple of S^3 floats) in flight while the
+  // right-hand sides are set up
+  {
+    const unsigned sdst = static_cast<unsigned>(__cvta_generic_to_shared(sm.W));
+    for (int k = tid; k < N * S / 4; k += 32 * NW)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst + 16u * k),
+                   "l"(Wg + 4 * k)
+                   : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  if (tid < nc) sm.col[tid] = t.col[sb.col_off + it.c0 + tid];
+  for (int k = tid; k < N; k += 32 * NW)
+    sm.ec[k] = k / S < S - 1
+                   ? static_cast<float>(-coef[3 * N + k] * coef[4 * N + k] * coef[4 * N + k + S])
+                   : 0.0f;
+  __syncthreads();
+  const bool act = c < nc;
+  ColInfo ci{};
+  if (act) ci = sm.col[c];
+  float *zc = sm.z[c];
+  double *Xc = X + static_cast<int64_t>(c) * N;
+  // right-hand side and scaled initial residual z = D b of this column
+  float bn = 0.0f;
+  if (act)
+    for (int j = 0; j < S; ++j) {
+      const int k = j * S + lane;
+      const float zv = static_cast<float>(coef[4 * N + k] * rhs_value<S>(t, sb, coef, q, ci, lane, j));
+      zc[k] = zv;
+      bn = fmaf(zv, zv, bn);
+      Xc[k] = 0.0;
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bn += __shfl_xor_sync(FULL, bn, o);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+
+  const float tol2 = static_cast<float>(tol) * static_cast<float>(tol);
+  int sweep = 0;
+  float prev2 = 3e38f, rel2 = 0.0f;
+  while (act) {
+    // forward: v_j = W_j (z_j - e_{j-1} v_{j-1}), in place over z (each lane
+    // reads and writes only its own entry; the exchange is by shuffles)
+    float vp = 0.0f;
+#pragma unroll 4
+    for (int j = 0; j < S; ++j) {
+      const float in = j == 0 ? zc[lane] : zc[j * S + lane] - sm.ec[(j - 1) * S + lane] * vp;
+      const float *Wa = sm.W + j * N + lane * S;
+      float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < S; k += 2) {
+        const int q0 = (k + lane) & (S - 1), q1 = (k + 1 + lane) & (S - 1);
+        a0 = fmaf(Wa[q0], __shfl_sync(FULL, in, q0), a0);
+        a1 = fmaf(Wa[q1], __shfl_sync(FULL, in, q1), a1);
+      }
+      vp = a0 + a1;
+      zc[j * S + lane] = vp;
+    }
+    // backward: y_j = v_j - W_j (e_j y_{j+1}), y_31 = v_31; then x += D y
+    // (the correction in FP32, accumulated in FP64)
+    Xc[(S - 1) * S + lane] += static_cast<double>(
+        static_cast<float>(coef[4 * N + (S - 1) * S + lane]) * vp);
+#pragma unroll 4
+    for (int j = S - 2; j >= 0; --j) {
+      const float tq = sm.ec[j * S + lane] * vp;
+      const float *Wa = sm.W + j * N + lane * S;
+      float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < S; k += 2) {
+        const int q0 = (k + lane) & (S - 1), q1 = (k + 1 + lane) & (S - 1);
+        a0 = fmaf(Wa[q0], __shfl_sync(FULL, tq, q0), a0);
+        a1 = fmaf(Wa[q1], __shfl_sync(FULL, tq, q1), a1);
+      }
+      vp = zc[j * S + lane] - (a0 + a1);
+      Xc[j * S + lane] += static_cast<double>(static_cast<float>(coef[4 * N + j * S + lane]) * vp);
+    }
+    if (sweep >= ir_max) break;
+    // FP64 residual r = b - A x over rows j-1, j, j+1 of this lane's cells
+    float rn = 0.0f;
+    double xm = 0.0, xc = Xc[lane];
+    for (int j = 0; j < S; ++j) {
+      const double xp = j < S - 1 ? Xc[(j + 1) * S + lane] : 0.0;
+      const double xl = __shfl_up_sync(FULL, xc, 1), xr = __shfl_down_sync(FULL, xc, 1);
+      const int k = j * S + lane;
+      const double tW = coef[k], tE = coef[N + k], tS = coef[2 * N + k], tN = coef[3 * N + k];
+      const double diag = tW + tE + tS + tN;
+      double r = fma(-diag, xc, rhs_value<S>(t, sb, coef, q, ci, lane, j));
+      if (lane > 0) r = fma(tW, xl, r);
+      if (lane < S - 1) r = fma(tE, xr, r);
+      if (j > 0) r = fma(tS, xm, r);
+      if (j < S - 1) r = fma(tN, xp, r);
+      const float zv = static_cast<float>(r) * static_cast<float>(coef[4 * N + k]);
+      zc[k] = zv;
+      rn = fmaf(zv, zv, rn);
+      xm = xc;
+      xc = xp;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rn += __shfl_xor_sync(FULL, rn, o);
+    rel2 = bn > 0.0f ? rn / bn : 0.0f;
+    if (rel2 != rel2) rel2 = 3e38f;
+    ++sweep;
+    if (rel2 <= tol2) break;
+    if (sweep > 2 && rel2 > 0.25f * prev2) break;  // stalled
+    prev2 = rel2;
+    __syncwarp();
+  }
+  if (act && lane == 0 && ir_max > 0) {
+    const double rel = sqrt(static_cast<double>(rel2));
+    atomicMax(&w.status[1], sweep);
+    atomic_max_pos_double(&w.dstat[0], rel);
+    if (!(rel <= 1e3 * tol)) atomicOr(&w.status[0], MRCM_FLAG_LOCAL_STALL);
+  }
+  __syncthreads();                 // every column done; W's space now holds the traces
+  double(*su)[S][NW] = reinterpret_cast<double(*)[S][NW]>(sm.W);
+  double(*sp)[S][NW] = reinterpret_cast<double(*)[S][NW]>(sm.W + 2 * 4 * S * NW);
+  traces_and_rows<S, NW>(t, w, sb, coef, sm.col, X, it.c0, nc, su, sp);
+}
+static_assert(2 * 2 * 4 * kS32 * 16 <= kS32 * kS32 * kS32, "the traces fit in W's space");
+
 }  // namespace
 
 cudaError_t launch_factor(const DeviceTables &t, const Workspace &w, int prec, const double *K,
@@ -1087,10 +1245,20 @@ static cudaError_t launch_basis_t(const DeviceTables &t, const Workspace &w,
     if (e != cudaSuccess) return e;
   }
   if (n32 > 0) {
-    switch (nc32) {
-      case 4: e = basis32<T, 4>(t, w, items + n16, n32, q, tol, ir_max, st); break;
-      case 8: e = basis32<T, 8>(t, w, items + n16, n32, q, tol, ir_max, st); break;
-      default: return cudaErrorInvalidValue;
+    if (std::is_same<T, float>::value) {   // mixed path: one warp per column
+      switch (nc32) {
+        case 4: k_basis32w<4><<<n32, 128, sizeof(Basis32W<4>), st>>>(t, w, items + n16, q, tol, ir_max); break;
+        case 8: k_basis32w<8><<<n32, 256, sizeof(Basis32W<8>), st>>>(t, w, items + n16, q, tol, ir_max); break;
+        case 16: k_basis32w<16><<<n32, 512, sizeof(Basis32W<16>), st>>>(t, w, items + n16, q, tol, ir_max); break;
+        default: return cudaErrorInvalidValue;
+      }
+      e = cudaGetLastError();
+    } else {
+      switch (nc32) {
+        case 4: e = basis32<T, 4>(t, w, items + n16, n32, q, tol, ir_max, st); break;
+        case 8: e = basis32<T, 8>(t, w, items + n16, n32, q, tol, ir_max, st); break;
+        default: return cudaErrorInvalidValue;
+      }
     }
   }
   return e;
@@ -1124,8 +1292,9 @@ cudaError_t init_local_attributes() {
       (e = smem_attr<decltype(&k_basis<double, 8>), BasisSmem<double, 8>>(k_basis<double, 8>)) ||
       (e = smem_attr<decltype(&k_basis<double, 12>), BasisSmem<double, 12>>(k_basis<double, 12>)) ||
       (e = smem_attr<decltype(&k_basis<double, 16>), BasisSmem<double, 16>>(k_basis<double, 16>)) ||
-      (e = smem_attr<decltype(&k_basis32<float, 4>), BasisSmem32<float, 4>>(k_basis32<float, 4>)) ||
-      (e = smem_attr<decltype(&k_basis32<float, 8>), BasisSmem32<float, 8>>(k_basis32<float, 8>)) ||
+      (e = smem_attr<decltype(&k_basis32w<4>), Basis32W<4>>(k_basis32w<4>)) ||
+      (e = smem_attr<decltype(&k_basis32w<8>), Basis32W<8>>(k_basis32w<8>)) ||
+      (e = smem_attr<decltype(&k_basis32w<16>), Basis32W<16>>(k_basis32w<16>)) ||
       (e = smem_attr<decltype(&k_basis32<double, 4>), BasisSmem32<double, 4>>(k_basis32<double, 4>)) ||
       (e = smem_attr<decltype(&k_basis32<double, 8>), BasisSmem32<double, 8>>(k_basis32<double, 8>)))
     return e;

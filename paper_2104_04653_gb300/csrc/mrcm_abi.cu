@@ -1894,8 +1894,11 @@ mrcm_status mrcm_set_precond_blocks(mrcm_ctx *ctx, const double *d_blocks) {
 
 mrcm_status mrcm_set_basis_width(mrcm_ctx *ctx, int32_t nc16, int32_t nc32) {
   if (!ctx) return MRCM_EINVAL;
-  if ((nc16 != 4 && nc16 != 8 && nc16 != 12 && nc16 != 16) || (nc32 != 4 && nc32 != 8))
-    return fail(ctx, MRCM_EINVAL, "basis widths: s = 16 one of 4, 8, 12, 16; s = 32 one of 4, 8");
+  const bool w32ok = nc32 == 4 || nc32 == 8 || (nc32 == 16 && ctx->prec != MRCM_PREC_FP64);
+  if ((nc16 != 4 && nc16 != 8 && nc16 != 12 && nc16 != 16) || !w32ok)
+    return fail(ctx, MRCM_EINVAL,
+                "basis widths: s = 16 one of 4, 8, 12, 16; s = 32 one of 4, 8 (16 also with "
+                "MRCM_PREC_FP32_IR)");
   rebuild_items(ctx, nc16, nc32);
   cudaError_t e = cudaMemcpyAsync(ctx->d_items, ctx->items.data(),
                                   ctx->items.size() * sizeof(BasisItem), cudaMemcpyHostToDevice,
@@ -1947,7 +1950,8 @@ mrcm_status mrcm_autotune(mrcm_ctx *ctx, const double *d_K, const double *d_lamb
   }
   if (s2 == MRCM_OK && has32) {
     tbest = 3.4e38f;
-    for (int w32 : {4, 8}) {
+    for (int w32 : {4, 8, 16}) {
+      if (w32 == 16 && ctx->prec == MRCM_PREC_FP64) continue;
       float t;
       if ((s2 = time_width(best16, w32, &t)) != MRCM_OK) break;
       if (t < tbest) { tbest = t; best32 = w32; }

@@ -150,7 +150,7 @@ constexpr int kLpMaxLoc = 160;    // largest neighbourhood (unknowns) of a targe
 constexpr double kLpClip = 2.0;   // entrywise bound of a target
 
 constexpr int kNC16 = 12;     // default basis columns per CTA, s = 16 (4, 8, 12, 16)
-constexpr int kNC32 = 8;      // default basis columns per CTA, s = 32 (4, 8)
+constexpr int kNC32 = 8;      // default basis columns per CTA, s = 32 (4, 8; 16 in FP32)
 
 // Direct interface path for slabs above 64 unknowns (iface_big.cu)
 constexpr int kBigMaxLev = 20;

@@ -132,7 +132,7 @@ def test_every_basis_width_and_autotune(case):
             "mixed": lambda: W.config3(n_real=2, n=64)}[case]()
     ref = O.mrcm_solve(prob)
     K, L, Q = mrcm.device_inputs(prob)
-    widths = [(w, 8) for w in (4, 8, 12, 16)] + [(12, 4)]
+    widths = [(w, 8) for w in (4, 8, 12, 16)] + [(12, 4), (12, 16)]
     s = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=1))
     for w16, w32 in widths:
         s.mrcm_set_basis_width(w16, w32)
@@ -140,8 +140,14 @@ def test_every_basis_width_and_autotune(case):
         ep, eu = O.errors(dict(p=p.cpu().numpy(), ux=ux.cpu().numpy(), uy=uy.cpu().numpy()), ref)
         assert ep <= TOL and eu <= TOL, (case, w16, w32, ep, eu)
     c16, c32 = s.mrcm_autotune(K, L, Q, reps=2)
-    assert c16 in (4, 8, 12, 16) and c32 in (4, 8)
+    assert c16 in (4, 8, 12, 16) and c32 in (4, 8, 16)
     p, ux, uy = s.solve(K, L, Q)
     ep, eu = O.errors(dict(p=p.cpu().numpy(), ux=ux.cpu().numpy(), uy=uy.cpu().numpy()), ref)
     assert ep <= TOL and eu <= TOL
     s.close()
+    # the FP64 path has widths 4 and 8 for s = 32 only
+    s64 = mrcm.Mrcm(prob, mrcm.SolverOptions(prec=mrcm.PREC_FP64))
+    with pytest.raises(RuntimeError):
+        s64.mrcm_set_basis_width(12, 16)
+    s64.mrcm_set_basis_width(12, 8)
+    s64.close()
