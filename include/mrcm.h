@@ -66,7 +66,9 @@ typedef enum {
   MRCM_EIRSTALL = 5,   /* refinement stopped above its tolerance           */
   MRCM_ENOCONV = 6,    /* interface refinement did not converge            */
   MRCM_ENAN = 7,       /* NaN / Inf in inputs or results                   */
-  MRCM_ETIMEOUT = 8    /* a bounded device wait ran out (result invalid)   */
+  MRCM_ETIMEOUT = 8,   /* a bounded device wait ran out (result invalid)   */
+  MRCM_EINCOMPAT = 9   /* pure Neumann: the sources do not balance the     */
+                       /* prescribed boundary outflow (no solution)        */
 } mrcm_status;
 
 /* Device status flags (bit OR), see mrcm_info.flags. */
@@ -80,6 +82,12 @@ typedef enum {
 #define MRCM_FLAG_PRECOND_FALLBACK 0x40  /* informational: the caller-supplied   */
                                          /* preconditioner stalled and GMRES was */
                                          /* rerun with block-Jacobi              */
+#define MRCM_FLAG_INCOMPATIBLE 0x200     /* pure Neumann: |sum q h^2 - sum u_b h| */
+                                         /* above 1e-10 of the absolute sums      */
+#define MRCM_FLAG_LOCAL_REFACTOR 0x100   /* informational: the FP32 refinement of */
+                                         /* some subdomains stalled and they     */
+                                         /* were re-factored and re-solved in    */
+                                         /* FP64 (mrcm_info.local_refactored)    */
 
 typedef enum {
   MRCM_PREC_FP64 = 0,     /* plain path: FP64 factors and solves            */
@@ -169,6 +177,13 @@ typedef struct {
                              /* step (d) by GMRES (block-Jacobi, the shared   */
                              /* neighbourhood form, or none);                 */
                              /* pure-Neumann problems and gravity are refused */
+  int32_t ir_recover;        /* MRCM_PREC_FP32_IR: a subdomain whose local    */
+                             /* refinement stalls (relative residual above    */
+                             /* 1e3 ir_tol) is re-factored in FP64 and its    */
+                             /* columns solved again, inside the same         */
+                             /* mrcm_build_basis; at most this many per       */
+                             /* factorisation (0: 16; < 0: none).  More       */
+                             /* stalls than that give MRCM_EIRSTALL           */
 } mrcm_desc;
 
 typedef struct {
@@ -178,7 +193,9 @@ typedef struct {
   int32_t gmres_iters;       /* GMRES steps (max over realisations, including  */
                              /* a block-Jacobi rerun); 0 on the direct path    */
   double  local_resid_max;   /* max ||b - A x|| / ||b|| over local solves      */
+                             /* (the columns re-solved in FP64 excluded)      */
   double  iface_resid;       /* max over realisations ||f - M x|| / ||f||      */
+  int32_t local_refactored;  /* subdomains re-factored in FP64 (ir_recover)    */
 } mrcm_info;
 
 /* Validate the descriptor, build subdomain / interface / slab tables, choose

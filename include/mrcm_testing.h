@@ -31,6 +31,18 @@ mrcm_status mrcm_test_gemm(int32_t impl, int32_t n, const float *d_a1, const flo
  * of range.  Synchronises the stream.  (No counterpart in the paper.) */
 mrcm_status mrcm_test_wait_timeout(uint32_t limit, int32_t *d_status, void *cuda_stream);
 
+/* Fault injection on the host side of the refinement: rounds the stored
+ * FP32 inverse Schur blocks of subdomain `sub` (the context's order:
+ * realisations in turn, each row-major by subdomain row then column) to
+ * `mantissa_bits` explicit mantissa bits, ties to even (7: bfloat16), so that
+ * the subdomain's FP32 refinement in the next mrcm_build_basis stalls on a
+ * high-contrast field as a low-precision factor would.  Call it between
+ * mrcm_factor_local and mrcm_build_basis.  MRCM_EINVAL: NULL context, an FP64
+ * context, sub out of range, mantissa_bits outside 1..22, or a 16 x 16
+ * subdomain whose FP32 factor the basis kernel forms itself (not stored).
+ * Asynchronous on the context's stream.  (No counterpart in the paper.) */
+mrcm_status mrcm_test_degrade_factor(mrcm_ctx *ctx, int32_t sub, int32_t mantissa_bits);
+
 #ifdef __cplusplus
 }
 #endif

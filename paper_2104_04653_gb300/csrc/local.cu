@@ -279,6 +279,28 @@ __device__ __forceinline__ void write_beta(const DeviceTables &t, const SubInfo 
   }
 }
 
+// One column's (or one CTA's) final relative refinement residual.  Up to
+// 1e3 tol it enters the maximum in dstat[0]; above, the subdomain is listed
+// (once) for the FP64 recovery, or, with no slot left or no recovery, the
+// stall is flagged (MRCM_EIRSTALL) and enters the maximum.
+__device__ __forceinline__ void report_local_resid(const Workspace &w, int g, double rel,
+                                                   double tol) {
+  if (rel <= 1e3 * tol) {
+    atomic_max_pos_double(&w.dstat[0], rel);
+    return;
+  }
+  if (w.rec_cap > 0) {
+    if (atomicExch(&w.stall_mark[g], 1) != 0) return;   // listed or flagged already
+    const int slot = atomicAdd(&w.status[4], 1);
+    if (slot < w.rec_cap) {
+      w.stall_list[slot] = g;
+      return;
+    }
+  }
+  atomicOr(&w.status[0], MRCM_FLAG_LOCAL_STALL);
+  atomic_max_pos_double(&w.dstat[0], rel);
+}
+
 // s = 16: one CTA of 256 threads per subdomain.  CHAIN = false: stage 1 only
 // (coefficients and Jacobi scale); the FP32 basis kernel then factors each
 // subdomain itself (k_basis with FUSED).
@@ -290,6 +312,7 @@ __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, 
   const SubInfo sb = t.sub[g];
   const int tid = threadIdx.x;
   const int a = tid % S, b = tid / S;
+  if (tid == 0 && w.rec_cap > 0) w.stall_mark[g] = 0;   // a new factorisation
   __shared__ double kap[N];
   __shared__ double dsc[N];
   __shared__ double tfE[N], tfN[N];   // E and N face transmissibilities
@@ -353,6 +376,7 @@ __global__ void __launch_bounds__(32 * kFW) k_factor_warp(DeviceTables t, Worksp
   FactorWarpSmem<T, S> &sm = reinterpret_cast<FactorWarpSmem<T, S> *>(smraw)[wid];
   const int g = t.sub_by_size[first + idx];
   const SubInfo sb = t.sub[g];
+  if (lane == 0 && w.rec_cap > 0) w.stall_mark[g] = 0;  // a new factorisation
   double *coef = w.coef + sb.coef_off;
   const int64_t row0 = static_cast<int64_t>(sb.r) * t.ny + sb.y0;
   auto kappa = [&](int a, int b) {
@@ -669,6 +693,7 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   extern __shared__ __align__(16) unsigned char smraw[];
   BasisSmem<T, NC> &sm = *reinterpret_cast<BasisSmem<T, NC> *>(smraw);
   const BasisItem it = items[blockIdx.x];
+  if (it.nc == 0) return;   // an unused slot of the recovery launch (whole CTA)
   const int g = it.sub;
   const SubInfo sb = t.sub[g];
   const int nc = it.nc;
@@ -803,10 +828,8 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
     prev2 = rel2;
   }
   if (tid == 0 && ir_max > 0) {
-    const double rel = sqrt(static_cast<double>(rel2));
     atomicMax(&w.status[1], sweep);
-    atomic_max_pos_double(&w.dstat[0], rel);
-    if (!(rel <= 1e3 * tol)) atomicOr(&w.status[0], MRCM_FLAG_LOCAL_STALL);
+    report_local_resid(w, g, sqrt(static_cast<double>(rel2)), tol);
   }
 
   // basis columns (FP64)
@@ -923,6 +946,7 @@ __global__ void __launch_bounds__(kS32 *kS32, 1) k_basis32(DeviceTables t, Works
   extern __shared__ __align__(16) unsigned char smraw[];
   BasisSmem32<T, NC> &sm = *reinterpret_cast<BasisSmem32<T, NC> *>(smraw);
   const BasisItem it = items[blockIdx.x];
+  if (it.nc == 0) return;   // an unused slot of the recovery launch (whole CTA)
   const SubInfo sb = t.sub[it.sub];
   const int nc = it.nc;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1021,10 +1045,8 @@ __global__ void __launch_bounds__(kS32 *kS32, 1) k_basis32(DeviceTables t, Works
     prev2 = rel2;
   }
   if (tid == 0 && ir_max > 0) {
-    const double rel = sqrt(static_cast<double>(rel2));
     atomicMax(&w.status[1], sweep);
-    atomic_max_pos_double(&w.dstat[0], rel);
-    if (!(rel <= 1e3 * tol)) atomicOr(&w.status[0], MRCM_FLAG_LOCAL_STALL);
+    report_local_resid(w, it.sub, sqrt(static_cast<double>(rel2)), tol);
   }
   traces_and_rows<S, NC>(t, w, sb, coef, sm.col, X, it.c0, nc, sm.su, sm.sp);
 }
@@ -1175,10 +1197,8 @@ __global__ void __launch_bounds__(32 * NW, 1) k_basis32w(DeviceTables t, Workspa
     __syncwarp();
   }
   if (act && lane == 0 && ir_max > 0) {
-    const double rel = sqrt(static_cast<double>(rel2));
     atomicMax(&w.status[1], sweep);
-    atomic_max_pos_double(&w.dstat[0], rel);
-    if (!(rel <= 1e3 * tol)) atomicOr(&w.status[0], MRCM_FLAG_LOCAL_STALL);
+    report_local_resid(w, it.sub, sqrt(static_cast<double>(rel2)), tol);
   }
   __syncthreads();                 // every column done; W's space now holds the traces
   double(*su)[S][NW] = reinterpret_cast<double(*)[S][NW]>(sm.W);
@@ -1187,7 +1207,150 @@ __global__ void __launch_bounds__(32 * NW, 1) k_basis32w(DeviceTables t, Workspa
 }
 static_assert(2 * 2 * 4 * kS32 * 16 <= kS32 * kS32 * kS32, "the traces fit in W's space");
 
+// ---------------------------------------------------------------------------
+// Refinement-stall recovery.  One warp per slot of the list the mixed basis
+// kernels wrote: it lays out the slot's work items for the FP64 basis kernels
+// (the unused slots' items are empty, so those CTAs return at once), copies
+// the subdomain's SubInfo with w_off pointing into the FP64 scratch, and forms
+// the FP64 inverse Schur blocks from the coefficients stage 1 of the factor
+// stored (the scaled couplings exactly as the factor kernels form them).
+template <int S>
+__device__ bool refactor_fp64(int lane, const double *coef, double *offx, double *ecp,
+                              double *W) {
+  constexpr int N = S * S;
+  const double *tE = coef + N, *tN = coef + 3 * N, *d = coef + 4 * N;
+  for (int cell = lane; cell < N; cell += 32) {
+    const int a = cell % S, b = cell / S;
+    offx[cell] = a < S - 1 ? -tE[cell] * d[cell] * d[cell + 1] : 0.0;
+    ecp[cell] = b < S - 1 ? -tN[cell] * d[cell] * d[cell + S] : 0.0;
+  }
+  __syncwarp();
+  return schur_inverses<double, S>(lane, offx, ecp, W);
+}
+
+__global__ void __launch_bounds__(32) k_refactor64(DeviceTables t, Workspace w) {
+  __shared__ double offx[kS32 * kS32], ecp[kS32 * kS32];
+  const int slot = blockIdx.x, lane = threadIdx.x;
+  const int nlisted = w.status[4];
+  const int listed = nlisted < w.rec_cap ? nlisted : w.rec_cap;
+  if (slot == 0 && lane == 0 && nlisted > 0) atomicOr(&w.status[0], MRCM_FLAG_LOCAL_REFACTOR);
+  BasisItem *it16 = w.rec_items + static_cast<int64_t>(slot) * w.rec_maxch;
+  BasisItem *it32 = it16 + static_cast<int64_t>(w.rec_cap) * w.rec_maxch;
+  int g = -1, s = 0, ncol = 0, nch = 0;
+  if (slot < listed) {
+    g = w.stall_list[slot];
+    s = t.sub[g].s;
+    ncol = t.sub[g].ncols;
+    nch = (ncol + kRecNC - 1) / kRecNC;   // <= rec_maxch (the largest ncols)
+  }
+  for (int k = lane; k < w.rec_maxch; k += 32) {
+    BasisItem e{slot, 0, 0};
+    if (k < nch) {
+      e.c0 = ncol * k / nch;
+      e.nc = ncol * (k + 1) / nch - e.c0;
+    }
+    it16[k] = s == 16 ? e : BasisItem{slot, 0, 0};
+    it32[k] = s == 32 ? e : BasisItem{slot, 0, 0};
+  }
+  if (slot >= listed) return;
+  SubInfo sb = t.sub[g];
+  sb.w_off = static_cast<int64_t>(slot) * w.rec_smax * w.rec_smax * w.rec_smax;
+  if (lane == 0) w.rec_sub[slot] = sb;
+  const double *coef = w.coef + sb.coef_off;
+  const bool bad = s == 16 ? refactor_fp64<kS>(lane, coef, offx, ecp, w.W64 + sb.w_off)
+                           : refactor_fp64<kS32>(lane, coef, offx, ecp, w.W64 + sb.w_off);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&w.status[0], MRCM_FLAG_NOTSPD);
+}
+
+// Pure-Neumann problems have a solution only when the sources balance the
+// prescribed boundary outflow: the cell balances summed over the domain give
+// sum_c q_c h^2 = sum_f u_f h (u_f the outward normal velocity of boundary
+// face f).  One CTA per realisation sums both in FP64 (a fixed order: the
+// result does not depend on timing) and raises MRCM_FLAG_INCOMPATIBLE when
+// they differ by more than 1e-10 of the sum of their absolute values.
+constexpr int kCompatThreads = 512;
+__global__ void __launch_bounds__(kCompatThreads) k_compat(DeviceTables t, Workspace w,
+                                                           const double *q) {
+  const int r = blockIdx.x, tid = threadIdx.x;
+  const int64_t n = static_cast<int64_t>(t.nx) * t.ny;
+  const double *qr = q + static_cast<int64_t>(r) * n;
+  double sq = 0.0, aq = 0.0, sb = 0.0, ab = 0.0;
+  for (int64_t k = tid; k < n; k += kCompatThreads) {
+    const double v = qr[k];
+    sq += v;
+    aq += fabs(v);
+  }
+  for (int k = tid; k < 2 * (t.nx + t.ny); k += kCompatThreads) {
+    const double v = t.bc_val[k];
+    sb += v;
+    ab += fabs(v);
+  }
+  __shared__ double part[4][kCompatThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    aq += __shfl_xor_sync(0xffffffffu, aq, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    ab += __shfl_xor_sync(0xffffffffu, ab, o);
+  }
+  if ((tid & 31) == 0) {
+    part[0][tid >> 5] = sq;
+    part[1][tid >> 5] = aq;
+    part[2][tid >> 5] = sb;
+    part[3][tid >> 5] = ab;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < kCompatThreads / 32; ++k)
+      for (int j = 0; j < 4; ++j) s4[j] += part[j][k];
+    const double h = t.h;
+    const double imbalance = s4[0] * h * h - s4[2] * h, scale = s4[1] * h * h + s4[3] * h;
+    if (!(fabs(imbalance) <= 1e-10 * scale)) atomicOr(&w.status[0], MRCM_FLAG_INCOMPATIBLE);
+  }
+}
+
+// Test hook: W[k] rounded to `bits` explicit mantissa bits, ties to even
+// (bits = 7: the precision of bfloat16).
+__global__ void k_degrade_factor(float *W, int n, int bits) {
+  const unsigned shift = 23u - static_cast<unsigned>(bits);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    unsigned u = __float_as_uint(W[k]);
+    u += ((1u << shift) >> 1) - 1u + ((u >> shift) & 1u);
+    W[k] = __uint_as_float(u & ~((1u << shift) - 1u));
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_recover(const DeviceTables &t, const Workspace &w, const double *q,
+                           double ir_tol, cudaStream_t st) {
+  if (w.rec_cap <= 0) return cudaSuccess;
+  k_refactor64<<<w.rec_cap, 32, 0, st>>>(t, w);
+  DeviceTables tr = t;
+  tr.sub = w.rec_sub;
+  Workspace wr = w;
+  wr.W = w.W64;
+  const int n = w.rec_cap * w.rec_maxch;
+  if (t.nsub16 > 0)
+    k_basis<double, kRecNC, false><<<n, kS * kS, sizeof(BasisSmem<double, kRecNC>), st>>>(
+        tr, wr, w.rec_items, q, ir_tol, 0);
+  if (t.nsub > t.nsub16)
+    k_basis32<double, kRecNC><<<n, kS32 * kS32, sizeof(BasisSmem32<double, kRecNC>), st>>>(
+        tr, wr, w.rec_items + n, q, ir_tol, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compat(const DeviceTables &t, const Workspace &w, const double *q,
+                          cudaStream_t st) {
+  k_compat<<<t.n_real, kCompatThreads, 0, st>>>(t, w, q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_degrade_factor(float *W, int n, int bits, cudaStream_t st) {
+  k_degrade_factor<<<(n + 255) / 256, 256, 0, st>>>(W, n, bits);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_factor(const DeviceTables &t, const Workspace &w, int prec, const double *K,
                           const double *lam, cudaStream_t st) {
@@ -1245,7 +1408,7 @@ static cudaError_t launch_basis_t(const DeviceTables &t, const Workspace &w,
     if (e != cudaSuccess) return e;
   }
   if (n32 > 0) {
-    if (std::is_same<T, float>::value) {   // mixed path: one warp per column
+    if constexpr (std::is_same<T, float>::value) {   // mixed path: one warp per column
       switch (nc32) {
         case 4: k_basis32w<4><<<n32, 128, sizeof(Basis32W<4>), st>>>(t, w, items + n16, q, tol, ir_max); break;
         case 8: k_basis32w<8><<<n32, 256, sizeof(Basis32W<8>), st>>>(t, w, items + n16, q, tol, ir_max); break;

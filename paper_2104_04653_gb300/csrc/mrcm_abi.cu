@@ -4,6 +4,7 @@
 #include "mrcm_internal.h"
 #include "../../include/mrcm.h"
 #include "../../include/mrcm_learned.h"
+#include "../../include/mrcm_testing.h"
 
 #include <algorithm>
 #include <cmath>
@@ -43,6 +44,7 @@ struct mrcm_ctx {
   std::vector<int> slab_if, slab_if_off;   // interfaces of every (realisation, slab)
   int mmax = 1, nslab_max = 0, bmax_max = 0, nlev_max = 0;
   int cluster_k = 0;                       // > 0: one-launch cluster interface path
+  int rec_cap = 0, rec_maxch = 0;          // refinement-stall recovery slots, items per slot
   int *d_slab_if = nullptr, *d_slab_if_off = nullptr;
   // cluster interface plans (see DeviceTables)
   std::vector<int> plan_info, plan_cnt, plan_goff, plan_fgoff, plan_tsc, pair_off, pair_goff;
@@ -1242,7 +1244,7 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                o_r = A.take<double>(nif ? nif : 1),
                o_vec = A.take<char>((c->npos ? c->npos : 1) * esz),
                o_ps = A.take<double>(nsub), o_gt = A.take<double>(c->gam_elems ? c->gam_elems : 1),
-               o_st = A.take<int>(4), o_dst = A.take<double>(2 + 2 * d.n_real),
+               o_st = A.take<int>(8), o_dst = A.take<double>(2 + 2 * d.n_real),
                o_done = A.take<int>(d.n_real + 1);
   const bool G = c->use_gmres;
   const int64_t Kp = c->gm_K;
@@ -1300,6 +1302,19 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                o_iscr = A.take<char>(BG ? inv_slots * slot_elems * esz : 0),
                o_ijob = A.take<InvJob>(BG ? n_inv : 0), o_gjob = A.take<GemmJob>(BG ? n_gemm : 0),
                o_levo = A.take<int>(BG ? c->big_lev_off.size() : 0);
+  // refinement-stall recovery (mixed path): FP64 blocks, SubInfo copies and
+  // work items of rec_cap subdomains, the list and the per-subdomain marks
+  int max_ncols = 1;
+  for (const SubInfo &sb : c->sub) max_ncols = std::max(max_ncols, sb.ncols);
+  c->rec_cap = (c->prec == MRCM_PREC_FP32_IR && d.ir_recover >= 0)
+                   ? std::min(d.ir_recover > 0 ? d.ir_recover : 16, nsub)
+                   : 0;
+  c->rec_maxch = (max_ncols + kRecNC - 1) / kRecNC;
+  const int RC = c->rec_cap;
+  const size_t o_rW = A.take<double>(static_cast<int64_t>(RC) * c->smax * c->smax * c->smax),
+               o_rsub = A.take<SubInfo>(RC),
+               o_ritems = A.take<BasisItem>(static_cast<int64_t>(2) * RC * c->rec_maxch),
+               o_rlist = A.take<int>(RC), o_rmark = A.take<int>(RC > 0 ? nsub : 0);
   e = cudaMalloc(&c->arena, A.off);
   if (e != cudaSuccess) {
     delete c;
@@ -1320,14 +1335,14 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                           o_sI,   o_X,      o_Y,      o_ds,     o_f,    o_x,     o_r,
                           o_vec,  o_ps,     o_gt,     o_st,     o_gmGp, o_gmPbj, o_gmPid,
                           o_gmPus, o_gmV,   o_gmW,    o_gmY,    o_gmpart, o_gmres, o_gmint,
-                          o_tcp,  o_tcm,    o_vec2,   o_iscr,   o_ijob};
+                          o_tcp,  o_tcm,    o_vec2,   o_iscr,   o_ijob,   o_rW,   o_rsub};
     // spans [cut[k], cut[k+1]) hold floating-point data except those that
-    // start at o_st, o_gmint and o_tcm (entries 17, 27 and 29); bit i names
-    // the i-th floating-point span: 0 coef .. 16 gt, 17 gmGp .. 25 gmres,
-    // 26 tcp, 27 vec2, 28 iscr
+    // start at o_st, o_gmint, o_tcm and o_ijob (entries 17, 27, 29 and 32);
+    // bit i names the i-th floating-point span: 0 coef .. 16 gt, 17 gmGp ..
+    // 25 gmres, 26 tcp, 27 vec2, 28 iscr, 29 the recovery's FP64 blocks
     int bit = 0;
     for (size_t k = 0; k + 1 < sizeof(cut) / sizeof(cut[0]); ++k) {
-      if (k == 17 || k == 27 || k == 29) continue;
+      if (k == 17 || k == 27 || k == 29 || k == 32) continue;
       const size_t a = cut[k], b = cut[k + 1];
       if (((mask >> bit++) & 1) && b > a &&
           (e = cudaMemset(base + a, 0xFF, b - a)) != cudaSuccess) {
@@ -1394,7 +1409,8 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                  cudaSuccess) ||
       (G && (e = up(o_nblist, c->nb_list.data(), c->nb_list.size() * sizeof(int))) !=
                 cudaSuccess) ||
-      (e = cudaMemset(base + o_st, 0, 4 * sizeof(int))) != cudaSuccess ||
+      (e = cudaMemset(base + o_st, 0, 8 * sizeof(int))) != cudaSuccess ||
+      (RC > 0 && (e = cudaMemset(base + o_rmark, 0, nsub * sizeof(int))) != cudaSuccess) ||
       (e = cudaMemset(base + o_dst, 0, (2 + 2 * d.n_real) * sizeof(double))) != cudaSuccess ||
       // slab vectors: positions past a slab's own width pad it to the widest
       // slab of its realisation; no kernel writes them and the block solves
@@ -1478,6 +1494,14 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
   w.dstat = reinterpret_cast<double *>(base + o_dst);
   w.ifnorm = nullptr;
   w.done = reinterpret_cast<int *>(base + o_done);
+  w.rec_cap = RC;
+  w.rec_maxch = c->rec_maxch;
+  w.rec_smax = c->smax;
+  w.W64 = RC > 0 ? reinterpret_cast<double *>(base + o_rW) : nullptr;
+  w.rec_sub = RC > 0 ? reinterpret_cast<SubInfo *>(base + o_rsub) : nullptr;
+  w.rec_items = RC > 0 ? reinterpret_cast<BasisItem *>(base + o_ritems) : nullptr;
+  w.stall_list = RC > 0 ? reinterpret_cast<int *>(base + o_rlist) : nullptr;
+  w.stall_mark = RC > 0 ? reinterpret_cast<int *>(base + o_rmark) : nullptr;
   if (G) {
     GmArgs &a = c->gm;
     a.row = reinterpret_cast<const GmRow *>(base + o_gmrow);
@@ -1678,7 +1702,7 @@ mrcm_status mrcm_factor_local(mrcm_ctx *ctx, const double *d_K, const double *d_
   if (!ctx) return MRCM_EINVAL;
   if (!d_K || !d_lambda) return fail(ctx, MRCM_EINVAL, "K and lambda must be device pointers");
   cudaError_t e;
-  if ((e = cudaMemsetAsync(ctx->w.status, 0, 4 * sizeof(int), ctx->stream)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(ctx->w.status, 0, 8 * sizeof(int), ctx->stream)) != cudaSuccess)
     return cuda_fail(ctx, e, "reset status");
   if ((e = cudaMemsetAsync(ctx->w.dstat, 0, (2 + 2 * ctx->d.n_real) * sizeof(double),
                            ctx->stream)) != cudaSuccess)
@@ -1699,6 +1723,16 @@ mrcm_status mrcm_build_basis(mrcm_ctx *ctx, const double *d_q) {
                                ctx->nc32, d_q, ctx->d.ir_tol, ctx->d.ir_max, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "build_basis launch");
   ctx->launches += n_sizes(ctx);
+  if (ctx->d.pure_neumann) {
+    if ((e = launch_compat(ctx->t, ctx->w, d_q, ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "build_basis compatibility check");
+    ctx->launches += 1;
+  }
+  if (ctx->rec_cap > 0) {
+    if ((e = launch_recover(ctx->t, ctx->w, d_q, ctx->d.ir_tol, ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "build_basis recovery launch");
+    ctx->launches += 1 + n_sizes(ctx);
+  }
   ctx->state = 2;
   return MRCM_OK;
 }
@@ -1706,7 +1740,7 @@ mrcm_status mrcm_build_basis(mrcm_ctx *ctx, const double *d_q) {
 static mrcm_status read_info(mrcm_ctx *ctx, mrcm_info *info) {
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
-  int st[4];
+  int st[8];
   double ds[2];
   if ((e = cudaMemcpy(st, ctx->w.status, sizeof st, cudaMemcpyDeviceToHost)) != cudaSuccess ||
       (e = cudaMemcpy(ds, ctx->w.dstat, sizeof ds, cudaMemcpyDeviceToHost)) != cudaSuccess)
@@ -1717,16 +1751,22 @@ static mrcm_status read_info(mrcm_ctx *ctx, mrcm_info *info) {
   info->gmres_iters = st[3];
   info->local_resid_max = ds[0];
   info->iface_resid = ds[1];
+  info->local_refactored = std::min(st[4], ctx->rec_cap);
   if (st[0] & MRCM_FLAG_TIMEOUT) return fail(ctx, MRCM_ETIMEOUT, "a bounded device wait ran out");
   if (st[0] & MRCM_FLAG_LAYOUT) return fail(ctx, MRCM_EINVAL, "internal slab layout error");
   if (st[0] & MRCM_FLAG_NAN) return fail(ctx, MRCM_ENAN, "NaN/Inf or non-positive kappa");
+  // the earliest step's failure first: a stalled local solve or unbalanced
+  // pure-Neumann data spoil the interface system that the later flags judge
   if (st[0] & MRCM_FLAG_NOTSPD) return fail(ctx, MRCM_ENOTSPD, "local pivot <= 0");
+  if (st[0] & MRCM_FLAG_INCOMPATIBLE)
+    return fail(ctx, MRCM_EINCOMPAT,
+                "pure Neumann: the sources do not balance the boundary outflow");
+  if (st[0] & MRCM_FLAG_LOCAL_STALL)
+    return fail(ctx, MRCM_EIRSTALL, "local refinement stopped at %.3e", ds[0]);
   if (st[0] & MRCM_FLAG_IFACE_PIVOT)
     return fail(ctx, MRCM_ENOTSPD, "interface pivot zero or not finite");
   if (st[0] & MRCM_FLAG_IFACE_STALL)
     return fail(ctx, MRCM_ENOCONV, "interface refinement stopped at %.3e", ds[1]);
-  if (st[0] & MRCM_FLAG_LOCAL_STALL)
-    return fail(ctx, MRCM_EIRSTALL, "local refinement stopped at %.3e", ds[0]);
   return MRCM_OK;
 }
 
@@ -1889,6 +1929,22 @@ mrcm_status mrcm_set_precond_blocks(mrcm_ctx *ctx, const double *d_blocks) {
                                   cudaMemcpyDeviceToDevice, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "copy preconditioner blocks");
   ctx->gm_user_set = true;
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_test_degrade_factor(mrcm_ctx *ctx, int32_t sub, int32_t mantissa_bits) {
+  if (!ctx) return MRCM_EINVAL;
+  if (ctx->prec == MRCM_PREC_FP64) return fail(ctx, MRCM_EINVAL, "FP64 context: no FP32 factor");
+  if (sub < 0 || sub >= static_cast<int32_t>(ctx->sub.size()))
+    return fail(ctx, MRCM_EINVAL, "subdomain %d out of range", sub);
+  if (mantissa_bits < 1 || mantissa_bits > 22)
+    return fail(ctx, MRCM_EINVAL, "mantissa_bits must be in 1..22");
+  const SubInfo &sb = ctx->sub[sub];
+  if (sb.s == 16 && ctx->t.fuse16)
+    return fail(ctx, MRCM_EINVAL, "the basis kernel forms this subdomain's factor itself");
+  float *W = static_cast<float *>(ctx->w.W) + sb.w_off;
+  cudaError_t e = launch_degrade_factor(W, sb.s * sb.s * sb.s, mantissa_bits, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "degrade launch");
   return MRCM_OK;
 }
 

@@ -258,10 +258,20 @@ struct Workspace {
   void *vec;          // [per real][nslab*bmax] BCR right-hand side / solution, prec-typed
   double *psum;       // [nsub] per-subdomain pressure sums
   double *gamma_tmp;  // one-sided velocities scratch (if user passes none)
-  int *status;        // [4] flags, local sweeps max, iface sweeps, spare
+  int *status;        // [8] flags, local sweeps max, iface sweeps, GMRES steps,
+                      // stalled subdomains listed for recovery, spare
   double *dstat;      // [2 + n_real] local resid max, iface resid, per real
   double *ifnorm;     // [n_real] ||f|| per realisation
   int *done;          // [n_real + 1] convergence flags
+  // refinement-stall recovery (mixed path): a subdomain whose FP32 refinement
+  // stalls is listed by the basis kernel, then re-factored in FP64 and its
+  // columns solved again by the same call (rec_cap = 0: no recovery)
+  int *stall_mark;     // [nsub] 1 once listed; cleared by the factor kernels
+  int *stall_list;     // [rec_cap] the listed subdomains (count: status[4])
+  double *W64;         // [rec_cap][rec_smax^3] their FP64 inverse Schur blocks
+  SubInfo *rec_sub;    // [rec_cap] their SubInfo, w_off pointing into W64
+  BasisItem *rec_items;  // [2][rec_cap * rec_maxch]: s = 16, then s = 32 items
+  int rec_cap, rec_maxch, rec_smax;
 };
 
 // Launch wrappers (return cudaGetLastError()).
@@ -271,6 +281,18 @@ cudaError_t launch_factor(const DeviceTables &t, const Workspace &w, int prec,
 cudaError_t launch_basis(const DeviceTables &t, const Workspace &w, int prec,
                          const BasisItem *items, int nitems16, int nitems32, int nc16, int nc32,
                          const double *q, double ir_tol, int ir_max, cudaStream_t st);
+// FP64 re-factor and re-solve of the subdomains the mixed basis kernels
+// listed (three launches; slots past the listed count return at once)
+cudaError_t launch_recover(const DeviceTables &t, const Workspace &w, const double *q,
+                           double ir_tol, cudaStream_t st);
+constexpr int kRecNC = 8;     // basis columns per CTA of the recovery solves
+// pure-Neumann problems: the compatibility check of the sources against the
+// boundary outflow (one launch, sets MRCM_FLAG_INCOMPATIBLE)
+cudaError_t launch_compat(const DeviceTables &t, const Workspace &w, const double *q,
+                          cudaStream_t st);
+// test hook: round n stored FP32 values (one subdomain's inverse Schur
+// blocks) to `bits` explicit mantissa bits, ties to even
+cudaError_t launch_degrade_factor(float *W, int n, int bits, cudaStream_t st);
 cudaError_t launch_iface_assemble(const DeviceTables &t, const Workspace &w, int prec,
                                   int64_t slab_elems, const int *pos2unk, int64_t npos,
                                   const int64_t *pos_real_off, cudaStream_t st);

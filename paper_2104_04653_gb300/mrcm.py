@@ -18,7 +18,7 @@ import numpy as np
 _LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libmrcm.so"
 
 MRCM_OK, MRCM_EINVAL, MRCM_ENOMEM, MRCM_ECUDA, MRCM_ENOTSPD = 0, 1, 2, 3, 4
-MRCM_EIRSTALL, MRCM_ENOCONV, MRCM_ENAN, MRCM_ETIMEOUT = 5, 6, 7, 8
+MRCM_EIRSTALL, MRCM_ENOCONV, MRCM_ENAN, MRCM_ETIMEOUT, MRCM_EINCOMPAT = 5, 6, 7, 8, 9
 PREC_FP64, PREC_FP32_IR = 0, 1
 BASIS_LEGENDRE, BASIS_MONOMIAL = 0, 1
 IFACE_AUTO, IFACE_DIRECT, IFACE_GMRES = 0, 1, 2
@@ -28,9 +28,12 @@ PATH_NONE, PATH_CLUSTER, PATH_SLAB, PATH_WIDE_SLAB, PATH_GMRES = 0, 1, 2, 3, 4
 PATH_NAMES = {0: "none", 1: "cluster", 2: "slab", 3: "wide-slab", 4: "gmres"}
 FLAG_PRECOND_FALLBACK = 0x40
 FLAG_TIMEOUT = 0x80          # a bounded device wait ran out (MRCM_ETIMEOUT)
+FLAG_LOCAL_STALL = 0x2
+FLAG_INCOMPATIBLE = 0x200    # pure Neumann: sources and boundary outflow do not balance
+FLAG_LOCAL_REFACTOR = 0x100  # stalled subdomains re-factored and re-solved in FP64
 STATUS_NAMES = {0: "MRCM_OK", 1: "MRCM_EINVAL", 2: "MRCM_ENOMEM", 3: "MRCM_ECUDA",
                 4: "MRCM_ENOTSPD", 5: "MRCM_EIRSTALL", 6: "MRCM_ENOCONV", 7: "MRCM_ENAN",
-                8: "MRCM_ETIMEOUT"}
+                8: "MRCM_ETIMEOUT", 9: "MRCM_EINCOMPAT"}
 
 EXPORTED = ["mrcm_setup", "mrcm_factor_local", "mrcm_build_basis", "mrcm_solve_interface",
             "mrcm_reconstruct", "mrcm_get_info", "mrcm_set_stream", "mrcm_launch_count",
@@ -61,13 +64,15 @@ class MrcmDesc(ctypes.Structure):
         ("gmres_tol", ctypes.c_double),
         ("iface_fn", ctypes.POINTER(ctypes.c_double)),
         ("refine", ctypes.POINTER(ctypes.c_int8)),
+        ("ir_recover", ctypes.c_int32),
     ]
 
 
 class MrcmInfo(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_int32), ("local_sweeps_max", ctypes.c_int32),
                 ("iface_sweeps", ctypes.c_int32), ("gmres_iters", ctypes.c_int32),
-                ("local_resid_max", ctypes.c_double), ("iface_resid", ctypes.c_double)]
+                ("local_resid_max", ctypes.c_double), ("iface_resid", ctypes.c_double),
+                ("local_refactored", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -164,6 +169,7 @@ class SolverOptions:
     gmres_restart: int = 40
     gmres_max: int = 5000
     gmres_tol: float = 0.0          # 0: iface_tol
+    ir_recover: int = 0             # FP64 re-factor of stalled subdomains: 0 = 16, < 0 = off
 
 
 class Mrcm:
@@ -222,6 +228,7 @@ class Mrcm:
         d.iface_solver, d.precond = opts.iface_solver, opts.precond
         d.gmres_restart, d.gmres_max = opts.gmres_restart, opts.gmres_max
         d.gmres_tol = opts.gmres_tol
+        d.ir_recover = opts.ir_recover
         self.desc = d
         if stream is None:
             stream = torch.cuda.current_stream()

@@ -87,6 +87,7 @@ def test_calls_on_null_context_fail_cleanly(L):
     assert L.mrcm_solve_interface(None, None) == mrcm.MRCM_EINVAL
     assert L.mrcm_reconstruct(None, None, None, None, None) == mrcm.MRCM_EINVAL
     assert L.mrcm_interface_path(None) == -1
+    assert L.mrcm_test_degrade_factor(None, 0, 7) == mrcm.MRCM_EINVAL
     L.mrcm_destroy(None)
 
 
