@@ -555,14 +555,10 @@ static cudaError_t big_factor_t(const BigPlan &bp, int *status, int *nlaunch, cu
       const int g0 = bp.gemm_off[2 * lev + set], ng = bp.gemm_off[2 * lev + set + 1] - g0;
       if (ng == 0) continue;
       if (sizeof(T) == sizeof(float) && bp.tensor_cores) {
-        for (int c0 = 0; c0 < ng; c0 += bp.tc_chunk) {
-          const int cnt = ng - c0 < bp.tc_chunk ? ng - c0 : bp.tc_chunk;
-          cudaError_t e = launch_tc_chunk(
-              bp.gemm + g0 + c0, static_cast<const char *>(bp.tc_maps) + (g0 + c0) * 8 * 128, cnt,
-              bp.bmax, bp.tc_planes, bp.tc_plane_elems, status, st);
-          if (e != cudaSuccess) return e;
-          ++*nlaunch;
-        }
+        cudaError_t e = launch_tc_split(bp.gemm + g0,
+                                        static_cast<const char *>(bp.tc_maps) + g0 * 4 * 128, ng,
+                                        bp.bmax, status, st);
+        if (e != cudaSuccess) return e;
       } else {
         k_bgemm<T><<<dim3(tiles * tiles, ng), 256, 0, st>>>(bp.gemm + g0);
       }

@@ -648,6 +648,10 @@ static mrcm_status build_tables(mrcm_ctx *c) {
       }
       if (pos > ri.bmax) ri.bmax = pos;
     }
+    // a multiple of 4 (positions past the widest slab are padding, identity
+    // on the diagonal): the FP32 slab blocks' rows start on 16-byte
+    // boundaries, as the tensor-core products' TMA copies require
+    ri.bmax = (ri.bmax + 3) & ~3;
     if (ri.bmax > 64) c->use_big = true;
     int nlev = 0;
     while ((1 << nlev) < ri.nslab) ++nlev;
@@ -1291,13 +1295,10 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     inv_slots = std::max<int64_t>(inv_slots, d.n_real);
   }
   const int64_t slot_elems = 64 * 64 + static_cast<int64_t>(c->bmax_max) * 64;
-  // tensor-core products (FP32 path): packed planes for one chunk of jobs and
-  // 8 tensor maps (128 bytes each) per job
+  // tensor-core products (FP32 path): 4 tensor maps (128 bytes each) per job,
+  // on the raw slab blocks
   const bool TC = BG && c->prec != MRCM_PREC_FP64 && !getenv("MRCM_NO_TENSOR_CORES");
-  const int tc_chunk = 64;
-  const int64_t tc_pe = static_cast<int64_t>(c->bmax_max) * tc_pack_ldp(c->bmax_max);
-  const size_t o_tcp = A.take<float>(TC ? static_cast<int64_t>(tc_chunk) * 8 * tc_pe : 0),
-               o_tcm = A.take<char>(TC ? n_gemm * 8 * 128 : 0);
+  const size_t o_tcm = A.take<char>(TC ? n_gemm * 4 * 128 : 0);
   const size_t o_vec2 = A.take<char>(BG ? (c->npos ? c->npos : 1) * esz : 0),
                o_iscr = A.take<char>(BG ? inv_slots * slot_elems * esz : 0),
                o_ijob = A.take<InvJob>(BG ? n_inv : 0), o_gjob = A.take<GemmJob>(BG ? n_gemm : 0),
@@ -1335,14 +1336,14 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
                           o_sI,   o_X,      o_Y,      o_ds,     o_f,    o_x,     o_r,
                           o_vec,  o_ps,     o_gt,     o_st,     o_gmGp, o_gmPbj, o_gmPid,
                           o_gmPus, o_gmV,   o_gmW,    o_gmY,    o_gmpart, o_gmres, o_gmint,
-                          o_tcp,  o_tcm,    o_vec2,   o_iscr,   o_ijob,   o_rW,   o_rsub};
+                          o_tcm,  o_vec2,   o_iscr,   o_ijob,   o_rW,     o_rsub};
     // spans [cut[k], cut[k+1]) hold floating-point data except those that
-    // start at o_st, o_gmint, o_tcm and o_ijob (entries 17, 27, 29 and 32);
+    // start at o_st, o_gmint, o_tcm and o_ijob (entries 17, 27, 28 and 31);
     // bit i names the i-th floating-point span: 0 coef .. 16 gt, 17 gmGp ..
-    // 25 gmres, 26 tcp, 27 vec2, 28 iscr, 29 the recovery's FP64 blocks
+    // 25 gmres, 26 vec2, 27 iscr, 28 the recovery's FP64 blocks
     int bit = 0;
     for (size_t k = 0; k + 1 < sizeof(cut) / sizeof(cut[0]); ++k) {
-      if (k == 17 || k == 27 || k == 29 || k == 32) continue;
+      if (k == 17 || k == 27 || k == 28 || k == 31) continue;
       const size_t a = cut[k], b = cut[k + 1];
       if (((mask >> bit++) & 1) && b > a &&
           (e = cudaMemset(base + a, 0xFF, b - a)) != cudaSuccess) {
@@ -1561,9 +1562,6 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     bp.nlev = bigLev;
     bp.bmax = c->bmax_max;
     bp.tensor_cores = TC ? 1 : 0;
-    bp.tc_chunk = tc_chunk;
-    bp.tc_planes = base + o_tcp;
-    bp.tc_plane_elems = tc_pe;
     bp.tc_maps = base + o_tcm;
     const size_t es = esz;
     char *sB = static_cast<char *>(w.slabB), *sA = static_cast<char *>(w.slabA),
@@ -1623,12 +1621,9 @@ mrcm_status mrcm_setup(const mrcm_desc *desc, void *cuda_stream, mrcm_ctx **out)
     std::vector<char> maps;
     bool maps_ok = true;
     if (TC) {
-      // job j of a set uses plane slot (j - set start) mod chunk
-      maps.assign(c->big_gemm.size() * 8 * 128, 0);
-      for (int sidx = 0; sidx < 2 * bigLev; ++sidx)
-        for (int j = bp.gemm_off[sidx]; j < bp.gemm_off[sidx + 1]; ++j)
-          maps_ok = maps_ok && tc_encode_maps(bp.tc_planes, tc_pe, (j - bp.gemm_off[sidx]) % tc_chunk,
-                                              c->big_gemm[j].n, maps.data() + static_cast<size_t>(j) * 8 * 128);
+      maps.assign(c->big_gemm.size() * 4 * 128, 0);
+      for (size_t j = 0; j < c->big_gemm.size(); ++j)
+        maps_ok = maps_ok && tc_encode_raw_maps(c->big_gemm[j], maps.data() + j * 4 * 128);
     }
     bp.inv = reinterpret_cast<const InvJob *>(base + o_ijob);
     bp.gemm = reinterpret_cast<const GemmJob *>(base + o_gjob);

@@ -172,10 +172,7 @@ struct GemmJob {     // C = alpha (A1 B1 + A2 B2) (+ C if acc), n x n row-major
 struct BigPlan {
   int K, nlev, bmax;             // slabs, levels, largest slab
   int tensor_cores;              // FP32 products on tcgen05 (3 x TF32)
-  const void *tc_maps;           // device tensor maps, 8 per GEMM job
-  void *tc_planes;               // packed operand planes of one chunk of jobs
-  int64_t tc_plane_elems;        // floats per plane
-  int tc_chunk;                  // jobs per chunk
+  const void *tc_maps;           // device tensor maps of the raw operands, 4 per GEMM job
   const int *lev_off;            // device [nlev + 1]: first multiplier slot of each level
   void *vec2;                    // second slab-ordered vector
   const InvJob *inv;             // device jobs, level by level, the root last
@@ -319,10 +316,9 @@ size_t tc_gemm_smem();
 cudaError_t launch_tc_gemm(const GemmJob *jobs, int njobs, int nmax, int *status,
                            cudaStream_t st);
 cudaError_t launch_simt_gemm(const GemmJob *jobs, int njobs, int nmax, cudaStream_t st);
-int tc_pack_ldp(int n);
-bool tc_encode_maps(void *plane_base, int64_t plane_elems, int slot, int n, void *out8);
-cudaError_t launch_tc_chunk(const GemmJob *jobs, const void *maps, int njobs, int nmax,
-                            void *plane_base, int64_t plane_elems, int *status, cudaStream_t st);
+bool tc_encode_raw_maps(const GemmJob &jb, void *out4);
+cudaError_t launch_tc_split(const GemmJob *jobs, const void *maps, int njobs, int nmax,
+                            int *status, cudaStream_t st);
 cudaError_t launch_big_factor(const BigPlan &bp, int prec, int *status, int *nlaunch,
                               cudaStream_t st);
 int big_solve_grid(int prec, int dev);

@@ -6,7 +6,8 @@
 // 2^-22 relative).  Used by the large-slab interface factor (the same job
 // descriptors as the SIMT kernel).
 //
-// Per CTA: one 128 x 128 output tile, 256 threads.  K advances in chunks of
+// Simple form (k_tc_gemm, the test hook's reference for the pipelined one):
+// one 128 x 128 output tile per CTA, 256 threads.  K advances in chunks of
 // 32: all threads load the chunk of A (128 rows) and B (128 columns),
 // split it and store the four operand tiles in shared memory in the
 // 128-byte-swizzled K-major layout; one thread issues 4 x 3 MMAs
@@ -20,6 +21,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cstdint>
+#include <cstring>
 #include <vector>
 
 namespace mrcm {
@@ -262,68 +264,29 @@ __global__ void __launch_bounds__(256) k_tc_gemm(const GemmJob *jobs, int *statu
 }
 
 // ---------------------------------------------------------------------------
-// Pipelined form.  A packing pass writes every product's operands as TF32
-// head and tail planes with rows padded to a multiple of 32 (zeros): A as
-// [n][ldp] (K contiguous), B transposed to [n][ldp] (row = output column,
-// K contiguous).  The GEMM kernel then streams 32-wide K chunks of the four
-// planes with TMA (cp.async.bulk.tensor, 128-byte swizzle, the MMA layout)
-// through a 3-stage ring: one thread issues the copies (full barriers with
-// transaction counts), one thread issues the MMAs and commits each stage
-// back to its empty barrier, and a final commit releases the epilogue.
-constexpr int kTcStages = 3;
-constexpr int kTcStageBytes = 4 * kTcTileBytes;       // A_hi A_lo B_hi B_lo
-
-// plane p (0 A_hi, 1 A_lo, 2 B_hi, 3 B_lo) of product q of job slot j
-__device__ __forceinline__ float *pack_plane(float *base, int64_t plane_elems, int slot, int q,
-                                             int p) {
-  return base + ((static_cast<int64_t>(slot) * 2 + q) * 4 + p) * plane_elems;
-}
-
-// grid: (32 x 32 tiles of [n][ldp], jobs of the chunk, product); 32 x 8 threads
-__global__ void __launch_bounds__(256) k_tc_pack(const GemmJob *jobs, float *base,
-                                                 int64_t plane_elems) {
-  __shared__ float tb[32][33];
-  const GemmJob jb = jobs[blockIdx.y];
-  const int q = blockIdx.z;
-  const float *A = static_cast<const float *>(q == 0 ? jb.a1 : jb.a2);
-  const float *B = static_cast<const float *>(q == 0 ? jb.b1 : jb.b2);
-  if (!A || !B) return;
-  const int n = jb.n, ldp = (n + kTcK - 1) / kTcK * kTcK;
-  const int tk = ldp / 32, tr = (n + 31) / 32;
-  if (static_cast<int>(blockIdx.x) >= tk * tr) return;
-  const int r0 = (blockIdx.x / tk) * 32, k0 = (blockIdx.x % tk) * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  float *ahi = pack_plane(base, plane_elems, blockIdx.y, q, 0);
-  float *alo = pack_plane(base, plane_elems, blockIdx.y, q, 1);
-  float *bhi = pack_plane(base, plane_elems, blockIdx.y, q, 2);
-  float *blo = pack_plane(base, plane_elems, blockIdx.y, q, 3);
-  for (int rr = ty; rr < 32; rr += 8) {
-    const int r = r0 + rr, k = k0 + tx;
-    if (r >= n) continue;
-    const float v = k < n ? A[static_cast<int64_t>(r) * n + k] : 0.0f;
-    const float hi = tf32_round(v);
-    ahi[static_cast<int64_t>(r) * ldp + k] = hi;
-    alo[static_cast<int64_t>(r) * ldp + k] = v - hi;
-  }
-  // B^T: tile rows k0.., columns r0.. of B become rows r0.., columns k0..
-  for (int kk = ty; kk < 32; kk += 8) {
-    const int k = k0 + kk, c = r0 + tx;
-    tb[kk][tx] = (k < n && c < n) ? B[static_cast<int64_t>(k) * n + c] : 0.0f;
-  }
-  __syncthreads();
-  for (int cc = ty; cc < 32; cc += 8) {
-    const int c = r0 + cc, k = k0 + tx;
-    if (c >= n) continue;
-    const float v = tb[tx][cc];
-    const float hi = tf32_round(v);
-    bhi[static_cast<int64_t>(c) * ldp + k] = hi;
-    blo[static_cast<int64_t>(c) * ldp + k] = v - hi;
-  }
-}
+// Pipelined form on the raw FP32 matrices (row strides a multiple of 16
+// bytes).  Per 32-wide K chunk, one thread issues two TMA copies
+// (cp.async.bulk.tensor): the 128 x 32 chunk of A in the 128-byte-swizzled
+// K-major layout the MMA reads, into the A-head slot, and the 32 x 128
+// row-major chunk of B, into the B-tail slot.  Four splitter warps then turn
+// the stage into TF32 head and tail tiles: A in place (head over the raw
+// value, tail at the same offset of the A-tail slot); B read into registers
+// (one output column per thread), then, after a named barrier of the four
+// warps, written transposed to K-major head and tail tiles (16-byte stores,
+// conflict-free under the swizzle).  One thread issues the MMAs of a stage
+// once the splitters have arrived, and commits the stage back to the
+// producer.  Three 64 KB stages; every mbarrier wait is bounded.
+constexpr int kTsStages = 3;
+constexpr int kTsStageBytes = 4 * kTcTileBytes;       // A_hi A_lo B_hi B_lo
+constexpr int kTsSplitters = 128;                      // warps 4..7
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
@@ -341,21 +304,22 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
       : "memory");
 }
 
-__global__ void __launch_bounds__(256) k_tc_gemm_tma(const GemmJob *jobs, const CUtensorMap *maps,
-                                                     int *status) {
+__global__ void __launch_bounds__(256) k_tc_gemm_split(const GemmJob *jobs,
+                                                       const CUtensorMap *maps, int *status) {
   extern __shared__ __align__(1024) unsigned char tcsm[];
-  __shared__ uint64_t full[kTcStages], empty[kTcStages], done;
+  __shared__ uint64_t full[kTsStages], split[kTsStages], empty[kTsStages], done;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   const uint32_t raw = smem_u32(tcsm);
   const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char *sm = tcsm + (base - raw);
 
   const GemmJob jb = jobs[blockIdx.y];
-  const CUtensorMap *mp = maps + static_cast<int64_t>(blockIdx.y) * 8;
+  const CUtensorMap *mp = maps + static_cast<int64_t>(blockIdx.y) * 4;
   const int n = jb.n;
   const int nt = (n + kTcM - 1) / kTcM;
   const int ti = blockIdx.x / nt, tj = blockIdx.x % nt;
-  if (ti >= nt) return;
+  if (ti >= nt) return;                       // whole CTA, before any barrier
   const int i0 = ti * kTcM, j0 = tj * kTcN;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int nk = (n + kTcK - 1) / kTcK;
@@ -369,8 +333,9 @@ __global__ void __launch_bounds__(256) k_tc_gemm_tma(const GemmJob *jobs, const 
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (t == 32) {
-    for (int s = 0; s < kTcStages; ++s) {
+    for (int s = 0; s < kTsStages; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&split[s]), kTsSplitters);
       mbar_init(smem_u32(&empty[s]), 1);
     }
     mbar_init(smem_u32(&done), 1);
@@ -383,32 +348,30 @@ __global__ void __launch_bounds__(256) k_tc_gemm_tma(const GemmJob *jobs, const 
   const uint32_t tmem = tmem_base;
 
   if (t == 0) {
-    // producer
+    // producer: raw A chunk -> A-head slot, raw B chunk -> B-tail slot
     for (int step = 0; step < total; ++step) {
-      const int s = step % kTcStages;
-      if (step >= kTcStages && !mbar_wait(smem_u32(&empty[s]), ((step / kTcStages) - 1) & 1)) {
+      const int s = step % kTsStages;
+      if (step >= kTsStages && !mbar_wait(smem_u32(&empty[s]), ((step / kTsStages) - 1) & 1)) {
         s_fail = 1;
         break;
       }
       const int q = first + step / nk, k0 = (step % nk) * kTcK;
-      const uint32_t st = base + s * kTcStageBytes, fb = smem_u32(&full[s]);
-      mbar_expect_tx(fb, kTcStageBytes);
-      tma_load_2d(st, mp + q * 4 + 0, k0, i0, fb);
-      tma_load_2d(st + kTcTileBytes, mp + q * 4 + 1, k0, i0, fb);
-      tma_load_2d(st + 2 * kTcTileBytes, mp + q * 4 + 2, k0, j0, fb);
-      tma_load_2d(st + 3 * kTcTileBytes, mp + q * 4 + 3, k0, j0, fb);
+      const uint32_t st = base + s * kTsStageBytes, fb = smem_u32(&full[s]);
+      mbar_expect_tx(fb, 2 * kTcTileBytes);
+      tma_load_2d(st, mp + 2 * q, k0, i0, fb);
+      tma_load_2d(st + 3 * kTcTileBytes, mp + 2 * q + 1, j0, k0, fb);
     }
   } else if (t == 32) {
     // MMA issuer
     const uint32_t idesc = idesc_tf32();
     for (int step = 0; step < total; ++step) {
-      const int s = step % kTcStages;
-      if (!mbar_wait(smem_u32(&full[s]), (step / kTcStages) & 1)) {
+      const int s = step % kTsStages;
+      if (!mbar_wait(smem_u32(&split[s]), (step / kTsStages) & 1)) {
         s_fail = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t st = base + s * kTcStageBytes;
+      const uint32_t st = base + s * kTsStageBytes;
 #pragma unroll
       for (int kk = 0; kk < kTcK / 8; ++kk) {
         const uint32_t off = kk * 32;
@@ -422,19 +385,73 @@ __global__ void __launch_bounds__(256) k_tc_gemm_tma(const GemmJob *jobs, const 
       tc_commit(smem_u32(&empty[s]));
     }
     tc_commit(smem_u32(&done));
+  } else if (warp >= 4) {
+    // splitters
+    const int u = t - 128;
+    for (int step = 0; step < total; ++step) {
+      const int s = step % kTsStages;
+      const bool okw = mbar_wait(smem_u32(&full[s]), (step / kTsStages) & 1);
+      unsigned char *stg = sm + s * kTsStageBytes;
+      float bv[kTcK];
+      if (okw) {
+        float4 *ah = reinterpret_cast<float4 *>(stg);
+        float4 *al = reinterpret_cast<float4 *>(stg + kTcTileBytes);
+#pragma unroll
+        for (int q = 0; q < kTcTileBytes / 16 / kTsSplitters; ++q) {
+          const int e = u + kTsSplitters * q;
+          const float4 v = ah[e];
+          const float4 h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z),
+                                       tf32_round(v.w));
+          ah[e] = h;
+          al[e] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        }
+        // B: column u of the 32 x 128 raw chunk into registers
+        const float *braw = reinterpret_cast<const float *>(stg + 3 * kTcTileBytes);
+#pragma unroll
+        for (int k = 0; k < kTcK; ++k) bv[k] = braw[k * kTcN + u];
+      }
+      // every splitter has read its column (the tail tile overwrites the raw
+      // chunk next); a wait that ran out anywhere stops all four warps alike
+      uint32_t anyfail;
+      asm volatile(
+          "{\n\t.reg .pred p, q;\n\t"
+          "setp.eq.u32 p, %1, 0;\n\t"
+          "bar.red.or.pred q, 1, 128, p;\n\t"
+          "selp.u32 %0, 1, 0, q;\n\t}\n"
+          : "=r"(anyfail)
+          : "r"(okw ? 1u : 0u)
+          : "memory");
+      if (anyfail) {
+        s_fail = 1;
+        break;
+      }
+      // row u of the K-major head and tail tiles of B
+#pragma unroll
+      for (int c = 0; c < kTcK / 4; ++c) {
+        const float4 v = make_float4(bv[4 * c], bv[4 * c + 1], bv[4 * c + 2], bv[4 * c + 3]);
+        const float4 h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z),
+                                     tf32_round(v.w));
+        const uint32_t o = sw128(u, 4 * c);
+        *reinterpret_cast<float4 *>(stg + 2 * kTcTileBytes + o) = h;
+        *reinterpret_cast<float4 *>(stg + 3 * kTcTileBytes + o) =
+            make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&split[s]));
+    }
   }
   __syncwarp();
   bool ok = mbar_wait(smem_u32(&done), 0);
   __syncthreads();
   ok = ok && !s_fail;
   asm volatile("tcgen05.fence::after_thread_sync;");
+  float *C = static_cast<float *>(jb.c);
   if (!ok) {
     if (t == 0) atomicOr(status, MRCM_FLAG_TIMEOUT);
     mbar_wait(smem_u32(&done), 0);
   } else if (total > 0) {
     const int quarter = warp & 3, half = warp >> 2;
     const int row = i0 + 32 * quarter + lane;
-    float *C = static_cast<float *>(jb.c);
     const float alpha = static_cast<float>(jb.alpha);
 #pragma unroll
     for (int cb = 0; cb < 2; ++cb) {
@@ -464,6 +481,12 @@ __global__ void __launch_bounds__(256) k_tc_gemm_tma(const GemmJob *jobs, const 
         }
       }
     }
+  } else if (!jb.acc) {
+    // no product: C = 0 (unchanged when accumulating)
+    for (int e = t; e < kTcM * kTcN; e += 256) {
+      const int r = i0 + e / kTcN, c = j0 + e % kTcN;
+      if (r < n && c < n) C[static_cast<int64_t>(r) * n + c] = 0.0f;
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -474,21 +497,22 @@ __global__ void __launch_bounds__(256) k_tc_gemm_tma(const GemmJob *jobs, const 
 }  // namespace
 
 size_t tc_gemm_smem() { return 4 * kTcTileBytes + 1024; }
-size_t tc_tma_smem() { return static_cast<size_t>(kTcStages) * kTcStageBytes + 1024; }
+size_t tc_split_smem() { return static_cast<size_t>(kTsStages) * kTsStageBytes + 1024; }
 
 cudaError_t init_tc_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(tc_gemm_smem()));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_tc_gemm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(tc_tma_smem()));
+  return cudaFuncSetAttribute(k_tc_gemm_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(tc_split_smem()));
 }
 
-int tc_pack_ldp(int n) { return (n + kTcK - 1) / kTcK * kTcK; }
-
-// Tensor maps of one job's packed planes (8 per job: product x plane), all
-// [n][ldp] FP32 with 32 x 128 boxes and the 128-byte swizzle.
-bool tc_encode_maps(void *plane_base, int64_t plane_elems, int slot, int n, void *out8) {
+// Tensor maps of one job's raw operands (4 per job: A1, B1, A2, B2; zero
+// for an absent product): n x n FP32 row-major.  A: 32 x 128 boxes (K, row)
+// with the 128-byte swizzle; B: 128 x 32 boxes (column, K), no swizzle.
+// False when the encoder refuses (e.g. a row stride that is not a multiple
+// of 16 bytes) or is unavailable.
+bool tc_encode_raw_maps(const GemmJob &jb, void *out4) {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   if (!enc) {
     cudaDriverEntryPointQueryResult q;
@@ -499,34 +523,32 @@ bool tc_encode_maps(void *plane_base, int64_t plane_elems, int slot, int n, void
       return false;
     enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const int ldp = tc_pack_ldp(n);
-  CUtensorMap *m = static_cast<CUtensorMap *>(out8);
-  for (int q = 0; q < 2; ++q)
-    for (int p = 0; p < 4; ++p) {
-      float *pl = static_cast<float *>(plane_base) +
-                  ((static_cast<int64_t>(slot) * 2 + q) * 4 + p) * plane_elems;
-      const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(ldp), static_cast<cuuint64_t>(n)};
-      const cuuint64_t gstr[1] = {static_cast<cuuint64_t>(ldp) * 4};
-      const cuuint32_t box[2] = {kTcK, kTcM};
-      const cuuint32_t es[2] = {1, 1};
-      if (enc(&m[q * 4 + p], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pl, gdim, gstr, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
-          CUDA_SUCCESS)
-        return false;
-    }
+  if (jb.n % 4 != 0) return false;
+  CUtensorMap *m = static_cast<CUtensorMap *>(out4);
+  const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(jb.n), static_cast<cuuint64_t>(jb.n)};
+  const cuuint64_t gstr[1] = {static_cast<cuuint64_t>(jb.n) * 4};
+  const cuuint32_t es[2] = {1, 1};
+  const void *ops[4] = {jb.a1, jb.b1, jb.a2, jb.b2};
+  for (int k = 0; k < 4; ++k) {
+    if (!ops[k]) continue;
+    const bool isA = (k % 2) == 0;
+    const cuuint32_t box[2] = {isA ? static_cast<cuuint32_t>(kTcK) : static_cast<cuuint32_t>(kTcN),
+                               isA ? static_cast<cuuint32_t>(kTcM) : static_cast<cuuint32_t>(kTcK)};
+    if (enc(&m[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(ops[k]), gdim, gstr, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            isA ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
   return true;
 }
 
-// one chunk of jobs (<= slots): pack, then the pipelined GEMM
-cudaError_t launch_tc_chunk(const GemmJob *jobs, const void *maps, int njobs, int nmax,
-                            void *plane_base, int64_t plane_elems, int *status, cudaStream_t st) {
+// all jobs of a set in one launch: (output tiles of the largest job, jobs)
+cudaError_t launch_tc_split(const GemmJob *jobs, const void *maps, int njobs, int nmax,
+                            int *status, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
-  const int ldp = tc_pack_ldp(nmax), t32 = (nmax + 31) / 32 * (ldp / 32);
-  k_tc_pack<<<dim3(t32, njobs, 2), 256, 0, st>>>(jobs, static_cast<float *>(plane_base),
-                                                 plane_elems);
   const int tiles = (nmax + kTcM - 1) / kTcM;
-  k_tc_gemm_tma<<<dim3(tiles * tiles, njobs), 256, tc_tma_smem(), st>>>(
+  k_tc_gemm_split<<<dim3(tiles * tiles, njobs), 256, tc_split_smem(), st>>>(
       jobs, static_cast<const CUtensorMap *>(maps), status);
   return cudaGetLastError();
 }
@@ -558,21 +580,19 @@ extern "C" mrcm_status mrcm_test_gemm(int32_t impl, int32_t n, const float *d_a1
     return MRCM_ECUDA;
   cudaError_t e;
   if (impl == 2) {
-    // scratch planes and maps for one job (allocated per call: a test hook)
-    const int64_t pe = static_cast<int64_t>(n) * tc_pack_ldp(n);
-    void *planes = nullptr, *dmaps = nullptr;
-    CUtensorMap hm[8];
-    if ((e = init_tc_attributes()) != cudaSuccess ||
-        cudaMalloc(&planes, sizeof(float) * pe * 8) != cudaSuccess ||
-        cudaMalloc(&dmaps, sizeof hm) != cudaSuccess)
+    // tensor maps of the caller's matrices (n a multiple of 4)
+    void *dmaps = nullptr;
+    CUtensorMap hm[4];
+    memset(hm, 0, sizeof hm);
+    if (n % 4 != 0) return MRCM_EINVAL;
+    if ((e = init_tc_attributes()) != cudaSuccess || cudaMalloc(&dmaps, sizeof hm) != cudaSuccess)
       return MRCM_ECUDA;
-    bool okm = tc_encode_maps(planes, pe, 0, n, hm);
-    if (okm && cudaMemcpyAsync(dmaps, hm, sizeof hm, cudaMemcpyHostToDevice, st) == cudaSuccess)
-      e = launch_tc_chunk(dj, dmaps, 1, n, planes, pe, d_status, st);
+    if (tc_encode_raw_maps(j, hm) &&
+        cudaMemcpyAsync(dmaps, hm, sizeof hm, cudaMemcpyHostToDevice, st) == cudaSuccess)
+      e = launch_tc_split(dj, dmaps, 1, n, d_status, st);
     else
       e = cudaErrorInvalidValue;
     cudaStreamSynchronize(st);
-    cudaFree(planes);
     cudaFree(dmaps);
   } else if (impl == 1) {
     if ((e = init_tc_attributes()) != cudaSuccess) return MRCM_ECUDA;

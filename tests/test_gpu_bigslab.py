@@ -110,9 +110,10 @@ def test_wide_slabs_graph_replay():
 def test_batched_gemm_kernels(impl, n):
     """C = alpha (A1 B1 + A2 B2) + C of the large-slab factor: the SIMT
     kernel (impl 0), the tcgen05 kernel with 3 x TF32 split products (impl
-    1: operands staged through registers; impl 2: packed head/tail planes
-    streamed by TMA through a 3-stage pipeline) against an FP64 product, in
-    both forms (one or two products, accumulate or not)."""
+    1: operands staged through registers; impl 2: the raw matrices streamed
+    by TMA through a 3-stage pipeline and split into head and tail in shared
+    memory, B transposed there) against an FP64 product, in both forms (one
+    or two products, accumulate or not)."""
     import ctypes
     import torch
     from paper_2104_04653_gb300 import mrcm
@@ -139,6 +140,12 @@ def test_batched_gemm_kernels(impl, n):
         # product and the TF32 tail truncation grow as sqrt(K) 2^-22
         assert err <= (2e-6 if impl == 0 else 1e-5), (impl, n, two, err)
     assert int(st.item()) == 0
+    if impl == 2:
+        # TMA needs row strides that are multiples of 16 bytes: n = 30 is refused
+        r = L.mrcm_test_gemm(2, 30, dev[0].data_ptr(), dev[1].data_ptr(), None, None,
+                             dev[4].data_ptr(), 1.0, 0, st.data_ptr(),
+                             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert r == mrcm.MRCM_EINVAL
 
 
 def test_bounded_wait_reports_timeout():
