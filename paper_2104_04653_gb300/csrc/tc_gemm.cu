@@ -265,19 +265,19 @@ __global__ void __launch_bounds__(256) k_tc_gemm(const GemmJob *jobs, int *statu
 
 // ---------------------------------------------------------------------------
 // Pipelined form on the raw FP32 matrices (row strides a multiple of 16
-// bytes).  Per 32-wide K chunk, one thread issues two TMA copies
-// (cp.async.bulk.tensor): the 128 x 32 chunk of A in the 128-byte-swizzled
-// K-major layout the MMA reads, into the A-head slot, and the 32 x 128
-// row-major chunk of B, into the B-tail slot.  Four splitter warps then turn
-// the stage into TF32 head and tail tiles: A in place (head over the raw
-// value, tail at the same offset of the A-tail slot); B read into registers
-// (one output column per thread), then, after a named barrier of the four
-// warps, written transposed to K-major head and tail tiles (16-byte stores,
-// conflict-free under the swizzle).  One thread issues the MMAs of a stage
-// once the splitters have arrived, and commits the stage back to the
-// producer.  Three 64 KB stages; every mbarrier wait is bounded.
-constexpr int kTsStages = 3;
-constexpr int kTsStageBytes = 4 * kTcTileBytes;       // A_hi A_lo B_hi B_lo
+// bytes), in two rings.  Raw ring (3 x 32 KB): per 32-wide K chunk one thread
+// issues two TMA copies (cp.async.bulk.tensor), the 128 x 32 chunk of A in
+// the 128-byte-swizzled K-major layout the MMA reads and the 32 x 128
+// row-major chunk of B.  Four splitter warps read a raw stage into registers
+// and release it at once (the copies run up to three chunks ahead, whatever
+// the MMAs are doing), then write the TF32 head and tail tiles into the
+// split ring (2 x 64 KB): A at the same offsets, B transposed to K-major
+// (16-byte stores, conflict-free under the swizzle).  One thread issues the
+// MMAs of a split stage and commits it back to the splitters.  Every
+// mbarrier wait is bounded.
+constexpr int kTsRaw = 3, kTsSplit = 2;
+constexpr int kTsRawBytes = 2 * kTcTileBytes;         // A (swizzled), B (row-major)
+constexpr int kTsSplitBytes = 4 * kTcTileBytes;       // A_hi A_lo B_hi B_lo
 constexpr int kTsSplitters = 128;                      // warps 4..7
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
@@ -307,12 +307,14 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
 __global__ void __launch_bounds__(256) k_tc_gemm_split(const GemmJob *jobs,
                                                        const CUtensorMap *maps, int *status) {
   extern __shared__ __align__(1024) unsigned char tcsm[];
-  __shared__ uint64_t full[kTsStages], split[kTsStages], empty[kTsStages], done;
+  __shared__ uint64_t rfull[kTsRaw], rempty[kTsRaw], hfull[kTsSplit], hempty[kTsSplit], done;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   const uint32_t raw = smem_u32(tcsm);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char *sm = tcsm + (base - raw);
+  const uint32_t hbase = base + kTsRaw * kTsRawBytes;     // split ring after the raw ring
+  unsigned char *hsm = sm + kTsRaw * kTsRawBytes;
 
   const GemmJob jb = jobs[blockIdx.y];
   const CUtensorMap *mp = maps + static_cast<int64_t>(blockIdx.y) * 4;
@@ -333,10 +335,13 @@ __global__ void __launch_bounds__(256) k_tc_gemm_split(const GemmJob *jobs,
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (t == 32) {
-    for (int s = 0; s < kTsStages; ++s) {
-      mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&split[s]), kTsSplitters);
-      mbar_init(smem_u32(&empty[s]), 1);
+    for (int s = 0; s < kTsRaw; ++s) {
+      mbar_init(smem_u32(&rfull[s]), 1);
+      mbar_init(smem_u32(&rempty[s]), kTsSplitters);
+    }
+    for (int s = 0; s < kTsSplit; ++s) {
+      mbar_init(smem_u32(&hfull[s]), kTsSplitters);
+      mbar_init(smem_u32(&hempty[s]), 1);
     }
     mbar_init(smem_u32(&done), 1);
     s_fail = 0;
@@ -348,30 +353,30 @@ __global__ void __launch_bounds__(256) k_tc_gemm_split(const GemmJob *jobs,
   const uint32_t tmem = tmem_base;
 
   if (t == 0) {
-    // producer: raw A chunk -> A-head slot, raw B chunk -> B-tail slot
+    // producer: raw chunks of A and B into the raw ring
     for (int step = 0; step < total; ++step) {
-      const int s = step % kTsStages;
-      if (step >= kTsStages && !mbar_wait(smem_u32(&empty[s]), ((step / kTsStages) - 1) & 1)) {
+      const int s = step % kTsRaw;
+      if (step >= kTsRaw && !mbar_wait(smem_u32(&rempty[s]), ((step / kTsRaw) - 1) & 1)) {
         s_fail = 1;
         break;
       }
       const int q = first + step / nk, k0 = (step % nk) * kTcK;
-      const uint32_t st = base + s * kTsStageBytes, fb = smem_u32(&full[s]);
-      mbar_expect_tx(fb, 2 * kTcTileBytes);
+      const uint32_t st = base + s * kTsRawBytes, fb = smem_u32(&rfull[s]);
+      mbar_expect_tx(fb, kTsRawBytes);
       tma_load_2d(st, mp + 2 * q, k0, i0, fb);
-      tma_load_2d(st + 3 * kTcTileBytes, mp + 2 * q + 1, j0, k0, fb);
+      tma_load_2d(st + kTcTileBytes, mp + 2 * q + 1, j0, k0, fb);
     }
   } else if (t == 32) {
     // MMA issuer
     const uint32_t idesc = idesc_tf32();
     for (int step = 0; step < total; ++step) {
-      const int s = step % kTsStages;
-      if (!mbar_wait(smem_u32(&split[s]), (step / kTsStages) & 1)) {
+      const int h = step % kTsSplit;
+      if (!mbar_wait(smem_u32(&hfull[h]), (step / kTsSplit) & 1)) {
         s_fail = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t st = base + s * kTsStageBytes;
+      const uint32_t st = hbase + h * kTsSplitBytes;
 #pragma unroll
       for (int kk = 0; kk < kTcK / 8; ++kk) {
         const uint32_t off = kk * 32;
@@ -382,62 +387,55 @@ __global__ void __launch_bounds__(256) k_tc_gemm_split(const GemmJob *jobs,
         mma_tf32(tmem, ah, bl, idesc, 1u);
         mma_tf32(tmem, al, bh, idesc, 1u);
       }
-      tc_commit(smem_u32(&empty[s]));
+      tc_commit(smem_u32(&hempty[h]));
     }
     tc_commit(smem_u32(&done));
   } else if (warp >= 4) {
-    // splitters
+    // splitters: raw stage -> registers (then released) -> head and tail tiles
     const int u = t - 128;
     for (int step = 0; step < total; ++step) {
-      const int s = step % kTsStages;
-      const bool okw = mbar_wait(smem_u32(&full[s]), (step / kTsStages) & 1);
-      unsigned char *stg = sm + s * kTsStageBytes;
-      float bv[kTcK];
-      if (okw) {
-        float4 *ah = reinterpret_cast<float4 *>(stg);
-        float4 *al = reinterpret_cast<float4 *>(stg + kTcTileBytes);
-#pragma unroll
-        for (int q = 0; q < kTcTileBytes / 16 / kTsSplitters; ++q) {
-          const int e = u + kTsSplitters * q;
-          const float4 v = ah[e];
-          const float4 h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z),
-                                       tf32_round(v.w));
-          ah[e] = h;
-          al[e] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-        }
-        // B: column u of the 32 x 128 raw chunk into registers
-        const float *braw = reinterpret_cast<const float *>(stg + 3 * kTcTileBytes);
-#pragma unroll
-        for (int k = 0; k < kTcK; ++k) bv[k] = braw[k * kTcN + u];
-      }
-      // every splitter has read its column (the tail tile overwrites the raw
-      // chunk next); a wait that ran out anywhere stops all four warps alike
-      uint32_t anyfail;
-      asm volatile(
-          "{\n\t.reg .pred p, q;\n\t"
-          "setp.eq.u32 p, %1, 0;\n\t"
-          "bar.red.or.pred q, 1, 128, p;\n\t"
-          "selp.u32 %0, 1, 0, q;\n\t}\n"
-          : "=r"(anyfail)
-          : "r"(okw ? 1u : 0u)
-          : "memory");
-      if (anyfail) {
+      const int s = step % kTsRaw, h = step % kTsSplit;
+      if (!mbar_wait(smem_u32(&rfull[s]), (step / kTsRaw) & 1)) {
         s_fail = 1;
         break;
       }
-      // row u of the K-major head and tail tiles of B
+      const unsigned char *rs = sm + s * kTsRawBytes;
+      float4 av[kTcTileBytes / 16 / kTsSplitters];
+#pragma unroll
+      for (int q = 0; q < kTcTileBytes / 16 / kTsSplitters; ++q)
+        av[q] = reinterpret_cast<const float4 *>(rs)[u + kTsSplitters * q];
+      float bv[kTcK];
+      const float *braw = reinterpret_cast<const float *>(rs + kTcTileBytes);
+#pragma unroll
+      for (int k = 0; k < kTcK; ++k) bv[k] = braw[k * kTcN + u];
+      mbar_arrive(smem_u32(&rempty[s]));
+      if (step >= kTsSplit && !mbar_wait(smem_u32(&hempty[h]), ((step / kTsSplit) - 1) & 1)) {
+        s_fail = 1;
+        break;
+      }
+      unsigned char *hs = hsm + h * kTsSplitBytes;
+#pragma unroll
+      for (int q = 0; q < kTcTileBytes / 16 / kTsSplitters; ++q) {
+        const float4 v = av[q];
+        const float4 hi = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z),
+                                      tf32_round(v.w));
+        const int e = u + kTsSplitters * q;
+        reinterpret_cast<float4 *>(hs)[e] = hi;
+        reinterpret_cast<float4 *>(hs + kTcTileBytes)[e] =
+            make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
+      }
 #pragma unroll
       for (int c = 0; c < kTcK / 4; ++c) {
         const float4 v = make_float4(bv[4 * c], bv[4 * c + 1], bv[4 * c + 2], bv[4 * c + 3]);
-        const float4 h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z),
-                                     tf32_round(v.w));
+        const float4 hi = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z),
+                                      tf32_round(v.w));
         const uint32_t o = sw128(u, 4 * c);
-        *reinterpret_cast<float4 *>(stg + 2 * kTcTileBytes + o) = h;
-        *reinterpret_cast<float4 *>(stg + 3 * kTcTileBytes + o) =
-            make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        *reinterpret_cast<float4 *>(hs + 2 * kTcTileBytes + o) = hi;
+        *reinterpret_cast<float4 *>(hs + 3 * kTcTileBytes + o) =
+            make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(smem_u32(&split[s]));
+      mbar_arrive(smem_u32(&hfull[h]));
     }
   }
   __syncwarp();
@@ -450,9 +448,14 @@ __global__ void __launch_bounds__(256) k_tc_gemm_split(const GemmJob *jobs,
     if (t == 0) atomicOr(status, MRCM_FLAG_TIMEOUT);
     mbar_wait(smem_u32(&done), 0);
   } else if (total > 0) {
+    // epilogue: warp w holds output rows 32 (w % 4) .. + 31 (its TMEM lane
+    // quarter), columns 64 (w / 4) .. + 63 in two 32-column blocks; each
+    // block goes through a padded 32 x 33 shared buffer (the split ring is
+    // idle now), so that every global load and store covers a 128-byte row
+    // segment instead of one word in each of 32 rows
     const int quarter = warp & 3, half = warp >> 2;
-    const int row = i0 + 32 * quarter + lane;
     const float alpha = static_cast<float>(jb.alpha);
+    float *buf = reinterpret_cast<float *>(hsm) + warp * 32 * 33;
 #pragma unroll
     for (int cb = 0; cb < 2; ++cb) {
       const int col0 = 64 * half + 32 * cb;
@@ -469,17 +472,20 @@ __global__ void __launch_bounds__(256) k_tc_gemm_split(const GemmJob *jobs,
             "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (row < n) {
-        float *cr = C + static_cast<int64_t>(row) * n;
 #pragma unroll
-        for (int qq = 0; qq < 32; ++qq) {
-          const int gj = j0 + col0 + qq;
-          if (gj < n) {
-            const float a = alpha * __uint_as_float(v[qq]);
-            cr[gj] = jb.acc ? cr[gj] + a : a;
-          }
+      for (int qq = 0; qq < 32; ++qq) buf[lane * 33 + qq] = __uint_as_float(v[qq]);
+      __syncwarp();
+      const int gj = j0 + col0 + lane;
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r) {
+        const int gi = i0 + 32 * quarter + r;
+        if (gi < n && gj < n) {
+          float *cp = C + static_cast<int64_t>(gi) * n + gj;
+          const float a = alpha * buf[r * 33 + lane];
+          *cp = jb.acc ? *cp + a : a;
         }
       }
+      __syncwarp();
     }
   } else if (!jb.acc) {
     // no product: C = 0 (unchanged when accumulating)
@@ -497,7 +503,10 @@ __global__ void __launch_bounds__(256) k_tc_gemm_split(const GemmJob *jobs,
 }  // namespace
 
 size_t tc_gemm_smem() { return 4 * kTcTileBytes + 1024; }
-size_t tc_split_smem() { return static_cast<size_t>(kTsStages) * kTsStageBytes + 1024; }
+size_t tc_split_smem() {
+  return static_cast<size_t>(kTsRaw) * kTsRawBytes + static_cast<size_t>(kTsSplit) * kTsSplitBytes +
+         1024;
+}
 
 cudaError_t init_tc_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
