@@ -333,6 +333,8 @@ __device__ __forceinline__ T row_dot(const T *row, const T *x, int n) {
   return warp_sum(acc);
 }
 
+constexpr int kBsCols = 4 * kMmax + 1;   // columns of a subdomain (uniform layouts)
+
 // Refinement with the big-slab reduction solve, all realisations in one
 // cooperative launch.  Each sweep: x += T^T y; r = f - M x (FP64), z = T
 // (sign r); stop test per realisation; y = Shat^{-1} z by cyclic reduction
@@ -344,6 +346,7 @@ __global__ void __launch_bounds__(256) k_big_solve(DeviceTables t, Workspace w, 
   __shared__ double red[8];
   __shared__ double s_rel;
   __shared__ double wbuf[8][kMmax];
+  __shared__ double xg[8][2 * kBsCols];   // per warp: x of the two subdomains' columns
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int gwarp = blockIdx.x * 8 + wid;
   const int nwarps = gridDim.x * 8;
@@ -369,19 +372,52 @@ __global__ void __launch_bounds__(256) k_big_solve(DeviceTables t, Workspace w, 
       }
       grid.sync();
     }
-    // B: FP64 residual, scaled into the slab vector
+    // B: FP64 residual, scaled into the slab vector.  The rows of an
+    // interface share the column lists of its two subdomains: the warp first
+    // gathers those columns' x into shared memory (independent loads, 32 at
+    // a time), then each lane (one unknown) sums its two contiguous G rows
+    // against them in four independent chains.
     for (int g = gwarp; g < t.niface; g += nwarps) {
       const IfaceInfo fi = t.iface[g];
       if (__ldcg(w.done + fi.r)) continue;
       const RealInfo &ri = t.real[fi.r];
       const int m = fi.nU + fi.nP;
+      const int ncL = t.sub[fi.L].ncols, ncR = t.sub[fi.R].ncols;
+      const int offL = t.sub[fi.L].col_off, offR = t.sub[fi.R].col_off;
+      const bool staged = ncL <= kBsCols && ncR <= kBsCols;
+      double *xl = xg[wid], *xr = xl + kBsCols;
+      if (staged) {
+        for (int c = 1 + lane; c < ncL; c += 32) xl[c] = __ldcg(w.x + t.col[offL + c].unk);
+        for (int c = 1 + lane; c < ncR; c += 32) xr[c] = __ldcg(w.x + t.col[offR + c].unk);
+      }
+      __syncwarp();
       double rv = 0.0;
       if (lane < m && fi.unk + lane != ri.pin) {
         const RowRef rr = row_ref(t, w, fi, lane);
-        double sacc = w.f[fi.unk + lane];
-        for (int c = 1; c < rr.ncL; ++c) sacc -= rr.gL[c] * __ldcg(w.x + t.col[rr.offL + c].unk);
-        for (int c = 1; c < rr.ncR; ++c) sacc -= rr.gR[c] * __ldcg(w.x + t.col[rr.offR + c].unk);
-        rv = sacc;
+        if (staged) {
+          double s0 = w.f[fi.unk + lane], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+          int c = 1;
+          for (; c + 3 < ncL; c += 4) {
+            s0 -= rr.gL[c] * xl[c];
+            s1 -= rr.gL[c + 1] * xl[c + 1];
+            s2 -= rr.gL[c + 2] * xl[c + 2];
+            s3 -= rr.gL[c + 3] * xl[c + 3];
+          }
+          for (; c < ncL; ++c) s0 -= rr.gL[c] * xl[c];
+          for (c = 1; c + 3 < ncR; c += 4) {
+            s0 -= rr.gR[c] * xr[c];
+            s1 -= rr.gR[c + 1] * xr[c + 1];
+            s2 -= rr.gR[c + 2] * xr[c + 2];
+            s3 -= rr.gR[c + 3] * xr[c + 3];
+          }
+          for (; c < ncR; ++c) s0 -= rr.gR[c] * xr[c];
+          rv = (s0 + s1) + (s2 + s3);
+        } else {
+          double sacc = w.f[fi.unk + lane];
+          for (int c = 1; c < ncL; ++c) sacc -= rr.gL[c] * __ldcg(w.x + t.col[offL + c].unk);
+          for (int c = 1; c < ncR; ++c) sacc -= rr.gR[c] * __ldcg(w.x + t.col[offR + c].unk);
+          rv = sacc;
+        }
       }
       double sq = rv * rv;
       for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
