@@ -111,7 +111,7 @@ def call_work(call: str, prob, solver=None) -> dict:
             tot_f32 += max(sweeps - 1, 0) * solve
         path = solver.interface_path() if solver is not None else "cluster"
         kern = {"cluster": "k_iface_cluster", "slab": "k_bcr_level + k_iface_solve",
-                "wide-slab": "k_gj_* + k_tc_gemm_tma + k_big_solve", "gmres": "k_gmres",
+                "wide-slab": "k_gj_* + k_tc_gemm_split + k_big_solve", "gmres": "k_gmres",
                 "none": "-"}[path]
         return {"kernel": kern, "bound": "alu", "flops": tot_f32 + tot_f64,
                 "flops_fp32": tot_f32, "flops_fp64": tot_f64,
