@@ -718,6 +718,25 @@ def roofline_entry(call, seconds, prob, solver, peaks, src, clocks):
         ach = w["bytes"] / seconds / 1e9
         unit = "GB/s"
         note = f"{src} HBM copy bandwidth"
+    elif w["bound"] == "tensor":
+        # composite: the time each part of the call takes at its own unit's
+        # peak.  Products (FP32-equivalent, 3 TF32 products each) at the
+        # measured sustained bf16 rate x the nominal TF32/bf16 ratio
+        # (1.1/2.25) / 3; inverses and solves at the FP32 SIMT rate; the FP64
+        # residual terms at 1.67 FP64 FMA per clock per SM (measured on this
+        # part); peak = all the call's flops / that time
+        simt = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        bf16 = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
+        tc = bf16 * (1.1 / 2.25) / 3.0
+        f64 = 152 * 1.67 * 2 * sm_mhz * 1e6 / 1e12
+        t_min = (w["flops_products"] / tc + (w["flops_inverse"] + w["flops_solve"]) / simt +
+                 w["flops_fp64"] / f64) / 1e12
+        peak = w["flops"] / t_min / 1e12
+        ach = w["flops"] / seconds / 1e12
+        unit = "TFLOP/s"
+        note = (f"composite at the sampled {sm_mhz:.0f} MHz: products at {tc:.0f} TFLOP/s "
+                f"({src} sustained bf16 {bf16:.0f} x 1.1/2.25 / 3 TF32 products), inverses and "
+                f"solves at FP32 SIMT {simt:.1f}, FP64 residual terms at {f64:.2f}")
     else:
         # FP32 SIMT issue rate: 152 SMs x 128 FP32 lanes x 2 flop x clock
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12

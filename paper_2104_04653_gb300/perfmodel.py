@@ -6,6 +6,8 @@ interface matrix by slabs), not the instructions a kernel happens to issue.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 
@@ -64,6 +66,7 @@ def call_work(call: str, prob, solver=None) -> dict:
         # block cyclic reduction over slabs (one column of subdomains each)
         # plus the refinement sweeps, counted on the method's own layout
         tot_f32 = tot_f64 = 0.0
+        inv_f32 = gemm_f32 = solve_f32 = 0.0
         sweeps = 1 + int(info.get("iface_sweeps", 0) or 0)
         for r in range(R):
             s_ = prob.sub_size[r]
@@ -86,15 +89,15 @@ def call_work(call: str, prob, solver=None) -> dict:
             while st < K:
                 surv = list(range(0, K, 2 * st))
                 odd = list(range(st, K, 2 * st))
-                tot_f32 += len(odd) * 2.0 * b ** 3                   # Gauss-Jordan inverses
+                inv_f32 += len(odd) * 2.0 * b ** 3                   # Gauss-Jordan inverses
                 for k in surv:
                     if k - st >= 0:
-                        tot_f32 += 3 * 2.0 * b ** 3                   # X, X C_l, X A_l
+                        gemm_f32 += 3 * 2.0 * b ** 3                  # X, X C_l, X A_l
                     if k + st < K:
-                        tot_f32 += 3 * 2.0 * b ** 3                   # Y, Y A_r, Y C_r
+                        gemm_f32 += 3 * 2.0 * b ** 3                  # Y, Y A_r, Y C_r
                 st *= 2
                 lev += 1
-            tot_f32 += 2.0 * b ** 3                                   # root inverse
+            inv_f32 += 2.0 * b ** 3                                   # root inverse
             # refinement: FP64 residual rows (2 flops per term) and the solve
             cols = _ncols(prob, r)
             terms = 0                     # FP64 terms of all interface rows
@@ -108,13 +111,19 @@ def call_work(call: str, prob, solver=None) -> dict:
                 terms += int(m[g]) * (cols[L] - 1 + cols[Rr] - 1)
             solve = 2.0 * b * b * (4 * (K - 1) + 1)
             tot_f64 += sweeps * 2.0 * terms
-            tot_f32 += max(sweeps - 1, 0) * solve
+            solve_f32 += max(sweeps - 1, 0) * solve
+        tot_f32 = inv_f32 + gemm_f32 + solve_f32
         path = solver.interface_path() if solver is not None else "cluster"
         kern = {"cluster": "k_iface_cluster", "slab": "k_bcr_level + k_iface_solve",
                 "wide-slab": "k_gj_* + k_tc_gemm_split + k_big_solve", "gmres": "k_gmres",
                 "none": "-"}[path]
-        return {"kernel": kern, "bound": "alu", "flops": tot_f32 + tot_f64,
+        # the wide-slab path's block products run on the tensor cores (FP32
+        # path, 3 x TF32); its inverses, solves and residuals on SIMT pipes
+        prec = getattr(getattr(solver, "desc", None), "prec", 1) if solver is not None else 1
+        tc = path == "wide-slab" and prec == 1 and not os.environ.get("MRCM_NO_TENSOR_CORES")
+        return {"kernel": kern, "bound": "tensor" if tc else "alu", "flops": tot_f32 + tot_f64,
                 "flops_fp32": tot_f32, "flops_fp64": tot_f64,
+                "flops_inverse": inv_f32, "flops_products": gemm_f32, "flops_solve": solve_f32,
                 "bytes": float(sum(int(np.sum(np.asarray(prob.iface_nU[r]) +
                                               np.asarray(prob.iface_nP[r]))) for r in range(R)) * 8),
                 "per_unit": "per level: 2 b^3 per eliminated slab (inverse) + 6 b^3 x2 per "
