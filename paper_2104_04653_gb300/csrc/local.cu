@@ -1072,6 +1072,8 @@ struct Basis32W {
   float W[kS32 * kS32 * kS32];   // W_j, j = 0..31, row-major [j][a][q]
   float ec[kS32 * kS32];         // scaled row couplings e_j[a]
   float z[NW][kS32 * kS32];      // each warp's scaled residual, [j][a]
+  double diag[kS32 * kS32];      // FP64 diagonal tW + tE + tS + tN of every cell
+  float dsf[kS32 * kS32];        // the Jacobi scale d in FP32
   ColInfo col[NW];
 };
 
@@ -1101,10 +1103,15 @@ __global__ void __launch_bounds__(32 * NW, 1) k_basis32w(DeviceTables t, Workspa
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
   if (tid < nc) sm.col[tid] = t.col[sb.col_off + it.c0 + tid];
-  for (int k = tid; k < N; k += 32 * NW)
+  // per-cell constants of every sweep, formed once per CTA (the FP64 pipe
+  // bounds this kernel)
+  for (int k = tid; k < N; k += 32 * NW) {
     sm.ec[k] = k / S < S - 1
                    ? static_cast<float>(-coef[3 * N + k] * coef[4 * N + k] * coef[4 * N + k + S])
                    : 0.0f;
+    sm.diag[k] = coef[k] + coef[N + k] + coef[2 * N + k] + coef[3 * N + k];
+    sm.dsf[k] = static_cast<float>(coef[4 * N + k]);
+  }
   __syncthreads();
   const bool act = c < nc;
   ColInfo ci{};
@@ -1150,7 +1157,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_basis32w(DeviceTables t, Workspa
     // backward: y_j = v_j - W_j (e_j y_{j+1}), y_31 = v_31; then x += D y
     // (the correction in FP32, accumulated in FP64)
     Xc[(S - 1) * S + lane] += static_cast<double>(
-        static_cast<float>(coef[4 * N + (S - 1) * S + lane]) * vp);
+        sm.dsf[(S - 1) * S + lane] * vp);
 #pragma unroll 4
     for (int j = S - 2; j >= 0; --j) {
       const float tq = sm.ec[j * S + lane] * vp;
@@ -1163,7 +1170,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_basis32w(DeviceTables t, Workspa
         a1 = fmaf(Wa[q1], __shfl_sync(FULL, tq, q1), a1);
       }
       vp = zc[j * S + lane] - (a0 + a1);
-      Xc[j * S + lane] += static_cast<double>(static_cast<float>(coef[4 * N + j * S + lane]) * vp);
+      Xc[j * S + lane] += static_cast<double>(sm.dsf[j * S + lane] * vp);
     }
     if (sweep >= ir_max) break;
     // FP64 residual r = b - A x over rows j-1, j, j+1 of this lane's cells
@@ -1174,13 +1181,13 @@ __global__ void __launch_bounds__(32 * NW, 1) k_basis32w(DeviceTables t, Workspa
       const double xl = __shfl_up_sync(FULL, xc, 1), xr = __shfl_down_sync(FULL, xc, 1);
       const int k = j * S + lane;
       const double tW = coef[k], tE = coef[N + k], tS = coef[2 * N + k], tN = coef[3 * N + k];
-      const double diag = tW + tE + tS + tN;
+      const double diag = sm.diag[k];
       double r = fma(-diag, xc, rhs_value<S>(t, sb, coef, q, ci, lane, j));
       if (lane > 0) r = fma(tW, xl, r);
       if (lane < S - 1) r = fma(tE, xr, r);
       if (j > 0) r = fma(tS, xm, r);
       if (j < S - 1) r = fma(tN, xp, r);
-      const float zv = static_cast<float>(r) * static_cast<float>(coef[4 * N + k]);
+      const float zv = static_cast<float>(r) * sm.dsf[k];
       zc[k] = zv;
       rn = fmaf(zv, zv, rn);
       xm = xc;
