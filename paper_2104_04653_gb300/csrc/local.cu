@@ -262,6 +262,114 @@ __device__ __forceinline__ bool schur_inverses(int lane, const T *offx, const T 
   return bad;
 }
 
+// Twisted form of the chain above (FP32, the fused basis path): the block
+// rows are eliminated from both ends at once and meet at the middle block
+// M = S / 2.  Warp 0 (half 0) forms W_j = (A_jj - E_{j-1} W_{j-1} E_{j-1})^-1
+// for j = 0 .. M-1 as before; warp 1 (half 1) forms W_j = (A_jj - E_j W_{j+1}
+// E_j)^-1 for j = S-1 down to M+1; warp 0 then inverts the middle block
+// A_MM - E_{M-1} W_{M-1} E_{M-1} - E_M W_{M+1} E_M, with W_{M+1} read from
+// shared memory after a 64-thread named barrier (id 2; warp 1 reaches it
+// once its chain is written).  The dependent chain is M + 1 block inverses
+// instead of S.  E_j = diag(ecp[j S ..]) couples block rows j and j + 1.
+template <int S>
+__device__ __forceinline__ bool schur_inverses_twisted(int half, int lane, const float *offx,
+                                                       const float *ecp, float *Wg) {
+  using T = float;
+  constexpr int N = S * S, LR = S / 4, LC = S / 8, M = S / 2;
+  static_assert(LR * 4 == S && LC * 8 == S && LR % 2 == 0 && LC % 2 == 0,
+                "S must be a multiple of 16 so that pivot pairs stay inside a lane block");
+  const int rb = lane >> 3, cb = lane & 7;
+  T R[LR][LC];
+#pragma unroll
+  for (int q = 0; q < LR; ++q)
+#pragma unroll
+    for (int w = 0; w < LC; ++w) R[q][w] = T(0);
+  bool bad = false;
+  const int nsteps = half == 0 ? M + 1 : S - 1 - M;
+#pragma unroll 1
+  for (int k = 0; k < nsteps; ++k) {
+    const int j = half == 0 ? k : S - 1 - k;
+    const bool mid = half == 0 && j == M;
+    if (mid) asm volatile("bar.sync 2, 64;" ::: "memory");   // W_{M+1} is in Wg
+    const bool has = half == 0 ? j > 0 : j < S - 1;        // a previous block of this chain
+    const int je = half == 0 ? j - 1 : j;                   // its coupling row of ecp
+    T ec[LC];
+#pragma unroll
+    for (int w = 0; w < LC; ++w) ec[w] = has ? ecp[je * S + LC * cb + w] : T(0);
+#pragma unroll
+    for (int q = 0; q < LR; ++q) {
+      const int r = LR * rb + q;
+      const T er = has ? ecp[je * S + r] : T(0);
+#pragma unroll
+      for (int w = 0; w < LC; ++w) {
+        const int c = LC * cb + w;
+        T v = T(0);
+        if (r == c) v = T(1);
+        else if (r - c == 1) v = offx[j * S + c];
+        else if (c - r == 1) v = offx[j * S + r];
+        if (has) v -= er * ec[w] * R[q][w];
+        if (mid) v -= ecp[M * S + r] * ecp[M * S + c] * Wg[(M + 1) * N + r * S + c];
+        R[q][w] = v;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < S; p += 2) {
+      const int prb = p / LR, pq = p % LR, pcb = p / LC, pw = p % LC;
+      const int lpiv = prb * 8 + pcb;
+      const T a00 = shfl(R[pq][pw], lpiv), a01 = shfl(R[pq][pw + 1], lpiv);
+      const T a10 = shfl(R[pq + 1][pw], lpiv), a11 = shfl(R[pq + 1][pw + 1], lpiv);
+      T rw0[LC], rw1[LC], cl0[LR], cl1[LR];
+#pragma unroll
+      for (int w = 0; w < LC; ++w) {
+        rw0[w] = shfl(R[pq][w], prb * 8 + cb);
+        rw1[w] = shfl(R[pq + 1][w], prb * 8 + cb);
+      }
+#pragma unroll
+      for (int q = 0; q < LR; ++q) {
+        cl0[q] = shfl(R[q][pw], rb * 8 + pcb);
+        cl1[q] = shfl(R[q][pw + 1], rb * 8 + pcb);
+      }
+      const T det = a00 * a11 - a01 * a10;
+      if (!(a00 > T(0)) || !(det > T(0))) bad = true;
+      const T idet = recip(det);
+      const T p00 = a11 * idet, p01 = -a01 * idet, p10 = -a10 * idet, p11 = a00 * idet;
+      T rp0[LC], rp1[LC];
+#pragma unroll
+      for (int w = 0; w < LC; ++w) {
+        rp0[w] = p00 * rw0[w] + p01 * rw1[w];
+        rp1[w] = p10 * rw0[w] + p11 * rw1[w];
+      }
+#pragma unroll
+      for (int q = 0; q < LR; ++q) {
+#pragma unroll
+        for (int w = 0; w < LC; ++w) {
+          T nv = R[q][w] - (cl0[q] * rp0[w] + cl1[q] * rp1[w]);
+          if (w == pw || w == pw + 1) {
+            const T pc = (w == pw) ? -(cl0[q] * p00 + cl1[q] * p10)
+                                   : -(cl0[q] * p01 + cl1[q] * p11);
+            nv = (cb == pcb) ? pc : nv;
+          }
+          if (q == pq || q == pq + 1) {
+            T prv = (q == pq) ? rp0[w] : rp1[w];
+            if (w == pw || w == pw + 1) {
+              const T pb = (q == pq) ? ((w == pw) ? p00 : p01) : ((w == pw) ? p10 : p11);
+              prv = (cb == pcb) ? pb : prv;
+            }
+            nv = (rb == prb) ? prv : nv;
+          }
+          R[q][w] = nv;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < LR; ++q)
+#pragma unroll
+      for (int w = 0; w < LC; ++w) Wg[j * N + (LR * rb + q) * S + LC * cb + w] = R[q][w];
+  }
+  if (half == 1) asm volatile("bar.sync 2, 64;" ::: "memory");   // this chain is written
+  return bad;
+}
+
 // beta = alpha H / kappa on the interface faces of cell (a, b) (Eq. "beta")
 template <int S>
 __device__ __forceinline__ void write_beta(const DeviceTables &t, const SubInfo &sb, double kc,
@@ -657,6 +765,73 @@ __device__ void block_solve(BasisSmem<T, NC> &sm, int nc) {
   __syncthreads();
 }
 
+// The same solve on the twisted factor (schur_inverses_twisted): one warp
+// per column (columns c, c + 8, ...), lanes 0-15 (row a = lane) walking the
+// block rows 0 .. M-1 down and lanes 16-31 the rows S-1 .. M+1 up, in
+// lock step; the middle row M joins them, then both halves substitute back
+// towards their ends.  17 dependent block steps instead of 31 at S = 16.
+//   forward:  v_j = W_j (z_j - E_{j-1} v_{j-1})  (top),
+//             v_j = W_j (z_j - E_j v_{j+1})      (bottom),
+//             v_M = W_M (z_M - E_{M-1} v_{M-1} - E_M v_{M+1});
+//   backward: y_j = v_j - W_j E_j y_{j+1}        (top, j = M-1 .. 0),
+//             y_j = v_j - W_j E_{j-1} y_{j-1}    (bottom, j = M+1 .. S-1).
+template <typename T, int NC>
+__device__ void block_solve_twisted(BasisSmem<T, NC> &sm, int nc) {
+  constexpr int S = kS, N = S * S, M = S / 2;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int a = lane & (S - 1);
+  const bool bot = lane >= S;
+  static_assert(2 * S == 32 && kS * kS / 32 == 8, "a half warp per block row, 8 warps");
+  for (int c = wid; c < nc; c += 8) {
+    T *v = sm.v + c * N;
+    const T *z = sm.z + c * N;
+    for (int k = 0; k < M; ++k) {
+      const int j = bot ? S - 1 - k : k;
+      if (!bot || j > M) {
+        const T *Wj = sm.Ws + j * N;
+        const T *zj = z + j * S;
+        T acc = T(0);
+        if (k == 0) {
+#pragma unroll
+          for (int bq = 0; bq < S; ++bq) acc += Wj[bq * S + a] * zj[bq];
+        } else {
+          const T *vp = v + (bot ? j + 1 : j - 1) * S;
+          const T *ep = sm.ec + (bot ? j : j - 1) * S;
+#pragma unroll
+          for (int bq = 0; bq < S; ++bq) acc += Wj[bq * S + a] * (zj[bq] - ep[bq] * vp[bq]);
+        }
+        v[j * S + a] = acc;
+      }
+      __syncwarp();
+    }
+    if (!bot) {
+      const T *Wm = sm.Ws + M * N;
+      const T *zm = z + M * S, *vt = v + (M - 1) * S, *vb = v + (M + 1) * S;
+      const T *et = sm.ec + (M - 1) * S, *eb = sm.ec + M * S;
+      T acc = T(0);
+#pragma unroll
+      for (int bq = 0; bq < S; ++bq)
+        acc += Wm[bq * S + a] * (zm[bq] - et[bq] * vt[bq] - eb[bq] * vb[bq]);
+      v[M * S + a] = acc;
+    }
+    __syncwarp();
+    for (int k = 0; k < M; ++k) {
+      const int j = bot ? M + 1 + k : M - 1 - k;
+      if (!bot || j < S) {
+        const T *Wj = sm.Ws + j * N;
+        const T *yn = v + (bot ? j - 1 : j + 1) * S;
+        const T *ep = sm.ec + (bot ? j - 1 : j) * S;
+        T acc = T(0);
+#pragma unroll
+        for (int bq = 0; bq < S; ++bq) acc += Wj[bq * S + a] * (ep[bq] * yn[bq]);
+        v[j * S + a] -= acc;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
 // per-column sum over the CTA of val[c] (c < nc) into out[c]
 template <typename T, int NC>
 __device__ void column_sums(BasisSmem<T, NC> &sm, const float *val, int nc, float *out) {
@@ -754,11 +929,22 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
     // set up the right-hand sides of all cells
     sm.offx[tid] = a < S - 1 ? static_cast<T>(-tEs[tid] * ds[tid] * ds[tid + 1]) : T(0);
     __syncthreads();
-    if (tid < 32) {
-      const bool bad = schur_inverses<T, S>(tid, sm.offx, sm.ec, sm.Ws);
-      if (__any_sync(0xffffffffu, bad) && tid == 0) atomicOr(&w.status[0], MRCM_FLAG_NOTSPD);
+    if constexpr (std::is_same<T, float>::value) {
+      // the twisted chain on warps 0 and 1, the right-hand sides on the rest
+      if (tid < 64) {
+        const bool bad = schur_inverses_twisted<S>(tid >> 5, tid & 31, sm.offx, sm.ec, sm.Ws);
+        if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0)
+          atomicOr(&w.status[0], MRCM_FLAG_NOTSPD);
+      } else {
+        for (int cell = tid - 64; cell < N; cell += N - 64) rhs_cell(cell);
+      }
     } else {
-      for (int cell = tid - 32; cell < N; cell += N - 32) rhs_cell(cell);
+      if (tid < 32) {
+        const bool bad = schur_inverses<T, S>(tid, sm.offx, sm.ec, sm.Ws);
+        if (__any_sync(0xffffffffu, bad) && tid == 0) atomicOr(&w.status[0], MRCM_FLAG_NOTSPD);
+      } else {
+        for (int cell = tid - 32; cell < N; cell += N - 32) rhs_cell(cell);
+      }
     }
     __syncthreads();
   } else {
@@ -784,7 +970,8 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   int sweep = 0;
   float prev2 = 3e38f, rel2 = 0.0f;
   for (;;) {
-    block_solve(sm, nc);
+    if constexpr (FUSED && std::is_same<T, float>::value) block_solve_twisted(sm, nc);
+    else block_solve(sm, nc);
     for (int c = 0; c < nc; ++c) {
       if (sizeof(T) == sizeof(float))
         sm.x[c * N + tid] += static_cast<double>(dsf * static_cast<float>(sm.v[c * N + tid]));
