@@ -455,10 +455,18 @@ __global__ void __launch_bounds__(kS *kS) k_factor(DeviceTables t, Workspace w, 
   offx[tid] = static_cast<T>(a < S - 1 ? -T4[1] * d * dsc[tid + 1] : 0.0);
   ecp[tid] = static_cast<T>(b < S - 1 ? -T4[3] * d * dsc[tid + S] : 0.0);
   __syncthreads();
-  if (tid >= 32) return;
   T *Wg = static_cast<T *>(w.W) + sb.w_off;
-  const bool bad = schur_inverses<T, S>(tid, offx, ecp, Wg);
-  if (__any_sync(0xffffffffu, bad) && tid == 0) atomicOr(&w.status[0], MRCM_FLAG_NOTSPD);
+  bool bad;
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32: the twisted chain on warps 0 and 1 (the basis kernel's FP32
+    // block solve expects that form)
+    if (tid >= 64) return;
+    bad = schur_inverses_twisted<S>(tid >> 5, tid & 31, offx, ecp, Wg);
+  } else {
+    if (tid >= 32) return;
+    bad = schur_inverses<T, S>(tid, offx, ecp, Wg);
+  }
+  if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(&w.status[0], MRCM_FLAG_NOTSPD);
 }
 
 // s = 32: one WARP per subdomain (kFW subdomains per CTA), stage 1 with
@@ -970,7 +978,7 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
   int sweep = 0;
   float prev2 = 3e38f, rel2 = 0.0f;
   for (;;) {
-    if constexpr (FUSED && std::is_same<T, float>::value) block_solve_twisted(sm, nc);
+    if constexpr (std::is_same<T, float>::value) block_solve_twisted(sm, nc);
     else block_solve(sm, nc);
     for (int c = 0; c < nc; ++c) {
       if (sizeof(T) == sizeof(float))
