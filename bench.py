@@ -690,10 +690,10 @@ def run_gpu(args):
 # DRAM traffic per launch from the committed ncu capture (profiles/
 # k_iface_cluster_channels-256x64.md), valid only while the kernel sources are
 # the ones that were profiled.
-TRAFFIC = {"k_iface_cluster": {"bytes": 1280512.0, "sha": "367d4fa54eba2fcb",
+TRAFFIC = {"k_iface_cluster": {"bytes": 1281792.0, "sha": "209df39d077bf46b",
                                "sources": ["csrc/iface_cluster.cu", "csrc/iface_common.cuh"]},
-           "k_basis": {"bytes": 1081856.0, "sha": "199e4d96ace12559", "sources": ["csrc/local.cu"]},
-           "k_factor": {"bytes": 315648.0, "sha": "199e4d96ace12559", "sources": ["csrc/local.cu"]}}
+           "k_basis": {"bytes": 1145600.0, "sha": "59bb576505df3741", "sources": ["csrc/local.cu"]},
+           "k_factor": {"bytes": 325120.0, "sha": "59bb576505df3741", "sources": ["csrc/local.cu"]}}
 
 
 def _traffic(kernel):
