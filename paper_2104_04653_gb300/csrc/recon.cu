@@ -31,23 +31,33 @@ __global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace 
     coefc[c] = u < 0 ? 1.0 : w.x[u];
   }
   __syncthreads();
+  // p = sum_c x_c basis_c: four independent sums, so that the basis loads
+  // of several columns are in flight at once
   const double *bas = w.basis + sb.basis_off;
-  double pc = 0.0;
-  for (int c = 0; c < sb.ncols; ++c) pc += coefc[c] * bas[static_cast<int64_t>(c) * N + tid];
+  double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+  int c = 0;
+  for (; c + 3 < sb.ncols; c += 4) {
+    p0 += coefc[c] * bas[static_cast<int64_t>(c) * N + tid];
+    p1 += coefc[c + 1] * bas[static_cast<int64_t>(c + 1) * N + tid];
+    p2 += coefc[c + 2] * bas[static_cast<int64_t>(c + 2) * N + tid];
+    p3 += coefc[c + 3] * bas[static_cast<int64_t>(c + 3) * N + tid];
+  }
+  for (; c < sb.ncols; ++c) p0 += coefc[c] * bas[static_cast<int64_t>(c) * N + tid];
+  const double pc = (p0 + p1) + (p2 + p3);
   p[tid] = pc;
   __syncthreads();
   const double *coef = w.coef + sb.coef_off;
   const double tW = coef[tid], tE = coef[N + tid], tS = coef[2 * N + tid], tN = coef[3 * N + tid];
-  const double h = t.h;
+  const double inv_h = t.inv_h;   // a product, not an FP64 division (slow here)
   const int gi = sb.x0 + a, gj = sb.y0 + b;
   const int nx = t.nx, ny = t.ny;
   const int64_t cell = (static_cast<int64_t>(sb.r) * ny + gj) * nx + gi;
   P[cell] = pc;
   double *ux = UX + static_cast<int64_t>(sb.r) * ny * (nx + 1);
   double *uy = UY + static_cast<int64_t>(sb.r) * (ny + 1) * nx;
-  if (a < S - 1) ux[static_cast<int64_t>(gj) * (nx + 1) + gi + 1] = tE * (pc - p[tid + 1]) / h;
+  if (a < S - 1) ux[static_cast<int64_t>(gj) * (nx + 1) + gi + 1] = tE * (pc - p[tid + 1]) * inv_h;
   if (b < S - 1) {
-    double v = tN * (pc - p[tid + S]) / h;
+    double v = tN * (pc - p[tid + S]) * inv_h;
     if (t.grav) {     // gravity flux of the face (the half-cell elimination)
       const double *wr = t.grav + static_cast<int64_t>(sb.r) * ny * nx;
       const double k0 = coef[5 * N + tid], k1 = coef[5 * N + tid + S];
@@ -73,7 +83,7 @@ __global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace 
       for (int k = 0; k < fi.nP; ++k)
         PH += w.x[fi.unk + fi.nU + k] * iface_fn_at(t, fe.len, fi.fnP + k, fe.e);
       const double gval = -beta * sgn * UH + PH;
-      un = Tf[side] * (pc - gval) / h;
+      un = Tf[side] * (pc - gval) * inv_h;
       if (t.grav && side >= kEdgeS)
         un += sgn * t.grav[(static_cast<int64_t>(sb.r) * ny + gj) * nx + gi] * Tf[side] /
               (2.0 * coef[5 * N + tid]);
@@ -85,7 +95,7 @@ __global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace 
     else if (side == kEdgeE) k = ny + gj;
     else if (side == kEdgeS) k = 2 * ny + gi;
     else k = 2 * ny + nx + gi;
-    un = t.bc_type[k] == 1 ? Tf[side] * (pc - t.bc_val[k]) / h : t.bc_val[k];
+    un = t.bc_type[k] == 1 ? Tf[side] * (pc - t.bc_val[k]) * inv_h : t.bc_val[k];
     if (t.grav && t.bc_type[k] == 1 && side >= kEdgeS)
       un += sgn * t.grav[(static_cast<int64_t>(sb.r) * ny + gj) * nx + gi];
     if (side == kEdgeW) ux[static_cast<int64_t>(gj) * (nx + 1)] = -un;
