@@ -423,7 +423,8 @@ def cpu_baseline_batch(all_cores: bool):
 def run_batched(args, flush, torch, ws, rank, local):
     """The batched workload: mixed path timed as CUDA-graph replays, FP64
     path by per-call events (its graph replay matches the eager sum within
-    0.1%), e2e through pinned host buffers, accuracy on sampled outputs."""
+    0.1%), e2e through pinned host buffers (3 warm-up steps, then as many
+    timed steps as the graph timing), accuracy on sampled outputs."""
     import numpy as np
     from paper_2104_04653_gb300 import mrcm, workloads as W
     from oracle import sampled as S
@@ -461,7 +462,7 @@ def run_batched(args, flush, torch, ws, rank, local):
     calls = _time_calls(s, K, L, Q, out, 3, flush, torch)
     calls.pop("_steps")
     launches = s.launch_count()
-    e2e_t, h2d, d2h = _e2e(inbuf, outbuf, g, 2, 1, flush, torch)
+    e2e_t, h2d, d2h = _e2e(inbuf, outbuf, g, nb, 3, flush, torch)
     e2e_t = _max_over_ranks(e2e_t, ws, "cuda")
     # accuracy on sampled outputs (oracle building blocks, FP64)
     p, ux, uy = (t_.cpu().numpy() for t_ in out)
