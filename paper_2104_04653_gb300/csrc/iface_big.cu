@@ -7,7 +7,8 @@
 //    (no pivoting: the scaled slab blocks are symmetric quasi-definite), one
 //    panel of 64 pivots at a time: k_gj_panel inverts the 64 x 64 diagonal
 //    tile and forms the pivot row panel, k_gj_trail applies the rank-64
-//    update to every other tile and forms the new pivot column panel;
+//    update to every other tile and forms the new pivot column panel (for
+//    FP32 blocks k_gj_rowpanel_vec and k_gj_trail_vec, 16-byte accesses);
 //  * the six block products of every surviving slab per level by a batched
 //    128 x 128-tile SIMT GEMM over job descriptors (k_bgemm), two products
 //    accumulated in one job for B_k -= X C_l + Y A_r;
@@ -135,6 +136,97 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_rowpanel(const InvJob *jobs, 
   }
 }
 
+// k_gj_rowpanel for FP32 blocks with 16-byte accesses (the alignment
+// argument of k_gj_trail_vec below): D is held with rows padded to 68 floats;
+// the products are summed in the same order as k_gj_rowpanel.
+constexpr int kGjDLd = kGjNb + 4;
+constexpr size_t kGjRowVecBytes = (kGjNb * kGjDLd + kGjNb * kGjNb) * sizeof(float);
+
+__global__ void __launch_bounds__(kGjThreads, 4) k_gj_rowpanel_vec(const InvJob *jobs, int p) {
+  extern __shared__ __align__(16) unsigned char gsmraw[];
+  float *D = reinterpret_cast<float *>(gsmraw);   // [row][kGjDLd]
+  float *tile = D + kGjNb * kGjDLd;               // [c][col]
+  const InvJob jb = jobs[blockIdx.y];
+  const int n = jb.n;
+  if (p >= n) return;
+  const int nt = (n + kGjNb - 1) / kGjNb;
+  if (static_cast<int>(blockIdx.x) >= nt) return;
+  const int j0 = blockIdx.x * kGjNb;
+  float *A = static_cast<float *>(jb.a);
+  const float *Dv = static_cast<const float *>(jb.dinv);
+  float *Cp = static_cast<float *>(jb.cpan);
+  const int w = n - p < kGjNb ? n - p : kGjNb;
+  const int wj = n - j0 < kGjNb ? n - j0 : kGjNb;
+  const int t = threadIdx.x;
+  const int q = (t % 16) * 4, a0 = t / 16;   // staging: columns q..q+3 of rows a0 + 16 k
+  if (j0 == p) {
+    // the panel tile: rows [p, p+w) become D
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = a0 + 16 * k;
+      if (i < w && q < w)
+        *reinterpret_cast<float4 *>(A + static_cast<int64_t>(p + i) * n + p + q) =
+            *reinterpret_cast<const float4 *>(Dv + i * kGjNb + q);
+    }
+    return;
+  }
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  {
+    float4 cv[4], dv[4], tv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int a = a0 + 16 * k;
+      // old column panel of the rows of this tile (rows j0 .. j0+wj)
+      cv[k] = (a < wj && q < w)
+                  ? *reinterpret_cast<const float4 *>(A + static_cast<int64_t>(j0 + a) * n + p + q)
+                  : z4;
+      dv[k] = *reinterpret_cast<const float4 *>(Dv + a * kGjNb + q);
+      tv[k] = (a < w && q < wj)
+                  ? *reinterpret_cast<const float4 *>(A + static_cast<int64_t>(p + a) * n + j0 + q)
+                  : z4;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int a = a0 + 16 * k;
+      if (a < wj && q < w) *reinterpret_cast<float4 *>(Cp + static_cast<int64_t>(j0 + a) * w + q) = cv[k];
+      *reinterpret_cast<float4 *>(D + a * kGjDLd + q) = dv[k];
+      *reinterpret_cast<float4 *>(tile + a * kGjNb + q) = tv[k];
+    }
+  }
+  __syncthreads();
+  // R = D tile: thread owns 4 rows x 4 columns
+  const int tr = (t / 16) * 4, tc = (t % 16) * 4;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int c = 0; c < w; c += 4) {
+    float4 da[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) da[a] = *reinterpret_cast<const float4 *>(D + (tr + a) * kGjDLd + c);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const float4 tb = *reinterpret_cast<const float4 *>(tile + (c + cc) * kGjNb + tc);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float x = cc == 0 ? da[a].x : cc == 1 ? da[a].y : cc == 2 ? da[a].z : da[a].w;
+        acc[a][0] += x * tb.x;
+        acc[a][1] += x * tb.y;
+        acc[a][2] += x * tb.z;
+        acc[a][3] += x * tb.w;
+      }
+    }
+  }
+  if (tc >= wj) return;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (tr + a >= w) continue;
+    *reinterpret_cast<float4 *>(A + static_cast<int64_t>(p + tr + a) * n + j0 + tc) =
+        make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+  }
+}
+
 // Rank-w update of panel step p: for rows i outside the panel,
 //   A[i, j] -= Cp[i, :] R[:, j]   (j outside the panel columns)
 //   A[i, panel] = -Cp[i, :] D
@@ -194,6 +286,103 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_trail(const InvJob *jobs, int
       if (tc + b >= wj) continue;
       row[tc + b] = pcol ? -acc[a][b] : row[tc + b] - acc[a][b];
     }
+  }
+}
+
+// The same rank-w update for FP32 blocks, with 16-byte accesses throughout.
+// Every FP32 slab block has n a multiple of 4 (the slab size is rounded up
+// when the layout is planned) and p, i0, j0 are multiples of 64, so w, hi,
+// wj are multiples of 4 and every row segment read or written here starts on
+// a 16-byte boundary of the 256-byte aligned workspace.  The column panel
+// rows are padded to 68 floats in shared memory (the two row groups of a
+// warp fall in different banks); the thread's 4 x 4 output values are read
+// ahead of the products.  Per output value the products are summed in the
+// same order as k_gj_trail, so both give identical results.
+constexpr int kGjCsLd = kGjNb + 4;
+constexpr size_t kGjTrailVecBytes = (kGjNb * kGjCsLd + kGjNb * kGjNb) * sizeof(float);
+
+__global__ void __launch_bounds__(kGjThreads, 4) k_gj_trail_vec(const InvJob *jobs, int p) {
+  extern __shared__ __align__(16) unsigned char gsmraw[];
+  float *Cs = reinterpret_cast<float *>(gsmraw);   // [row][kGjCsLd]
+  float *Rs = Cs + kGjNb * kGjCsLd;                // [c][col]
+  const InvJob jb = jobs[blockIdx.y];
+  const int n = jb.n;
+  if (p >= n) return;
+  const int nt = (n + kGjNb - 1) / kGjNb;
+  const int ti = blockIdx.x / nt, tj = blockIdx.x % nt;
+  if (ti >= nt) return;
+  const int i0 = ti * kGjNb, j0 = tj * kGjNb;
+  if (i0 == p) return;                          // the pivot rows are final
+  float *A = static_cast<float *>(jb.a);
+  const float *Dv = static_cast<const float *>(jb.dinv);
+  const float *Cp = static_cast<const float *>(jb.cpan);
+  const int w = n - p < kGjNb ? n - p : kGjNb;
+  const int hi = n - i0 < kGjNb ? n - i0 : kGjNb, wj = n - j0 < kGjNb ? n - j0 : kGjNb;
+  const bool pcol = (j0 == p);
+  const int t = threadIdx.x;
+  const int tr = (t / 16) * 4, tc = (t % 16) * 4;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 old[4];
+  if (!pcol) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+      old[a] = (tr + a < hi && tc < wj)
+                   ? *reinterpret_cast<const float4 *>(A + static_cast<int64_t>(i0 + tr + a) * n + j0 + tc)
+                   : z4;
+  }
+  {
+    // staging: thread t copies columns q .. q+3 of rows a0 + 16 k
+    const int q = (t % 16) * 4, a0 = t / 16;
+    float4 cv[4], rv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int a = a0 + 16 * k;
+      cv[k] = (a < hi && q < w)
+                  ? *reinterpret_cast<const float4 *>(Cp + static_cast<int64_t>(i0 + a) * w + q)
+                  : z4;
+      rv[k] = (a < w && q < wj)
+                  ? *reinterpret_cast<const float4 *>(pcol ? Dv + a * kGjNb + q
+                                                           : A + static_cast<int64_t>(p + a) * n + j0 + q)
+                  : z4;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int a = a0 + 16 * k;
+      *reinterpret_cast<float4 *>(Cs + a * kGjCsLd + q) = cv[k];
+      *reinterpret_cast<float4 *>(Rs + a * kGjNb + q) = rv[k];
+    }
+  }
+  __syncthreads();
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int c = 0; c < w; c += 4) {
+    float4 ca[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) ca[a] = *reinterpret_cast<const float4 *>(Cs + (tr + a) * kGjCsLd + c);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const float4 rb = *reinterpret_cast<const float4 *>(Rs + (c + cc) * kGjNb + tc);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float x = cc == 0 ? ca[a].x : cc == 1 ? ca[a].y : cc == 2 ? ca[a].z : ca[a].w;
+        acc[a][0] += x * rb.x;
+        acc[a][1] += x * rb.y;
+        acc[a][2] += x * rb.z;
+        acc[a][3] += x * rb.w;
+      }
+    }
+  }
+  if (tc >= wj) return;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (tr + a >= hi) continue;
+    const float4 r = pcol ? make_float4(-acc[a][0], -acc[a][1], -acc[a][2], -acc[a][3])
+                          : make_float4(old[a].x - acc[a][0], old[a].y - acc[a][1],
+                                        old[a].z - acc[a][2], old[a].w - acc[a][3]);
+    *reinterpret_cast<float4 *>(A + static_cast<int64_t>(i0 + tr + a) * n + j0 + tc) = r;
   }
 }
 
@@ -578,10 +767,16 @@ static cudaError_t big_factor_t(const BigPlan &bp, int *status, int *nlaunch, cu
       const int tiles = (bp.bmax + kGjNb - 1) / kGjNb;
       for (int p = 0; p < bp.bmax; p += kGjNb) {
         k_gj_panel<T><<<ni, kGjThreads, kGjPanelElems * sizeof(T), st>>>(bp.inv + i0, p, status);
-        k_gj_rowpanel<T><<<dim3(tiles, ni), kGjThreads, kGjTrailElems * sizeof(T), st>>>(
-            bp.inv + i0, p);
-        k_gj_trail<T><<<dim3(tiles * tiles, ni), kGjThreads, kGjTrailElems * sizeof(T), st>>>(
-            bp.inv + i0, p);
+        if constexpr (sizeof(T) == sizeof(float)) {
+          k_gj_rowpanel_vec<<<dim3(tiles, ni), kGjThreads, kGjRowVecBytes, st>>>(bp.inv + i0, p);
+          k_gj_trail_vec<<<dim3(tiles * tiles, ni), kGjThreads, kGjTrailVecBytes, st>>>(
+              bp.inv + i0, p);
+        } else {
+          k_gj_rowpanel<T><<<dim3(tiles, ni), kGjThreads, kGjTrailElems * sizeof(T), st>>>(
+              bp.inv + i0, p);
+          k_gj_trail<T><<<dim3(tiles * tiles, ni), kGjThreads, kGjTrailElems * sizeof(T), st>>>(
+              bp.inv + i0, p);
+        }
         *nlaunch += 3;
       }
     }
@@ -610,10 +805,10 @@ cudaError_t init_big_attributes() {
                                 static_cast<int>(kGjPanelElems * sizeof(float)))) != cudaSuccess ||
       (e = cudaFuncSetAttribute(k_gj_panel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kGjPanelElems * sizeof(double)))) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_gj_trail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(kGjTrailElems * sizeof(float)))) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_gj_rowpanel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(kGjTrailElems * sizeof(float)))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_gj_trail_vec, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kGjTrailVecBytes))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_gj_rowpanel_vec, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kGjRowVecBytes))) != cudaSuccess ||
       (e = cudaFuncSetAttribute(k_gj_rowpanel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kGjTrailElems * sizeof(double)))) != cudaSuccess)
     return e;
