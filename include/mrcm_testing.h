@@ -43,6 +43,22 @@ mrcm_status mrcm_test_wait_timeout(uint32_t limit, int32_t *d_status, void *cuda
  * Asynchronous on the context's stream.  (No counterpart in the paper.) */
 mrcm_status mrcm_test_degrade_factor(mrcm_ctx *ctx, int32_t sub, int32_t mantissa_bits);
 
+/* The integer-pipe conversions between binary32 and binary64 that the FP32
+ * refinement loops of the local solves use (IEEE 754 encodings, round to
+ * nearest, ties to even), against the hardware conversions.  For every i in
+ * [start, start + count): the float with bit pattern i mod 2^32 is converted
+ * to double; four doubles derived from i are converted to float: a hashed
+ * 64-bit pattern, the value of float pattern i times (1 + k 2^-24) for
+ * k = i/8 mod 4 (rounding ties and near-ties), and that float scaled by
+ * 2^-(40 + i mod 128) and by 2^(i mod 128) (subnormal, zero and overflow
+ * results).  Results must agree bit for bit; a NaN input must give a NaN.
+ * d_mismatch (device, two uint64) accumulates the float->double and the
+ * double->float mismatch counts.  count at most 2^32; synchronises the
+ * stream.  MRCM_EINVAL: NULL d_mismatch or count out of range.  (No
+ * counterpart in the paper.) */
+mrcm_status mrcm_test_fp_convert(uint64_t start, uint64_t count, uint64_t *d_mismatch,
+                                 void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,9 @@
 // would leave most SMs idle, while with many subdomains the separate,
 // throughput-bound factor launch is cheaper than one chain per column chunk.
 #include "mrcm_internal.h"
+#include "fpconv.cuh"
 #include "../../include/mrcm.h"
+#include "../../include/mrcm_testing.h"
 
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -982,7 +984,7 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
     else block_solve(sm, nc);
     for (int c = 0; c < nc; ++c) {
       if (sizeof(T) == sizeof(float))
-        sm.x[c * N + tid] += static_cast<double>(dsf * static_cast<float>(sm.v[c * N + tid]));
+        sm.x[c * N + tid] += f32_to_f64(dsf * static_cast<float>(sm.v[c * N + tid]));
       else
         sm.x[c * N + tid] += dsl * static_cast<double>(sm.v[c * N + tid]);
     }
@@ -1001,7 +1003,7 @@ __global__ void __launch_bounds__(kS *kS) k_basis(DeviceTables t, Workspace w,
       if (b > 0) r = fma(myT[2], xc[tid - S], r);
       if (b < S - 1) r = fma(myT[3], xc[tid + S], r);
       T zv;
-      if (sizeof(T) == sizeof(float)) zv = static_cast<T>(static_cast<float>(r) * dsf);
+      if (sizeof(T) == sizeof(float)) zv = static_cast<T>(f64_to_f32(r) * dsf);
       else zv = static_cast<T>(dsl * r);
       sm.z[c * N + tid] = zv;
       rn[c] = static_cast<float>(zv) * static_cast<float>(zv);
@@ -1199,7 +1201,7 @@ __global__ void __launch_bounds__(kS32 *kS32, 1) k_basis32(DeviceTables t, Works
     block_solve32(sm, Wg, nc);
     for (int c = 0; c < nc; ++c) {
       if (sizeof(T) == sizeof(float))
-        X[c * N + tid] += static_cast<double>(dsf * static_cast<float>(sm.v[c * N + tid]));
+        X[c * N + tid] += f32_to_f64(dsf * static_cast<float>(sm.v[c * N + tid]));
       else
         X[c * N + tid] += dsl * static_cast<double>(sm.v[c * N + tid]);
     }
@@ -1218,7 +1220,7 @@ __global__ void __launch_bounds__(kS32 *kS32, 1) k_basis32(DeviceTables t, Works
       if (b > 0) r = fma(myT[2], xc[tid - S], r);
       if (b < S - 1) r = fma(myT[3], xc[tid + S], r);
       T zv;
-      if (sizeof(T) == sizeof(float)) zv = static_cast<T>(static_cast<float>(r) * dsf);
+      if (sizeof(T) == sizeof(float)) zv = static_cast<T>(f64_to_f32(r) * dsf);
       else zv = static_cast<T>(dsl * r);
       sm.z[c * N + tid] = zv;
       rn[c] = static_cast<float>(zv) * static_cast<float>(zv);
@@ -1351,8 +1353,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_basis32w(DeviceTables t, Workspa
     }
     // backward: y_j = v_j - W_j (e_j y_{j+1}), y_31 = v_31; then x += D y
     // (the correction in FP32, accumulated in FP64)
-    Xc[(S - 1) * S + lane] += static_cast<double>(
-        sm.dsf[(S - 1) * S + lane] * vp);
+    Xc[(S - 1) * S + lane] += f32_to_f64(sm.dsf[(S - 1) * S + lane] * vp);
 #pragma unroll 4
     for (int j = S - 2; j >= 0; --j) {
       const float tq = sm.ec[j * S + lane] * vp;
@@ -1365,7 +1366,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_basis32w(DeviceTables t, Workspa
         a1 = fmaf(Wa[q1], __shfl_sync(FULL, tq, q1), a1);
       }
       vp = zc[j * S + lane] - (a0 + a1);
-      Xc[j * S + lane] += static_cast<double>(sm.dsf[j * S + lane] * vp);
+      Xc[j * S + lane] += f32_to_f64(sm.dsf[j * S + lane] * vp);
     }
     if (sweep >= ir_max) break;
     // FP64 residual r = b - A x over rows j-1, j, j+1 of this lane's cells
@@ -1382,7 +1383,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_basis32w(DeviceTables t, Workspa
       if (lane < S - 1) r = fma(tE, xr, r);
       if (j > 0) r = fma(tS, xm, r);
       if (j < S - 1) r = fma(tN, xp, r);
-      const float zv = static_cast<float>(r) * sm.dsf[k];
+      const float zv = f64_to_f32(r) * sm.dsf[k];
       zc[k] = zv;
       rn = fmaf(zv, zv, rn);
       xm = xc;
@@ -1682,4 +1683,40 @@ cudaError_t launch_basis(const DeviceTables &t, const Workspace &w, int prec,
                                st);
 }
 
+
+namespace {
+__global__ void k_fp_convert_check(uint64_t start, uint64_t count, unsigned long long *bad) {
+  for (uint64_t i = start + blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+       i < start + count; i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const float f = __uint_as_float(static_cast<unsigned>(i));
+    const double a = static_cast<double>(f), b = f32_to_f64(f);
+    if (!((f != f) ? (b != b) : (__double_as_longlong(a) == __double_as_longlong(b))))
+      atomicAdd(&bad[0], 1ull);
+    uint64_t h = i * 0x9E3779B97F4A7C15ull;
+    h ^= h >> 31;
+    const double dv[4] = {__longlong_as_double(static_cast<long long>(h)),
+                          static_cast<double>(f) * (1.0 + ldexp(1.0, -24) * static_cast<double>((i >> 3) & 3)),
+                          ldexp(static_cast<double>(f), -static_cast<int>(i & 127) - 40),
+                          ldexp(static_cast<double>(f), static_cast<int>(i & 127))};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float x = static_cast<float>(dv[k]), y = f64_to_f32(dv[k]);
+      if (!((dv[k] != dv[k]) ? (y != y) : (__float_as_uint(x) == __float_as_uint(y))))
+        atomicAdd(&bad[1], 1ull);
+    }
+  }
+}
+}  // namespace
+
 }  // namespace mrcm
+
+extern "C" mrcm_status mrcm_test_fp_convert(uint64_t start, uint64_t count, uint64_t *d_mismatch,
+                                            void *cuda_stream) {
+  if (!d_mismatch || count > (1ull << 32)) return MRCM_EINVAL;
+  if (count == 0) return MRCM_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  mrcm::k_fp_convert_check<<<152 * 16, 256, 0, st>>>(
+      start, count, reinterpret_cast<unsigned long long *>(d_mismatch));
+  if (cudaGetLastError() != cudaSuccess) return MRCM_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? MRCM_OK : MRCM_ECUDA;
+}

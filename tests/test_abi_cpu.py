@@ -88,6 +88,9 @@ def test_calls_on_null_context_fail_cleanly(L):
     assert L.mrcm_reconstruct(None, None, None, None, None) == mrcm.MRCM_EINVAL
     assert L.mrcm_interface_path(None) == -1
     assert L.mrcm_test_degrade_factor(None, 0, 7) == mrcm.MRCM_EINVAL
+    L.mrcm_test_fp_convert.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
+                                       ctypes.c_void_p]
+    assert L.mrcm_test_fp_convert(0, 16, None, None) == mrcm.MRCM_EINVAL
     L.mrcm_destroy(None)
 
 
