@@ -522,6 +522,39 @@ __device__ __forceinline__ T row_dot(const T *row, const T *x, int n) {
   return warp_sum(acc);
 }
 
+// The FP32 form: the solve streams the stored blocks once per sweep, one row
+// per warp, so the bandwidth it reaches is set by the row bytes each warp
+// keeps in flight.  Every lane issues all of its 16-byte loads of a
+// 1024-float chunk (8 x 512 B per warp) before the first product.  Rows and
+// vectors here start on 16-byte boundaries and n is a multiple of 4: the
+// slab size is rounded up to a multiple of 4 and every block and vector
+// offset is a multiple of it, in 256-byte aligned workspace buffers.
+template <>
+__device__ __forceinline__ float row_dot<float>(const float *row, const float *x, int n) {
+  const int lane = threadIdx.x & 31;
+  float acc = 0.f;
+  for (int base = 0; base < n; base += 1024) {
+    float4 rv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int j = base + 4 * (lane + 32 * k);
+      rv[k] = j < n ? __ldcs(reinterpret_cast<const float4 *>(row + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int j = base + 4 * (lane + 32 * k);
+      if (j < n) {
+        const float4 xv = *reinterpret_cast<const float4 *>(x + j);
+        acc = fmaf(rv[k].x, xv.x, acc);
+        acc = fmaf(rv[k].y, xv.y, acc);
+        acc = fmaf(rv[k].z, xv.z, acc);
+        acc = fmaf(rv[k].w, xv.w, acc);
+      }
+    }
+  }
+  return warp_sum(acc);
+}
+
 constexpr int kBsCols = 4 * kMmax + 1;   // columns of a subdomain (uniform layouts)
 
 // Refinement with the big-slab reduction solve, all realisations in one
@@ -529,7 +562,7 @@ constexpr int kBsCols = 4 * kMmax + 1;   // columns of a subdomain (uniform layo
 // (sign r); stop test per realisation; y = Shat^{-1} z by cyclic reduction
 // (forward levels, root, backward levels), one warp per block row.
 template <typename T>
-__global__ void __launch_bounds__(256) k_big_solve(DeviceTables t, Workspace w, BigPlan bp,
+__global__ void __launch_bounds__(256, 4) k_big_solve(DeviceTables t, Workspace w, BigPlan bp,
                                                    double tol, int max_solves) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double red[8];
