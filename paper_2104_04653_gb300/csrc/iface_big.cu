@@ -524,32 +524,26 @@ __device__ __forceinline__ T row_dot(const T *row, const T *x, int n) {
 
 // The FP32 form: the solve streams the stored blocks once per sweep, one row
 // per warp, so the bandwidth it reaches is set by the row bytes each warp
-// keeps in flight.  Every lane issues all of its 16-byte loads of a
-// 1024-float chunk (8 x 512 B per warp) before the first product.  Rows and
-// vectors here start on 16-byte boundaries and n is a multiple of 4: the
-// slab size is rounded up to a multiple of 4 and every block and vector
-// offset is a multiple of it, in 256-byte aligned workspace buffers.
+// keeps in flight.  Every lane issues all 16 of its loads of a 512-float
+// chunk (16 coalesced 128-byte requests per warp) before the first product,
+// then sums them in the same order as the loop above (element lane + 32 i,
+// i ascending), so both forms give identical results: the interface
+// refinement's stop test sees the same residuals.
 template <>
 __device__ __forceinline__ float row_dot<float>(const float *row, const float *x, int n) {
   const int lane = threadIdx.x & 31;
   float acc = 0.f;
-  for (int base = 0; base < n; base += 1024) {
-    float4 rv[8];
+  for (int base = 0; base < n; base += 512) {
+    float rv[16];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int j = base + 4 * (lane + 32 * k);
-      rv[k] = j < n ? __ldcs(reinterpret_cast<const float4 *>(row + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < 16; ++i) {
+      const int j = base + lane + 32 * i;
+      rv[i] = j < n ? __ldcs(row + j) : 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int j = base + 4 * (lane + 32 * k);
-      if (j < n) {
-        const float4 xv = *reinterpret_cast<const float4 *>(x + j);
-        acc = fmaf(rv[k].x, xv.x, acc);
-        acc = fmaf(rv[k].y, xv.y, acc);
-        acc = fmaf(rv[k].z, xv.z, acc);
-        acc = fmaf(rv[k].w, xv.w, acc);
-      }
+    for (int i = 0; i < 16; ++i) {
+      const int j = base + lane + 32 * i;
+      if (j < n) acc = fmaf(rv[i], x[j], acc);
     }
   }
   return warp_sum(acc);
