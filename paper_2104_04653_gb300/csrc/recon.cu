@@ -14,40 +14,16 @@
 namespace mrcm {
 namespace {
 
-// One CTA of S*S threads per subdomain of size S (ids from first on).
+// Pressure and face velocities of cell k of a subdomain of size S (pc its
+// pressure; p holds the subdomain's pressures in shared memory).
 template <int S>
-__global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace w, double *P,
-                                                      double *UX, double *UY, double *GAM,
-                                                      int first) {
+__device__ __forceinline__ void recon_cell(const DeviceTables &t, const Workspace &w,
+                                           const SubInfo &sb, double *P, double *UX, double *UY,
+                                           double *GAM, const double *p, int k, double pc) {
   constexpr int N = S * S;
-  const int g = t.sub_by_size[first + blockIdx.x];
-  const SubInfo sb = t.sub[g];
-  const int tid = threadIdx.x, a = tid % S, b = tid / S;
-  __shared__ double p[N];
-  __shared__ double coefc[1 + 8 * S];
-  __shared__ double red[N / 32];
-  for (int c = tid; c < sb.ncols; c += N) {
-    const int u = t.col[sb.col_off + c].unk;
-    coefc[c] = u < 0 ? 1.0 : w.x[u];
-  }
-  __syncthreads();
-  // p = sum_c x_c basis_c: four independent sums, so that the basis loads
-  // of several columns are in flight at once
-  const double *bas = w.basis + sb.basis_off;
-  double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-  int c = 0;
-  for (; c + 3 < sb.ncols; c += 4) {
-    p0 += coefc[c] * bas[static_cast<int64_t>(c) * N + tid];
-    p1 += coefc[c + 1] * bas[static_cast<int64_t>(c + 1) * N + tid];
-    p2 += coefc[c + 2] * bas[static_cast<int64_t>(c + 2) * N + tid];
-    p3 += coefc[c + 3] * bas[static_cast<int64_t>(c + 3) * N + tid];
-  }
-  for (; c < sb.ncols; ++c) p0 += coefc[c] * bas[static_cast<int64_t>(c) * N + tid];
-  const double pc = (p0 + p1) + (p2 + p3);
-  p[tid] = pc;
-  __syncthreads();
+  const int a = k % S, b = k / S;
   const double *coef = w.coef + sb.coef_off;
-  const double tW = coef[tid], tE = coef[N + tid], tS = coef[2 * N + tid], tN = coef[3 * N + tid];
+  const double tW = coef[k], tE = coef[N + k], tS = coef[2 * N + k], tN = coef[3 * N + k];
   const double inv_h = t.inv_h;   // a product, not an FP64 division (slow here)
   const int gi = sb.x0 + a, gj = sb.y0 + b;
   const int nx = t.nx, ny = t.ny;
@@ -55,12 +31,12 @@ __global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace 
   P[cell] = pc;
   double *ux = UX + static_cast<int64_t>(sb.r) * ny * (nx + 1);
   double *uy = UY + static_cast<int64_t>(sb.r) * (ny + 1) * nx;
-  if (a < S - 1) ux[static_cast<int64_t>(gj) * (nx + 1) + gi + 1] = tE * (pc - p[tid + 1]) * inv_h;
+  if (a < S - 1) ux[static_cast<int64_t>(gj) * (nx + 1) + gi + 1] = tE * (pc - p[k + 1]) * inv_h;
   if (b < S - 1) {
-    double v = tN * (pc - p[tid + S]) * inv_h;
+    double v = tN * (pc - p[k + S]) * inv_h;
     if (t.grav) {     // gravity flux of the face (the half-cell elimination)
       const double *wr = t.grav + static_cast<int64_t>(sb.r) * ny * nx;
-      const double k0 = coef[5 * N + tid], k1 = coef[5 * N + tid + S];
+      const double k0 = coef[5 * N + k], k1 = coef[5 * N + k + S];
       const double w0 = wr[static_cast<int64_t>(gj) * nx + gi], w1 = wr[static_cast<int64_t>(gj + 1) * nx + gi];
       v += (k0 * w1 + k1 * w0) / (k0 + k1);
     }
@@ -79,34 +55,92 @@ __global__ void __launch_bounds__(S *S) k_recon_cells(DeviceTables t, Workspace 
       const IfaceInfo fi = t.iface[fe.g];
       const double beta = coef[6 * N + side * S + e];
       double UH = 0.0, PH = 0.0;
-      for (int k = 0; k < fi.nU; ++k) UH += w.x[fi.unk + k] * iface_fn_at(t, fe.len, fi.fnU + k, fe.e);
-      for (int k = 0; k < fi.nP; ++k)
-        PH += w.x[fi.unk + fi.nU + k] * iface_fn_at(t, fe.len, fi.fnP + k, fe.e);
+      for (int q = 0; q < fi.nU; ++q) UH += w.x[fi.unk + q] * iface_fn_at(t, fe.len, fi.fnU + q, fe.e);
+      for (int q = 0; q < fi.nP; ++q)
+        PH += w.x[fi.unk + fi.nU + q] * iface_fn_at(t, fe.len, fi.fnP + q, fe.e);
       const double gval = -beta * sgn * UH + PH;
       un = Tf[side] * (pc - gval) * inv_h;
       if (t.grav && side >= kEdgeS)
         un += sgn * t.grav[(static_cast<int64_t>(sb.r) * ny + gj) * nx + gi] * Tf[side] /
-              (2.0 * coef[5 * N + tid]);
+              (2.0 * coef[5 * N + k]);
       GAM[fi.gam_off + (sgn > 0 ? 0 : fe.len) + fe.e] = un;
       continue;
     }
-    int k;
-    if (side == kEdgeW) k = gj;
-    else if (side == kEdgeE) k = ny + gj;
-    else if (side == kEdgeS) k = 2 * ny + gi;
-    else k = 2 * ny + nx + gi;
-    un = t.bc_type[k] == 1 ? Tf[side] * (pc - t.bc_val[k]) * inv_h : t.bc_val[k];
-    if (t.grav && t.bc_type[k] == 1 && side >= kEdgeS)
+    int kb;
+    if (side == kEdgeW) kb = gj;
+    else if (side == kEdgeE) kb = ny + gj;
+    else if (side == kEdgeS) kb = 2 * ny + gi;
+    else kb = 2 * ny + nx + gi;
+    un = t.bc_type[kb] == 1 ? Tf[side] * (pc - t.bc_val[kb]) * inv_h : t.bc_val[kb];
+    if (t.grav && t.bc_type[kb] == 1 && side >= kEdgeS)
       un += sgn * t.grav[(static_cast<int64_t>(sb.r) * ny + gj) * nx + gi];
     if (side == kEdgeW) ux[static_cast<int64_t>(gj) * (nx + 1)] = -un;
     else if (side == kEdgeE) ux[static_cast<int64_t>(gj) * (nx + 1) + nx] = un;
     else if (side == kEdgeS) uy[gi] = -un;
     else uy[static_cast<int64_t>(ny) * nx + gi] = un;
   }
-  // per-subdomain pressure sum (deterministic order) for the mean shift
-  double s = pc;
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((tid & 31) == 0) red[tid >> 5] = s;
+}
+
+// One CTA of kReconThreads threads per subdomain of size S (ids from first
+// on); thread tid owns cells tid + i kReconThreads (i < CPT).
+constexpr int kReconThreads = 256;
+
+template <int S>
+__global__ void __launch_bounds__(kReconThreads, 3) k_recon_cells(DeviceTables t, Workspace w,
+                                                                  double *P, double *UX,
+                                                                  double *UY, double *GAM,
+                                                                  int first) {
+  constexpr int N = S * S, NT = kReconThreads, CPT = N / NT;
+  static_assert(CPT * NT == N, "whole cells per thread");
+  const int g = t.sub_by_size[first + blockIdx.x];
+  const SubInfo sb = t.sub[g];
+  const int tid = threadIdx.x;
+  __shared__ double p[N];
+  __shared__ double coefc[1 + 8 * S];
+  __shared__ double red[N / 32];
+  for (int c = tid; c < sb.ncols; c += NT) {
+    const int u = t.col[sb.col_off + c].unk;
+    coefc[c] = u < 0 ? 1.0 : w.x[u];
+  }
+  __syncthreads();
+  // p = sum_c x_c basis_c: per cell four independent sums over the columns,
+  // the thread's cells interleaved, so that 4 CPT basis loads are in flight
+  // at once (every cell sums in the same order whatever CPT is)
+  const double *bas = w.basis + sb.basis_off;
+  double p0[CPT], p1[CPT], p2[CPT], p3[CPT];
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) p0[i] = p1[i] = p2[i] = p3[i] = 0.0;
+  int c = 0;
+  for (; c + 3 < sb.ncols; c += 4) {
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+      const int k = tid + i * NT;
+      p0[i] += coefc[c] * bas[static_cast<int64_t>(c) * N + k];
+      p1[i] += coefc[c + 1] * bas[static_cast<int64_t>(c + 1) * N + k];
+      p2[i] += coefc[c + 2] * bas[static_cast<int64_t>(c + 2) * N + k];
+      p3[i] += coefc[c + 3] * bas[static_cast<int64_t>(c + 3) * N + k];
+    }
+  }
+  for (; c < sb.ncols; ++c)
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) p0[i] += coefc[c] * bas[static_cast<int64_t>(c) * N + tid + i * NT];
+  double pc[CPT];
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    pc[i] = (p0[i] + p1[i]) + (p2[i] + p3[i]);
+    p[tid + i * NT] = pc[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) recon_cell<S>(t, w, sb, P, UX, UY, GAM, p, tid + i * NT, pc[i]);
+  // per-subdomain pressure sum (deterministic order) for the mean shift:
+  // each warp sums 32 consecutive cells, the partials are added in cell order
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    double s = pc[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((tid & 31) == 0) red[(tid + i * NT) >> 5] = s;
+  }
   __syncthreads();
   if (tid == 0) {
     double acc = 0.0;
@@ -165,9 +199,10 @@ __global__ void k_recon_final(DeviceTables t, Workspace w, double *P, double *UX
 cudaError_t launch_reconstruct(const DeviceTables &t, const Workspace &w, double *p, double *ux,
                                double *uy, double *gam, cudaStream_t st) {
   double *G = gam ? gam : w.gamma_tmp;
-  if (t.nsub16 > 0) k_recon_cells<16><<<t.nsub16, 256, 0, st>>>(t, w, p, ux, uy, G, 0);
+  if (t.nsub16 > 0)
+    k_recon_cells<16><<<t.nsub16, kReconThreads, 0, st>>>(t, w, p, ux, uy, G, 0);
   if (t.nsub > t.nsub16)
-    k_recon_cells<32><<<t.nsub - t.nsub16, 1024, 0, st>>>(t, w, p, ux, uy, G, t.nsub16);
+    k_recon_cells<32><<<t.nsub - t.nsub16, kReconThreads, 0, st>>>(t, w, p, ux, uy, G, t.nsub16);
   double *pmean = w.dstat + 2 + t.n_real;
   if (t.pure_neumann) k_recon_mean<<<t.n_real, 256, 0, st>>>(t, w, pmean);
   const int64_t ncells = static_cast<int64_t>(t.n_real) * t.nx * t.ny;
